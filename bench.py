@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the chunked Gaussian-splatting mapper hot path on one B300.
+
+Workload (default): one keyframe window of 8 views of mixed size
+(4 x 1200x680, 2 x 640x480, 2 x 320x240 = 4,032,000 pixels) over 2M Gaussians
+(SH degree 3, FP32) in 64 chunks of 4 m.  One step = the optimisation pass of
+Sec. III-E for the window: cull chunks, gather the visible Gaussians, render
+RGB + depth (forward), L1 loss of Eq. 2-4, backward to every parameter and
+the pose, scatter the active set back to its chunks.
+
+  batched : all 8 views in one render call (one preprocess over the Gaussians,
+            one sort, one persistent blend launch per direction)
+  plain   : the per-keyframe method, 8 sequential passes with one view each
+            (cull, gather, forward, loss, backward, scatter per keyframe)
+
+Prints one JSON line (metric, value = batched Mpix/s, ...).  `--impl
+reference` times the CPU FP64 oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd render Mpix/s per keyframe window (batched vs plain); % HBM roofline"
+UNIT = "Mpix/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--gaussians", type=int, default=2_000_000)
+    ap.add_argument("--tile", default="auto", help="WxH, or auto (autotuned)")
+    ap.add_argument("--stage", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-pixels", type=int, default=48, help="oracle sample: pixels per sampled view")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2032.0)), "measured"
+    except Exception:
+        return 6400.0, 2032.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- our implementation
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2511_23030_b300 import build, dcg, synth
+
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    sc = synth.window_scene(0, n=args.gaussians)
+    P = sc["params"]
+    cams = sc["cams"]
+    deg = sc["deg"]
+    n_all = P.shape[0]
+    F = P.shape[1]
+    npix = sum(c.W * c.H for c in cams)
+    cfg = dcg.config(sh_degree=deg, max_active=n_all + 1024, max_views=8, max_pixels=npix, max_instances=160 << 20,
+                     chunk_size=sc["chunk_size"], device_budget=6_000_000, host_capacity=n_all + 1024, dfar=60.0)
+    ctx = dcg.dcg_create(cfg)
+    stream = torch.cuda.current_stream()
+    g_t = torch.from_numpy(np.ascontiguousarray(P.T)).cuda()
+    dcg.dcg_chunk_table_update(ctx, g_t, n_all)
+    del g_t
+    # targets (pinned host copies for the end-to-end run)
+    trgb_h = torch.from_numpy(np.concatenate([t.reshape(-1) for t in sc["target_rgb"]])).pin_memory()
+    tdep_h = torch.from_numpy(np.concatenate([t.reshape(-1) for t in sc["target_depth"]])).pin_memory()
+    trgb, tdep = trgb_h.cuda(), tdep_h.cuda()
+    rgb = torch.zeros(3 * npix, device="cuda")
+    depth = torch.zeros(npix, device="cuda")
+    dr = torch.zeros_like(rgb)
+    dd = torch.zeros_like(depth)
+    loss = torch.zeros(1, device="cuda")
+    loss_h = torch.zeros(1).pin_memory()
+    grads_t = torch.zeros((F, n_all + 1024), device="cuda")
+    grads = dcg.gaussians(grads_t, deg)
+    dpose = torch.zeros(8 * 6, device="cuda")
+    lam = sc["lambda_depth"]
+    offs = np.cumsum([0] + [c.W * c.H for c in cams])
+
+    # launch shape: autotuned over tile x staging depth on this window (forward + backward)
+    tune = None
+    if args.tile == "auto":
+        lst = dcg.dcg_cull_chunks(ctx, cams)
+        g, n = dcg.dcg_gather_active(ctx, lst)
+        dcg.dcg_render_fwd(ctx, g, n, cams, rgb, depth)
+        dcg.dcg_loss_l1(ctx, rgb, depth, trgb, tdep, cams, lam, dr, dd, loss)
+        tune = dcg.dcg_autotune(ctx, g, n, cams, rgb, depth, dr, dd, grads, reps=2)
+        tile = tuple(tune["tile"])
+        stage = tune["stage"]
+    else:
+        tile = tuple(int(x) for x in args.tile.split("x"))
+        stage = args.stage or 128
+        dcg.dcg_set_launch(ctx, tile[0], tile[1], stage)
+
+    def step_batched():
+        lst = dcg.dcg_cull_chunks(ctx, cams)
+        g, n = dcg.dcg_gather_active(ctx, lst)
+        dcg.dcg_render_fwd(ctx, g, n, cams, rgb, depth)
+        loss.zero_()
+        dcg.dcg_loss_l1(ctx, rgb, depth, trgb, tdep, cams, lam, dr, dd, loss)
+        dcg.dcg_render_bwd(ctx, dr, dd, grads, dpose)
+        dcg.dcg_scatter_back(ctx, g, n)
+        return n
+
+    def step_plain():
+        n = 0
+        for v, c in enumerate(cams):
+            lst = dcg.dcg_cull_chunks(ctx, [c])
+            g, n = dcg.dcg_gather_active(ctx, lst)
+            o = int(offs[v])
+            Pv = c.W * c.H
+            r = rgb[3 * o: 3 * (o + Pv)]
+            d = depth[o: o + Pv]
+            dcg.dcg_render_fwd(ctx, g, n, [c], r, d)
+            dcg.dcg_loss_l1(ctx, r, d, trgb[3 * o: 3 * (o + Pv)], tdep[o: o + Pv], [c], lam, dr[3 * o: 3 * (o + Pv)],
+                            dd[o: o + Pv], loss)
+            dcg.dcg_render_bwd(ctx, dr[3 * o: 3 * (o + Pv)], dd[o: o + Pv], grads, dpose[6 * v: 6 * v + 6])
+            dcg.dcg_scatter_back(ctx, g, n)
+        return n
+
+    def step_e2e():
+        trgb.copy_(trgb_h, non_blocking=True)
+        tdep.copy_(tdep_h, non_blocking=True)
+        step_batched()
+        loss_h.copy_(loss, non_blocking=True)
+        stream.synchronize()
+        return float(loss_h.item())
+
+    def timed(fn, k, w, profile=False):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        if profile:
+            dcg.dcg_profile(ctx, True)
+            dcg.dcg_profile_read(ctx)
+        l0 = dcg.dcg_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = dcg.dcg_launch_count() - l0
+        prof = None
+        if profile:
+            prof = dcg.dcg_profile_read(ctx)
+            dcg.dcg_profile(ctx, False)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches, prof
+
+    K, W = args.steps, args.warmup
+    with Clocks(torch.cuda.current_device()) as clk:
+        ms_b, launches_b, prof = timed(step_batched, K, W, profile=True)
+    clocks = clk.summary()
+    n_vis, n_inst, n_tiles = dcg.dcg_state_stats(ctx)
+    n_eval = dcg.dcg_state_evals(ctx)
+    ms_p, launches_p, _ = timed(step_plain, max(2, K // 2), max(1, W // 2))
+    K_p = max(2, K // 2)
+    ms_e, _, _ = timed(step_e2e, K, 2)
+    dcg.dcg_sync(ctx)
+
+    mpix_b = npix * K * world / (ms_b / 1e3) / 1e6
+    mpix_p = npix * K_p * world / (ms_p / 1e3) / 1e6
+    mpix_e = npix * K * world / (ms_e / 1e3) / 1e6
+    phases = {k: round(v[0] / K, 4) for k, v in prof.items()}
+    n_act = n_all
+    roof = roofline(phases, n_act, n_vis, n_inst, n_eval, npix, deg, F, clocks)
+    out = {
+        "metric": METRIC, "value": round(mpix_b, 2), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(ms_b / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded; stands in for KITTI/Replica-shaped keyframe windows)",
+        "config": {"workload": "keyframe window: 8 views (4x1200x680, 2x640x480, 2x320x240) = 4,032,000 px over "
+                               f"{n_all} Gaussians (SH3, FP32) in 64 chunks of 4 m",
+                   "gaussians": n_all, "views": 8, "pixels": npix, "tile": f"{tile[0]}x{tile[1]}", "stage": stage,
+                   "autotune": tune, "l2": "inputs larger than L2 (parameters 472 MB per step)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "plain": {"value": round(mpix_p, 2), "unit": UNIT, "ms_per_step": round(ms_p / K_p, 4),
+                  "speedup_batched_over_plain": round(mpix_b / mpix_p, 3)},
+        "phases_ms_per_step": phases,
+        "counts": {"visible_pairs": n_vis, "instances": n_inst, "tiles": n_tiles, "blend_evaluations": n_eval},
+        "roofline": roof,
+        "e2e": {"value": round(mpix_e, 2), "unit": UNIT, "h2d_bytes_per_step": int(4 * 4 * npix),
+                "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches_b),
+        "clocks": clocks,
+    }
+    dcg.dcg_destroy(ctx)
+    return out
+
+
+def roofline(phases, n_act, n_vis, n_inst, n_eval, npix, deg, F, clocks):
+    """Dominant phase with its algorithmic bytes (or FLOPs) per launch over its live duration."""
+    hbm, sm_max, src = peaks()
+    rec = 48
+    algo_bytes = {
+        # parameters once per call; per visible pair: record + depth + rect + zeroed 2D gradient; flags all pairs
+        "preprocess_fwd": 4 * F * n_act + n_vis * (rec + 4 + 8 + 48) + 4 * 8 * n_act,
+        # key write/read per visible pair and per instance (5 + 2 passes, 3 touches each), emission and ranges
+        "binning": 8 * 3 * n_vis * 5 + 8 * 3 * n_inst * 2 + 8 * n_inst + 12 * n_vis,
+        "blend_fwd": n_inst * (8 + rec) + npix * (4 * 4 + 8),
+        "blend_bwd": n_inst * (8 + rec + 40) + npix * (4 * 4 + 8),
+        "preprocess_bwd": 4 * F * n_act + n_vis * 48 + 4 * F * n_act,
+        "gather": 2 * 4 * F * n_act,
+        "scatter": 2 * 4 * F * n_act,
+    }
+    dom = max((k for k in algo_bytes), key=lambda k: phases.get(k, 0.0))
+    t = phases[dom] / 1e3
+    if dom in ("blend_fwd", "blend_bwd"):
+        # FP32 issue bound: 148 SMs x 128 lanes x 2 FLOP per clock; 18 FLOP per forward evaluation
+        # (backward: ~2.5x), MUFU ex2 counted as one FLOP
+        flop_per_eval = 18 if dom == "blend_fwd" else 45
+        peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12
+        ach = n_eval * flop_per_eval / t / 1e12
+        return {"kernel": dom, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": None, "hbm_gbs": round(algo_bytes[dom] / t / 1e9, 1),
+                "hbm_frac": round(algo_bytes[dom] / t / 1e9 / hbm, 4), "peak_source": f"derived (sm_max {sm_max} MHz)"}
+    ach = algo_bytes[dom] / t / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(ach / hbm, 4), "traffic": None, "peak_source": src}
+
+
+# ----------------------------------------------------------------------------- CPU baseline (oracle)
+def cpu_baseline(pix_per_view: int, views=None, n_gaussians=2_000_000, seed=0):
+    """FP64 oracle fwd+bwd on a bounded pixel sample of the window (the whole
+    scene is projected for every sampled view)."""
+    import oracle
+
+    from paper_2511_23030_b300 import synth
+
+    oracle.build()
+    sc = synth.window_scene(0, n=n_gaussians)
+    P, cams = sc["params"], sc["cams"]
+    views = range(len(cams)) if views is None else views
+    rng = np.random.default_rng(seed)
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    m = 0
+    for v in views:
+        c = cams[v]
+        pix = synth.pixel_sample(rng, c.W, c.H, pix_per_view)
+        o = oracle.render(P, sc["deg"], c, pix=pix, n_threads=cores)
+        gr = np.sign(o["rgb"] - 0.5) / (3.0 * c.W * c.H)
+        gd = 0.1 * np.sign(o["depth"] - 10.0) / (c.W * c.H)
+        oracle.render_bwd(P, sc["deg"], c, gr, gd, pix=pix, n_threads=cores)
+        m += len(pix)
+    dt = time.perf_counter() - t0
+    return {"value": round(m / dt / 1e6, 8), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{m} pixels ({pix_per_view} per view, views {list(views)}) of the window, fwd+bwd, "
+                      f"{n_gaussians} Gaussians projected per view", "seconds": round(dt, 2)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    K, W = args.steps, args.warmup
+    views = [5]  # one 640x480 view per step keeps the whole run within minutes
+    for _ in range(min(W, 1)):
+        cpu_baseline(8, views=views, n_gaussians=args.gaussians)
+    t0 = time.perf_counter()
+    m = 0
+    for _ in range(K):
+        cb = cpu_baseline(16, views=views, n_gaussians=args.gaussians)
+        m += 16
+    dt = time.perf_counter() - t0
+    val = m / dt / 1e6
+    cb["value"] = round(val, 8)
+    cb["sample"] = f"per step 16 pixels of view 5 (640x480) of the window, fwd+bwd, {args.gaussians} Gaussians"
+    return {"metric": METRIC, "value": round(val, 8), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": round(dt / K * 1e3, 2), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "keyframe window: 8 views (4x1200x680, 2x640x480, 2x320x240) = 4,032,000 px over "
+                                   f"{args.gaussians} Gaussians (SH3) in 64 chunks of 4 m",
+                       "parallelism": "host cores"},
+            "cpu_baseline": cb, "e2e": {"value": round(val, 8), "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group(backend)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+        if rank == 0 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.cpu_pixels, views=[0, 5], n_gaussians=args.gaussians)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,279 @@
+/*
+ * dcg.h -- C ABI of the B300 (sm_103a) chunked Gaussian-splatting mapper hot path.
+ *
+ * The calls follow the optimisation pass of a chunk-based 3DGS mapper
+ * (DiskChunGS, Sec. III-D "Chunk 3DGS Mapping" and Sec. III-E "Optimization",
+ * Fig. 2): compute chunk ids of new Gaussians (Eq. 5, Eq. 6), cull chunks
+ * against a keyframe frustum, make the visible chunks resident under a
+ * Gaussian budget with LRU eviction to a slower tier, gather the visible
+ * Gaussians into one active buffer, rasterise RGB and depth, back-propagate
+ * the loss of Eq. 2-4 to every Gaussian parameter and the camera pose, and
+ * write the updated Gaussians back to their chunks.
+ *
+ * Conventions shared by every call
+ *  - Pointers marked (dev) are CUDA device pointers, (host) are host pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are stream-ordered and asynchronous unless stated otherwise.
+ *  - Argument and capacity errors are returned synchronously.  Errors found
+ *    by a kernel (a chunk coordinate outside the +-2^20 range, an instance or
+ *    list capacity overflow, a bounded wait that gave up) are written to a
+ *    device error word; dcg_sync() and the calls documented as synchronising
+ *    return them.  No kernel traps or asserts.
+ *  - A dcg_ctx is not thread-safe; use one per host thread.
+ *  - All device memory the library needs is allocated in dcg_create /
+ *    dcg_state_create from the capacities in dcg_config; the render and chunk
+ *    calls allocate nothing.
+ */
+#ifndef DCG_H
+#define DCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DCG_OK = 0,
+  DCG_ERR_ARG = 1,       /* invalid argument (null pointer, size <= 0, too many views ...) */
+  DCG_ERR_OOM = 2,       /* allocation at create time failed */
+  DCG_ERR_CUDA = 3,      /* a CUDA runtime call failed; dcg_last_error has the text */
+  DCG_ERR_BUDGET = 4,    /* the visible chunks alone exceed the device Gaussian budget */
+  DCG_ERR_KEY_RANGE = 5, /* a chunk coordinate lies outside [-2^20, 2^20-1] (Eq. 6) */
+  DCG_ERR_CAPACITY = 6,  /* a configured capacity (instances, pixels, chunks, host tier) was exceeded */
+  DCG_ERR_TIMEOUT = 7,   /* a bounded device-side wait gave up */
+  DCG_ERR_FAULT = 8,     /* an injected host-side fault (testing) */
+  DCG_ERR_STATE = 9      /* call order violated (e.g. backward without a forward) */
+} dcg_status;
+
+typedef struct dcg_ctx dcg_ctx;
+typedef struct dcg_render_state dcg_render_state;
+
+/* Pinhole camera, x right, y down, z forward.  Pixel (x, y) is sampled at
+ * image-plane point (x, y) with u = fx X/Z + cx, v = fy Y/Z + cy.
+ * Tcw is the row-major 4x4 world->camera rigid transform. */
+typedef struct {
+  float fx, fy, cx, cy;
+  int32_t W, H;
+  float Tcw[16];
+  float znear, zfar;
+} dcg_camera;
+
+/* Gaussians, component-major ("planar"): component c of Gaussian i is
+ * data[c * stride + i].  F = 11 + 3 (deg+1)^2 components:
+ *   0..2 mean, 3..5 log-scale, 6..9 quaternion (w,x,y,z; normalised on use),
+ *   10 opacity logit, 11 + 3k + ch SH coefficient k of channel ch.
+ * The 3DGS representation with SH up to degree 3 (Sec. II). */
+typedef struct {
+  float* data;       /* (dev) */
+  int64_t stride;    /* >= number of Gaussians */
+  int32_t sh_degree; /* 0..3 */
+  int32_t pad;
+} dcg_gaussians;
+
+typedef struct {
+  float chunk_size;        /* s of Eq. 5, metres (the paper uses 10 m) */
+  int32_t sh_degree;       /* 0..3 */
+  int64_t device_budget;   /* max resident Gaussians on the device (paper: 1.5 M) */
+  int64_t host_capacity;   /* Gaussians the pinned host tier (stand-in for disk) can hold */
+  int32_t max_chunks;      /* chunk table capacity */
+  int32_t max_views;       /* views per render call (<= 16) */
+  int64_t max_active;      /* Gaussians per render call / active buffer */
+  int64_t max_pixels;      /* total pixels over the views of one render call */
+  int64_t max_instances;   /* (view, tile, Gaussian) instances per render call */
+  int32_t tile_w, tile_h;  /* default blend tile: 16x16, 32x16 or 32x32 */
+  int32_t stage;           /* default Gaussians staged per block batch: 64..256 */
+  float dfar;              /* distance filter of the chunk cull, metres */
+  int32_t page_gaussians;  /* Gaussians per device/host page (power of two) */
+  int32_t flags;           /* reserved, 0 */
+} dcg_config;
+
+/* Fill *cfg with defaults (s = 4 m, degree 3, budget 6 M, 8 views ...). */
+void dcg_config_default(dcg_config* cfg);
+
+/* Create a context on the current CUDA device; allocates the chunk table,
+ * the device page pool (device_budget), the pinned host tier (host_capacity),
+ * the active buffer (max_active) and one render state.  Synchronous. */
+dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out);
+dcg_status dcg_destroy(dcg_ctx* ctx);
+
+/* Text of the last error on this context (valid until the next call). */
+const char* dcg_last_error(const dcg_ctx* ctx);
+
+/* Synchronise `stream` and return the first device-detected error since the
+ * last dcg_sync (then clear it). */
+dcg_status dcg_sync(dcg_ctx* ctx, void* stream);
+
+/* ---------------------------------------------------------------- chunks
+ * Eq. 5 / Eq. 6: chunk coordinate floor((p + s/2)/s) per axis, evaluated in
+ * FP32 (one rounding for the add, one for the divide, then floor), and
+ * EncodedID = (cx+2^20) 2^42 + (cy+2^20) 2^21 + (cz+2^20).
+ * dcg_chunk_keys: keys_out[i] (dev, n) for means (dev, [n,3] row-major);
+ * a coordinate outside [-2^20, 2^20-1] or a non-finite mean writes key 0 and
+ * raises DCG_ERR_KEY_RANGE at the next dcg_sync. */
+dcg_status dcg_chunk_keys(dcg_ctx* ctx, const float* means, int64_t n, uint64_t* keys_out, void* stream);
+
+/* dcg_chunk_table_update: insert n new Gaussians (dev, planar with `stride`,
+ * the context's SH degree) into the chunk table (Sec. III-D: "an O(1) chunk
+ * location" keyed by EncodedID).  Their keys are computed on the device, the
+ * Gaussians are grouped by chunk (stable, in input order) and appended to
+ * their chunks in the pinned host tier; new chunks are created.  A resident
+ * chunk that receives Gaussians is written back (if dirty) and dropped from
+ * the device so that the next gather reloads it whole.  keys_out (dev, n)
+ * may be NULL.  Synchronises `stream`. */
+dcg_status dcg_chunk_table_update(dcg_ctx* ctx, const float* params, int64_t stride, int64_t n,
+                                  uint64_t* keys_out, void* stream);
+
+/* Number of chunks, and per chunk (host arrays of length dcg_chunk_count, in
+ * ascending EncodedID order -- the order every chunk index of this API uses):
+ * integer coordinates [C,3], ids, Gaussian counts, resident flag, last access
+ * step.  Any output may be NULL.  Synchronous host query. */
+int32_t dcg_chunk_count(const dcg_ctx* ctx);
+dcg_status dcg_chunk_info(const dcg_ctx* ctx, int32_t* coords, uint64_t* keys, int64_t* counts,
+                          uint8_t* resident, int64_t* last_access);
+
+/* Frustum cull of chunks (Sec. III-D "Frustum Culling"): six planes are
+ * extracted from the view-projection matrix P Tcw (P maps u in [0,W],
+ * v in [0,H], Z in [znear, zfar] to the clip cube); chunk k (the cube
+ * [c s - s/2, c s + s/2)^3) is visible in view v iff for every plane the cube
+ * vertex furthest along the plane normal is on the inner side, and the
+ * distance from the camera centre to the cube is <= dfar.  FP64, fixed
+ * evaluation order.  Outputs: mask_out (dev, [n_views, C] u8, may be NULL),
+ * list_out (host, capacity C) = ascending chunk indices visible in any view,
+ * *n_out (host) = their number.  Synchronises `stream` (the list is needed on
+ * the host by dcg_gather_active). */
+dcg_status dcg_cull_chunks(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views, uint8_t* mask_out,
+                           int32_t* list_out, int32_t* n_out, void* stream);
+
+/* Make the listed chunks (host, ascending chunk indices) resident and gather
+ * their Gaussians into the library-owned active buffer (Sec. III-E: load
+ * visible chunks, evict with LRU when over budget, index the visible
+ * Gaussians).  Missing chunks are copied host->device on the context's copy
+ * stream; when the budget would be exceeded, resident chunks not in the list
+ * are evicted oldest first (ties by id), the fewest that make room, and dirty
+ * ones are copied back to the host tier.  Active order: listed chunks in
+ * ascending id, each in stored order.  *active_out receives a view of the
+ * active buffer (stride = max_active), *n_active_out its size.
+ * DCG_ERR_BUDGET if the listed chunks alone exceed the budget. */
+dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* chunk_list, int32_t n_chunks,
+                             dcg_gaussians* active_out, int64_t* n_active_out, void* stream);
+
+/* Inverse of the last dcg_gather_active: copy `active` (dev, planar, n must
+ * equal the gathered count) back into the resident chunks and mark them
+ * dirty, so that an eviction writes them to the host tier. */
+dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n, void* stream);
+
+/* Copy every resident dirty chunk back to the host tier and wait. */
+dcg_status dcg_flush(dcg_ctx* ctx, void* stream);
+
+/* Read n Gaussians of chunk `chunk` (ascending-id index) from the host tier
+ * into params_out (host, planar with stride n).  For checks and checkpoints. */
+dcg_status dcg_chunk_read(dcg_ctx* ctx, int32_t chunk, float* params_out, int64_t n);
+
+/* ---------------------------------------------------------------- rendering
+ * Differentiable rasterisation of RGB and depth (Sec. III-E: the selected
+ * Gaussians are rasterised into RGB and depth images; Eq. 4 needs the depth)
+ * with the 3DGS representation.  Per view and Gaussian: camera point
+ * t = R mu + t_cw, culled if t_z <= znear; u, v as in dcg_camera; the 2D
+ * covariance J R Sigma R^T J^T + 0.3 I with Sigma = R(q) S S^T R(q)^T and
+ * the perspective Jacobian J (x/z, y/z clamped to the image extended by 15%);
+ * colour max(0, sum_k c_k Y_k(dir) + 0.5) with real SH (Condon-Shortley
+ * phase) of the direction from the camera centre; opacity sigmoid(logit).
+ * Per pixel (sample point (x, y)): Gaussians with q = d^T Sigma'^-1 d <= 9
+ * and alpha = min(0.99, o exp(-q/2)) >= 1/255, in ascending (depth, index)
+ * order, front to back; stop before T (1 - alpha) < 1e-4; background 0;
+ * depth = sum T alpha t_z.
+ *
+ * Output layout: views are stacked; view v starts at pixel offset
+ * off_v = sum_{w<v} W_w H_w; rgb (dev) holds [3][H_v][W_v] at 3 off_v,
+ * depth (dev) holds [H_v][W_v] at off_v.  The state keeps what the backward
+ * needs (sorted per-tile lists, per-pixel final transmittance and last
+ * contributor); it refers to `g` and `cams`, which must stay unchanged until
+ * the backward. */
+dcg_status dcg_state_create(dcg_ctx* ctx, dcg_render_state** out);
+/* The state every context creates for itself (used when a call gets NULL). */
+dcg_render_state* dcg_default_state(dcg_ctx* ctx);
+dcg_status dcg_state_destroy(dcg_render_state* st);
+
+dcg_status dcg_render_fwd(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams,
+                          int32_t n_views, float* rgb, float* depth, dcg_render_state* state, void* stream);
+
+/* Gradient of L through the last forward of `state`: dL_drgb and dL_ddepth
+ * (dev, layouts as rgb / depth) in; grads (dev, planar, same n and degree as
+ * the forward, overwritten) and dL_dpose (dev, [n_views, 6], overwritten; may
+ * be NULL) out.  The pose gradient is w.r.t. the left perturbation
+ * Tcw <- exp(xi^) Tcw, xi = (v, w): a camera-frame point moves by v + w x t.
+ * Transmittance is recomputed front-from-back from the stored final value. */
+dcg_status dcg_render_bwd(dcg_ctx* ctx, dcg_render_state* state, const float* dL_drgb, const float* dL_ddepth,
+                          dcg_gaussians* grads, float* dL_dpose, void* stream);
+
+/* L1 parts of Eq. 2-4 summed over views: L = sum_v [ mean|C - C_gt| +
+ * lambda_depth mean|D - D_gt| ]; writes dL/dC and dL/dD (dev, layouts as
+ * rgb / depth; sign(0) = 0) and adds L to *loss (dev, one float, caller
+ * zeroes). */
+dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const float* tgt_rgb,
+                       const float* tgt_depth, const dcg_camera* cams, int32_t n_views, float lambda_depth,
+                       float* dL_drgb, float* dL_ddepth, float* loss, void* stream);
+
+/* Blend launch shape used by the next render calls: tile 16x16, 32x16 or
+ * 32x32 pixels and 64..256 Gaussians staged per block batch. */
+dcg_status dcg_set_launch(dcg_ctx* ctx, int32_t tile_w, int32_t tile_h, int32_t stage);
+
+/* Autotuner of the blend launch shape: times render_fwd + render_bwd of this
+ * call (default state, `reps` repetitions after one warm-up, CUDA events on
+ * `stream`) for every tile {16x16, 32x16, 32x32} x staging depth
+ * {64, 96, 128, 192, 256}, keeps the fastest as the context's launch shape
+ * and returns it.  ms_out (15 floats in that order, may be NULL) receives the
+ * mean time of each candidate.  rgb/depth/grads are overwritten; dL_drgb and
+ * dL_ddepth are the seeds used for the backward.  Synchronous. */
+dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams, int32_t n_views,
+                        float* rgb, float* depth, const float* dL_drgb, const float* dL_ddepth, dcg_gaussians* grads,
+                        int32_t reps, int32_t* tile_w, int32_t* tile_h, int32_t* stage, float* ms_out, void* stream);
+
+/* Diagnostics of the last forward of `state` (host copies; any may be NULL):
+ * visible (view, Gaussian) pairs, instances, tiles. Synchronises `stream`. */
+dcg_status dcg_state_stats(dcg_render_state* st, int64_t* n_visible, int64_t* n_instances, int64_t* n_tiles,
+                           void* stream);
+
+/* Pixel-Gaussian evaluations performed by the last forward blend of `st`
+ * (a pixel stops counting at its termination).  Synchronises `stream`. */
+dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, void* stream);
+
+/* Copies of the state's per-tile sorted lists for checks (host outputs; any
+ * may be NULL): ranges [n_tiles, 2] (start, end) into ids, ids [n_instances]
+ * (view-local Gaussian index), per (view, Gaussian) FP32 depth [n_views * n],
+ * tile rectangle [n_views * n, 4] (x0, y0, x1, y1 inclusive; x1 < x0 if culled),
+ * per-pixel final transmittance and contributor count.  Synchronises. */
+dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, float* depth, int32_t* rect,
+                          float* T_final, int32_t* n_contrib, void* stream);
+
+/* ---------------------------------------------------------------- profiling
+ * Optional per-phase device timers.  When enabled, every call records CUDA
+ * events around its phases on the stream it runs on; dcg_profile_read
+ * synchronises on those events and returns, per phase, the summed
+ * milliseconds (ms, DCG_PH_COUNT floats) and the number of timed intervals
+ * (counts, may be NULL) since the last read.  Enabling creates the events;
+ * the timed calls allocate nothing. */
+enum {
+  DCG_PH_CULL = 0,
+  DCG_PH_GATHER = 1,
+  DCG_PH_PRE_FWD = 2,   /* per-Gaussian projection, conic, SH colour, tile rectangle */
+  DCG_PH_BINNING = 3,   /* compaction, depth sort, instance emission, tile sort, ranges */
+  DCG_PH_BLEND_FWD = 4, /* per-tile front-to-back blending */
+  DCG_PH_LOSS = 5,
+  DCG_PH_BLEND_BWD = 6, /* per-tile reverse traversal, 2D gradients */
+  DCG_PH_PRE_BWD = 7,   /* chain rule to the parameters and the pose */
+  DCG_PH_SCATTER = 8,
+  DCG_PH_COUNT = 9
+};
+dcg_status dcg_profile(dcg_ctx* ctx, int32_t enable);
+dcg_status dcg_profile_read(dcg_ctx* ctx, float* ms, int32_t* counts);
+
+/* Kernel launches issued by the library in this process so far. */
+uint64_t dcg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCG_H */

@@ -144,6 +144,7 @@ def sh_basis(deg: int, dirs: np.ndarray) -> np.ndarray:
 
 # ---------------------------------------------------------------- projection / rendering
 PROJ_FIELDS = ["vis", "u", "v", "z", "A", "B", "C", "o", "r", "g", "b", "ex", "ey", "a", "b2", "c"]
+# Blend order and the near-plane test use the FP32 depth key (see depth_f32).
 
 
 def project(params: np.ndarray, deg: int, cam) -> dict:
@@ -162,7 +163,7 @@ def depth_f32(means: np.ndarray, cam) -> np.ndarray:
     return z
 
 
-DEFAULT_EPS = (1e-4, 1e-4, 1e-4, 1e-6)
+DEFAULT_EPS = (1e-4, 1e-4, 1e-4, 0.0)  # relative bands of q = 9, alpha = 1/255, T = 1e-4
 
 
 def all_pixels(W: int, H: int) -> np.ndarray:

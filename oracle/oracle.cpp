@@ -330,6 +330,7 @@ int orc_sh_basis(int deg, const double* dirs, int64_t n, double* out) {
 // ---------------------------------------------------------------------------
 struct OrcProj {
   int vis;
+  float z32;          // FP32 depth: the blend-order key and the near-plane decision
   double t[3];
   double u, v, z;
   double tx_c, ty_c;  // clamped camera-plane coordinates used by the Jacobian
@@ -354,7 +355,19 @@ static void orc_project(const double* p, int deg, const OrcCam* cam, OrcProj* g)
   for (int r = 0; r < 3; ++r)
     g->t[r] = Wm[3 * r + 0] * p[0] + Wm[3 * r + 1] * p[1] + Wm[3 * r + 2] * p[2] + T[4 * r + 3];
   g->z = g->t[2];
-  g->vis = g->z > cam->znear;
+  // The order of blending and the near-plane test are discrete decisions; they
+  // are taken on the FP32 depth ((W20*mx + W21*my) + W22*mz) + t2 (one
+  // rounding per operation), the precision the kernel decides them in.
+  {
+    volatile float a = (float)T[8] * (float)p[0];
+    volatile float b = (float)T[9] * (float)p[1];
+    volatile float ab = a + b;
+    volatile float c = (float)T[10] * (float)p[2];
+    volatile float abc = ab + c;
+    volatile float r = abc + (float)T[11];
+    g->z32 = r;
+  }
+  g->vis = g->z32 > (float)cam->znear;
   if (!g->vis) return;
   const double tx = g->t[0], ty = g->t[1], tz = g->t[2];
   g->u = cam->fx * tx / tz + cam->cx;
@@ -474,14 +487,14 @@ int orc_depth_f32(const float* means, int64_t n, const float* Tcw, float* z) {
 //   order: ascending (depth, index);
 //   front to back: stop before any Gaussian with T (1-alpha) < 1e-4;
 //   otherwise C += T alpha c, D += T alpha z, T *= (1 - alpha).  Background 0.
+// Order: ascending (FP32 depth key, index), see orc_project.
 // flags (for comparing with an FP32 implementation): bit0 a Gaussian at
 // |q-9| <= eps_q*9 that would pass the alpha test, bit1 alpha within
 // eps_a*(1/255) of the cut-off, bit2 T(1-alpha) within eps_t*1e-4 of the
-// cut-off, bit3 two blended Gaussians with |dz| <= eps_z*z, bit4 a Gaussian
-// with depth within eps_z of the near plane covers the pixel.
+// cut-off.
 // ---------------------------------------------------------------------------
 struct OrcCand {
-  double z;
+  float z;
   int64_t i;
   double alpha, G, q;
 };
@@ -504,7 +517,7 @@ static void orc_scene(const double* params, int64_t n, int deg, const OrcCam* ca
 }
 
 struct OrcEps {
-  double q, a, t, z;
+  double q, a, t;
 };
 
 static int orc_collect(const OrcScene& sc, const OrcCam* cam, double x, double y,
@@ -523,10 +536,9 @@ static int orc_collect(const OrcScene& sc, const OrcCam* cam, double x, double y
     double G = std::exp(-0.5 * q);
     double araw = g.o * G;
     if (eps && std::fabs(araw - a_cut) <= eps->a * a_cut) fl |= 2;
-    if (eps && std::fabs(g.z - cam->znear) <= eps->z * cam->znear) fl |= 16;
     double alpha = araw < 0.99 ? araw : 0.99;
     if (alpha < a_cut) continue;
-    cand.push_back({g.z, i, alpha, G, q});
+    cand.push_back({g.z32, i, alpha, G, q});
   }
   std::sort(cand.begin(), cand.end(), [](const OrcCand& l, const OrcCand& r) {
     return l.z < r.z || (l.z == r.z && l.i < r.i);
@@ -546,11 +558,6 @@ static size_t orc_blend_prefix(const std::vector<OrcCand>& cand, const OrcEps* e
     if (eps && std::fabs(Tn - 1e-4) <= eps->t * 1e-4) fl |= 4;
     if (Tn < 1e-4) break;
     T = Tn;
-  }
-  if (eps) {
-    size_t lim = std::min(n + 1, cand.size());
-    for (size_t k = 1; k < lim; ++k)
-      if (std::fabs(cand[k].z - cand[k - 1].z) <= eps->z * std::fabs(cand[k].z)) fl |= 8;
   }
   if (flags) *flags = fl;
   if (T_out) *T_out = T;
@@ -572,7 +579,7 @@ int orc_render(const double* params, int64_t n, int deg, const OrcCam* cam, cons
                double* T_final, int32_t* n_contrib, int32_t* flags) {
   OrcScene sc;
   orc_scene(params, n, deg, cam, &sc);
-  OrcEps eps = {eps4[0], eps4[1], eps4[2], eps4[3]};
+  OrcEps eps = {eps4[0], eps4[1], eps4[2]};
   const int nt = orc_threads(n_threads);
 #pragma omp parallel num_threads(nt)
   {

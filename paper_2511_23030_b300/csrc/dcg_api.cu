@@ -1,0 +1,1027 @@
+// C ABI of the dcg library: context, chunk table, pinned host tier (stand-in
+// for the paper's disk tier), device page pool with LRU eviction, and the
+// render / loss calls (Sec. III-D, III-E).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace dcg {
+
+struct Chunk {
+  uint64_t key = 0;
+  int32_t c[3] = {0, 0, 0};
+  int64_t count = 0;
+  std::vector<int32_t> host_pages;  // slots [p * page_g, (p+1) * page_g) of the chunk
+  std::vector<int32_t> dev_pages;   // same layout on the device when resident
+  bool resident = false;
+  bool dirty = false;
+  int64_t last_access = -1;
+};
+
+}  // namespace dcg
+
+using namespace dcg;
+
+struct dcg_render_state {
+  dcg_ctx* ctx = nullptr;
+  int64_t cap_pairs = 0, cap_inst = 0, cap_pix = 0, cap_tiles = 0, cap_n = 0;
+  int V = 0;
+  int64_t n = 0, n_pix = 0;
+  int n_tiles = 0;
+  bool valid = false;
+  int gen = 0;
+  dcg_gaussians g{};
+  int tile_w = 16, tile_h = 16, stage = 128;
+  int idx_bits = 1, view_bits = 0;
+  DevCam* d_cams = nullptr;
+  DevCam* h_cams = nullptr;
+  cudaEvent_t ev_cams = nullptr;
+  float4* rec = nullptr;
+  float* depth = nullptr;
+  uint32_t* touched = nullptr;
+  short4* rect = nullptr;
+  float4* grad2d = nullptr;
+  u64 *list_a = nullptr, *list_b = nullptr, *inst_a = nullptr, *inst_b = nullptr;
+  u64 *list_sorted = nullptr, *inst_sorted = nullptr;
+  uint2* ranges = nullptr;
+  float* T_final = nullptr;
+  uint32_t* n_contrib = nullptr;
+  DevCounters* counters = nullptr;
+  u64* part = nullptr;
+  uint32_t* hist = nullptr;
+  int P = 592;
+  std::vector<DevCam> cams_host;
+};
+
+struct dcg_ctx {
+  dcg_config cfg{};
+  int F = 0;
+  int device = 0;
+  int num_sms = 148;
+  std::string err;
+  int tile_w = 16, tile_h = 16, stage = 128;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copy = nullptr, ev_compute = nullptr, ev_desc = nullptr;
+  unsigned* d_errword = nullptr;
+  unsigned* h_errword = nullptr;
+  // chunk table
+  std::vector<Chunk> chunks;  // ascending key
+  std::unordered_map<uint64_t, int32_t> index;
+  int32_t* d_coords = nullptr;
+  uint8_t* d_vis = nullptr;
+  int32_t* d_list = nullptr;
+  int32_t* d_nlist = nullptr;
+  int32_t* h_list = nullptr;
+  int32_t* h_nlist = nullptr;
+  dcg_camera* d_cullcams = nullptr;
+  dcg_camera* h_cullcams = nullptr;
+  // page pools
+  int64_t page_g = 2048, page_floats = 0;
+  float* d_pool = nullptr;
+  int64_t dev_pages = 0;
+  std::vector<int32_t> dev_free;
+  float* h_tier = nullptr;
+  int64_t host_pages = 0;
+  std::vector<int32_t> host_free;
+  int64_t resident_g = 0;
+  int64_t step = 0;
+  // active buffer
+  float* d_active = nullptr;
+  int64_t n_active = 0;
+  std::vector<uint64_t> active_keys;
+  bool active_valid = false;
+  long long* d_desc = nullptr;
+  long long* h_desc = nullptr;
+  int64_t max_desc = 0;
+  int n_desc = 0;
+  // staging for table updates
+  uint64_t* d_keys = nullptr;
+  int64_t keys_cap = 0;
+  uint64_t* h_keys = nullptr;
+  float* h_stage = nullptr;
+  int64_t stage_cap = 0;
+  // statistics
+  int64_t loads = 0, evictions = 0, bytes_h2d = 0, bytes_d2h = 0;
+  dcg_render_state* st0 = nullptr;
+  DevCam* d_losscams = nullptr;
+  DevCam* h_losscams = nullptr;
+  cudaEvent_t ev_loss = nullptr;
+  int fault = 0;
+  // profiler
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_next = 0;
+  cudaEvent_t open_ev[PH_COUNT] = {};
+  struct Rec {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+};
+
+namespace {
+
+void prof_mark(void* h, int phase, bool begin, cudaStream_t s) {
+  dcg_ctx* ctx = (dcg_ctx*)h;
+  if (!ctx->prof_on || ctx->ev_next >= ctx->ev_pool.size()) return;
+  cudaEvent_t e = ctx->ev_pool[ctx->ev_next++];
+  cudaEventRecord(e, s);
+  if (begin) {
+    ctx->open_ev[phase] = e;
+  } else if (ctx->open_ev[phase]) {
+    ctx->recs.push_back({phase, ctx->open_ev[phase], e});
+    ctx->open_ev[phase] = nullptr;
+  }
+}
+
+ProfHook hook(dcg_ctx* ctx) {
+  ProfHook p;
+  if (ctx->prof_on) {
+    p.h = ctx;
+    p.mark = prof_mark;
+  }
+  return p;
+}
+
+dcg_status fail(dcg_ctx* ctx, dcg_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                                         \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess) return fail(ctx, DCG_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+int nsh(int deg) { return (deg + 1) * (deg + 1); }
+
+template <class T>
+cudaError_t dmalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1));
+}
+
+dcg_status upload_coords(dcg_ctx* ctx) {
+  std::vector<int32_t> co(ctx->chunks.size() * 3);
+  for (size_t k = 0; k < ctx->chunks.size(); ++k)
+    for (int a = 0; a < 3; ++a) co[3 * k + a] = ctx->chunks[k].c[a];
+  if (!co.empty()) CK(cudaMemcpy(ctx->d_coords, co.data(), co.size() * 4, cudaMemcpyHostToDevice));
+  return DCG_OK;
+}
+
+float* host_page(dcg_ctx* ctx, int32_t p) { return ctx->h_tier + (int64_t)p * ctx->page_floats; }
+float* dev_page(dcg_ctx* ctx, int32_t p) { return ctx->d_pool + (int64_t)p * ctx->page_floats; }
+
+// Copy the used part (cnt slots of every component) of one page.
+cudaError_t page_copy(dcg_ctx* ctx, float* dst, const float* src, int64_t cnt, cudaMemcpyKind kind, cudaStream_t s) {
+  if (cnt <= 0) return cudaSuccess;
+  const size_t pitch = (size_t)ctx->page_g * 4;
+  if (cnt == ctx->page_g) return cudaMemcpyAsync(dst, src, (size_t)ctx->page_floats * 4, kind, s);
+  return cudaMemcpy2DAsync(dst, pitch, src, pitch, (size_t)cnt * 4, (size_t)ctx->F, kind, s);
+}
+
+int64_t pages_for(dcg_ctx* ctx, int64_t count) { return (count + ctx->page_g - 1) / ctx->page_g; }
+
+dcg_status evict_chunk(dcg_ctx* ctx, Chunk& ch) {
+  if (!ch.resident) return DCG_OK;
+  if (ch.dirty) {
+    for (size_t p = 0; p < ch.dev_pages.size(); ++p) {
+      const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - (int64_t)p * ctx->page_g);
+      CK(page_copy(ctx, host_page(ctx, ch.host_pages[p]), dev_page(ctx, ch.dev_pages[p]), cnt,
+                   cudaMemcpyDeviceToHost, ctx->copy_stream));
+      ctx->bytes_d2h += cnt * ctx->F * 4;
+    }
+    ch.dirty = false;
+  }
+  for (int32_t p : ch.dev_pages) ctx->dev_free.push_back(p);
+  ch.dev_pages.clear();
+  ch.resident = false;
+  ctx->resident_g -= ch.count;
+  ctx->evictions++;
+  return DCG_OK;
+}
+
+dcg_status load_chunk(dcg_ctx* ctx, Chunk& ch) {
+  const int64_t np = pages_for(ctx, ch.count);
+  if ((int64_t)ctx->dev_free.size() < np) return fail(ctx, DCG_ERR_BUDGET, "device page pool exhausted");
+  if (ctx->fault == 1) return fail(ctx, DCG_ERR_FAULT, "injected host->device copy failure");
+  ch.dev_pages.resize((size_t)np);
+  for (int64_t p = 0; p < np; ++p) {
+    ch.dev_pages[(size_t)p] = ctx->dev_free.back();
+    ctx->dev_free.pop_back();
+    const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - p * ctx->page_g);
+    CK(page_copy(ctx, dev_page(ctx, ch.dev_pages[(size_t)p]), host_page(ctx, ch.host_pages[(size_t)p]), cnt,
+                 cudaMemcpyHostToDevice, ctx->copy_stream));
+    ctx->bytes_h2d += cnt * ctx->F * 4;
+  }
+  ch.resident = true;
+  ch.dirty = false;
+  ctx->resident_g += ch.count;
+  ctx->loads++;
+  return DCG_OK;
+}
+
+dcg_status state_alloc(dcg_ctx* ctx, dcg_render_state* st) {
+  const dcg_config& c = ctx->cfg;
+  st->ctx = ctx;
+  st->cap_n = c.max_active;
+  st->cap_pairs = (int64_t)c.max_views * c.max_active;
+  st->cap_inst = c.max_instances;
+  st->cap_pix = c.max_pixels;
+  st->cap_tiles = c.max_pixels / 16 + 64 * (int64_t)c.max_views + 64;  // generous bound incl. ragged edges
+  st->P = ctx->num_sms * 4;
+  CK(dmalloc(&st->d_cams, kMaxViewsApi));
+  CK(cudaHostAlloc((void**)&st->h_cams, sizeof(DevCam) * kMaxViewsApi, cudaHostAllocDefault));
+  CK(cudaEventCreateWithFlags(&st->ev_cams, cudaEventDisableTiming));
+  CK(dmalloc(&st->rec, 3 * (size_t)st->cap_pairs));
+  CK(dmalloc(&st->depth, (size_t)st->cap_pairs));
+  CK(dmalloc(&st->touched, (size_t)st->cap_pairs));
+  CK(dmalloc(&st->rect, (size_t)st->cap_pairs));
+  CK(dmalloc(&st->grad2d, 3 * (size_t)st->cap_pairs));
+  CK(dmalloc(&st->list_a, (size_t)st->cap_pairs));
+  CK(dmalloc(&st->list_b, (size_t)st->cap_pairs));
+  CK(dmalloc(&st->inst_a, (size_t)st->cap_inst));
+  CK(dmalloc(&st->inst_b, (size_t)st->cap_inst));
+  CK(dmalloc(&st->ranges, (size_t)st->cap_tiles));
+  CK(dmalloc(&st->T_final, (size_t)st->cap_pix));
+  CK(dmalloc(&st->n_contrib, (size_t)st->cap_pix));
+  CK(dmalloc(&st->counters, 1));
+  CK(dmalloc(&st->part, (size_t)st->P + 1));
+  CK(dmalloc(&st->hist, 256 * (size_t)st->P));
+  return DCG_OK;
+}
+
+void state_free(dcg_render_state* st) {
+  cudaFree(st->d_cams);
+  if (st->h_cams) cudaFreeHost(st->h_cams);
+  if (st->ev_cams) cudaEventDestroy(st->ev_cams);
+  cudaFree(st->rec); cudaFree(st->depth); cudaFree(st->touched); cudaFree(st->rect); cudaFree(st->grad2d);
+  cudaFree(st->list_a); cudaFree(st->list_b); cudaFree(st->inst_a); cudaFree(st->inst_b);
+  cudaFree(st->ranges); cudaFree(st->T_final); cudaFree(st->n_contrib); cudaFree(st->counters);
+  cudaFree(st->part); cudaFree(st->hist);
+}
+
+bool valid_tile(int tw, int th) { return (tw == 16 && th == 16) || (tw == 32 && th == 16) || (tw == 32 && th == 32); }
+bool valid_stage(int s) { return s == 64 || s == 96 || s == 128 || s == 192 || s == 256; }
+
+dcg_status check_cams(dcg_ctx* ctx, const dcg_camera* cams, int V) {
+  if (!cams || V <= 0 || V > ctx->cfg.max_views || V > kMaxViewsApi) return fail(ctx, DCG_ERR_ARG, "bad views");
+  for (int v = 0; v < V; ++v) {
+    const dcg_camera& c = cams[v];
+    if (c.W <= 0 || c.H <= 0 || !(c.fx > 0) || !(c.fy > 0) || !(c.znear > 0) || !(c.zfar > c.znear))
+      return fail(ctx, DCG_ERR_ARG, "bad camera");
+  }
+  return DCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dcg_config_default(dcg_config* c) {
+  std::memset(c, 0, sizeof(*c));
+  c->chunk_size = 4.0f;
+  c->sh_degree = 3;
+  c->device_budget = 6000000;
+  c->host_capacity = 6000000;
+  c->max_chunks = 8192;
+  c->max_views = 8;
+  c->max_active = 6000000;
+  c->max_pixels = 8 * 1241 * 376;
+  c->max_instances = 64 << 20;
+  c->tile_w = 16;
+  c->tile_h = 16;
+  c->stage = 128;
+  c->dfar = 100.0f;
+  c->page_gaussians = 2048;
+}
+
+const char* dcg_last_error(const dcg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
+  if (!cfg || !out) return DCG_ERR_ARG;
+  *out = nullptr;
+  dcg_ctx* ctx = new dcg_ctx();
+  ctx->cfg = *cfg;
+  const dcg_config& c = ctx->cfg;
+  dcg_status bad = DCG_OK;
+  if (c.sh_degree < 0 || c.sh_degree > 3 || !(c.chunk_size > 0) || c.device_budget <= 0 || c.host_capacity <= 0 ||
+      c.max_chunks <= 0 || c.max_views <= 0 || c.max_views > kMaxViewsApi || c.max_active <= 0 || c.max_pixels <= 0 ||
+      c.max_instances <= 0 || c.max_instances >= (1ll << 32) || c.page_gaussians <= 0 ||
+      (c.page_gaussians & (c.page_gaussians - 1)) != 0 || !valid_tile(c.tile_w, c.tile_h) || !valid_stage(c.stage) ||
+      (int64_t)c.max_views * c.max_active >= (1ll << 32))
+    bad = DCG_ERR_ARG;
+  if (bad != DCG_OK) {
+    delete ctx;
+    return bad;
+  }
+  ctx->F = 11 + 3 * nsh(c.sh_degree);
+  ctx->tile_w = c.tile_w;
+  ctx->tile_h = c.tile_h;
+  ctx->stage = c.stage;
+  ctx->page_g = c.page_gaussians;
+  ctx->page_floats = ctx->page_g * ctx->F;
+  auto cleanup_fail = [&](dcg_status s) {
+    dcg_destroy(ctx);
+    return s;
+  };
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
+  cudaEventCreateWithFlags(&ctx->ev_copy, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_compute, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_desc, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_loss, cudaEventDisableTiming);
+  if (dmalloc(&ctx->d_losscams, kMaxViewsApi) != cudaSuccess ||
+      cudaHostAlloc((void**)&ctx->h_losscams, sizeof(DevCam) * kMaxViewsApi, 0) != cudaSuccess)
+    return cleanup_fail(DCG_ERR_OOM);
+  if (dmalloc(&ctx->d_errword, 1) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
+  cudaMemset(ctx->d_errword, 0, sizeof(unsigned));
+  if (cudaHostAlloc((void**)&ctx->h_errword, sizeof(unsigned), 0) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
+  // chunk table mirror
+  if (dmalloc(&ctx->d_coords, 3 * (size_t)c.max_chunks) != cudaSuccess ||
+      dmalloc(&ctx->d_vis, (size_t)c.max_chunks) != cudaSuccess || dmalloc(&ctx->d_list, (size_t)c.max_chunks) != cudaSuccess ||
+      dmalloc(&ctx->d_nlist, 1) != cudaSuccess || dmalloc(&ctx->d_cullcams, kMaxViewsApi) != cudaSuccess)
+    return cleanup_fail(DCG_ERR_OOM);
+  if (cudaHostAlloc((void**)&ctx->h_list, sizeof(int32_t) * c.max_chunks, 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&ctx->h_nlist, sizeof(int32_t), 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&ctx->h_cullcams, sizeof(dcg_camera) * kMaxViewsApi, 0) != cudaSuccess)
+    return cleanup_fail(DCG_ERR_OOM);
+  // page pools: the budget in Gaussians plus one partly filled page per chunk that can be resident
+  ctx->dev_pages = (c.device_budget + ctx->page_g - 1) / ctx->page_g + std::min<int64_t>(c.max_chunks, 4096);
+  ctx->host_pages = (c.host_capacity + ctx->page_g - 1) / ctx->page_g + c.max_chunks;
+  if (dmalloc(&ctx->d_pool, (size_t)(ctx->dev_pages * ctx->page_floats)) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
+  if (cudaHostAlloc((void**)&ctx->h_tier, sizeof(float) * (size_t)(ctx->host_pages * ctx->page_floats), 0) != cudaSuccess)
+    return cleanup_fail(DCG_ERR_OOM);
+  for (int64_t p = ctx->dev_pages - 1; p >= 0; --p) ctx->dev_free.push_back((int32_t)p);
+  for (int64_t p = ctx->host_pages - 1; p >= 0; --p) ctx->host_free.push_back((int32_t)p);
+  // active buffer and page descriptors
+  if (dmalloc(&ctx->d_active, (size_t)ctx->F * c.max_active) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
+  ctx->max_desc = ctx->dev_pages;
+  if (dmalloc(&ctx->d_desc, 3 * (size_t)ctx->max_desc) != cudaSuccess ||
+      cudaHostAlloc((void**)&ctx->h_desc, sizeof(long long) * 3 * (size_t)ctx->max_desc, 0) != cudaSuccess)
+    return cleanup_fail(DCG_ERR_OOM);
+  ctx->st0 = new dcg_render_state();
+  if (state_alloc(ctx, ctx->st0) != DCG_OK) return cleanup_fail(DCG_ERR_OOM);
+  if (cudaDeviceSynchronize() != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
+  *out = ctx;
+  return DCG_OK;
+}
+
+dcg_status dcg_destroy(dcg_ctx* ctx) {
+  if (!ctx) return DCG_ERR_ARG;
+  cudaDeviceSynchronize();
+  if (ctx->st0) {
+    state_free(ctx->st0);
+    delete ctx->st0;
+  }
+  cudaFree(ctx->d_errword);
+  if (ctx->h_errword) cudaFreeHost(ctx->h_errword);
+  cudaFree(ctx->d_coords); cudaFree(ctx->d_vis); cudaFree(ctx->d_list); cudaFree(ctx->d_nlist); cudaFree(ctx->d_cullcams);
+  if (ctx->h_list) cudaFreeHost(ctx->h_list);
+  if (ctx->h_nlist) cudaFreeHost(ctx->h_nlist);
+  if (ctx->h_cullcams) cudaFreeHost(ctx->h_cullcams);
+  cudaFree(ctx->d_pool);
+  if (ctx->h_tier) cudaFreeHost(ctx->h_tier);
+  cudaFree(ctx->d_active);
+  cudaFree(ctx->d_desc);
+  if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
+  cudaFree(ctx->d_keys);
+  if (ctx->h_keys) cudaFreeHost(ctx->h_keys);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->ev_copy) cudaEventDestroy(ctx->ev_copy);
+  if (ctx->ev_compute) cudaEventDestroy(ctx->ev_compute);
+  if (ctx->ev_desc) cudaEventDestroy(ctx->ev_desc);
+  if (ctx->ev_loss) cudaEventDestroy(ctx->ev_loss);
+  for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
+  cudaFree(ctx->d_losscams);
+  if (ctx->h_losscams) cudaFreeHost(ctx->h_losscams);
+  delete ctx;
+  return DCG_OK;
+}
+
+dcg_status dcg_sync(dcg_ctx* ctx, void* stream) {
+  if (!ctx) return DCG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(ctx->h_errword, ctx->d_errword, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaStreamSynchronize(ctx->copy_stream));
+  const unsigned w = *ctx->h_errword;
+  if (w) {
+    CK(cudaMemsetAsync(ctx->d_errword, 0, sizeof(unsigned), s));
+    CK(cudaStreamSynchronize(s));
+    if (w & ERRW_KEY_RANGE_BIT) return fail(ctx, DCG_ERR_KEY_RANGE, "chunk coordinate outside [-2^20, 2^20-1]");
+    if (w & ERRW_CAPACITY_BIT) return fail(ctx, DCG_ERR_CAPACITY, "instance capacity exceeded");
+    if (w & ERRW_TIMEOUT_BIT) return fail(ctx, DCG_ERR_TIMEOUT, "bounded device wait gave up");
+  }
+  return DCG_OK;
+}
+
+// ---------------------------------------------------------------- chunks
+dcg_status dcg_chunk_keys(dcg_ctx* ctx, const float* means, int64_t n, uint64_t* keys_out, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!means || !keys_out))) return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  launch_chunk_keys(means, 3, 1, n, ctx->cfg.chunk_size, (u64*)keys_out, ctx->d_errword, ctx->num_sms,
+                    (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return DCG_OK;
+}
+
+dcg_status dcg_chunk_table_update(dcg_ctx* ctx, const float* params, int64_t stride, int64_t n, uint64_t* keys_out,
+                                  void* stream) {
+  if (!ctx || n < 0 || (n > 0 && !params) || stride < n) return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  if (n == 0) return DCG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int F = ctx->F;
+  if (n > ctx->keys_cap) {
+    cudaFree(ctx->d_keys);
+    if (ctx->h_keys) cudaFreeHost(ctx->h_keys);
+    ctx->d_keys = nullptr;
+    ctx->h_keys = nullptr;
+    ctx->keys_cap = 0;
+    CK(dmalloc(&ctx->d_keys, (size_t)n));
+    CK(cudaHostAlloc((void**)&ctx->h_keys, sizeof(uint64_t) * (size_t)n, 0));
+    ctx->keys_cap = n;
+  }
+  if (n * F > ctx->stage_cap) {
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->stage_cap = 0;
+    CK(cudaHostAlloc((void**)&ctx->h_stage, sizeof(float) * (size_t)(n * F), 0));
+    ctx->stage_cap = n * F;
+  }
+  // Eq. 5 / 6 on the device (planar means: component stride `stride`)
+  launch_chunk_keys(params, 1, stride, n, ctx->cfg.chunk_size, (u64*)ctx->d_keys, ctx->d_errword, ctx->num_sms, s);
+  CK(cudaGetLastError());
+  if (keys_out) CK(cudaMemcpyAsync(keys_out, ctx->d_keys, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(ctx->h_keys, ctx->d_keys, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpy2DAsync(ctx->h_stage, (size_t)n * 4, params, (size_t)stride * 4, (size_t)n * 4, (size_t)F,
+                       cudaMemcpyDeviceToHost, s));
+  dcg_status es = dcg_sync(ctx, stream);
+  if (es != DCG_OK) return es;
+  // group by chunk, stable in input order
+  std::unordered_map<uint64_t, std::vector<int64_t>> groups;
+  for (int64_t i = 0; i < n; ++i) groups[ctx->h_keys[i]].push_back(i);
+  std::vector<uint64_t> new_keys;
+  for (auto& kv : groups)
+    if (!ctx->index.count(kv.first)) new_keys.push_back(kv.first);
+  if ((int64_t)(ctx->chunks.size() + new_keys.size()) > ctx->cfg.max_chunks)
+    return fail(ctx, DCG_ERR_CAPACITY, "chunk table full");
+  int64_t need_pages = 0;
+  for (auto& kv : groups) {
+    int64_t have = 0, cnt0 = 0;
+    auto it = ctx->index.find(kv.first);
+    if (it != ctx->index.end()) {
+      have = (int64_t)ctx->chunks[it->second].host_pages.size();
+      cnt0 = ctx->chunks[it->second].count;
+    }
+    need_pages += pages_for(ctx, cnt0 + (int64_t)kv.second.size()) - have;
+  }
+  if (need_pages > (int64_t)ctx->host_free.size()) return fail(ctx, DCG_ERR_CAPACITY, "host tier full");
+  // new chunks, table kept in ascending key order
+  for (uint64_t k : new_keys) {
+    Chunk ch;
+    ch.key = k;
+    const int64_t m = (1 << 21) - 1;
+    ch.c[0] = (int32_t)((int64_t)((k >> 42) & m) - (1 << 20));
+    ch.c[1] = (int32_t)((int64_t)((k >> 21) & m) - (1 << 20));
+    ch.c[2] = (int32_t)((int64_t)(k & m) - (1 << 20));
+    ctx->chunks.push_back(ch);
+  }
+  if (!new_keys.empty()) {
+    std::sort(ctx->chunks.begin(), ctx->chunks.end(), [](const Chunk& a, const Chunk& b) { return a.key < b.key; });
+    ctx->index.clear();
+    for (size_t k = 0; k < ctx->chunks.size(); ++k) ctx->index[ctx->chunks[k].key] = (int32_t)k;
+    dcg_status us = upload_coords(ctx);
+    if (us != DCG_OK) return us;
+  }
+  CK(cudaStreamSynchronize(ctx->copy_stream));
+  for (auto& kv : groups) {
+    Chunk& ch = ctx->chunks[ctx->index[kv.first]];
+    if (ch.resident) {  // write back and drop: the next gather reloads the whole chunk
+      dcg_status e = evict_chunk(ctx, ch);
+      if (e != DCG_OK) return e;
+      ctx->evictions--;
+      CK(cudaStreamSynchronize(ctx->copy_stream));
+    }
+    for (int64_t i : kv.second) {
+      const int64_t slot = ch.count;
+      const int64_t p = slot / ctx->page_g, j = slot - p * ctx->page_g;
+      if (p >= (int64_t)ch.host_pages.size()) {
+        ch.host_pages.push_back(ctx->host_free.back());
+        ctx->host_free.pop_back();
+      }
+      float* page = host_page(ctx, ch.host_pages[(size_t)p]);
+      for (int f = 0; f < F; ++f) page[(int64_t)f * ctx->page_g + j] = ctx->h_stage[(int64_t)f * n + i];
+      ch.count++;
+    }
+  }
+  return DCG_OK;
+}
+
+int32_t dcg_chunk_count(const dcg_ctx* ctx) { return ctx ? (int32_t)ctx->chunks.size() : 0; }
+
+dcg_status dcg_chunk_info(const dcg_ctx* ctx, int32_t* coords, uint64_t* keys, int64_t* counts, uint8_t* resident,
+                          int64_t* last_access) {
+  if (!ctx) return DCG_ERR_ARG;
+  for (size_t k = 0; k < ctx->chunks.size(); ++k) {
+    const Chunk& ch = ctx->chunks[k];
+    if (coords)
+      for (int a = 0; a < 3; ++a) coords[3 * k + a] = ch.c[a];
+    if (keys) keys[k] = ch.key;
+    if (counts) counts[k] = ch.count;
+    if (resident) resident[k] = ch.resident ? 1 : 0;
+    if (last_access) last_access[k] = ch.last_access;
+  }
+  return DCG_OK;
+}
+
+dcg_status dcg_cull_chunks(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views, uint8_t* mask_out, int32_t* list_out,
+                           int32_t* n_out, void* stream) {
+  if (!ctx) return DCG_ERR_ARG;
+  dcg_status cs = check_cams(ctx, cams, n_views);
+  if (cs != DCG_OK) return cs;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int C = (int)ctx->chunks.size();
+  std::memcpy(ctx->h_cullcams, cams, sizeof(dcg_camera) * n_views);
+  CK(cudaMemcpyAsync(ctx->d_cullcams, ctx->h_cullcams, sizeof(dcg_camera) * n_views, cudaMemcpyHostToDevice, s));
+  hook(ctx)(PH_CULL, true, s);
+  launch_cull(ctx->d_coords, C, ctx->d_cullcams, n_views, ctx->cfg.chunk_size, ctx->cfg.dfar, mask_out, ctx->d_vis,
+              ctx->d_list, ctx->d_nlist, s);
+  hook(ctx)(PH_CULL, false, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->h_nlist, ctx->d_nlist, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (C > 0) CK(cudaMemcpyAsync(ctx->h_list, ctx->d_list, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (n_out) *n_out = *ctx->h_nlist;
+  if (list_out) std::memcpy(list_out, ctx->h_list, sizeof(int32_t) * (size_t)*ctx->h_nlist);
+  return DCG_OK;
+}
+
+dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, dcg_gaussians* active_out,
+                             int64_t* n_active_out, void* stream) {
+  if (!ctx || n_list < 0 || (n_list > 0 && !list) || !active_out || !n_active_out)
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int C = (int)ctx->chunks.size();
+  std::vector<uint8_t> need((size_t)C, 0);
+  int64_t total = 0, incoming = 0, need_pages = 0;
+  for (int k = 0; k < n_list; ++k) {
+    const int32_t c = list[k];
+    if (c < 0 || c >= C || (k > 0 && list[k - 1] >= c)) return fail(ctx, DCG_ERR_ARG, "chunk list must be ascending indices");
+    need[(size_t)c] = 1;
+    total += ctx->chunks[c].count;
+    if (!ctx->chunks[c].resident) {
+      incoming += ctx->chunks[c].count;
+      need_pages += pages_for(ctx, ctx->chunks[c].count);
+    }
+  }
+  if (total > ctx->cfg.device_budget || total > ctx->cfg.max_active)
+    return fail(ctx, DCG_ERR_BUDGET, "visible chunks exceed the device budget");
+  if (ctx->fault == 2) return fail(ctx, DCG_ERR_BUDGET, "injected budget failure");
+  ctx->step++;
+  // LRU eviction (Sec. III-E): oldest first, ties by id, the fewest chunks that make room
+  int64_t deficit_g = ctx->resident_g + incoming - ctx->cfg.device_budget;
+  int64_t deficit_p = need_pages - (int64_t)ctx->dev_free.size();
+  if (deficit_g > 0 || deficit_p > 0) {
+    std::vector<int32_t> cand;
+    for (int c = 0; c < C; ++c)
+      if (ctx->chunks[c].resident && !need[(size_t)c]) cand.push_back(c);
+    std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
+      const Chunk &x = ctx->chunks[a], &y = ctx->chunks[b];
+      return x.last_access < y.last_access || (x.last_access == y.last_access && x.key < y.key);
+    });
+    CK(cudaEventRecord(ctx->ev_compute, s));
+    CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_compute, 0));
+    for (int32_t c : cand) {
+      if (deficit_g <= 0 && deficit_p <= 0) break;
+      const int64_t cnt = ctx->chunks[c].count;
+      const int64_t np = (int64_t)ctx->chunks[c].dev_pages.size();
+      dcg_status e = evict_chunk(ctx, ctx->chunks[c]);
+      if (e != DCG_OK) return e;
+      deficit_g -= cnt;
+      deficit_p -= np;
+    }
+    if (deficit_g > 0 || deficit_p > 0) return fail(ctx, DCG_ERR_BUDGET, "cannot make room within the budget");
+  }
+  // loads on the copy stream
+  bool any_load = false;
+  for (int k = 0; k < n_list; ++k) {
+    Chunk& ch = ctx->chunks[list[k]];
+    if (!ch.resident) {
+      if (!any_load) {
+        CK(cudaEventRecord(ctx->ev_compute, s));
+        CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_compute, 0));
+        any_load = true;
+      }
+      dcg_status e = load_chunk(ctx, ch);
+      if (e != DCG_OK) return e;
+    }
+    ch.last_access = ctx->step;
+  }
+  CK(cudaEventRecord(ctx->ev_copy, ctx->copy_stream));
+  CK(cudaStreamWaitEvent(s, ctx->ev_copy, 0));
+  // page descriptors: (page, count, offset in the active buffer)
+  CK(cudaEventSynchronize(ctx->ev_desc));  // the previous descriptor upload has been consumed
+  int nd = 0;
+  int64_t off = 0;
+  ctx->active_keys.clear();
+  for (int k = 0; k < n_list; ++k) {
+    const Chunk& ch = ctx->chunks[list[k]];
+    ctx->active_keys.push_back(ch.key);
+    for (size_t p = 0; p < ch.dev_pages.size(); ++p) {
+      const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - (int64_t)p * ctx->page_g);
+      ctx->h_desc[3 * nd + 0] = ch.dev_pages[p];
+      ctx->h_desc[3 * nd + 1] = cnt;
+      ctx->h_desc[3 * nd + 2] = off;
+      off += cnt;
+      ++nd;
+    }
+  }
+  ctx->n_desc = nd;
+  if (nd > 0) CK(cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(long long) * 3 * nd, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(ctx->ev_desc, s));
+  hook(ctx)(PH_GATHER, true, s);
+  launch_page_copy(true, ctx->d_pool, ctx->page_g, ctx->F, ctx->d_desc, nd, ctx->d_active, ctx->cfg.max_active, s);
+  hook(ctx)(PH_GATHER, false, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev_compute, s));
+  ctx->n_active = total;
+  ctx->active_valid = true;
+  active_out->data = ctx->d_active;
+  active_out->stride = ctx->cfg.max_active;
+  active_out->sh_degree = ctx->cfg.sh_degree;
+  active_out->pad = 0;
+  *n_active_out = total;
+  return DCG_OK;
+}
+
+dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n, void* stream) {
+  if (!ctx || !active || !active->data) return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  if (!ctx->active_valid) return fail(ctx, DCG_ERR_STATE, "scatter_back without a gather");
+  if (n != ctx->n_active || active->sh_degree != ctx->cfg.sh_degree || active->stride < n)
+    return fail(ctx, DCG_ERR_ARG, "scatter_back size or degree differs from the gather");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (uint64_t k : ctx->active_keys) {
+    auto it = ctx->index.find(k);
+    if (it == ctx->index.end() || !ctx->chunks[it->second].resident)
+      return fail(ctx, DCG_ERR_STATE, "a gathered chunk is no longer resident");
+  }
+  hook(ctx)(PH_SCATTER, true, s);
+  launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->F, ctx->d_desc, ctx->n_desc, active->data, active->stride, s);
+  hook(ctx)(PH_SCATTER, false, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev_compute, s));
+  for (uint64_t k : ctx->active_keys) ctx->chunks[ctx->index[k]].dirty = true;
+  return DCG_OK;
+}
+
+dcg_status dcg_flush(dcg_ctx* ctx, void* stream) {
+  if (!ctx) return DCG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaEventRecord(ctx->ev_compute, s));
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_compute, 0));
+  for (Chunk& ch : ctx->chunks) {
+    if (!ch.resident || !ch.dirty) continue;
+    for (size_t p = 0; p < ch.dev_pages.size(); ++p) {
+      const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - (int64_t)p * ctx->page_g);
+      CK(page_copy(ctx, host_page(ctx, ch.host_pages[p]), dev_page(ctx, ch.dev_pages[p]), cnt, cudaMemcpyDeviceToHost,
+                   ctx->copy_stream));
+      ctx->bytes_d2h += cnt * ctx->F * 4;
+    }
+    ch.dirty = false;
+  }
+  CK(cudaStreamSynchronize(ctx->copy_stream));
+  return DCG_OK;
+}
+
+dcg_status dcg_chunk_read(dcg_ctx* ctx, int32_t chunk, float* out, int64_t n) {
+  if (!ctx || chunk < 0 || chunk >= (int32_t)ctx->chunks.size() || !out) return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  const Chunk& ch = ctx->chunks[chunk];
+  if (n != ch.count) return fail(ctx, DCG_ERR_ARG, "n must equal the chunk's count");
+  CK(cudaStreamSynchronize(ctx->copy_stream));
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t p = i / ctx->page_g, j = i - p * ctx->page_g;
+    const float* page = host_page(ctx, ch.host_pages[(size_t)p]);
+    for (int f = 0; f < ctx->F; ++f) out[(int64_t)f * n + i] = page[(int64_t)f * ctx->page_g + j];
+  }
+  return DCG_OK;
+}
+
+// ---------------------------------------------------------------- rendering
+dcg_status dcg_state_create(dcg_ctx* ctx, dcg_render_state** out) {
+  if (!ctx || !out) return DCG_ERR_ARG;
+  dcg_render_state* st = new dcg_render_state();
+  dcg_status s = state_alloc(ctx, st);
+  if (s != DCG_OK) {
+    state_free(st);
+    delete st;
+    return s;
+  }
+  *out = st;
+  return DCG_OK;
+}
+
+dcg_render_state* dcg_default_state(dcg_ctx* ctx) { return ctx ? ctx->st0 : nullptr; }
+
+dcg_status dcg_state_destroy(dcg_render_state* st) {
+  if (!st) return DCG_ERR_ARG;
+  cudaDeviceSynchronize();
+  state_free(st);
+  delete st;
+  return DCG_OK;
+}
+
+dcg_status dcg_set_launch(dcg_ctx* ctx, int32_t tw, int32_t th, int32_t stage) {
+  if (!ctx || !valid_tile(tw, th) || !valid_stage(stage)) return fail(ctx, DCG_ERR_ARG, "bad launch shape");
+  ctx->tile_w = tw;
+  ctx->tile_h = th;
+  ctx->stage = stage;
+  return DCG_OK;
+}
+
+static void fill_args(dcg_render_state* st, RasterArgs& a) {
+  dcg_ctx* ctx = st->ctx;
+  a.g = st->g.data;
+  a.stride = st->g.stride;
+  a.n = st->n;
+  a.deg = st->g.sh_degree;
+  a.V = st->V;
+  a.cams = st->d_cams;
+  a.tile_w = st->tile_w;
+  a.tile_h = st->tile_h;
+  a.stage = st->stage;
+  a.n_tiles = st->n_tiles;
+  a.n_pix = st->n_pix;
+  a.idx_bits = st->idx_bits;
+  a.view_bits = st->view_bits;
+  a.rec = st->rec;
+  a.depth = st->depth;
+  a.touched = st->touched;
+  a.rect = st->rect;
+  a.grad2d = st->grad2d;
+  a.list_a = st->list_a;
+  a.list_b = st->list_b;
+  a.inst_a = st->inst_a;
+  a.inst_b = st->inst_b;
+  a.cap_pairs = st->cap_pairs;
+  a.cap_inst = st->cap_inst;
+  a.ranges = st->ranges;
+  a.T_final = st->T_final;
+  a.n_contrib = st->n_contrib;
+  a.counters = st->counters;
+  a.part = st->part;
+  a.hist = st->hist;
+  a.P = st->P;
+  a.errword = ctx->d_errword;
+  a.num_sms = ctx->num_sms;
+  a.prof = hook(ctx);
+}
+
+dcg_status dcg_render_fwd(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams, int32_t V,
+                          float* rgb, float* depth, dcg_render_state* st, void* stream) {
+  if (!ctx) return DCG_ERR_ARG;
+  if (!st) st = ctx->st0;
+  if (!g || n < 0 || (n > 0 && !g->data) || g->stride < n || g->sh_degree < 0 || g->sh_degree > 3 || !rgb || !depth)
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  dcg_status cs = check_cams(ctx, cams, V);
+  if (cs != DCG_OK) return cs;
+  if (n > st->cap_n) return fail(ctx, DCG_ERR_CAPACITY, "more Gaussians than max_active");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int tw = ctx->tile_w, th = ctx->tile_h;
+  int64_t pix = 0;
+  int tiles = 0;
+  CK(cudaEventSynchronize(st->ev_cams));  // staging buffer free again
+  for (int v = 0; v < V; ++v) {
+    const dcg_camera& c = cams[v];
+    DevCam& d = st->h_cams[v];
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    for (int r = 0; r < 3; ++r) {
+      for (int k = 0; k < 3; ++k) d.R[3 * r + k] = c.Tcw[4 * r + k];
+      d.t[r] = c.Tcw[4 * r + 3];
+    }
+    for (int k = 0; k < 3; ++k)
+      d.C[k] = (float)(-((double)c.Tcw[0 + k] * c.Tcw[3] + (double)c.Tcw[4 + k] * c.Tcw[7] + (double)c.Tcw[8 + k] * c.Tcw[11]));
+    d.znear = c.znear; d.zfar = c.zfar;
+    d.xlo = (float)((-0.15 * c.W - c.cx) / c.fx);
+    d.xhi = (float)((1.15 * c.W - c.cx) / c.fx);
+    d.ylo = (float)((-0.15 * c.H - c.cy) / c.fy);
+    d.yhi = (float)((1.15 * c.H - c.cy) / c.fy);
+    d.W = c.W; d.H = c.H;
+    d.ntx = (c.W + tw - 1) / tw;
+    d.nty = (c.H + th - 1) / th;
+    d.tile_base = tiles;
+    d.pad = 0;
+    d.pix_off = pix;
+    tiles += d.ntx * d.nty;
+    pix += (int64_t)c.W * c.H;
+  }
+  if (pix > st->cap_pix || tiles > st->cap_tiles) return fail(ctx, DCG_ERR_CAPACITY, "pixel or tile capacity exceeded");
+  CK(cudaMemcpyAsync(st->d_cams, st->h_cams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(st->ev_cams, s));
+  st->g = *g;
+  st->n = n;
+  st->V = V;
+  st->n_pix = pix;
+  st->n_tiles = tiles;
+  st->tile_w = tw;
+  st->tile_h = th;
+  st->stage = ctx->stage;
+  st->idx_bits = 1;
+  while ((1ll << st->idx_bits) < n) ++st->idx_bits;
+  st->view_bits = 0;
+  while ((1 << st->view_bits) < V) ++st->view_bits;
+  RasterArgs a;
+  fill_args(st, a);
+  raster_forward(a, rgb, depth, &st->list_sorted, &st->inst_sorted, s);
+  CK(cudaGetLastError());
+  st->valid = true;
+  st->gen++;
+  return DCG_OK;
+}
+
+dcg_status dcg_render_bwd(dcg_ctx* ctx, dcg_render_state* st, const float* dL_drgb, const float* dL_ddepth,
+                          dcg_gaussians* grads, float* dL_dpose, void* stream) {
+  if (!ctx) return DCG_ERR_ARG;
+  if (!st) st = ctx->st0;
+  if (!st->valid) return fail(ctx, DCG_ERR_STATE, "backward without a forward");
+  if (!dL_drgb || !dL_ddepth || !grads || (st->n > 0 && !grads->data) || grads->stride < st->n ||
+      grads->sh_degree != st->g.sh_degree)
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  RasterArgs a;
+  fill_args(st, a);
+  raster_backward(a, st->inst_sorted, dL_drgb, dL_ddepth, grads->data, grads->stride, dL_dpose, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return DCG_OK;
+}
+
+dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const float* trgb, const float* tdepth,
+                       const dcg_camera* cams, int32_t V, float lam, float* dr, float* dd, float* loss, void* stream) {
+  if (!ctx || !rgb || !depth || !trgb || !tdepth || !dr || !dd || !loss) return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  dcg_status cs = check_cams(ctx, cams, V);
+  if (cs != DCG_OK) return cs;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaEventSynchronize(ctx->ev_loss));  // staging buffer free again
+  int64_t pix = 0;
+  for (int v = 0; v < V; ++v) {
+    DevCam& d = ctx->h_losscams[v];
+    std::memset(&d, 0, sizeof(d));
+    d.W = cams[v].W;
+    d.H = cams[v].H;
+    d.pix_off = pix;
+    pix += (int64_t)cams[v].W * cams[v].H;
+  }
+  CK(cudaMemcpyAsync(ctx->d_losscams, ctx->h_losscams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(ctx->ev_loss, s));
+  hook(ctx)(PH_LOSS, true, s);
+  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, lam, dr, dd, loss, ctx->num_sms, s);
+  hook(ctx)(PH_LOSS, false, s);
+  CK(cudaGetLastError());
+  return DCG_OK;
+}
+
+dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams, int32_t V,
+                        float* rgb, float* depth, const float* dr, const float* dd, dcg_gaussians* grads, int32_t reps,
+                        int32_t* tile_w, int32_t* tile_h, int32_t* stage, float* ms_out, void* stream) {
+  if (!ctx || reps <= 0) return DCG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  static const int tiles[3][2] = {{16, 16}, {32, 16}, {32, 32}};
+  static const int stages[5] = {64, 96, 128, 192, 256};
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best = 1e30f;
+  int bt = 0, bs = 2;
+  const bool prof = ctx->prof_on;
+  ctx->prof_on = false;
+  dcg_status rc = DCG_OK;
+  for (int t = 0; t < 3 && rc == DCG_OK; ++t)
+    for (int k = 0; k < 5 && rc == DCG_OK; ++k) {
+      dcg_set_launch(ctx, tiles[t][0], tiles[t][1], stages[k]);
+      float ms = 0.f;
+      for (int r = 0; r <= reps && rc == DCG_OK; ++r) {
+        if (r == 1) cudaEventRecord(a, s);
+        rc = dcg_render_fwd(ctx, g, n, cams, V, rgb, depth, nullptr, stream);
+        if (rc == DCG_OK) rc = dcg_render_bwd(ctx, nullptr, dr, dd, grads, nullptr, stream);
+      }
+      if (rc != DCG_OK) break;
+      cudaEventRecord(b, s);
+      cudaEventSynchronize(b);
+      cudaEventElapsedTime(&ms, a, b);
+      ms /= reps;
+      if (ms_out) ms_out[5 * t + k] = ms;
+      if (ms < best) {
+        best = ms;
+        bt = t;
+        bs = k;
+      }
+    }
+  ctx->prof_on = prof;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc != DCG_OK) return rc;
+  dcg_set_launch(ctx, tiles[bt][0], tiles[bt][1], stages[bs]);
+  if (tile_w) *tile_w = tiles[bt][0];
+  if (tile_h) *tile_h = tiles[bt][1];
+  if (stage) *stage = stages[bs];
+  return dcg_sync(ctx, stream);
+}
+
+dcg_status dcg_profile(dcg_ctx* ctx, int32_t enable) {
+  if (!ctx) return DCG_ERR_ARG;
+  if (enable && ctx->ev_pool.empty()) {
+    ctx->ev_pool.resize(8192);
+    for (auto& e : ctx->ev_pool) CK(cudaEventCreate(&e));
+  }
+  ctx->prof_on = enable != 0;
+  return DCG_OK;
+}
+
+dcg_status dcg_profile_read(dcg_ctx* ctx, float* ms, int32_t* counts) {
+  if (!ctx || !ms) return DCG_ERR_ARG;
+  for (int p = 0; p < PH_COUNT; ++p) {
+    ms[p] = 0.f;
+    if (counts) counts[p] = 0;
+  }
+  for (auto& r : ctx->recs) {
+    CK(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.phase] += t;
+    if (counts) counts[r.phase] += 1;
+  }
+  ctx->recs.clear();
+  ctx->ev_next = 0;
+  for (auto& e : ctx->open_ev) e = nullptr;
+  return DCG_OK;
+}
+
+uint64_t dcg_launch_count(void) { return (uint64_t)g_launches; }
+
+dcg_status dcg_state_stats(dcg_render_state* st, int64_t* n_visible, int64_t* n_instances, int64_t* n_tiles,
+                           void* stream) {
+  if (!st) return DCG_ERR_ARG;
+  DevCounters h;
+  dcg_ctx* ctx = st->ctx;
+  CK(cudaMemcpyAsync(&h, st->counters, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  if (n_visible) *n_visible = (int64_t)h.n_vis;
+  if (n_instances) *n_instances = (int64_t)h.n_inst;
+  if (n_tiles) *n_tiles = st->n_tiles;
+  return DCG_OK;
+}
+
+dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, void* stream) {
+  if (!st || !n_eval) return DCG_ERR_ARG;
+  dcg_ctx* ctx = st->ctx;
+  DevCounters h;
+  CK(cudaMemcpyAsync(&h, st->counters, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  *n_eval = (int64_t)h.n_eval;
+  return DCG_OK;
+}
+
+dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, float* depth, int32_t* rect,
+                          float* T_final, int32_t* n_contrib, void* stream) {
+  if (!st || !st->valid) return DCG_ERR_STATE;
+  dcg_ctx* ctx = st->ctx;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevCounters h;
+  CK(cudaMemcpyAsync(&h, st->counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int64_t K = (int64_t)h.n_inst_c, pairs = (int64_t)st->V * st->n;
+  if (ranges) CK(cudaMemcpyAsync(ranges, st->ranges, sizeof(uint2) * st->n_tiles, cudaMemcpyDeviceToHost, s));
+  std::vector<u64> inst;
+  if (ids) {
+    inst.resize((size_t)K);
+    if (K) CK(cudaMemcpyAsync(inst.data(), st->inst_sorted, 8 * (size_t)K, cudaMemcpyDeviceToHost, s));
+  }
+  if (depth && pairs) CK(cudaMemcpyAsync(depth, st->depth, 4 * (size_t)pairs, cudaMemcpyDeviceToHost, s));
+  std::vector<short4> r;
+  if (rect) {
+    r.resize((size_t)pairs);
+    if (pairs) CK(cudaMemcpyAsync(r.data(), st->rect, sizeof(short4) * (size_t)pairs, cudaMemcpyDeviceToHost, s));
+  }
+  if (T_final) CK(cudaMemcpyAsync(T_final, st->T_final, 4 * (size_t)st->n_pix, cudaMemcpyDeviceToHost, s));
+  if (n_contrib) CK(cudaMemcpyAsync(n_contrib, st->n_contrib, 4 * (size_t)st->n_pix, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (ids)
+    for (int64_t k = 0; k < K; ++k) ids[k] = (uint32_t)(inst[(size_t)k] & 0xffffffffu);
+  if (rect)
+    for (int64_t k = 0; k < pairs; ++k) {
+      rect[4 * k + 0] = r[(size_t)k].x;
+      rect[4 * k + 1] = r[(size_t)k].y;
+      rect[4 * k + 2] = r[(size_t)k].z;
+      rect[4 * k + 3] = r[(size_t)k].w;
+    }
+  return DCG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Kernel launchers of the dcg library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/dcg.h"
+
+namespace dcg {
+
+typedef unsigned long long u64;
+
+constexpr int kMaxViewsApi = 16;  // views per render call
+
+// Phases timed by the optional profiler (dcg_profile); same order as in dcg.h.
+enum Phase { PH_CULL = 0, PH_GATHER, PH_PRE_FWD, PH_BINNING, PH_BLEND_FWD, PH_LOSS, PH_BLEND_BWD, PH_PRE_BWD,
+             PH_SCATTER, PH_COUNT };
+
+// Kernel launches issued by the library in this process (for launch accounting).
+extern unsigned long long g_launches;
+inline void count_launch(unsigned long long k = 1) { g_launches += k; }
+
+struct ProfHook {
+  void* h = nullptr;
+  void (*mark)(void* h, int phase, bool begin, cudaStream_t s) = nullptr;
+  void operator()(int phase, bool begin, cudaStream_t s) const {
+    if (mark) mark(h, phase, begin, s);
+  }
+};
+
+// device error word bits
+constexpr unsigned ERRW_KEY_RANGE_BIT = 1u;
+constexpr unsigned ERRW_CAPACITY_BIT = 2u;
+constexpr unsigned ERRW_TIMEOUT_BIT = 4u;
+
+// ---------------------------------------------------------------- chunk.cu
+void launch_chunk_keys(const float* means, long long row, long long col, long long n, float s, u64* keys,
+                       unsigned* errword, int num_sms, cudaStream_t st);
+void launch_cull(const int32_t* coords, int C, const dcg_camera* cams, int V, float s, float dfar, uint8_t* mask,
+                 uint8_t* vis, int32_t* list, int32_t* n, cudaStream_t st);
+void launch_page_copy(bool gather, float* pool, long long page_g, int F, const long long* desc, int nd,
+                      float* active, long long stride, cudaStream_t st);
+
+// ---------------------------------------------------------------- raster
+// Per-view camera constants (built on the host from dcg_camera).
+struct DevCam {
+  float fx, fy, cx, cy;
+  float R[9];
+  float t[3];
+  float C[3];   // camera centre -R^T t
+  float znear, zfar;
+  float xlo, xhi, ylo, yhi;  // clamp of x/z and y/z inside the Jacobian
+  int W, H;
+  int ntx, nty;     // tiles along x / y
+  int tile_base;    // global index of tile (0,0) of this view
+  int pad;
+  long long pix_off;  // pixel offset of this view in the stacked outputs
+};
+
+struct DevCounters {
+  u64 n_vis;    // visible (view, Gaussian) pairs
+  u64 n_inst;   // instances requested (> capacity means overflow)
+  u64 n_inst_c; // instances kept (min with capacity)
+  u64 n_eval;   // pixel-Gaussian evaluations of the forward blend
+  unsigned tile_queue;
+  unsigned tile_queue_bwd;
+  unsigned pad[8];
+};
+
+struct RasterArgs {
+  // inputs
+  const float* g;      // planar Gaussians
+  long long stride;
+  long long n;
+  int deg;
+  int V;
+  const DevCam* cams;
+  int tile_w, tile_h, stage;
+  int n_tiles;
+  long long n_pix;
+  int idx_bits;        // bits of the Gaussian index in the depth keys
+  int view_bits;
+  // per (view, Gaussian) pair: index v * n + i
+  float4* rec;
+  float* depth;
+  uint32_t* touched;
+  short4* rect;
+  float4* grad2d;
+  // lists
+  u64* list_a;
+  u64* list_b;
+  u64* inst_a;
+  u64* inst_b;
+  long long cap_pairs, cap_inst;
+  uint2* ranges;
+  float* T_final;
+  uint32_t* n_contrib;
+  DevCounters* counters;
+  u64* part;
+  uint32_t* hist;
+  int P;
+  unsigned* errword;
+  int num_sms;
+  ProfHook prof;
+};
+
+// Runs preprocess, depth sort, instance emission, tile sort and ranges; then
+// the forward blend.  Returns the sorted instance buffer via *inst_sorted.
+void raster_forward(RasterArgs& a, float* rgb, float* depth_out, u64** list_sorted, u64** inst_sorted,
+                    cudaStream_t st);
+void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb, const float* dL_ddepth,
+                     float* grads, long long g_stride, float* dL_dpose, cudaStream_t st);
+
+// ---------------------------------------------------------------- loss
+void launch_loss_l1(const float* rgb, const float* depth, const float* trgb, const float* tdepth, const DevCam* cams,
+                    int V, long long n_pix, float lam, float* dr, float* dd, float* loss, int num_sms,
+                    cudaStream_t st);
+
+}  // namespace dcg

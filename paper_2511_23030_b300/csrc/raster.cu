@@ -1,0 +1,1007 @@
+// Differentiable tile rasteriser of RGB and depth for the active Gaussians of
+// one or several views (Sec. III-E: the visible subset is rasterised and the
+// loss of Eq. 2-4 is back-propagated), written for sm_103a.
+//
+// Forward per render call:
+//   1. k_preprocess_fwd   one thread per Gaussian, all views: parameters are
+//                         read once per call; per (view, Gaussian) pair the
+//                         projection, 2D conic, 3-sigma tile rectangle and SH
+//                         colour are written as one 48-byte record.
+//   2. compaction         ordered scan over pairs -> keys (view, depth, index)
+//   3. depth sort         stable LSD radix sort on (view, depth bits)
+//   4. instance emission  ordered scan of tiles-touched in depth order; each
+//                         instance is (global tile id, pair index)
+//   5. tile sort          stable LSD radix sort on the tile id only: the depth
+//                         order inside a tile survives from step 3
+//   6. ranges             [start, end) per tile
+//   7. k_blend_fwd        persistent blocks take tiles from a device queue,
+//                         stage records in shared memory, blend front to back
+// Backward:
+//   8. k_blend_bwd        reverse traversal from each pixel's last contributor,
+//                         transmittance recomputed by division, per-Gaussian
+//                         2D gradients reduced per warp (transposed butterfly),
+//                         per block in shared memory, then vector atomics
+//   9. k_preprocess_bwd   one thread per Gaussian, all views: chain rule to the
+//                         parameters (written once) and the pose twist of each view
+#include <cstdio>
+
+#include "device_scan.cuh"
+#include "kernels.cuh"
+
+namespace dcg {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kPMin = -4.5f * 1.4426950408889634f;  // q <= 9  <=>  p = -(q/2) log2(e) >= -4.5 log2(e)
+constexpr float kDilate = 0.3f;
+
+// Real spherical harmonics with Condon-Shortley phase as polynomials of the
+// unit direction (x, y, z); constants are K_l^m (times sqrt2 for m != 0) of
+// the normalised Legendre form, written out in closed form.
+#define SH_C0 0.28209479177387814f   /* 1 / (2 sqrt(pi)) */
+#define SH_C1 0.48860251190291992f   /* sqrt(3 / (4 pi)) */
+#define SH_C2A 1.0925484305920792f   /* sqrt(15 / pi) / 2 */
+#define SH_C2B 0.31539156525252005f  /* sqrt(5 / pi) / 4 */
+#define SH_C2C 0.54627421529603959f  /* sqrt(15 / pi) / 4 */
+#define SH_C3A -0.59004358992664352f /* -sqrt(35 / (2 pi)) / 4 */
+#define SH_C3B 2.8906114426405538f   /* sqrt(105 / pi) / 2 */
+#define SH_C3C -0.45704579946446572f /* -sqrt(21 / (2 pi)) / 4 */
+#define SH_C3D 0.37317633259011540f  /* sqrt(7 / pi) / 4 */
+#define SH_C3E 1.4453057213202769f   /* sqrt(105 / pi) / 4 */
+
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float* Y) {
+  Y[0] = SH_C0;
+  if (deg < 1) return;
+  Y[1] = -SH_C1 * y;
+  Y[2] = SH_C1 * z;
+  Y[3] = -SH_C1 * x;
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, yz = y * z, xz = x * z;
+  Y[4] = SH_C2A * xy;
+  Y[5] = -SH_C2A * yz;
+  Y[6] = SH_C2B * (2.f * zz - xx - yy);
+  Y[7] = -SH_C2A * xz;
+  Y[8] = SH_C2C * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = SH_C3A * y * (3.f * xx - yy);
+  Y[10] = SH_C3B * xy * z;
+  Y[11] = SH_C3C * y * (4.f * zz - xx - yy);
+  Y[12] = SH_C3D * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = SH_C3C * x * (4.f * zz - xx - yy);
+  Y[14] = SH_C3E * z * (xx - yy);
+  Y[15] = SH_C3A * x * (xx - 3.f * yy);
+}
+
+// Gradient (in R^3) of the basis polynomials above, accumulated as
+// g += w_k * grad Y_k for weights w[k].
+__device__ __forceinline__ void sh_grad_acc(int deg, float x, float y, float z, const float* w, float* g) {
+  if (deg < 1) return;
+  g[0] += -SH_C1 * w[3];
+  g[1] += -SH_C1 * w[1];
+  g[2] += SH_C1 * w[2];
+  if (deg < 2) return;
+  g[0] += SH_C2A * y * w[4] - 2.f * SH_C2B * x * w[6] - SH_C2A * z * w[7] + 2.f * SH_C2C * x * w[8];
+  g[1] += SH_C2A * x * w[4] - SH_C2A * z * w[5] - 2.f * SH_C2B * y * w[6] - 2.f * SH_C2C * y * w[8];
+  g[2] += -SH_C2A * y * w[5] + 4.f * SH_C2B * z * w[6] - SH_C2A * x * w[7];
+  if (deg < 3) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  g[0] += 6.f * SH_C3A * x * y * w[9] + SH_C3B * y * z * w[10] - 2.f * SH_C3C * x * y * w[11] -
+          6.f * SH_C3D * x * z * w[12] + SH_C3C * (4.f * zz - 3.f * xx - yy) * w[13] + 2.f * SH_C3E * x * z * w[14] +
+          3.f * SH_C3A * (xx - yy) * w[15];
+  g[1] += 3.f * SH_C3A * (xx - yy) * w[9] + SH_C3B * x * z * w[10] + SH_C3C * (4.f * zz - xx - 3.f * yy) * w[11] -
+          6.f * SH_C3D * y * z * w[12] - 2.f * SH_C3C * x * y * w[13] - 2.f * SH_C3E * y * z * w[14] -
+          6.f * SH_C3A * x * y * w[15];
+  g[2] += SH_C3B * x * y * w[10] + 8.f * SH_C3C * y * z * w[11] + SH_C3D * (6.f * zz - 3.f * xx - 3.f * yy) * w[12] +
+          8.f * SH_C3C * x * z * w[13] + SH_C3E * (xx - yy) * w[14];
+}
+
+// ----------------------------------------------------------------------------
+// Double-float (hi + lo) arithmetic from error-free transformations, used for
+// the projected centre so that pixel offsets keep ~1e-7 relative precision at
+// any image coordinate.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+// (r0 m0 + r1 m1 + r2 m2) + t
+__device__ __forceinline__ DF df_affine(float r0, float r1, float r2, float m0, float m1, float m2, float t) {
+  const DF p0 = two_prod(r0, m0), p1 = two_prod(r1, m1), p2 = two_prod(r2, m2);
+  DF s = two_sum(p0.hi, p1.hi);
+  float lo = __fadd_rn(s.lo, __fadd_rn(p0.lo, p1.lo));
+  DF s2 = two_sum(s.hi, p2.hi);
+  lo = __fadd_rn(lo, __fadd_rn(s2.lo, p2.lo));
+  DF s3 = two_sum(s2.hi, t);
+  lo = __fadd_rn(lo, s3.lo);
+  return quick_two_sum(s3.hi, lo);
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const DF p = two_prod(q1, b.hi);
+  const float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), a.lo), __fmul_rn(q1, b.lo));
+  return quick_two_sum(q1, __fdiv_rn(r, b.hi));
+}
+// f * x + c
+__device__ __forceinline__ DF df_scale_add(float f, DF x, float c) {
+  const DF p = two_prod(f, x.hi);
+  float lo = __fadd_rn(p.lo, __fmul_rn(f, x.lo));
+  const DF s = two_sum(p.hi, c);
+  lo = __fadd_rn(lo, s.lo);
+  return quick_two_sum(s.hi, lo);
+}
+// (hi + lo) - x0 rounded once to float
+__device__ __forceinline__ float df_sub_round(float hi, float lo, float x0) {
+  const DF d = two_sum(hi, -x0);
+  return __fadd_rn(d.hi, __fadd_rn(d.lo, lo));
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// The blend decision shared bit-for-bit by the forward and backward kernels.
+// sx = dx * (A' dx), bx = B' dx are per Gaussian and pixel column.
+__device__ __forceinline__ float blend_power(float sx, float bx, float Cp, float dy) {
+  return __fmaf_rn(dy, __fmaf_rn(Cp, dy, bx), sx);
+}
+
+// FP32 camera depth in the fixed order ((R20 mx + R21 my) + R22 mz) + t2.
+__device__ __forceinline__ float cam_depth(const DevCam& c, float mx, float my, float mz) {
+  return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.R[6], mx), __fmul_rn(c.R[7], my)), __fmul_rn(c.R[8], mz)), c.t[2]);
+}
+
+// Rotation of the normalised quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float* R) {
+  R[0] = 1.f - 2.f * (y * y + z * z);
+  R[1] = 2.f * (x * y - w * z);
+  R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);
+  R[4] = 1.f - 2.f * (x * x + z * z);
+  R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);
+  R[7] = 2.f * (y * z + w * x);
+  R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// ============================================================================
+// 1. preprocess
+// ============================================================================
+__global__ void __launch_bounds__(256) k_preprocess_fwd(RasterArgs a) {
+  const long long n = a.n;
+  const int D = (a.deg + 1) * (a.deg + 1);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float* g = a.g;
+    const long long S = a.stride;
+    const float mx = g[0 * S + i], my = g[1 * S + i], mz = g[2 * S + i];
+    // 3D covariance Sigma = M M^T, M = R(q) diag(exp(log s))
+    const float s0 = __expf(g[3 * S + i]), s1 = __expf(g[4 * S + i]), s2 = __expf(g[5 * S + i]);
+    float qw = g[6 * S + i], qx = g[7 * S + i], qy = g[8 * S + i], qz = g[9 * S + i];
+    const float qinv = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= qinv; qx *= qinv; qy *= qinv; qz *= qinv;
+    float R[9];
+    quat_rot(qw, qx, qy, qz, R);
+    const float M[9] = {R[0] * s0, R[1] * s1, R[2] * s2, R[3] * s0, R[4] * s1, R[5] * s2, R[6] * s0, R[7] * s1, R[8] * s2};
+    const float S00 = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    const float S01 = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    const float S02 = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    const float S11 = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    const float S12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    const float S22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    const float opac = 1.f / (1.f + __expf(-g[10 * S + i]));
+    for (int v = 0; v < a.V; ++v) {
+      const long long vi = (long long)v * n + i;
+      const DevCam& c = a.cams[v];
+      const float z = cam_depth(c, mx, my, mz);
+      a.depth[vi] = z;
+      if (!(z > c.znear)) {
+        a.touched[vi] = 0;
+        a.rect[vi] = make_short4(0, 0, -1, -1);
+        continue;
+      }
+      // projected centre in double-float
+      const DF txd = df_affine(c.R[0], c.R[1], c.R[2], mx, my, mz, c.t[0]);
+      const DF tyd = df_affine(c.R[3], c.R[4], c.R[5], mx, my, mz, c.t[1]);
+      const DF tzd = df_affine(c.R[6], c.R[7], c.R[8], mx, my, mz, c.t[2]);
+      const DF ud = df_scale_add(c.fx, df_div(txd, tzd), c.cx);
+      const DF vd = df_scale_add(c.fy, df_div(tyd, tzd), c.cy);
+      // Jacobian of the perspective map with x/z, y/z clamped
+      const float iz = 1.f / z;
+      const float rx = fminf(fmaxf(txd.hi * iz, c.xlo), c.xhi);
+      const float ry = fminf(fmaxf(tyd.hi * iz, c.ylo), c.yhi);
+      const float jx = c.fx * iz, jy = c.fy * iz;
+      // Tm = J W: rows (fx/z)(W0 - rx W2), (fy/z)(W1 - ry W2)
+      const float T0x = jx * (c.R[0] - rx * c.R[6]), T0y = jx * (c.R[1] - rx * c.R[7]), T0z = jx * (c.R[2] - rx * c.R[8]);
+      const float T1x = jy * (c.R[3] - ry * c.R[6]), T1y = jy * (c.R[4] - ry * c.R[7]), T1z = jy * (c.R[5] - ry * c.R[8]);
+      const float u0 = S00 * T0x + S01 * T0y + S02 * T0z;
+      const float u1 = S01 * T0x + S11 * T0y + S12 * T0z;
+      const float u2 = S02 * T0x + S12 * T0y + S22 * T0z;
+      const float ca = T0x * u0 + T0y * u1 + T0z * u2 + kDilate;
+      const float cb = T1x * u0 + T1y * u1 + T1z * u2;
+      const float w0 = S00 * T1x + S01 * T1y + S02 * T1z;
+      const float w1 = S01 * T1x + S11 * T1y + S12 * T1z;
+      const float w2 = S02 * T1x + S12 * T1y + S22 * T1z;
+      const float cc = T1x * w0 + T1y * w1 + T1z * w2 + kDilate;
+      const float det = ca * cc - cb * cb;
+      // exact bounding box of q <= 9, rounded outwards to whole pixels
+      const float ex = 3.f * sqrtf(ca), ey = 3.f * sqrtf(cc);
+      const float px0 = fmaxf(floorf(__fsub_rn(ud.hi, ex)), 0.f);
+      const float px1 = fminf(ceilf(__fadd_rn(ud.hi, ex)), (float)(c.W - 1));
+      const float py0 = fmaxf(floorf(__fsub_rn(vd.hi, ey)), 0.f);
+      const float py1 = fminf(ceilf(__fadd_rn(vd.hi, ey)), (float)(c.H - 1));
+      if (!(det > 0.f) || !(px0 <= px1) || !(py0 <= py1)) {
+        a.touched[vi] = 0;
+        a.rect[vi] = make_short4(0, 0, -1, -1);
+        continue;
+      }
+      const int tx0 = (int)px0 / a.tile_w, tx1 = (int)px1 / a.tile_w;
+      const int ty0 = (int)py0 / a.tile_h, ty1 = (int)py1 / a.tile_h;
+      a.touched[vi] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+      a.rect[vi] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
+      const float idet = 1.f / det;
+      const float A = cc * idet, B = -cb * idet, Cn = ca * idet;
+      // colour: SH of the direction from the camera centre
+      float dx = mx - c.C[0], dy = my - c.C[1], dz = mz - c.C[2];
+      const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+      dx *= il; dy *= il; dz *= il;
+      float Y[16];
+      sh_basis(a.deg, dx, dy, dz, Y);
+      float col[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.f;
+        for (int k = 0; k < D; ++k) acc += g[(11 + 3 * k + ch) * S + i] * Y[k];
+        col[ch] = fmaxf(acc + 0.5f, 0.f);
+      }
+      a.rec[3 * vi + 0] = make_float4(ud.hi, vd.hi, ud.lo, vd.lo);
+      a.rec[3 * vi + 1] = make_float4(-0.5f * kLog2e * A, -kLog2e * B, -0.5f * kLog2e * Cn, opac);
+      a.rec[3 * vi + 2] = make_float4(col[0], col[1], col[2], z);
+      a.grad2d[3 * vi + 0] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.grad2d[3 * vi + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.grad2d[3 * vi + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// ============================================================================
+// 2-6. binning
+// ============================================================================
+struct VisCount {
+  const uint32_t* touched;
+  __device__ u64 operator()(u64 k) const { return touched[k] ? 1ull : 0ull; }
+};
+struct VisEmit {
+  const float* depth;
+  u64* list;
+  long long n;
+  int ib;
+  __device__ void operator()(u64 k, u64 off, u64) const {
+    const u64 v = k / (u64)n, i = k - v * (u64)n;
+    list[off] = (v << (31 + ib)) | ((u64)__float_as_uint(depth[k]) << ib) | i;
+  }
+};
+__device__ __forceinline__ u64 pair_of_key(u64 key, int ib, long long n) {
+  const u64 v = key >> (31 + ib);
+  const u64 i = key & ((1ull << ib) - 1);
+  return v * (u64)n + i;
+}
+struct InstCount {
+  const u64* list;
+  const uint32_t* touched;
+  long long n;
+  int ib;
+  __device__ u64 operator()(u64 s) const { return touched[pair_of_key(list[s], ib, n)]; }
+};
+struct InstEmit {
+  const u64* list;
+  const short4* rect;
+  const DevCam* cams;
+  long long n;
+  int ib;
+  u64* inst;
+  u64 cap;
+  __device__ void operator()(u64 s, u64 off, u64) const {
+    const u64 key = list[s];
+    const u64 vi = pair_of_key(key, ib, n);
+    const int v = (int)(key >> (31 + ib));
+    const short4 r = rect[vi];
+    const u64 base = (u64)cams[v].tile_base;
+    const int ntx = cams[v].ntx;
+    u64 o = off;
+    for (int ty = r.y; ty <= r.w; ++ty)
+      for (int tx = r.x; tx <= r.z; ++tx, ++o)
+        if (o < cap) inst[o] = ((base + (u64)ty * ntx + tx) << 32) | vi;
+  }
+};
+
+__global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
+  const u64 k = c->n_inst;
+  c->n_inst_c = k < cap ? k : cap;
+  if (k > cap) atomicOr(errword, ERRW_CAPACITY_BIT);
+}
+
+__global__ void k_ranges(const u64* __restrict__ inst, const u64* n_ptr, uint2* __restrict__ ranges) {
+  const u64 K = *n_ptr;
+  for (u64 k = blockIdx.x * (u64)blockDim.x + threadIdx.x; k < K; k += (u64)gridDim.x * blockDim.x) {
+    const unsigned t = (unsigned)(inst[k] >> 32);
+    if (k == 0 || (unsigned)(inst[k - 1] >> 32) != t) ranges[t].x = (unsigned)k;
+    if (k + 1 == K || (unsigned)(inst[k + 1] >> 32) != t) ranges[t].y = (unsigned)(k + 1);
+  }
+}
+
+// ============================================================================
+// 7. forward blend
+// ============================================================================
+__device__ __forceinline__ int view_of_tile(const DevCam* cams, int V, unsigned gt) {
+  int v = 0;
+  while (v + 1 < V && (int)gt >= cams[v + 1].tile_base) ++v;
+  return v;
+}
+
+template <int TW, int TH, int STAGE>
+__global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __restrict__ inst, float* __restrict__ rgb,
+                                                   float* __restrict__ dout) {
+  constexpr int ROWS = 256 / TW;
+  constexpr int PPT = TH / ROWS;
+  __shared__ float2 s_xy[STAGE];
+  __shared__ float4 s_con[STAGE];
+  __shared__ float4 s_col[STAGE];
+  __shared__ unsigned s_tile;
+  const int tid = threadIdx.x;
+  const int lx = tid % TW, ly = tid / TW;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_tile = atomicAdd(&a.counters->tile_queue, 1u);
+    __syncthreads();
+    const unsigned gt = s_tile;
+    if (gt >= (unsigned)a.n_tiles) break;
+    const int v = view_of_tile(a.cams, a.V, gt);
+    const DevCam& c = a.cams[v];
+    const int W = c.W, H = c.H;
+    const int local = (int)gt - c.tile_base;
+    const int ty = local / c.ntx, tx = local - ty * c.ntx;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const float x0f = (float)x0, y0f = (float)y0;
+    float T[PPT], Tf[PPT], Cr[PPT], Cg[PPT], Cb[PPT], Dz[PPT];
+    uint32_t last[PPT], stop[PPT];
+    const int px = x0 + lx;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int py = y0 + ly + k * ROWS;
+      T[k] = (px < W && py < H) ? 1.f : 0.f;
+      Tf[k] = T[k];
+      Cr[k] = Cg[k] = Cb[k] = Dz[k] = 0.f;
+      last[k] = 0;
+      stop[k] = 0;
+    }
+    const uint2 rg = a.ranges[gt];
+    for (unsigned b0 = rg.x; b0 < rg.y; b0 += STAGE) {
+      int alive = 0;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) alive |= (T[k] > 0.f);
+      if (__syncthreads_count(alive) == 0) break;
+      for (int j = tid; j < STAGE; j += 256) {
+        const unsigned idx = b0 + j;
+        if (idx < rg.y) {
+          const unsigned vi = (unsigned)inst[idx];
+          const float4 r0 = a.rec[3ull * vi + 0];
+          s_xy[j] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+          s_con[j] = a.rec[3ull * vi + 1];
+          s_col[j] = a.rec[3ull * vi + 2];
+        }
+      }
+      __syncthreads();
+      const int cnt = min(STAGE, (int)(rg.y - b0));
+      if (__any_sync(0xffffffffu, alive)) {
+        for (int j = 0; j < cnt; ++j) {
+          const float2 xy = s_xy[j];
+          const float4 cn = s_con[j];
+          const float dx = __fsub_rn((float)lx, xy.x);
+          const float sx = __fmul_rn(dx, __fmul_rn(cn.x, dx));
+          const float bx = __fmul_rn(cn.y, dx);
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const float dy = __fsub_rn((float)(ly + k * ROWS), xy.y);
+            const float p = blend_power(sx, bx, cn.z, dy);
+            if (T[k] > 0.f && p >= kPMin) {
+              const float al = fminf(kAlphaMax, __fmul_rn(cn.w, ex2_approx(p)));
+              if (al >= kAlphaMin) {
+                const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, al));
+                if (Tn < kTMin) {
+                  Tf[k] = T[k];
+                  T[k] = 0.f;
+                  stop[k] = b0 - rg.x + j + 1;
+                } else {
+                  const float4 cl = s_col[j];
+                  const float w = al * T[k];
+                  Cr[k] += w * cl.x;
+                  Cg[k] += w * cl.y;
+                  Cb[k] += w * cl.z;
+                  Dz[k] += w * cl.w;
+                  T[k] = Tn;
+                  last[k] = b0 - rg.x + j + 1;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    unsigned long long ev = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) ev += T[k] > 0.f ? (rg.y - rg.x) : stop[k];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    if ((tid & 31) == 0 && ev) atomicAdd(&a.counters->n_eval, ev);
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int py = y0 + ly + k * ROWS;
+      if (px < W && py < H) {
+        const long long P = (long long)W * H;
+        const long long pix = (long long)py * W + px;
+        rgb[3 * c.pix_off + pix] = Cr[k];
+        rgb[3 * c.pix_off + P + pix] = Cg[k];
+        rgb[3 * c.pix_off + 2 * P + pix] = Cb[k];
+        dout[c.pix_off + pix] = Dz[k];
+        a.T_final[c.pix_off + pix] = T[k] > 0.f ? T[k] : Tf[k];
+        a.n_contrib[c.pix_off + pix] = last[k];
+      }
+    }
+  }
+}
+
+// ============================================================================
+// 8. backward blend
+// ============================================================================
+// Sum over the 32 lanes of N values with a transposed butterfly: after the
+// call lane l holds the total of component *comp (valid iff *has), each
+// component owned by one even lane.  ceil(N/2)+... shuffles instead of 5N.
+template <int N>
+__device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int* comp, bool* has) {
+  const unsigned lane = threadIdx.x & 31u;
+  int base = 0, cnt = N;
+  int n = N;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool bit = (lane & (unsigned)o) != 0u;
+    if (n > 1) {
+      const int half = (n + 1) / 2;
+#pragma unroll
+      for (int k = 0; k < (N + 1) / 2; ++k) {
+        if (k < half) {
+          const float hi = (k + half < n) ? v[k + half] : 0.f;
+          const float send = bit ? v[k] : hi;
+          const float keep = bit ? hi : v[k];
+          v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      if (bit) {
+        base += half;
+        cnt = cnt > half ? cnt - half : 0;
+      } else {
+        cnt = cnt < half ? cnt : half;
+      }
+      n = half;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    }
+  }
+  *comp = base;
+  *has = cnt > 0 && (lane & 1u) == 0u;
+  return v[0];
+}
+
+template <int TW, int TH, int STAGE>
+__global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __restrict__ inst,
+                                                   const float* __restrict__ dL_drgb,
+                                                   const float* __restrict__ dL_ddepth) {
+  constexpr int ROWS = 256 / TW;
+  constexpr int PPT = TH / ROWS;
+  __shared__ float2 s_xy[STAGE];
+  __shared__ float4 s_con[STAGE];
+  __shared__ float4 s_col[STAGE];
+  __shared__ unsigned s_vi[STAGE];
+  __shared__ float s_acc[STAGE][10];
+  __shared__ unsigned s_tile;
+  __shared__ unsigned s_maxlast;
+  const int tid = threadIdx.x;
+  const int lx = tid % TW, ly = tid / TW;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      s_tile = atomicAdd(&a.counters->tile_queue_bwd, 1u);
+      s_maxlast = 0;
+    }
+    __syncthreads();
+    const unsigned gt = s_tile;
+    if (gt >= (unsigned)a.n_tiles) break;
+    const int v = view_of_tile(a.cams, a.V, gt);
+    const DevCam& c = a.cams[v];
+    const int W = c.W, H = c.H;
+    const int local = (int)gt - c.tile_base;
+    const int ty = local / c.ntx, tx = local - ty * c.ntx;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const float x0f = (float)x0, y0f = (float)y0;
+    const long long P = (long long)W * H;
+    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Sr[PPT], Sg[PPT], Sb[PPT], Sd[PPT];
+    uint32_t last[PPT];
+    const int px = x0 + lx;
+    uint32_t mylast = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int py = y0 + ly + k * ROWS;
+      last[k] = 0;
+      T[k] = 0.f;
+      gr[k] = gg[k] = gb[k] = gd[k] = 0.f;
+      if (px < W && py < H) {
+        const long long pix = (long long)py * W + px;
+        T[k] = a.T_final[c.pix_off + pix];
+        last[k] = a.n_contrib[c.pix_off + pix];
+        gr[k] = dL_drgb[3 * c.pix_off + pix];
+        gg[k] = dL_drgb[3 * c.pix_off + P + pix];
+        gb[k] = dL_drgb[3 * c.pix_off + 2 * P + pix];
+        gd[k] = dL_ddepth[c.pix_off + pix];
+      }
+      Sr[k] = Sg[k] = Sb[k] = Sd[k] = 0.f;
+      mylast = max(mylast, last[k]);
+    }
+    // block maximum of the last contributor
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mylast = max(mylast, __shfl_xor_sync(0xffffffffu, mylast, o));
+    if ((tid & 31) == 0) atomicMax(&s_maxlast, mylast);
+    __syncthreads();
+    const int maxlast = (int)s_maxlast;
+    const uint2 rg = a.ranges[gt];
+    for (int bend = maxlast; bend > 0; bend -= STAGE) {
+      const int bstart = max(0, bend - STAGE);
+      const int cnt = bend - bstart;
+      for (int j = tid; j < cnt; j += 256) {
+        const unsigned vi = (unsigned)inst[rg.x + bstart + j];
+        const float4 r0 = a.rec[3ull * vi + 0];
+        s_xy[j] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+        s_con[j] = a.rec[3ull * vi + 1];
+        s_col[j] = a.rec[3ull * vi + 2];
+        s_vi[j] = vi;
+      }
+      for (int e = tid; e < cnt * 10; e += 256) (&s_acc[0][0])[e] = 0.f;
+      __syncthreads();
+      for (int j = cnt - 1; j >= 0; --j) {
+        const int rel = bstart + j;
+        const float2 xy = s_xy[j];
+        const float4 cn = s_con[j];
+        const float dx = __fsub_rn((float)lx, xy.x);
+        const float sx = __fmul_rn(dx, __fmul_rn(cn.x, dx));
+        const float bx = __fmul_rn(cn.y, dx);
+        float acc[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) acc[q] = 0.f;
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (rel < (int)last[k]) {
+            const float dy = __fsub_rn((float)(ly + k * ROWS), xy.y);
+            const float p = blend_power(sx, bx, cn.z, dy);
+            if (p >= kPMin) {
+              const float G = ex2_approx(p);
+              const float araw = __fmul_rn(cn.w, G);
+              const float al = fminf(kAlphaMax, araw);
+              if (al >= kAlphaMin) {
+                any = true;
+                const float4 cl = s_col[j];
+                T[k] = __fdividef(T[k], 1.f - al);
+                const float w = al * T[k];
+                acc[6] += w * gr[k];
+                acc[7] += w * gg[k];
+                acc[8] += w * gb[k];
+                acc[9] += w * gd[k];
+                const float dal =
+                    T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] + (cl.w - Sd[k]) * gd[k]);
+                Sr[k] = al * cl.x + (1.f - al) * Sr[k];
+                Sg[k] = al * cl.y + (1.f - al) * Sg[k];
+                Sb[k] = al * cl.z + (1.f - al) * Sb[k];
+                Sd[k] = al * cl.w + (1.f - al) * Sd[k];
+                if (araw < kAlphaMax) {
+                  acc[5] += dal * G;
+                  const float dp = dal * cn.w * G * kLn2;
+                  acc[2] += dp * dx * dx;
+                  acc[3] += dp * dx * dy;
+                  acc[4] += dp * dy * dy;
+                  acc[0] -= dp * (2.f * cn.x * dx + cn.y * dy);
+                  acc[1] -= dp * (cn.y * dx + 2.f * cn.z * dy);
+                }
+              }
+            }
+          }
+        }
+        if (__any_sync(0xffffffffu, any)) {
+          int comp;
+          bool has;
+          const float tot = warp_sum_transpose<10>(acc, &comp, &has);
+          if (has) atomicAdd(&s_acc[j][comp], tot);
+        }
+      }
+      __syncthreads();
+      for (int j = tid; j < cnt; j += 256) {
+        const float* q = s_acc[j];
+        float4* gp = a.grad2d + 3ull * s_vi[j];
+        const float4 g0 = make_float4(q[0], q[1], q[2], q[3]);
+        const float4 g1 = make_float4(q[4], q[5], q[6], q[7]);
+        if (g0.x != 0.f || g0.y != 0.f || g0.z != 0.f || g0.w != 0.f) atomicAdd(gp + 0, g0);
+        if (g1.x != 0.f || g1.y != 0.f || g1.z != 0.f || g1.w != 0.f) atomicAdd(gp + 1, g1);
+        if (q[8] != 0.f || q[9] != 0.f) atomicAdd(reinterpret_cast<float2*>(gp + 2), make_float2(q[8], q[9]));
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ============================================================================
+// 9. preprocess backward
+// ============================================================================
+__global__ void __launch_bounds__(256) k_preprocess_bwd(RasterArgs a, float* __restrict__ out, long long ostride,
+                                                        float* __restrict__ dpose) {
+  const long long n = a.n;
+  const int D = (a.deg + 1) * (a.deg + 1);
+  const int F = 11 + 3 * D;
+  const long long S = a.stride;
+  // one pass over all threads of the grid; lanes past n still join the warp reductions
+  const long long n_round = ((n + 31) / 32) * 32;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_round; i += (long long)gridDim.x * blockDim.x) {
+    const bool live = i < n;
+    const float* g = a.g;
+    float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.f;
+    float gsh[48];
+#pragma unroll
+    for (int k = 0; k < 48; ++k) gsh[k] = 0.f;
+    float mx = 0, my = 0, mz = 0, sc[3] = {1, 1, 1}, qn[4] = {1, 0, 0, 0}, qlen = 1.f, R[9], M[9], opac = 0.5f;
+    float S00 = 0, S01 = 0, S02 = 0, S11 = 0, S12 = 0, S22 = 0;
+    if (live) {
+      mx = g[0 * S + i]; my = g[1 * S + i]; mz = g[2 * S + i];
+      sc[0] = __expf(g[3 * S + i]); sc[1] = __expf(g[4 * S + i]); sc[2] = __expf(g[5 * S + i]);
+      const float q0 = g[6 * S + i], q1 = g[7 * S + i], q2 = g[8 * S + i], q3 = g[9 * S + i];
+      qlen = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+      const float iq = 1.f / qlen;
+      qn[0] = q0 * iq; qn[1] = q1 * iq; qn[2] = q2 * iq; qn[3] = q3 * iq;
+      opac = 1.f / (1.f + __expf(-g[10 * S + i]));
+    }
+    quat_rot(qn[0], qn[1], qn[2], qn[3], R);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) M[3 * r + k] = R[3 * r + k] * sc[k];
+    S00 = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    S01 = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    S02 = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    S11 = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    S12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    S22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    float dSig[6] = {0, 0, 0, 0, 0, 0};  // dS + dS^T accumulated over views: entries 00 01 02 11 12 22
+    for (int v = 0; v < a.V; ++v) {
+      float pose[6] = {0, 0, 0, 0, 0, 0};
+      const long long vi = (long long)v * n + i;
+      bool act = live && a.touched[vi] != 0u;
+      float4 g0 = make_float4(0, 0, 0, 0), g1 = g0, g2 = g0;
+      if (act) {
+        g0 = a.grad2d[3 * vi + 0];
+        g1 = a.grad2d[3 * vi + 1];
+        g2 = a.grad2d[3 * vi + 2];
+        act = (g0.x != 0.f) | (g0.y != 0.f) | (g0.z != 0.f) | (g0.w != 0.f) | (g1.x != 0.f) | (g1.y != 0.f) |
+              (g1.z != 0.f) | (g1.w != 0.f) | (g2.x != 0.f) | (g2.y != 0.f);
+      }
+      if (act) {
+        const DevCam& c = a.cams[v];
+        const float tx = c.R[0] * mx + c.R[1] * my + c.R[2] * mz + c.t[0];
+        const float ty = c.R[3] * mx + c.R[4] * my + c.R[5] * mz + c.t[1];
+        const float tz = cam_depth(c, mx, my, mz);
+        const float iz = 1.f / tz, iz2 = iz * iz;
+        const float rxu = tx * iz, ryu = ty * iz;
+        const bool clx = rxu < c.xlo || rxu > c.xhi, cly = ryu < c.ylo || ryu > c.yhi;
+        const float rx = fminf(fmaxf(rxu, c.xlo), c.xhi), ry = fminf(fmaxf(ryu, c.ylo), c.yhi);
+        const float J00 = c.fx * iz, J02 = -c.fx * rx * iz, J11 = c.fy * iz, J12 = -c.fy * ry * iz;
+        const float T0[3] = {J00 * c.R[0] + J02 * c.R[6], J00 * c.R[1] + J02 * c.R[7], J00 * c.R[2] + J02 * c.R[8]};
+        const float T1[3] = {J11 * c.R[3] + J12 * c.R[6], J11 * c.R[4] + J12 * c.R[7], J11 * c.R[5] + J12 * c.R[8]};
+        const float ST0[3] = {S00 * T0[0] + S01 * T0[1] + S02 * T0[2], S01 * T0[0] + S11 * T0[1] + S12 * T0[2],
+                              S02 * T0[0] + S12 * T0[1] + S22 * T0[2]};
+        const float ST1[3] = {S00 * T1[0] + S01 * T1[1] + S02 * T1[2], S01 * T1[0] + S11 * T1[1] + S12 * T1[2],
+                              S02 * T1[0] + S12 * T1[1] + S22 * T1[2]};
+        const float ca = T0[0] * ST0[0] + T0[1] * ST0[1] + T0[2] * ST0[2] + kDilate;
+        const float cb = T1[0] * ST0[0] + T1[1] * ST0[1] + T1[2] * ST0[2];
+        const float cc = T1[0] * ST1[0] + T1[1] * ST1[1] + T1[2] * ST1[2] + kDilate;
+        const float det = ca * cc - cb * cb;
+        const float id = 1.f / det, id2 = id * id;
+        // 2D gradients: du, dv, dA', dB', dC', do, dr, dg, db, dz
+        const float du = g0.x, dv = g0.y;
+        const float dA = g0.z * (-0.5f * kLog2e), dB = g0.w * (-kLog2e), dC = g1.x * (-0.5f * kLog2e);
+        const float dop = g1.y;
+        const float dcol[3] = {g1.z, g1.w, g2.x};
+        const float dzz = g2.y;
+        // conic = inverse of [[a, b], [b, c]]
+        const float da = dA * (-cc * cc * id2) + dB * (cb * cc * id2) + dC * (id - ca * cc * id2);
+        const float db = dA * (2.f * cb * cc * id2) + dB * (-id - 2.f * cb * cb * id2) + dC * (2.f * ca * cb * id2);
+        const float dc = dA * (id - cc * ca * id2) + dB * (cb * ca * id2) + dC * (-ca * ca * id2);
+        // Sigma gradient (symmetrised: G = dS + dS^T)
+        dSig[0] += 2.f * (da * T0[0] * T0[0] + db * T0[0] * T1[0] + dc * T1[0] * T1[0]);
+        dSig[1] += 2.f * da * T0[0] * T0[1] + db * (T0[0] * T1[1] + T1[0] * T0[1]) + 2.f * dc * T1[0] * T1[1];
+        dSig[2] += 2.f * da * T0[0] * T0[2] + db * (T0[0] * T1[2] + T1[0] * T0[2]) + 2.f * dc * T1[0] * T1[2];
+        dSig[3] += 2.f * (da * T0[1] * T0[1] + db * T0[1] * T1[1] + dc * T1[1] * T1[1]);
+        dSig[4] += 2.f * da * T0[1] * T0[2] + db * (T0[1] * T1[2] + T1[1] * T0[2]) + 2.f * dc * T1[1] * T1[2];
+        dSig[5] += 2.f * (da * T0[2] * T0[2] + db * T0[2] * T1[2] + dc * T1[2] * T1[2]);
+        // Tm gradient
+        float dT0[3], dT1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          dT0[k] = 2.f * da * ST0[k] + db * ST1[k];
+          dT1[k] = db * ST0[k] + 2.f * dc * ST1[k];
+        }
+        // Tm = J W -> dJ = dTm W^T ; dW = J^T dTm
+        const float dJ00 = dT0[0] * c.R[0] + dT0[1] * c.R[1] + dT0[2] * c.R[2];
+        const float dJ02 = dT0[0] * c.R[6] + dT0[1] * c.R[7] + dT0[2] * c.R[8];
+        const float dJ11 = dT1[0] * c.R[3] + dT1[1] * c.R[4] + dT1[2] * c.R[5];
+        const float dJ12 = dT1[0] * c.R[6] + dT1[1] * c.R[7] + dT1[2] * c.R[8];
+        float dt[3];
+        dt[0] = du * c.fx * iz;
+        dt[1] = dv * c.fy * iz;
+        dt[2] = -(du * c.fx * tx + dv * c.fy * ty) * iz2 + dzz;
+        dt[2] += -(dJ00 * c.fx + dJ11 * c.fy) * iz2;
+        if (!clx) {
+          dt[0] += -dJ02 * c.fx * iz2;
+          dt[2] += 2.f * dJ02 * c.fx * tx * iz2 * iz;
+        } else {
+          dt[2] += dJ02 * c.fx * rx * iz2;
+        }
+        if (!cly) {
+          dt[1] += -dJ12 * c.fy * iz2;
+          dt[2] += 2.f * dJ12 * c.fy * ty * iz2 * iz;
+        } else {
+          dt[2] += dJ12 * c.fy * ry * iz2;
+        }
+        // dW (rows k, cols j) = J[0][k] dT0[j] + J[1][k] dT1[j]; J = [[J00,0,J02],[0,J11,J12]]
+        float dW[9];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          dW[0 + j] = J00 * dT0[j];
+          dW[3 + j] = J11 * dT1[j];
+          dW[6 + j] = J02 * dT0[j] + J12 * dT1[j];
+        }
+        // opacity
+        go += dop * opac * (1.f - opac);
+        // colour
+        float dx = mx - c.C[0], dy = my - c.C[1], dz = mz - c.C[2];
+        const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+        const float il = 1.f / dist;
+        dx *= il; dy *= il; dz *= il;
+        float Y[16];
+        sh_basis(a.deg, dx, dy, dz, Y);
+        float wsum[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          float acc = 0.f;
+          for (int k = 0; k < D; ++k) acc += g[(11 + 3 * k + ch) * S + i] * Y[k];
+          if (acc + 0.5f < 0.f) continue;  // clamped channel
+          const float gc = dcol[ch];
+          for (int k = 0; k < D; ++k) {
+            gsh[3 * k + ch] += gc * Y[k];
+            wsum[k] += gc * g[(11 + 3 * k + ch) * S + i];
+          }
+        }
+        float gdir[3] = {0, 0, 0};
+        sh_grad_acc(a.deg, dx, dy, dz, wsum, gdir);
+        const float dd = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
+        const float gmu_sh[3] = {(gdir[0] - dx * dd) * il, (gdir[1] - dy * dd) * il, (gdir[2] - dz * dd) * il};
+        // mean: t = W mu + t_cw
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gm[k] += c.R[k] * dt[0] + c.R[3 + k] * dt[1] + c.R[6 + k] * dt[2] + gmu_sh[k];
+        // pose twist (v, w)
+        pose[0] = dt[0] + c.R[0] * gmu_sh[0] + c.R[1] * gmu_sh[1] + c.R[2] * gmu_sh[2];
+        pose[1] = dt[1] + c.R[3] * gmu_sh[0] + c.R[4] * gmu_sh[1] + c.R[5] * gmu_sh[2];
+        pose[2] = dt[2] + c.R[6] * gmu_sh[0] + c.R[7] * gmu_sh[1] + c.R[8] * gmu_sh[2];
+        pose[3] = ty * dt[2] - tz * dt[1];
+        pose[4] = tz * dt[0] - tx * dt[2];
+        pose[5] = tx * dt[1] - ty * dt[0];
+        // rotation inside Tm: Mr = W dW^T, dw = (Mr12 - Mr21, Mr20 - Mr02, Mr01 - Mr10)
+        float Mr[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            Mr[3 * r + q] = c.R[3 * r + 0] * dW[3 * q + 0] + c.R[3 * r + 1] * dW[3 * q + 1] + c.R[3 * r + 2] * dW[3 * q + 2];
+        pose[3] += Mr[5] - Mr[7];
+        pose[4] += Mr[6] - Mr[2];
+        pose[5] += Mr[1] - Mr[3];
+      }
+      if (dpose && __any_sync(0xffffffffu, act)) {
+        int comp;
+        bool has;
+        const float tot = warp_sum_transpose<6>(pose, &comp, &has);
+        if (has) atomicAdd(&dpose[v * 6 + comp], tot);
+      }
+    }
+    if (!live) continue;
+    // Sigma = M M^T -> dM = G M with G the symmetrised gradient
+    const float G[9] = {dSig[0], dSig[1], dSig[2], dSig[1], dSig[3], dSig[4], dSig[2], dSig[4], dSig[5]};
+    float dRm[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float dMrk = G[3 * r + 0] * M[0 + k] + G[3 * r + 1] * M[3 + k] + G[3 * r + 2] * M[6 + k];
+        dRm[3 * r + k] = dMrk * sc[k];
+        gs[k] += dMrk * R[3 * r + k];
+      }
+    const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    float dq[4];
+    dq[0] = 2.f * (-dRm[1] * z + dRm[2] * y + dRm[3] * z - dRm[5] * x - dRm[6] * y + dRm[7] * x);
+    dq[1] = 2.f * (dRm[1] * y + dRm[2] * z + dRm[3] * y - 2.f * dRm[4] * x - dRm[5] * w + dRm[6] * z + dRm[7] * w -
+                   2.f * dRm[8] * x);
+    dq[2] = 2.f * (-2.f * dRm[0] * y + dRm[1] * x + dRm[2] * w + dRm[3] * x + dRm[5] * z - dRm[6] * w + dRm[7] * z -
+                   2.f * dRm[8] * y);
+    dq[3] = 2.f * (-2.f * dRm[0] * z - dRm[1] * w + dRm[2] * x + dRm[3] * w - 2.f * dRm[4] * z + dRm[5] * y +
+                   dRm[6] * x + dRm[7] * y);
+    const float qd = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * z;
+    const float iq = 1.f / qlen;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gq[k] = (dq[k] - qn[k] * qd) * iq;
+    out[0 * ostride + i] = gm[0];
+    out[1 * ostride + i] = gm[1];
+    out[2 * ostride + i] = gm[2];
+    out[3 * ostride + i] = gs[0] * sc[0];
+    out[4 * ostride + i] = gs[1] * sc[1];
+    out[5 * ostride + i] = gs[2] * sc[2];
+    out[6 * ostride + i] = gq[0];
+    out[7 * ostride + i] = gq[1];
+    out[8 * ostride + i] = gq[2];
+    out[9 * ostride + i] = gq[3];
+    out[10 * ostride + i] = go;
+    for (int k = 0; k < 3 * D; ++k) out[(11 + k) * ostride + i] = gsh[k];
+    (void)F;
+  }
+}
+
+// ============================================================================
+// host orchestration
+// ============================================================================
+template <int TW, int TH, int STAGE>
+static void blend_fwd_launch(RasterArgs& a, const u64* inst, float* rgb, float* dout, cudaStream_t st) {
+  static int occ = -1;
+  if (occ < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_fwd<TW, TH, STAGE>, 256, 0);
+  const int grid = max(1, min(a.n_tiles, a.num_sms * max(occ, 1)));
+  k_blend_fwd<TW, TH, STAGE><<<grid, 256, 0, st>>>(a, inst, rgb, dout);
+}
+template <int TW, int TH, int STAGE>
+static void blend_bwd_launch(RasterArgs& a, const u64* inst, const float* dr, const float* dd, cudaStream_t st) {
+  static int occ = -1;
+  if (occ < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_bwd<TW, TH, STAGE>, 256, 0);
+  const int grid = max(1, min(a.n_tiles, a.num_sms * max(occ, 1)));
+  k_blend_bwd<TW, TH, STAGE><<<grid, 256, 0, st>>>(a, inst, dr, dd);
+}
+
+#define DCG_STAGES(TW, TH, CALL)                  \
+  switch (a.stage) {                              \
+    case 64: CALL(TW, TH, 64); break;             \
+    case 96: CALL(TW, TH, 96); break;             \
+    case 192: CALL(TW, TH, 192); break;           \
+    case 256: CALL(TW, TH, 256); break;           \
+    default: CALL(TW, TH, 128); break;            \
+  }
+#define DCG_TILES(CALL)                                                   \
+  if (a.tile_w == 32 && a.tile_h == 32) { DCG_STAGES(32, 32, CALL) }      \
+  else if (a.tile_w == 32 && a.tile_h == 16) { DCG_STAGES(32, 16, CALL) } \
+  else { DCG_STAGES(16, 16, CALL) }
+
+static int grid_for(long long n, int num_sms) {
+  long long b = (n + 255) / 256;
+  long long cap = (long long)num_sms * 8;
+  return (int)max(1ll, min(b, cap));
+}
+
+void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u64** inst_sorted, cudaStream_t st) {
+  cudaMemsetAsync(a.counters, 0, sizeof(DevCounters), st);
+  const long long pairs = (long long)a.V * a.n;
+  a.prof(PH_PRE_FWD, true, st);
+  if (a.n > 0) {
+    k_preprocess_fwd<<<grid_for(a.n, a.num_sms), 256, 0, st>>>(a);
+    count_launch();
+  }
+  a.prof(PH_PRE_FWD, false, st);
+  a.prof(PH_BINNING, true, st);
+  // compaction into depth keys
+  part_scan_emit(nullptr, (u64)pairs, VisCount{a.touched}, VisEmit{a.depth, a.list_a, a.n, a.idx_bits}, a.part, a.P,
+                 &a.counters->n_vis, st);
+  const int lbits = 31 + a.view_bits;
+  u64* ls = radix_sort(a.list_a, a.list_b, &a.counters->n_vis, a.idx_bits, a.idx_bits + lbits, a.hist, a.P, st);
+  part_scan_emit(&a.counters->n_vis, 0, InstCount{ls, a.touched, a.n, a.idx_bits},
+                 InstEmit{ls, a.rect, a.cams, a.n, a.idx_bits, a.inst_a, (u64)a.cap_inst}, a.part, a.P,
+                 &a.counters->n_inst, st);
+  k_clamp_inst<<<1, 1, 0, st>>>(a.counters, (u64)a.cap_inst, a.errword);
+  int tb = 1;
+  while ((1ll << tb) < (long long)a.n_tiles) ++tb;
+  u64* is = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, 32, 32 + tb, a.hist, a.P, st);
+  cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)max(a.n_tiles, 1), st);
+  k_ranges<<<a.num_sms * 4, 256, 0, st>>>(is, &a.counters->n_inst_c, a.ranges);
+  count_launch(6 + 3 * ((lbits + 7) / 8) + 3 * ((tb + 7) / 8) + 2);
+  a.prof(PH_BINNING, false, st);
+  a.prof(PH_BLEND_FWD, true, st);
+#define FWD_CALL(TW, TH, SG) blend_fwd_launch<TW, TH, SG>(a, is, rgb, dout, st)
+  DCG_TILES(FWD_CALL)
+#undef FWD_CALL
+  count_launch();
+  a.prof(PH_BLEND_FWD, false, st);
+  *list_sorted = ls;
+  *inst_sorted = is;
+}
+
+void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb, const float* dL_ddepth, float* grads,
+                     long long g_stride, float* dL_dpose, cudaStream_t st) {
+  cudaMemsetAsync(&a.counters->tile_queue_bwd, 0, sizeof(unsigned), st);
+  if (dL_dpose) cudaMemsetAsync(dL_dpose, 0, sizeof(float) * 6 * a.V, st);
+  a.prof(PH_BLEND_BWD, true, st);
+#define BWD_CALL(TW, TH, SG) blend_bwd_launch<TW, TH, SG>(a, inst_sorted, dL_drgb, dL_ddepth, st)
+  DCG_TILES(BWD_CALL)
+#undef BWD_CALL
+  count_launch();
+  a.prof(PH_BLEND_BWD, false, st);
+  a.prof(PH_PRE_BWD, true, st);
+  if (a.n > 0) {
+    k_preprocess_bwd<<<grid_for(a.n, a.num_sms), 256, 0, st>>>(a, grads, g_stride, dL_dpose);
+    count_launch();
+  }
+  a.prof(PH_PRE_BWD, false, st);
+}
+
+// ============================================================================
+// L1 loss of Eq. 2-4 (image L1 part and depth L1), per view means
+// ============================================================================
+__global__ void k_loss_l1(const float* __restrict__ rgb, const float* __restrict__ depth,
+                          const float* __restrict__ trgb, const float* __restrict__ tdepth, const DevCam* cams, int V,
+                          long long n_pix, float lam, float* __restrict__ dr, float* __restrict__ dd, float* loss) {
+  float acc = 0.f;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n_pix; p += (long long)gridDim.x * blockDim.x) {
+    int v = 0;
+    while (v + 1 < V && p >= cams[v + 1].pix_off) ++v;
+    const long long off = cams[v].pix_off;
+    const long long P = (long long)cams[v].W * cams[v].H;
+    const long long l = p - off;
+    const float i3 = 1.f / (3.f * (float)P), i1 = lam / (float)P;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const long long k = 3 * off + ch * P + l;
+      const float d = rgb[k] - trgb[k];
+      dr[k] = d > 0.f ? i3 : (d < 0.f ? -i3 : 0.f);
+      acc += fabsf(d) * i3;
+    }
+    const float e = depth[p] - tdepth[p];
+    dd[p] = e > 0.f ? i1 : (e < 0.f ? -i1 : 0.f);
+    acc += fabsf(e) * i1;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.f) atomicAdd(loss, acc);
+}
+
+void launch_loss_l1(const float* rgb, const float* depth, const float* trgb, const float* tdepth, const DevCam* cams,
+                    int V, long long n_pix, float lam, float* dr, float* dd, float* loss, int num_sms,
+                    cudaStream_t st) {
+  if (n_pix <= 0) return;
+  k_loss_l1<<<grid_for(n_pix, num_sms), 256, 0, st>>>(rgb, depth, trgb, tdepth, cams, V, n_pix, lam, dr, dd, loss);
+  count_launch();
+}
+
+}  // namespace dcg

@@ -1,0 +1,142 @@
+// Device scan top level and the stable LSD radix sort (hand-written; no library sort).
+#include "device_scan.cuh"
+
+namespace dcg {
+
+__global__ void k_part_scan(u64* part, int P, u64* total_out) {
+  // one block of 1024 threads; each thread scans a contiguous run of part[]
+  const int T = blockDim.x;
+  const int per = (P + T - 1) / T;
+  const int b = threadIdx.x * per;
+  const int e = min(P, b + per);
+  u64 s = 0;
+  for (int i = b; i < e; ++i) s += part[i];
+  u64 tot;
+  u64 ex = block_excl_scan<u64>(s, &tot);
+  for (int i = b; i < e; ++i) {
+    u64 v = part[i];
+    part[i] = ex;
+    ex += v;
+  }
+  if (threadIdx.x == 0) {
+    part[P] = tot;
+    if (total_out) *total_out = tot;
+  }
+}
+
+// Per-block digit histogram of the block's partition, warp-aggregated with match_any.
+__global__ void k_radix_hist(const u64* keys, const u64* n_ptr, int shift, int nbits, uint32_t* hist) {
+  __shared__ uint32_t h[256];
+  const u64 n = *n_ptr;
+  u64 beg, end;
+  partition_of(n, &beg, &end);
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const u64 mask = (1ull << nbits) - 1;
+  for (u64 c0 = beg; c0 < end; c0 += blockDim.x) {
+    const u64 i = c0 + threadIdx.x;
+    const bool valid = i < end;
+    const unsigned d = valid ? (unsigned)((keys[i] >> shift) & mask) : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (valid && lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of hist[256 * P] in digit-major order (one block of 1024 threads).
+__global__ void k_radix_scan(uint32_t* hist, int P) {
+  const int N = 256 * P;
+  const int T = blockDim.x;
+  const int per = (N + T - 1) / T;
+  const int b = threadIdx.x * per;
+  const int e = min(N, b + per);
+  uint32_t s = 0;
+  for (int i = b; i < e; ++i) s += hist[i];
+  uint32_t tot;
+  uint32_t ex = block_excl_scan<uint32_t>(s, &tot);
+  for (int i = b; i < e; ++i) {
+    uint32_t v = hist[i];
+    hist[i] = ex;
+    ex += v;
+  }
+}
+
+// Stable scatter.  The block walks its partition in chunks of 8 warps x 256
+// items; warp w owns the chunk's w-th run of 256 consecutive items and ranks
+// them round by round (32 lanes per round) with match_any and per-warp digit
+// counters, so that the rank order equals the input order.
+constexpr int kSortWarps = 8;
+constexpr int kSortRounds = 8;
+constexpr int kSortChunk = kSortWarps * 32 * kSortRounds;
+
+__global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, const u64* n_ptr, int shift,
+                                                       int nbits, const uint32_t* hist) {
+  __shared__ uint32_t wcnt[kSortWarps][256];
+  __shared__ uint32_t run[256];
+  const u64 n = *n_ptr;
+  u64 beg, end;
+  partition_of(n, &beg, &end);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const u64 mask = (1ull << nbits) - 1;
+  run[tid] = hist[tid * gridDim.x + blockIdx.x];
+  for (u64 c0 = beg; c0 < end; c0 += kSortChunk) {
+#pragma unroll
+    for (int k = 0; k < kSortWarps; ++k) wcnt[k][tid] = 0;
+    __syncthreads();
+    u64 key[kSortRounds];
+    uint32_t pos[kSortRounds];
+    unsigned dig[kSortRounds];
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+      const u64 i = c0 + (u64)w * 256 + (u64)r * 32 + lane;
+      const bool valid = i < end;
+      key[r] = valid ? in[i] : 0ull;
+      const unsigned d = valid ? (unsigned)((key[r] >> shift) & mask) : 256u;
+      dig[r] = d;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const unsigned rank = __popc(peers & lt);
+      const unsigned base = valid ? wcnt[w][d] : 0u;
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) wcnt[w][d] = base + __popc(peers);
+      __syncwarp();
+      pos[r] = base + rank;
+    }
+    __syncthreads();
+    // exclusive scan across warps for digit `tid`
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kSortWarps; ++k) {
+      const uint32_t t = wcnt[k][tid];
+      wcnt[k][tid] = acc;
+      acc += t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+      const unsigned d = dig[r];
+      if (d < 256u) out[run[d] + wcnt[w][d] + pos[r]] = key[r];
+    }
+    __syncthreads();
+    run[tid] += acc;
+    __syncthreads();
+  }
+}
+
+u64* radix_sort(u64* a, u64* b, const u64* n_ptr, int lo, int hi, uint32_t* hist, int P, cudaStream_t s) {
+  u64* src = a;
+  u64* dst = b;
+  for (int sh = lo; sh < hi; sh += 8) {
+    const int nb = min(8, hi - sh);
+    k_radix_hist<<<P, 256, 0, s>>>(src, n_ptr, sh, nb, hist);
+    k_radix_scan<<<1, 1024, 0, s>>>(hist, P);
+    k_radix_scatter<<<P, 256, 0, s>>>(src, dst, n_ptr, sh, nb, hist);
+    u64* t = src;
+    src = dst;
+    dst = t;
+  }
+  return src;
+}
+
+}  // namespace dcg

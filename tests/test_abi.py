@@ -1,0 +1,66 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+function that include/*.h declares (no compute calls here)."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(dcg_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2511_23030_b300 import build
+
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["dcg_create", "dcg_chunk_table_update", "dcg_cull_chunks", "dcg_gather_active", "dcg_render_fwd",
+              "dcg_render_bwd", "dcg_scatter_back"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", libpath]).decode()
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_without_gpu(libpath):
+    from paper_2511_23030_b300 import dcg
+
+    L = dcg.lib()
+    for n in declared_functions():
+        assert hasattr(L, n)
+    c = dcg.config()
+    assert c.sh_degree == 3 and c.tile_w == 16 and c.page_gaussians == 2048
+
+
+def test_no_library_means_no_fallback(tmp_path, monkeypatch):
+    from paper_2511_23030_b300 import dcg
+
+    monkeypatch.setattr(dcg, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(dcg, "_lib", None)
+    with pytest.raises(ImportError):
+        dcg.lib()
+
+
+def test_build_targets_sm_103a_only():
+    from paper_2511_23030_b300 import build
+
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

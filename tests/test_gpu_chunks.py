@@ -1,0 +1,195 @@
+"""Chunk path on the GPU against the oracle: Eq. 5/6 ids bit-exact, cull masks
+bit-exact, gather order, gather/scatter round trip, LRU residency."""
+import numpy as np
+import pytest
+
+from paper_2511_23030_b300 import dcg, synth
+
+from gpu_util import make_ctx, planar
+
+pytestmark = pytest.mark.gpu
+
+
+def _keys_gpu(ctx, means):
+    import torch
+
+    m = torch.from_numpy(np.ascontiguousarray(means, np.float32)).cuda()
+    k = torch.zeros(means.shape[0], dtype=torch.int64, device="cuda")
+    dcg.dcg_chunk_keys(ctx, m, k)
+    return k
+
+
+def test_chunk_keys_bit_exact(orc):
+    ctx = make_ctx(deg=0, n_max=1000, chunk=8.0)
+    try:
+        rng = np.random.default_rng(0)
+        p = rng.uniform(-2e4, 2e4, (200_000, 3)).astype(np.float32)
+        p[:5000, 0] = (rng.integers(-500, 500, 5000) * 8.0 + 4.0).astype(np.float32)  # exact boundaries
+        p[5000:6000, 1] = np.float32(-4.0)
+        p[6000:7000] = np.nextafter(np.float32(-4.0), np.float32(-10.0))
+        p[7000] = (0.0, -0.0, 0.0)
+        k = _keys_gpu(ctx, p)
+        dcg.dcg_sync(ctx)
+        _, ok, bad = orc.chunk_keys(p, 8.0)
+        assert not bad.any()
+        assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
+        # golden ids with s = 10
+        ctx2 = make_ctx(deg=0, n_max=1000, chunk=10.0)
+        g = np.array([[0, 0, 0], [5, 0, 0], [-5, 0, 0], [-5.0000005, 0, 0]], np.float32)
+        kk = _keys_gpu(ctx2, g).cpu().numpy().view(np.uint64)
+        dcg.dcg_sync(ctx2)
+        assert list(kk) == [4611688217451692032, 4611692615498203136, 4611688217451692032, 4611683819405180928]
+        # out of range / NaN -> DCG_ERR_KEY_RANGE at sync, key 0
+        bad_p = np.array([[1e9, 0, 0], [np.nan, 0, 0], [1, 2, 3]], np.float32)
+        kb = _keys_gpu(ctx2, bad_p)
+        with pytest.raises(dcg.DcgError) as e:
+            dcg.dcg_sync(ctx2)
+        assert e.value.status == 5
+        assert list(kb.cpu().numpy()[:2]) == [0, 0]
+        dcg.dcg_sync(ctx2)  # cleared
+        dcg.dcg_destroy(ctx2)
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
+def _window_table(n=64_000, deg=1, budget=None, page=512):
+    sc = synth.window_scene(0, n=n, deg=deg)
+    ctx = make_ctx(deg=deg, n_max=n, chunk=sc["chunk_size"], budget=budget, host=n, page=page, dfar=60.0)
+    g = planar(sc["params"])
+    dcg.dcg_chunk_table_update(ctx, g, n)
+    return ctx, sc
+
+
+def test_table_update_groups_and_round_trips(orc):
+    ctx, sc = _window_table()
+    try:
+        P = sc["params"]
+        info = dcg.dcg_chunk_info(ctx)
+        coords, keys, _ = orc.chunk_keys(P[:, :3], sc["chunk_size"])
+        uk, cnt = np.unique(keys, return_counts=True)
+        assert np.array_equal(info["keys"], uk) and np.array_equal(info["counts"], cnt)
+        assert len(uk) == 64
+        for c in (0, 17, 63):
+            got = dcg.dcg_chunk_read(ctx, c, int(info["counts"][c]), P.shape[1])
+            want = P[keys == info["keys"][c]]  # stored order = input order within the chunk
+            assert np.array_equal(got.T, want)
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
+def test_cull_bit_exact_flat_and_hierarchical(orc):
+    import torch
+
+    ctx, sc = _window_table()
+    try:
+        info = dcg.dcg_chunk_info(ctx)
+        C = len(info["keys"])
+        rng = np.random.default_rng(1)
+        cams = list(sc["cams"])
+        for _ in range(12):  # extra random poses, some inside the volume
+            eye = rng.uniform(-10, 14, 3)
+            cams.append(synth.Camera(300.0, 300.0, 320.0, 240.0, 640, 480,
+                                     synth.look_at(eye, eye + rng.normal(0, 1, 3)), 0.2, float(rng.uniform(5, 40))))
+        for k0 in range(0, len(cams), 8):
+            cs = cams[k0:k0 + 8]
+            mask = torch.zeros(len(cs) * C, dtype=torch.uint8, device="cuda")
+            lst = dcg.dcg_cull_chunks(ctx, cs, mask)
+            m = mask.view(len(cs), C).cpu().numpy()
+            for v, cam in enumerate(cs):
+                flat = orc.cull(info["coords"], sc["chunk_size"], cam, 60.0)
+                hier = orc.cull(info["coords"], sc["chunk_size"], cam, 60.0, hierarchical=True)
+                assert np.array_equal(m[v], flat) and np.array_equal(flat, hier)
+            assert np.array_equal(lst, np.nonzero(m.any(0))[0])
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
+def test_gather_order_and_scatter_round_trip(orc):
+    import torch
+
+    ctx, sc = _window_table()
+    try:
+        P = sc["params"]
+        info = dcg.dcg_chunk_info(ctx)
+        lst = dcg.dcg_cull_chunks(ctx, sc["cams"][:3])
+        g, n = dcg.dcg_gather_active(ctx, lst)
+        vis = np.zeros(len(info["keys"]), bool)
+        vis[lst] = True
+        order, n_ref = orc.gather_order(info["keys"], info["counts"], vis)
+        assert n == n_ref
+        F = P.shape[1]
+        _, keys, _ = orc.chunk_keys(P[:, :3], sc["chunk_size"])
+        want = np.concatenate([P[keys == info["keys"][c]] for c, _ in order])
+        act_np = _read_active(g, n, F)
+        assert np.array_equal(act_np, want)
+        # modify, scatter back, flush, read from the host tier
+        mod = torch.from_numpy(np.ascontiguousarray((want * 2 + 1).T)).cuda()
+        g2 = dcg.gaussians(mod, 1)
+        dcg.dcg_scatter_back(ctx, g2, n)
+        dcg.dcg_flush(ctx)
+        for c, _ in order[:5]:
+            got = dcg.dcg_chunk_read(ctx, c, int(info["counts"][c]), F)
+            assert np.array_equal(got.T, P[keys == info["keys"][c]] * 2 + 1)
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
+def _read_active(g, n, F):
+    """Copy of the library-owned active buffer (planar, stride g.stride) as numpy [n, F]."""
+    return dcg.active_tensor(g, n, F).T.cpu().numpy()
+
+
+def test_lru_eviction_follows_oracle(orc):
+    """Budget of ~40% of the scene; a sequence of views; residency after every
+    gather equals the oracle's LRU simulation; evicted dirty chunks are saved."""
+    import torch
+
+    n = 64_000
+    ctx, sc = _window_table(n=n, budget=26_000, page=256)
+    try:
+        info = dcg.dcg_chunk_info(ctx)
+        C = len(info["keys"])
+        counts = info["counts"]
+        resident = np.zeros(C, bool)
+        last = np.full(C, -1)
+        step = 0
+        rng = np.random.default_rng(2)
+        for it in range(14):
+            eye = rng.uniform(-6, 10, 3)
+            cam = synth.Camera(120.0, 120.0, 160.0, 120.0, 320, 240, synth.look_at(eye, eye + rng.normal(0, 1, 3)),
+                               0.2, 8.0)
+            lst = dcg.dcg_cull_chunks(ctx, [cam])
+            if counts[lst].sum() > 26_000 or len(lst) == 0:
+                continue
+            vis = np.zeros(C, bool)
+            vis[lst] = True
+            step += 1
+            deficit = counts[resident].sum() + counts[vis & ~resident].sum() - 26_000
+            sel = orc.lru_select(resident, vis, last, info["keys"], counts, deficit)
+            assert sel is not None
+            resident[sel] = False
+            resident[vis] = True
+            last[vis] = step
+            g, nact = dcg.dcg_gather_active(ctx, lst)
+            # write back +1 to make the chunks dirty
+            F = synth.n_fields(1)
+            cur = torch.from_numpy(np.ascontiguousarray(_read_active(g, nact, F).T + 1)).cuda()
+            dcg.dcg_scatter_back(ctx, dcg.gaussians(cur, 1), nact)
+            got = dcg.dcg_chunk_info(ctx)
+            assert np.array_equal(got["resident"].astype(bool), resident), it
+            assert got["counts"][resident].sum() <= 26_000
+        assert step >= 5
+        dcg.dcg_flush(ctx)
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
+def test_budget_error_when_visible_exceeds_budget():
+    ctx, sc = _window_table(n=64_000, budget=10_000, page=256)
+    try:
+        lst = np.arange(dcg.dcg_chunk_count(ctx), dtype=np.int32)
+        with pytest.raises(dcg.DcgError) as e:
+            dcg.dcg_gather_active(ctx, lst)
+        assert e.value.status == 4
+    finally:
+        dcg.dcg_destroy(ctx)

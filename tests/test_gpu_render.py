@@ -1,0 +1,248 @@
+"""Parity of the CUDA renderer (forward and backward) with the FP64 oracle.
+
+Tolerances (fixed by the FP32/FP64 comparison): RGB within 1e-5 absolute per
+channel, depth within 1e-5 * max(1, depth) (depth is un-normalised metres),
+final transmittance within 1e-5 absolute, at every pixel the oracle does not
+flag as near a discrete boundary (support q = 9, alpha = 1/255, T = 1e-4,
+depth ties); flagged pixels stay below 0.5 %.  Gradients: relative L2 error
+<= 1e-4 per parameter group and for the pose twist.  Sort keys (FP32 depth)
+bit-exact; per-tile lists are the unique (depth bits, index) order of the
+Gaussians whose rectangle covers the tile."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2511_23030_b300 import dcg, synth
+
+from gpu_util import GROUPS, backward, make_ctx, out_buffers, planar, rel_l2, render, split_views
+
+pytestmark = pytest.mark.gpu
+
+RGB_TOL = 1e-5
+T_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def check_image(orc_out, rgb, depth, T, tag, max_flag=0.005):
+    ok = orc_out["flags"] == 0
+    assert ok.mean() >= 1 - max_flag, f"{tag}: flagged {1 - ok.mean():.4%}"
+    e_rgb = np.abs(rgb[ok] - orc_out["rgb"][ok]).max()
+    dz = np.abs(depth[ok] - orc_out["depth"][ok]) / np.maximum(1.0, np.abs(orc_out["depth"][ok]))
+    e_T = np.abs(T[ok] - orc_out["T"][ok]).max()
+    assert e_rgb <= RGB_TOL, f"{tag}: rgb err {e_rgb}"
+    assert dz.max() <= RGB_TOL, f"{tag}: depth err {dz.max()}"
+    assert e_T <= T_TOL, f"{tag}: T err {e_T}"
+    return e_rgb
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = make_ctx(deg=3, n_max=600_000, views=8)
+    yield c
+    dcg.dcg_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def ctx0():
+    c = make_ctx(deg=0, n_max=100_000, views=8)
+    yield c
+    dcg.dcg_destroy(c)
+
+
+def _pix_arrays(rgb_v, depth_v):
+    H, W = depth_v.shape
+    return rgb_v.reshape(3, -1).T.astype(np.float64), depth_v.reshape(-1).astype(np.float64)
+
+
+def test_small_view_forward_matches_oracle(ctx0, orc):
+    sc = synth.room_small(0)
+    P, cam = sc["params"], sc["cams"][0]
+    _, _, rgb, depth = render(ctx0, P, 0, [cam])
+    (rv, dv), = split_views(rgb, depth, [cam])
+    st = dcg.dcg_state_read(ctx0, None, 1, P.shape[0], cam.W * cam.H)
+    o = orc.render(P, 0, cam)
+    r, d = _pix_arrays(rv, dv)
+    check_image(o, r, d, st["T"].astype(np.float64), "room_small")
+    assert (o["n"] > 0).mean() > 0.5
+
+
+def test_sort_keys_bit_exact_and_tile_lists_valid(ctx0, orc):
+    sc = synth.room_small(0)
+    P, cam = sc["params"], sc["cams"][0]
+    n = P.shape[0]
+    render(ctx0, P, 0, [cam])
+    st = dcg.dcg_state_read(ctx0, None, 1, n, cam.W * cam.H)
+    z32 = orc.depth_f32(P[:, :3], cam)
+    assert np.array_equal(st["depth"].view(np.uint32), z32.view(np.uint32))
+    # per tile: exactly the Gaussians whose rectangle covers it, in (depth bits, index) order
+    rect = st["rect"]
+    vis = rect[:, 2] >= rect[:, 0]
+    ntx = (cam.W + 15) // 16
+    ranges, ids = st["ranges"], st["ids"]
+    zb = st["depth"].view(np.uint32)
+    for t in range(ranges.shape[0]):
+        ty, tx = divmod(t, ntx)
+        lst = ids[ranges[t, 0]:ranges[t, 1]]
+        want = np.nonzero(vis & (rect[:, 0] <= tx) & (rect[:, 2] >= tx) & (rect[:, 1] <= ty) & (rect[:, 3] >= ty))[0]
+        want = want[np.lexsort((want, zb[want]))]
+        assert np.array_equal(lst, want), t
+    # rectangles agree with the oracle's FP64 extents except within rounding of a pixel boundary
+    pr = orc.project(P, 0, cam)
+    x0 = np.floor(pr["u"] - pr["ex"])
+    x1 = np.ceil(pr["u"] + pr["ex"])
+    near = (np.abs(pr["u"] - pr["ex"] - np.round(pr["u"] - pr["ex"])) < 1e-4) | (
+        np.abs(pr["u"] + pr["ex"] - np.round(pr["u"] + pr["ex"])) < 1e-4)
+    inside = (pr["vis"] > 0) & (x1 >= 0) & (x0 <= cam.W - 1)
+    tx0 = (np.clip(x0, 0, cam.W - 1) // 16).astype(int)
+    good = inside & ~near & vis
+    assert np.array_equal(rect[good, 0], tx0[good])
+
+
+def test_small_view_backward_matches_oracle(ctx0, orc):
+    sc = synth.room_small(0)
+    P, cam = sc["params"], sc["cams"][0]
+    n = P.shape[0]
+    g_t, g, rgb, depth = render(ctx0, P, 0, [cam])
+    o = orc.render(P, 0, cam)
+    rng = np.random.default_rng(5)
+    Pn = cam.W * cam.H
+    gr = rng.normal(size=(Pn, 3))
+    gd = rng.normal(size=Pn) * 0.1
+    gr[o["flags"] != 0] = 0
+    gd[o["flags"] != 0] = 0
+    import torch
+
+    dr = torch.from_numpy(np.ascontiguousarray(gr.T.reshape(-1)).astype(np.float32)).cuda()
+    dd = torch.from_numpy(gd.astype(np.float32)).cuda()
+    grad, pose = backward(ctx0, g_t, 0, n, dr, dd, 1)
+    og, opose = orc.render_bwd(P, 0, cam, gr, gd)
+    for name, sl in GROUPS.items():
+        e = rel_l2(grad[:, sl], og[:, sl])
+        assert e <= GRAD_TOL, (name, e)
+    assert rel_l2(pose[0], opose) <= GRAD_TOL, (pose[0], opose)
+
+
+def _room_views(n=120_000, n_views=3, seed=1):
+    sc = synth.room_indoor(seed, n=n, n_steps=n_views)
+    return sc["params"], sc["cams"]
+
+
+def test_room_sh3_sampled_pixels_and_sparse_seed_gradients(ctx, orc):
+    P, cams = _room_views(n=60_000, n_views=1, seed=1)
+    cam = cams[0]
+    n = P.shape[0]
+    g_t, g, rgb, depth = render(ctx, P, 3, [cam])
+    (rv, dv), = split_views(rgb, depth, [cam])
+    rng = np.random.default_rng(3)
+    # a dense 40x32 window plus scattered pixels
+    ys, xs = np.mgrid[200:232, 300:340]
+    win = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
+    pix = np.concatenate([win, synth.pixel_sample(rng, cam.W, cam.H, 1500)])
+    pix = np.unique(pix, axis=0)
+    o = orc.render(P, 3, cam, pix=pix)
+    r = rv[:, pix[:, 1], pix[:, 0]].T.astype(np.float64)
+    d = dv[pix[:, 1], pix[:, 0]].astype(np.float64)
+    st = dcg.dcg_state_read(ctx, None, 1, n, cam.W * cam.H)
+    T = st["T"].reshape(cam.H, cam.W)[pix[:, 1], pix[:, 0]].astype(np.float64)
+    check_image(o, r, d, T, "room_indoor")
+    # gradient of a loss seeded only on these pixels
+    gr = rng.normal(size=(len(pix), 3))
+    gd = rng.normal(size=len(pix)) * 0.1
+    gr[o["flags"] != 0] = 0
+    gd[o["flags"] != 0] = 0
+    import torch
+
+    full_r = np.zeros((3, cam.H, cam.W), np.float32)
+    full_d = np.zeros((cam.H, cam.W), np.float32)
+    full_r[:, pix[:, 1], pix[:, 0]] = gr.T
+    full_d[pix[:, 1], pix[:, 0]] = gd
+    dr = torch.from_numpy(full_r.reshape(-1)).cuda()
+    dd = torch.from_numpy(full_d.reshape(-1)).cuda()
+    grad, pose = backward(ctx, g_t, 3, n, dr, dd, 1)
+    og, opose = orc.render_bwd(P, 3, cam, gr, gd, pix=pix)
+    for name, sl in GROUPS.items():
+        e = rel_l2(grad[:, sl], og[:, sl])
+        assert e <= GRAD_TOL, (name, e)
+    assert rel_l2(pose[0], opose) <= GRAD_TOL
+
+
+def test_batched_views_equal_single_views(ctx):
+    P, cams = _room_views(n=60_000, n_views=3, seed=2)
+    sizes = [(640, 480), (320, 240), (200, 150)]
+    for c, (W, H) in zip(cams, sizes):
+        c.W, c.H, c.cx, c.cy = W, H, W / 2, H / 2
+        c.fx = c.fy = 0.8 * W
+    _, _, rgb_b, depth_b = render(ctx, P, 3, cams)
+    batched = split_views(rgb_b, depth_b, cams)
+    for v, c in enumerate(cams):
+        _, _, rgb_s, depth_s = render(ctx, P, 3, [c])
+        (rs, ds), = split_views(rgb_s, depth_s, [c])
+        assert np.array_equal(rs, batched[v][0]) and np.array_equal(ds, batched[v][1])
+
+
+@pytest.mark.parametrize("tile,stage", [((16, 16), 64), ((32, 16), 128), ((32, 32), 256), ((16, 16), 192),
+                                        ((32, 32), 96)])
+def test_launch_shapes_agree(ctx, tile, stage):
+    P, cams = _room_views(n=60_000, n_views=1, seed=4)
+    dcg.dcg_set_launch(ctx, 16, 16, 128)
+    _, _, r0, d0 = render(ctx, P, 3, cams)
+    dcg.dcg_set_launch(ctx, tile[0], tile[1], stage)
+    try:
+        _, _, r1, d1 = render(ctx, P, 3, cams)
+    finally:
+        dcg.dcg_set_launch(ctx, 16, 16, 128)
+    assert (r0 - r1).abs().max().item() <= 2e-6
+    assert ((d0 - d1).abs() / d0.abs().clamp(min=1)).max().item() <= 2e-6
+
+
+def test_edge_cases(ctx0):
+    import torch
+
+    sc = synth.room_small(0)
+    cam = sc["cams"][0]
+    # no Gaussians
+    P = sc["params"][:0]
+    _, _, rgb, depth = render(ctx0, P, 0, [cam])
+    assert rgb.abs().max().item() == 0 and depth.abs().max().item() == 0
+    # everything behind the camera
+    P = sc["params"].copy()
+    P[:, 2] = -3.0
+    _, _, rgb, depth = render(ctx0, P, 0, [cam])
+    assert rgb.abs().max().item() == 0
+    # ragged 1x1 and 17x33 images
+    for W, H in ((1, 1), (17, 33)):
+        c = synth.Camera(100.0, 100.0, W / 2, H / 2, W, H, cam.Tcw, 0.2, 100.0)
+        _, _, rgb, depth = render(ctx0, sc["params"], 0, [c])
+        assert torch.isfinite(rgb).all()
+    # backward with zero seed gives zero gradients
+    g_t, g, rgb, depth = render(ctx0, sc["params"], 0, [cam])
+    grad, pose = backward(ctx0, g_t, 0, sc["params"].shape[0], torch.zeros_like(rgb), torch.zeros_like(depth), 1)
+    assert np.abs(grad).max() == 0 and np.abs(pose).max() == 0
+
+
+def test_loss_l1_matches_definition(ctx0, orc):
+    import torch
+
+    sc = synth.room_small(0)
+    cams = sc["cams"] * 2
+    P = sum(c.W * c.H for c in cams)
+    rng = np.random.default_rng(0)
+    rgb = torch.from_numpy(rng.uniform(0, 1, 3 * P).astype(np.float32)).cuda()
+    dep = torch.from_numpy(rng.uniform(0, 5, P).astype(np.float32)).cuda()
+    trgb = torch.from_numpy(rng.uniform(0, 1, 3 * P).astype(np.float32)).cuda()
+    tdep = torch.from_numpy(rng.uniform(0, 5, P).astype(np.float32)).cuda()
+    dr, dd, loss = torch.zeros_like(rgb), torch.zeros_like(dep), torch.zeros(1, device="cuda")
+    dcg.dcg_loss_l1(ctx0, rgb, dep, trgb, tdep, cams, 0.1, dr, dd, loss)
+    dcg.dcg_sync(ctx0)
+    L = 0.0
+    for v in range(2):
+        Pv = cams[v].W * cams[v].H
+        sl3 = slice(3 * v * Pv, 3 * (v + 1) * Pv)
+        sl = slice(v * Pv, (v + 1) * Pv)
+        Lv, gr, gd = orc.l1_loss(rgb[sl3].cpu().numpy(), dep[sl].cpu().numpy(), trgb[sl3].cpu().numpy(),
+                                 tdep[sl].cpu().numpy(), 0.1)
+        L += Lv
+        assert np.allclose(dr[sl3].cpu().numpy(), gr, rtol=1e-6, atol=0)
+        assert np.allclose(dd[sl].cpu().numpy(), gd, rtol=1e-6, atol=0)
+    assert math.isclose(loss.item(), L, rel_tol=1e-5)

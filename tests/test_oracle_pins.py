@@ -314,7 +314,8 @@ def test_back_to_front_painter_equals_oracle(orc):
     proj = orc.project(P, 3, cam)
     out = orc.render(P, 3, cam)
     vis = np.nonzero(proj["vis"] > 0)[0]
-    order = vis[np.lexsort((vis, proj["z"][vis]))]
+    z32 = orc.depth_f32(P[:, :3].astype(np.float32), cam)
+    order = vis[np.lexsort((vis, z32[vis]))]
     n_checked = 0
     for k, (x, y) in enumerate(out["pix"]):
         dx = x - proj["u"][order]
