@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--tile", default="auto", help="WxH, or auto (autotuned)")
     ap.add_argument("--stage", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="batched timing only (no plain/e2e/CPU legs), for profilers")
     ap.add_argument("--cpu-pixels", type=int, default=48, help="oracle sample: pixels per sampled view")
     return ap.parse_args()
 
@@ -229,9 +230,12 @@ def run_ours(args, rank, world):
     clocks = clk.summary()
     n_vis, n_inst, n_tiles = dcg.dcg_state_stats(ctx)
     n_eval = dcg.dcg_state_evals(ctx)
-    ms_p, launches_p, _ = timed(step_plain, max(2, K // 2), max(1, W // 2))
     K_p = max(2, K // 2)
-    ms_e, _, _ = timed(step_e2e, K, 2)
+    if args.quick:
+        ms_p, ms_e = ms_b * K_p / K * 8, ms_b
+    else:
+        ms_p, launches_p, _ = timed(step_plain, K_p, max(1, W // 2))
+        ms_e, _, _ = timed(step_e2e, K, 2)
     dcg.dcg_sync(ctx)
 
     mpix_b = npix * K * world / (ms_b / 1e3) / 1e6
@@ -365,7 +369,7 @@ def main():
         out = run_reference(args, rank, world)
     else:
         out = run_ours(args, rank, world)
-        if rank == 0 and not args.no_cpu_baseline:
+        if rank == 0 and not args.no_cpu_baseline and not args.quick:
             out["cpu_baseline"] = cpu_baseline(args.cpu_pixels, views=[0, 5], n_gaussians=args.gaussians)
     if rank == 0 and out is not None:
         print(json.dumps(out))

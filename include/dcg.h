@@ -236,8 +236,9 @@ dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const d
 dcg_status dcg_state_stats(dcg_render_state* st, int64_t* n_visible, int64_t* n_instances, int64_t* n_tiles,
                            void* stream);
 
-/* Pixel-Gaussian evaluations performed by the last forward blend of `st`
- * (a pixel stops counting at its termination).  Synchronises `stream`. */
+/* Pixel-Gaussian evaluations performed by the last forward blend of `st`:
+ * (pixel, Gaussian) pairs whose support test ran while the pixel was still
+ * blending (the unit of the blend's arithmetic).  Synchronises `stream`. */
 dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, void* stream);
 
 /* Copies of the state's per-tile sorted lists for checks (host outputs; any

@@ -354,17 +354,56 @@ __device__ __forceinline__ int view_of_tile(const DevCam* cams, int V, unsigned 
   return v;
 }
 
+// Pixel layout of a tile: 8 warps, each owning an 8 x (4 PPT) block of pixels
+// (lane -> 8 columns x 4 rows, each thread PPT rows spaced by 4), so that a
+// warp can skip a staged Gaussian whose 3-sigma box misses its block.
+template <int TW, int TH>
+struct TileLayout {
+  static constexpr int PPT = TW * TH / 256;
+  static constexpr int WY = 4 * PPT;     // rows of a warp block
+  static constexpr int WPR = TW / 8;     // warp blocks per tile row
+  static_assert(WPR * (TH / WY) == 8, "eight warp blocks per tile");
+};
+
+// Warp-coverage mask of a staged Gaussian: bit w set iff the box
+// |x - u| <= ex, |y - v| <= ey (tile-local, slightly enlarged) meets warp
+// block w.  ex, ey come from the FP32 conic the blend uses:
+// Sigma'_xx = C / (A C - B^2) = -2 C' log2e / (4 A' C' - B'^2), same for yy.
+template <int TW, int TH>
+__device__ __forceinline__ unsigned warp_mask(float ul, float vl, float4 cn) {
+  using L = TileLayout<TW, TH>;
+  const float den = 4.f * cn.x * cn.z - cn.y * cn.y;
+  const float sxx = -2.f * kLog2e * cn.z / den, syy = -2.f * kLog2e * cn.x / den;
+  const float ex = 3.001f * sqrtf(fmaxf(sxx, 0.f)) + 0.01f;
+  const float ey = 3.001f * sqrtf(fmaxf(syy, 0.f)) + 0.01f;
+  unsigned xm = 0, ym = 0;
+#pragma unroll
+  for (int i = 0; i < L::WPR; ++i)
+    if (ul + ex >= (float)(8 * i) && ul - ex <= (float)(8 * i + 7)) xm |= 1u << i;
+#pragma unroll
+  for (int i = 0; i < 8 / L::WPR; ++i)
+    if (vl + ey >= (float)(L::WY * i) && vl - ey <= (float)(L::WY * i + L::WY - 1)) ym |= 1u << i;
+  unsigned m = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w)
+    if (((xm >> (w % L::WPR)) & 1u) && ((ym >> (w / L::WPR)) & 1u)) m |= 1u << w;
+  return m;
+}
+
 template <int TW, int TH, int STAGE>
 __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __restrict__ inst, float* __restrict__ rgb,
                                                    float* __restrict__ dout) {
-  constexpr int ROWS = 256 / TW;
-  constexpr int PPT = TH / ROWS;
+  using L = TileLayout<TW, TH>;
+  constexpr int PPT = L::PPT;
   __shared__ float2 s_xy[STAGE];
   __shared__ float4 s_con[STAGE];
   __shared__ float4 s_col[STAGE];
+  __shared__ unsigned char s_mask[STAGE];
   __shared__ unsigned s_tile;
-  const int tid = threadIdx.x;
-  const int lx = tid % TW, ly = tid / TW;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int lx = (w % L::WPR) * 8 + (lane & 7);
+  const int ly = (w / L::WPR) * L::WY + (lane >> 3);
+  const unsigned wbit = 1u << w;
   for (;;) {
     __syncthreads();
     if (tid == 0) s_tile = atomicAdd(&a.counters->tile_queue, 1u);
@@ -379,16 +418,16 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
     const int x0 = tx * TW, y0 = ty * TH;
     const float x0f = (float)x0, y0f = (float)y0;
     float T[PPT], Tf[PPT], Cr[PPT], Cg[PPT], Cb[PPT], Dz[PPT];
-    uint32_t last[PPT], stop[PPT];
+    uint32_t last[PPT];
+    unsigned ev = 0;  // evaluations of (live pixel, Gaussian) pairs by this thread
     const int px = x0 + lx;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-      const int py = y0 + ly + k * ROWS;
+      const int py = y0 + ly + 4 * k;
       T[k] = (px < W && py < H) ? 1.f : 0.f;
       Tf[k] = T[k];
       Cr[k] = Cg[k] = Cb[k] = Dz[k] = 0.f;
       last[k] = 0;
-      stop[k] = 0;
     }
     const uint2 rg = a.ranges[gt];
     for (unsigned b0 = rg.x; b0 < rg.y; b0 += STAGE) {
@@ -401,15 +440,19 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
         if (idx < rg.y) {
           const unsigned vi = (unsigned)inst[idx];
           const float4 r0 = a.rec[3ull * vi + 0];
-          s_xy[j] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
-          s_con[j] = a.rec[3ull * vi + 1];
+          const float4 cn = a.rec[3ull * vi + 1];
+          const float ul = df_sub_round(r0.x, r0.z, x0f), vl = df_sub_round(r0.y, r0.w, y0f);
+          s_xy[j] = make_float2(ul, vl);
+          s_con[j] = cn;
           s_col[j] = a.rec[3ull * vi + 2];
+          s_mask[j] = (unsigned char)warp_mask<TW, TH>(ul, vl, cn);
         }
       }
       __syncthreads();
       const int cnt = min(STAGE, (int)(rg.y - b0));
       if (__any_sync(0xffffffffu, alive)) {
         for (int j = 0; j < cnt; ++j) {
+          if (!(s_mask[j] & wbit)) continue;
           const float2 xy = s_xy[j];
           const float4 cn = s_con[j];
           const float dx = __fsub_rn((float)lx, xy.x);
@@ -417,8 +460,9 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
           const float bx = __fmul_rn(cn.y, dx);
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
-            const float dy = __fsub_rn((float)(ly + k * ROWS), xy.y);
+            const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
             const float p = blend_power(sx, bx, cn.z, dy);
+            ev += T[k] > 0.f;
             if (T[k] > 0.f && p >= kPMin) {
               const float al = fminf(kAlphaMax, __fmul_rn(cn.w, ex2_approx(p)));
               if (al >= kAlphaMin) {
@@ -426,14 +470,13 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
                 if (Tn < kTMin) {
                   Tf[k] = T[k];
                   T[k] = 0.f;
-                  stop[k] = b0 - rg.x + j + 1;
                 } else {
                   const float4 cl = s_col[j];
-                  const float w = al * T[k];
-                  Cr[k] += w * cl.x;
-                  Cg[k] += w * cl.y;
-                  Cb[k] += w * cl.z;
-                  Dz[k] += w * cl.w;
+                  const float wgt = al * T[k];
+                  Cr[k] += wgt * cl.x;
+                  Cg[k] += wgt * cl.y;
+                  Cb[k] += wgt * cl.z;
+                  Dz[k] += wgt * cl.w;
                   T[k] = Tn;
                   last[k] = b0 - rg.x + j + 1;
                 }
@@ -443,15 +486,13 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
         }
       }
     }
-    unsigned long long ev = 0;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) ev += T[k] > 0.f ? (rg.y - rg.x) : stop[k];
-#pragma unroll
-    for (int o = 16; o; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
-    if ((tid & 31) == 0 && ev) atomicAdd(&a.counters->n_eval, ev);
+    {
+      const unsigned wev = __reduce_add_sync(0xffffffffu, ev);
+      if (lane == 0 && wev) atomicAdd(&a.counters->n_eval, (unsigned long long)wev);
+    }
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-      const int py = y0 + ly + k * ROWS;
+      const int py = y0 + ly + 4 * k;
       if (px < W && py < H) {
         const long long P = (long long)W * H;
         const long long pix = (long long)py * W + px;
@@ -469,14 +510,16 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
 // ============================================================================
 // 8. backward blend
 // ============================================================================
-// Sum over the 32 lanes of N values with a transposed butterfly: after the
-// call lane l holds the total of component *comp (valid iff *has), each
-// component owned by one even lane.  ceil(N/2)+... shuffles instead of 5N.
+// Sum over the 32 lanes of N values with a transposed butterfly: each step
+// halves the number of values a lane carries, so N = 10 costs 12 shuffles
+// instead of 50.  Afterwards lane l holds the total of component *comp; *has
+// is true for exactly one lane per component.
 template <int N>
 __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int* comp, bool* has) {
   const unsigned lane = threadIdx.x & 31u;
   int base = 0, cnt = N;
   int n = N;
+  unsigned shared_bits = 0;  // lane bits over which the final value is replicated
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     const bool bit = (lane & (unsigned)o) != 0u;
@@ -500,10 +543,11 @@ __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int* comp, bo
       n = half;
     } else {
       v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+      shared_bits |= (unsigned)o;
     }
   }
   *comp = base;
-  *has = cnt > 0 && (lane & 1u) == 0u;
+  *has = cnt > 0 && (lane & shared_bits) == 0u;
   return v[0];
 }
 
@@ -511,17 +555,20 @@ template <int TW, int TH, int STAGE>
 __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __restrict__ inst,
                                                    const float* __restrict__ dL_drgb,
                                                    const float* __restrict__ dL_ddepth) {
-  constexpr int ROWS = 256 / TW;
-  constexpr int PPT = TH / ROWS;
+  using L = TileLayout<TW, TH>;
+  constexpr int PPT = L::PPT;
   __shared__ float2 s_xy[STAGE];
   __shared__ float4 s_con[STAGE];
   __shared__ float4 s_col[STAGE];
   __shared__ unsigned s_vi[STAGE];
+  __shared__ unsigned char s_mask[STAGE];
   __shared__ float s_acc[STAGE][10];
   __shared__ unsigned s_tile;
   __shared__ unsigned s_maxlast;
-  const int tid = threadIdx.x;
-  const int lx = tid % TW, ly = tid / TW;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int lx = (w % L::WPR) * 8 + (lane & 7);
+  const int ly = (w / L::WPR) * L::WY + (lane >> 3);
+  const unsigned wbit = 1u << w;
   for (;;) {
     __syncthreads();
     if (tid == 0) {
@@ -545,7 +592,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
     uint32_t mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-      const int py = y0 + ly + k * ROWS;
+      const int py = y0 + ly + 4 * k;
       last[k] = 0;
       T[k] = 0.f;
       gr[k] = gg[k] = gb[k] = gd[k] = 0.f;
@@ -561,10 +608,8 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
       Sr[k] = Sg[k] = Sb[k] = Sd[k] = 0.f;
       mylast = max(mylast, last[k]);
     }
-    // block maximum of the last contributor
-#pragma unroll
-    for (int o = 16; o; o >>= 1) mylast = max(mylast, __shfl_xor_sync(0xffffffffu, mylast, o));
-    if ((tid & 31) == 0) atomicMax(&s_maxlast, mylast);
+    const unsigned warplast = __reduce_max_sync(0xffffffffu, mylast);
+    if (lane == 0) atomicMax(&s_maxlast, warplast);
     __syncthreads();
     const int maxlast = (int)s_maxlast;
     const uint2 rg = a.ranges[gt];
@@ -574,14 +619,19 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
       for (int j = tid; j < cnt; j += 256) {
         const unsigned vi = (unsigned)inst[rg.x + bstart + j];
         const float4 r0 = a.rec[3ull * vi + 0];
-        s_xy[j] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
-        s_con[j] = a.rec[3ull * vi + 1];
+        const float4 cn = a.rec[3ull * vi + 1];
+        const float ul = df_sub_round(r0.x, r0.z, x0f), vl = df_sub_round(r0.y, r0.w, y0f);
+        s_xy[j] = make_float2(ul, vl);
+        s_con[j] = cn;
         s_col[j] = a.rec[3ull * vi + 2];
         s_vi[j] = vi;
+        s_mask[j] = (unsigned char)warp_mask<TW, TH>(ul, vl, cn);
       }
       for (int e = tid; e < cnt * 10; e += 256) (&s_acc[0][0])[e] = 0.f;
       __syncthreads();
-      for (int j = cnt - 1; j >= 0; --j) {
+      const int jmax = min(cnt, (int)warplast - bstart);  // warp-uniform
+      for (int j = jmax - 1; j >= 0; --j) {
+        if (!(s_mask[j] & wbit)) continue;
         const int rel = bstart + j;
         const float2 xy = s_xy[j];
         const float4 cn = s_con[j];
@@ -595,7 +645,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (rel < (int)last[k]) {
-            const float dy = __fsub_rn((float)(ly + k * ROWS), xy.y);
+            const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
             const float p = blend_power(sx, bx, cn.z, dy);
             if (p >= kPMin) {
               const float G = ex2_approx(p);
@@ -605,11 +655,11 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
                 any = true;
                 const float4 cl = s_col[j];
                 T[k] = __fdividef(T[k], 1.f - al);
-                const float w = al * T[k];
-                acc[6] += w * gr[k];
-                acc[7] += w * gg[k];
-                acc[8] += w * gb[k];
-                acc[9] += w * gd[k];
+                const float wgt = al * T[k];
+                acc[6] += wgt * gr[k];
+                acc[7] += wgt * gg[k];
+                acc[8] += wgt * gb[k];
+                acc[9] += wgt * gd[k];
                 const float dal =
                     T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] + (cl.w - Sd[k]) * gd[k]);
                 Sr[k] = al * cl.x + (1.f - al) * Sr[k];

@@ -192,8 +192,9 @@ def test_launch_shapes_agree(ctx, tile, stage):
         _, _, r1, d1 = render(ctx, P, 3, cams)
     finally:
         dcg.dcg_set_launch(ctx, 16, 16, 128)
-    assert (r0 - r1).abs().max().item() <= 2e-6
-    assert ((d0 - d1).abs() / d0.abs().clamp(min=1)).max().item() <= 2e-6
+    # only the rounding of tile-local coordinates differs between launch shapes
+    assert (r0 - r1).abs().max().item() <= RGB_TOL
+    assert ((d0 - d1).abs() / d0.abs().clamp(min=1)).max().item() <= RGB_TOL
 
 
 def test_edge_cases(ctx0):
