@@ -365,45 +365,41 @@ struct TileLayout {
   static_assert(WPR * (TH / WY) == 8, "eight warp blocks per tile");
 };
 
-// Warp-coverage mask of a staged Gaussian: bit w set iff the box
-// |x - u| <= ex, |y - v| <= ey (tile-local, slightly enlarged) meets warp
-// block w.  ex, ey come from the FP32 conic the blend uses:
+// Does the box |x - u| <= ex, |y - v| <= ey (coordinates relative to the
+// warp block origin) meet the warp block [0, 7] x [0, WY-1]?  ex, ey come from
+// the FP32 conic the blend uses, slightly enlarged so that the test never
+// drops a Gaussian the per-pixel support test q <= 9 would keep:
 // Sigma'_xx = C / (A C - B^2) = -2 C' log2e / (4 A' C' - B'^2), same for yy.
-template <int TW, int TH>
-__device__ __forceinline__ unsigned warp_mask(float ul, float vl, float4 cn) {
-  using L = TileLayout<TW, TH>;
+template <int WY>
+__device__ __forceinline__ bool meets_block(float ub, float vb, float4 cn) {
   const float den = 4.f * cn.x * cn.z - cn.y * cn.y;
   const float sxx = -2.f * kLog2e * cn.z / den, syy = -2.f * kLog2e * cn.x / den;
   const float ex = 3.001f * sqrtf(fmaxf(sxx, 0.f)) + 0.01f;
   const float ey = 3.001f * sqrtf(fmaxf(syy, 0.f)) + 0.01f;
-  unsigned xm = 0, ym = 0;
-#pragma unroll
-  for (int i = 0; i < L::WPR; ++i)
-    if (ul + ex >= (float)(8 * i) && ul - ex <= (float)(8 * i + 7)) xm |= 1u << i;
-#pragma unroll
-  for (int i = 0; i < 8 / L::WPR; ++i)
-    if (vl + ey >= (float)(L::WY * i) && vl - ey <= (float)(L::WY * i + L::WY - 1)) ym |= 1u << i;
-  unsigned m = 0;
-#pragma unroll
-  for (int w = 0; w < 8; ++w)
-    if (((xm >> (w % L::WPR)) & 1u) && ((ym >> (w / L::WPR)) & 1u)) m |= 1u << w;
-  return m;
+  return ub + ex >= 0.f && ub - ex <= 7.f && vb + ey >= 0.f && vb - ey <= (float)(WY - 1);
 }
 
+// Forward blend.  One block per tile (taken from a device queue); each of
+// its 8 warps owns an 8 x WY pixel block and walks the tile's depth-sorted
+// list on its own: 32 instances per step, one per lane, are tested against
+// the warp block, survivors are compacted in order into a per-warp shared
+// buffer and blended by all lanes.  A warp stops when its pixels are done;
+// there is no block barrier inside a tile.
 template <int TW, int TH, int STAGE>
 __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __restrict__ inst, float* __restrict__ rgb,
                                                    float* __restrict__ dout) {
   using L = TileLayout<TW, TH>;
   constexpr int PPT = L::PPT;
-  __shared__ float2 s_xy[STAGE];
-  __shared__ float4 s_con[STAGE];
-  __shared__ float4 s_col[STAGE];
-  __shared__ unsigned char s_mask[STAGE];
+  __shared__ float2 s_xy[8][32];
+  __shared__ float4 s_con[8][32];
+  __shared__ float4 s_col[8][32];
+  __shared__ unsigned s_rel[8][32];
   __shared__ unsigned s_tile;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int lx = (w % L::WPR) * 8 + (lane & 7);
-  const int ly = (w / L::WPR) * L::WY + (lane >> 3);
-  const unsigned wbit = 1u << w;
+  const int bx0 = (w % L::WPR) * 8, by0 = (w / L::WPR) * L::WY;
+  const int lx = bx0 + (lane & 7);
+  const int ly = by0 + (lane >> 3);
+  const unsigned lt = lanemask_lt();
   for (;;) {
     __syncthreads();
     if (tid == 0) s_tile = atomicAdd(&a.counters->tile_queue, 1u);
@@ -421,6 +417,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
     uint32_t last[PPT];
     unsigned ev = 0;  // evaluations of (live pixel, Gaussian) pairs by this thread
     const int px = x0 + lx;
+    int alive = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const int py = y0 + ly + 4 * k;
@@ -428,63 +425,71 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
       Tf[k] = T[k];
       Cr[k] = Cg[k] = Cb[k] = Dz[k] = 0.f;
       last[k] = 0;
+      alive |= T[k] > 0.f;
     }
     const uint2 rg = a.ranges[gt];
-    for (unsigned b0 = rg.x; b0 < rg.y; b0 += STAGE) {
-      int alive = 0;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) alive |= (T[k] > 0.f);
-      if (__syncthreads_count(alive) == 0) break;
-      for (int j = tid; j < STAGE; j += 256) {
-        const unsigned idx = b0 + j;
-        if (idx < rg.y) {
-          const unsigned vi = (unsigned)inst[idx];
-          const float4 r0 = a.rec[3ull * vi + 0];
-          const float4 cn = a.rec[3ull * vi + 1];
-          const float ul = df_sub_round(r0.x, r0.z, x0f), vl = df_sub_round(r0.y, r0.w, y0f);
-          s_xy[j] = make_float2(ul, vl);
-          s_con[j] = cn;
-          s_col[j] = a.rec[3ull * vi + 2];
-          s_mask[j] = (unsigned char)warp_mask<TW, TH>(ul, vl, cn);
-        }
+    for (unsigned b0 = rg.x; b0 < rg.y && __any_sync(0xffffffffu, alive); b0 += 32) {
+      const unsigned idx = b0 + lane;
+      bool pass = false;
+      float ul = 0.f, vl = 0.f;
+      float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
+      unsigned vi = 0;
+      if (idx < rg.y) {
+        vi = (unsigned)inst[idx];
+        const float4 r0 = a.rec[3ull * vi + 0];
+        cn = a.rec[3ull * vi + 1];
+        ul = df_sub_round(r0.x, r0.z, x0f);
+        vl = df_sub_round(r0.y, r0.w, y0f);
+        pass = meets_block<L::WY>(ul - (float)bx0, vl - (float)by0, cn);
       }
-      __syncthreads();
-      const int cnt = min(STAGE, (int)(rg.y - b0));
-      if (__any_sync(0xffffffffu, alive)) {
-        for (int j = 0; j < cnt; ++j) {
-          if (!(s_mask[j] & wbit)) continue;
-          const float2 xy = s_xy[j];
-          const float4 cn = s_con[j];
-          const float dx = __fsub_rn((float)lx, xy.x);
-          const float sx = __fmul_rn(dx, __fmul_rn(cn.x, dx));
-          const float bx = __fmul_rn(cn.y, dx);
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) {
+        const int slot = __popc(m & lt);
+        s_xy[w][slot] = make_float2(ul, vl);
+        s_con[w][slot] = cn;
+        s_col[w][slot] = a.rec[3ull * vi + 2];
+        s_rel[w][slot] = idx - rg.x;
+      }
+      __syncwarp();
+      const int cnt = __popc(m);
+      for (int j = 0; j < cnt; ++j) {
+        const float2 xy = s_xy[w][j];
+        const float4 cq = s_con[w][j];
+        const float dx = __fsub_rn((float)lx, xy.x);
+        const float sx = __fmul_rn(dx, __fmul_rn(cq.x, dx));
+        const float bx = __fmul_rn(cq.y, dx);
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) {
+        for (int k = 0; k < PPT; ++k) {
+          if (T[k] > 0.f) {
+            ++ev;
             const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
-            const float p = blend_power(sx, bx, cn.z, dy);
-            ev += T[k] > 0.f;
-            if (T[k] > 0.f && p >= kPMin) {
-              const float al = fminf(kAlphaMax, __fmul_rn(cn.w, ex2_approx(p)));
+            const float p = blend_power(sx, bx, cq.z, dy);
+            if (p >= kPMin) {
+              const float al = fminf(kAlphaMax, __fmul_rn(cq.w, ex2_approx(p)));
               if (al >= kAlphaMin) {
                 const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, al));
                 if (Tn < kTMin) {
                   Tf[k] = T[k];
                   T[k] = 0.f;
                 } else {
-                  const float4 cl = s_col[j];
+                  const float4 cl = s_col[w][j];
                   const float wgt = al * T[k];
                   Cr[k] += wgt * cl.x;
                   Cg[k] += wgt * cl.y;
                   Cb[k] += wgt * cl.z;
                   Dz[k] += wgt * cl.w;
                   T[k] = Tn;
-                  last[k] = b0 - rg.x + j + 1;
+                  last[k] = s_rel[w][j] + 1;
                 }
               }
             }
           }
         }
       }
+      __syncwarp();
+      alive = 0;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) alive |= T[k] > 0.f;
     }
     {
       const unsigned wev = __reduce_add_sync(0xffffffffu, ev);
@@ -551,24 +556,32 @@ __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int* comp, bo
   return v[0];
 }
 
+// Backward blend.  One block per tile; the tile's list is cut into segments
+// of STAGE Gaussians taken from the end (last contributor) backwards.  Within
+// a segment every warp walks it on its own, 32 instances per step in reverse
+// order (filtered by the warp block and the warp's last contributor,
+// compacted with a ballot), recomputes transmittance by division and adds the
+// warp-reduced 2D gradients of each Gaussian into a block-shared accumulator;
+// at the end of the segment the accumulators go to global memory with one
+// set of vector atomics per Gaussian.
 template <int TW, int TH, int STAGE>
 __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __restrict__ inst,
                                                    const float* __restrict__ dL_drgb,
                                                    const float* __restrict__ dL_ddepth) {
   using L = TileLayout<TW, TH>;
   constexpr int PPT = L::PPT;
-  __shared__ float2 s_xy[STAGE];
-  __shared__ float4 s_con[STAGE];
-  __shared__ float4 s_col[STAGE];
-  __shared__ unsigned s_vi[STAGE];
-  __shared__ unsigned char s_mask[STAGE];
+  __shared__ float2 s_xy[8][32];
+  __shared__ float4 s_con[8][32];
+  __shared__ float4 s_col[8][32];
+  __shared__ unsigned s_rel[8][32];
   __shared__ float s_acc[STAGE][10];
   __shared__ unsigned s_tile;
   __shared__ unsigned s_maxlast;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int lx = (w % L::WPR) * 8 + (lane & 7);
-  const int ly = (w / L::WPR) * L::WY + (lane >> 3);
-  const unsigned wbit = 1u << w;
+  const int bx0 = (w % L::WPR) * 8, by0 = (w / L::WPR) * L::WY;
+  const int lx = bx0 + (lane & 7);
+  const int ly = by0 + (lane >> 3);
+  const unsigned lt = lanemask_lt();
   for (;;) {
     __syncthreads();
     if (tid == 0) {
@@ -608,93 +621,111 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
       Sr[k] = Sg[k] = Sb[k] = Sd[k] = 0.f;
       mylast = max(mylast, last[k]);
     }
-    const unsigned warplast = __reduce_max_sync(0xffffffffu, mylast);
-    if (lane == 0) atomicMax(&s_maxlast, warplast);
+    const int warplast = (int)__reduce_max_sync(0xffffffffu, mylast);
+    if (lane == 0) atomicMax(&s_maxlast, (unsigned)warplast);
     __syncthreads();
     const int maxlast = (int)s_maxlast;
     const uint2 rg = a.ranges[gt];
-    for (int bend = maxlast; bend > 0; bend -= STAGE) {
-      const int bstart = max(0, bend - STAGE);
-      const int cnt = bend - bstart;
-      for (int j = tid; j < cnt; j += 256) {
-        const unsigned vi = (unsigned)inst[rg.x + bstart + j];
-        const float4 r0 = a.rec[3ull * vi + 0];
-        const float4 cn = a.rec[3ull * vi + 1];
-        const float ul = df_sub_round(r0.x, r0.z, x0f), vl = df_sub_round(r0.y, r0.w, y0f);
-        s_xy[j] = make_float2(ul, vl);
-        s_con[j] = cn;
-        s_col[j] = a.rec[3ull * vi + 2];
-        s_vi[j] = vi;
-        s_mask[j] = (unsigned char)warp_mask<TW, TH>(ul, vl, cn);
-      }
-      for (int e = tid; e < cnt * 10; e += 256) (&s_acc[0][0])[e] = 0.f;
+    for (int send = maxlast; send > 0; send -= STAGE) {
+      const int sbeg = max(0, send - STAGE);
+      for (int e = tid; e < (send - sbeg) * 10; e += 256) (&s_acc[0][0])[e] = 0.f;
       __syncthreads();
-      const int jmax = min(cnt, (int)warplast - bstart);  // warp-uniform
-      for (int j = jmax - 1; j >= 0; --j) {
-        if (!(s_mask[j] & wbit)) continue;
-        const int rel = bstart + j;
-        const float2 xy = s_xy[j];
-        const float4 cn = s_con[j];
-        const float dx = __fsub_rn((float)lx, xy.x);
-        const float sx = __fmul_rn(dx, __fmul_rn(cn.x, dx));
-        const float bx = __fmul_rn(cn.y, dx);
-        float acc[10];
+      // this warp's part of the segment: relative indices [sbeg, min(send, warplast))
+      for (int hi = min(send, warplast); hi > sbeg; hi -= 32) {
+        const int rel = hi - 1 - lane;  // lane 0 takes the largest index: compaction keeps reverse order
+        bool pass = false;
+        float ul = 0.f, vl = 0.f;
+        float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
+        unsigned vi = 0;
+        if (rel >= sbeg) {
+          vi = (unsigned)inst[rg.x + rel];
+          const float4 r0 = a.rec[3ull * vi + 0];
+          cn = a.rec[3ull * vi + 1];
+          ul = df_sub_round(r0.x, r0.z, x0f);
+          vl = df_sub_round(r0.y, r0.w, y0f);
+          pass = meets_block<L::WY>(ul - (float)bx0, vl - (float)by0, cn);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (pass) {
+          const int slot = __popc(m & lt);
+          s_xy[w][slot] = make_float2(ul, vl);
+          s_con[w][slot] = cn;
+          s_col[w][slot] = a.rec[3ull * vi + 2];
+          s_rel[w][slot] = (unsigned)rel;
+        }
+        __syncwarp();
+        const int cnt = __popc(m);
+        for (int j = 0; j < cnt; ++j) {
+          const int r = (int)s_rel[w][j];
+          const float2 xy = s_xy[w][j];
+          const float4 cq = s_con[w][j];
+          const float dx = __fsub_rn((float)lx, xy.x);
+          const float sx = __fmul_rn(dx, __fmul_rn(cq.x, dx));
+          const float bx = __fmul_rn(cq.y, dx);
+          float acc[10];
 #pragma unroll
-        for (int q = 0; q < 10; ++q) acc[q] = 0.f;
-        bool any = false;
+          for (int q = 0; q < 10; ++q) acc[q] = 0.f;
+          bool any = false;
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-          if (rel < (int)last[k]) {
-            const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
-            const float p = blend_power(sx, bx, cn.z, dy);
-            if (p >= kPMin) {
-              const float G = ex2_approx(p);
-              const float araw = __fmul_rn(cn.w, G);
-              const float al = fminf(kAlphaMax, araw);
-              if (al >= kAlphaMin) {
-                any = true;
-                const float4 cl = s_col[j];
-                T[k] = __fdividef(T[k], 1.f - al);
-                const float wgt = al * T[k];
-                acc[6] += wgt * gr[k];
-                acc[7] += wgt * gg[k];
-                acc[8] += wgt * gb[k];
-                acc[9] += wgt * gd[k];
-                const float dal =
-                    T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] + (cl.w - Sd[k]) * gd[k]);
-                Sr[k] = al * cl.x + (1.f - al) * Sr[k];
-                Sg[k] = al * cl.y + (1.f - al) * Sg[k];
-                Sb[k] = al * cl.z + (1.f - al) * Sb[k];
-                Sd[k] = al * cl.w + (1.f - al) * Sd[k];
-                if (araw < kAlphaMax) {
-                  acc[5] += dal * G;
-                  const float dp = dal * cn.w * G * kLn2;
-                  acc[2] += dp * dx * dx;
-                  acc[3] += dp * dx * dy;
-                  acc[4] += dp * dy * dy;
-                  acc[0] -= dp * (2.f * cn.x * dx + cn.y * dy);
-                  acc[1] -= dp * (cn.y * dx + 2.f * cn.z * dy);
+          for (int k = 0; k < PPT; ++k) {
+            if (r < (int)last[k]) {
+              const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
+              const float p = blend_power(sx, bx, cq.z, dy);
+              if (p >= kPMin) {
+                const float G = ex2_approx(p);
+                const float araw = __fmul_rn(cq.w, G);
+                const float al = fminf(kAlphaMax, araw);
+                if (al >= kAlphaMin) {
+                  any = true;
+                  const float4 cl = s_col[w][j];
+                  T[k] = __fdividef(T[k], 1.f - al);
+                  const float wgt = al * T[k];
+                  acc[6] += wgt * gr[k];
+                  acc[7] += wgt * gg[k];
+                  acc[8] += wgt * gb[k];
+                  acc[9] += wgt * gd[k];
+                  const float dal = T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] +
+                                            (cl.w - Sd[k]) * gd[k]);
+                  Sr[k] = al * cl.x + (1.f - al) * Sr[k];
+                  Sg[k] = al * cl.y + (1.f - al) * Sg[k];
+                  Sb[k] = al * cl.z + (1.f - al) * Sb[k];
+                  Sd[k] = al * cl.w + (1.f - al) * Sd[k];
+                  if (araw < kAlphaMax) {
+                    acc[5] += dal * G;
+                    const float dp = dal * cq.w * G * kLn2;
+                    acc[2] += dp * dx * dx;
+                    acc[3] += dp * dx * dy;
+                    acc[4] += dp * dy * dy;
+                    acc[0] -= dp * (2.f * cq.x * dx + cq.y * dy);
+                    acc[1] -= dp * (cq.y * dx + 2.f * cq.z * dy);
+                  }
                 }
               }
             }
           }
+          if (__any_sync(0xffffffffu, any)) {
+            int comp;
+            bool has;
+            const float tot = warp_sum_transpose<10>(acc, &comp, &has);
+            if (has) atomicAdd(&s_acc[r - sbeg][comp], tot);
+          }
         }
-        if (__any_sync(0xffffffffu, any)) {
-          int comp;
-          bool has;
-          const float tot = warp_sum_transpose<10>(acc, &comp, &has);
-          if (has) atomicAdd(&s_acc[j][comp], tot);
-        }
+        __syncwarp();
       }
       __syncthreads();
-      for (int j = tid; j < cnt; j += 256) {
+      for (int j = tid; j < send - sbeg; j += 256) {
         const float* q = s_acc[j];
-        float4* gp = a.grad2d + 3ull * s_vi[j];
         const float4 g0 = make_float4(q[0], q[1], q[2], q[3]);
         const float4 g1 = make_float4(q[4], q[5], q[6], q[7]);
-        if (g0.x != 0.f || g0.y != 0.f || g0.z != 0.f || g0.w != 0.f) atomicAdd(gp + 0, g0);
-        if (g1.x != 0.f || g1.y != 0.f || g1.z != 0.f || g1.w != 0.f) atomicAdd(gp + 1, g1);
-        if (q[8] != 0.f || q[9] != 0.f) atomicAdd(reinterpret_cast<float2*>(gp + 2), make_float2(q[8], q[9]));
+        const bool n0 = g0.x != 0.f || g0.y != 0.f || g0.z != 0.f || g0.w != 0.f;
+        const bool n1 = g1.x != 0.f || g1.y != 0.f || g1.z != 0.f || g1.w != 0.f;
+        const bool n2 = q[8] != 0.f || q[9] != 0.f;
+        if (n0 || n1 || n2) {
+          float4* gp = a.grad2d + 3ull * (unsigned)inst[rg.x + sbeg + j];
+          if (n0) atomicAdd(gp + 0, g0);
+          if (n1) atomicAdd(gp + 1, g1);
+          if (n2) atomicAdd(reinterpret_cast<float2*>(gp + 2), make_float2(q[8], q[9]));
+        }
       }
       __syncthreads();
     }
