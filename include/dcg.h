@@ -249,6 +249,31 @@ dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, void* stream);
 dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, float* depth, int32_t* rect,
                           float* T_final, int32_t* n_contrib, void* stream);
 
+/* ---------------------------------------------------------------- cull without allocation
+ * The paper has no counterpart of this call; it exists for callers that
+ * cannot allocate device memory: programs whose device memory is owned by
+ * their own allocator or pool, or that run under a memory budget fixed in
+ * advance, and so can neither let the library call cudaMalloc nor create a
+ * dcg_ctx (whose creation allocates).
+ * Same result as dcg_cull_chunks for chunk cubes of side chunk_size with
+ * integer coordinates coords (dev, [n_chunks, 3] int32, any order; indices
+ * below refer to this order) and distance filter dfar: mask_out (dev,
+ * [n_views, n_chunks] u8, may be NULL), list_out (dev, capacity n_chunks)
+ * ascending indices visible in any view, *n_out (dev, one int32).
+ * Asynchronous on `stream`; cams is a host array (copied before return).
+ * Its scratch (camera table and per-chunk flags) is a fixed array in device
+ * memory that every GPU loading the library keeps until the process exits:
+ * at most 2^20 chunks and 16 views per call, larger requests return
+ * DCG_ERR_CAPACITY without doing anything.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the previous call's contents (the call clears what it needs), so
+ * calls that overlap on the GPU -- on different streams, or from different
+ * host threads -- race and must be serialised by the caller. */
+dcg_status dcg_cull_chunks_noalloc(const int32_t* coords, int32_t n_chunks, float chunk_size, float dfar,
+                                   const dcg_camera* cams, int32_t n_views, uint8_t* mask_out, int32_t* list_out,
+                                   int32_t* n_out, void* stream);
+
 /* ---------------------------------------------------------------- profiling
  * Optional per-phase device timers.  When enabled, every call records CUDA
  * events around its phases on the stream it runs on; dcg_profile_read

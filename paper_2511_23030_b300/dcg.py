@@ -83,6 +83,8 @@ _SIGS = {
     "dcg_state_evals": (ctypes.c_int, [_P, ctypes.POINTER(_I64), _P]),
     "dcg_profile_read": (ctypes.c_int, [_P, _P, _P]),
     "dcg_launch_count": (ctypes.c_uint64, []),
+    "dcg_cull_chunks_noalloc": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(dcg_camera),
+                                               _I32, _P, _P, _P, _P]),
 }
 
 PHASES = ["cull", "gather", "preprocess_fwd", "binning", "blend_fwd", "loss", "blend_bwd", "preprocess_bwd", "scatter"]
@@ -339,3 +341,12 @@ def dcg_autotune(ctx, g: dcg_gaussians, n: int, cams, rgb, depth, dL_drgb, dL_dd
     table = {f"{TUNE_TILES[i // 5][0]}x{TUNE_TILES[i // 5][1]}/{TUNE_STAGES[i % 5]}": round(float(ms[i]), 4)
              for i in range(15)}
     return {"tile": [tw.value, th.value], "stage": sg.value, "ms": table}
+
+
+def dcg_cull_chunks_noalloc(coords, chunk_size: float, dfar: float, cams, mask_out, list_out, n_out, stream=None):
+    """Allocation-free cull: coords (dev int32 [C,3]), outputs on the device."""
+    arr = make_cameras(cams)
+    st = lib().dcg_cull_chunks_noalloc(ptr(coords), int(coords.shape[0]), float(chunk_size), float(dfar), arr,
+                                       len(cams), ptr(mask_out), ptr(list_out), ptr(n_out), stream_ptr(stream))
+    if st != DCG_OK:
+        raise DcgError(st, "dcg_cull_chunks_noalloc failed")
