@@ -220,6 +220,25 @@ dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const
  * 32x32 pixels and 64..256 Gaussians staged per block batch. */
 dcg_status dcg_set_launch(dcg_ctx* ctx, int32_t tile_w, int32_t tile_h, int32_t stage);
 
+/* Batched keyframe window as one CUDA graph.  dcg_window_capture records,
+ * on `stream`, the forward render of all n_views views of `g`, the L1 loss
+ * of Eq. 2-4 against tgt_rgb / tgt_depth (lambda_depth for depth), and the
+ * backward to `grads` and dL_dpose, with every item count read from device
+ * memory, and instantiates the graph (replacing a previous one).
+ * dcg_window_run replays it on `stream` with the camera poses and
+ * intrinsics of `cams`; view count and image sizes, buffers, n and the launch
+ * shape must equal those of the capture (DCG_ERR_ARG otherwise).  *loss is
+ * zeroed by the graph.  The render state used is the context's default one. */
+dcg_status dcg_window_capture(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams,
+                              int32_t n_views, float* rgb, float* depth, const float* tgt_rgb, const float* tgt_depth,
+                              float lambda_depth, float* dL_drgb, float* dL_ddepth, float* loss,
+                              dcg_gaussians* grads, float* dL_dpose, void* stream);
+dcg_status dcg_window_run(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views, void* stream);
+
+/* Generation of a render state: incremented by every forward into it (a
+ * backward can tell whether the state still holds its forward). */
+int64_t dcg_state_generation(const dcg_render_state* st);
+
 /* Autotuner of the blend launch shape: times render_fwd + render_bwd of this
  * call (default state, `reps` repetitions after one warm-up, CUDA events on
  * `stream`) for every tile {16x16, 32x16, 32x32} x staging depth

@@ -114,6 +114,14 @@ struct dcg_ctx {
   DevCam* h_losscams = nullptr;
   cudaEvent_t ev_loss = nullptr;
   int fault = 0;
+  // captured window graph
+  cudaGraphExec_t win_exec = nullptr;
+  DevCam* h_wcams = nullptr;   // pinned camera staging read by the graph's copy node
+  cudaEvent_t ev_win = nullptr;
+  int win_V = 0;
+  int win_W[kMaxViewsApi] = {}, win_H[kMaxViewsApi] = {};
+  int win_launch[3] = {0, 0, 0};
+  unsigned long long win_kernels = 0;
   // profiler
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -339,6 +347,9 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
   cudaEventCreateWithFlags(&ctx->ev_compute, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ctx->ev_desc, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ctx->ev_loss, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_win, cudaEventDisableTiming);
+  if (cudaHostAlloc((void**)&ctx->h_wcams, sizeof(DevCam) * 2 * kMaxViewsApi, 0) != cudaSuccess)
+    return cleanup_fail(DCG_ERR_OOM);
   if (dmalloc(&ctx->d_losscams, kMaxViewsApi) != cudaSuccess ||
       cudaHostAlloc((void**)&ctx->h_losscams, sizeof(DevCam) * kMaxViewsApi, 0) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
@@ -401,6 +412,9 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   if (ctx->ev_compute) cudaEventDestroy(ctx->ev_compute);
   if (ctx->ev_desc) cudaEventDestroy(ctx->ev_desc);
   if (ctx->ev_loss) cudaEventDestroy(ctx->ev_loss);
+  if (ctx->win_exec) cudaGraphExecDestroy(ctx->win_exec);
+  if (ctx->h_wcams) cudaFreeHost(ctx->h_wcams);
+  if (ctx->ev_win) cudaEventDestroy(ctx->ev_win);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
   cudaFree(ctx->d_losscams);
   if (ctx->h_losscams) cudaFreeHost(ctx->h_losscams);
@@ -785,23 +799,13 @@ static void fill_args(dcg_render_state* st, RasterArgs& a) {
   a.prof = hook(ctx);
 }
 
-dcg_status dcg_render_fwd(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams, int32_t V,
-                          float* rgb, float* depth, dcg_render_state* st, void* stream) {
-  if (!ctx) return DCG_ERR_ARG;
-  if (!st) st = ctx->st0;
-  if (!g || n < 0 || (n > 0 && !g->data) || g->stride < n || g->sh_degree < 0 || g->sh_degree > 3 || !rgb || !depth)
-    return fail(ctx, DCG_ERR_ARG, "bad arguments");
-  dcg_status cs = check_cams(ctx, cams, V);
-  if (cs != DCG_OK) return cs;
-  if (n > st->cap_n) return fail(ctx, DCG_ERR_CAPACITY, "more Gaussians than max_active");
-  cudaStream_t s = (cudaStream_t)stream;
-  const int tw = ctx->tile_w, th = ctx->tile_h;
+static void fill_devcams(const dcg_camera* cams, int V, int tw, int th, DevCam* out, int64_t* pix_out,
+                         int* tiles_out) {
   int64_t pix = 0;
   int tiles = 0;
-  CK(cudaEventSynchronize(st->ev_cams));  // staging buffer free again
   for (int v = 0; v < V; ++v) {
     const dcg_camera& c = cams[v];
-    DevCam& d = st->h_cams[v];
+    DevCam& d = out[v];
     d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
     for (int r = 0; r < 3; ++r) {
       for (int k = 0; k < 3; ++k) d.R[3 * r + k] = c.Tcw[4 * r + k];
@@ -823,6 +827,25 @@ dcg_status dcg_render_fwd(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const
     tiles += d.ntx * d.nty;
     pix += (int64_t)c.W * c.H;
   }
+  *pix_out = pix;
+  *tiles_out = tiles;
+}
+
+dcg_status dcg_render_fwd(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams, int32_t V,
+                          float* rgb, float* depth, dcg_render_state* st, void* stream) {
+  if (!ctx) return DCG_ERR_ARG;
+  if (!st) st = ctx->st0;
+  if (!g || n < 0 || (n > 0 && !g->data) || g->stride < n || g->sh_degree < 0 || g->sh_degree > 3 || !rgb || !depth)
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  dcg_status cs = check_cams(ctx, cams, V);
+  if (cs != DCG_OK) return cs;
+  if (n > st->cap_n) return fail(ctx, DCG_ERR_CAPACITY, "more Gaussians than max_active");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int tw = ctx->tile_w, th = ctx->tile_h;
+  int64_t pix = 0;
+  int tiles = 0;
+  CK(cudaEventSynchronize(st->ev_cams));  // staging buffer free again
+  fill_devcams(cams, V, tw, th, st->h_cams, &pix, &tiles);
   if (pix > st->cap_pix || tiles > st->cap_tiles) return fail(ctx, DCG_ERR_CAPACITY, "pixel or tile capacity exceeded");
   CK(cudaMemcpyAsync(st->d_cams, st->h_cams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(st->ev_cams, s));
@@ -886,6 +909,102 @@ dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const
   CK(cudaGetLastError());
   return DCG_OK;
 }
+
+dcg_status dcg_window_capture(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams, int32_t V,
+                              float* rgb, float* depth, const float* trgb, const float* tdepth, float lam, float* dr,
+                              float* dd, float* loss, dcg_gaussians* grads, float* dL_dpose, void* stream) {
+  if (!ctx) return DCG_ERR_ARG;
+  dcg_render_state* st = ctx->st0;
+  if (!g || n < 0 || (n > 0 && !g->data) || g->stride < n || !rgb || !depth || !trgb || !tdepth || !dr || !dd ||
+      !loss || !grads || grads->stride < n || grads->sh_degree != g->sh_degree)
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  dcg_status cs = check_cams(ctx, cams, V);
+  if (cs != DCG_OK) return cs;
+  if (n > st->cap_n) return fail(ctx, DCG_ERR_CAPACITY, "more Gaussians than max_active");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int tw = ctx->tile_w, th = ctx->tile_h;
+  CK(cudaStreamSynchronize(s));
+  int64_t pix = 0;
+  int tiles = 0;
+  fill_devcams(cams, V, tw, th, ctx->h_wcams, &pix, &tiles);
+  if (pix > st->cap_pix || tiles > st->cap_tiles) return fail(ctx, DCG_ERR_CAPACITY, "pixel or tile capacity exceeded");
+  // loss cameras (pixel offsets) live in the second half of the staging buffer
+  DevCam* lc = ctx->h_wcams + kMaxViewsApi;
+  for (int v = 0; v < V; ++v) lc[v] = ctx->h_wcams[v];
+  st->g = *g;
+  st->n = n;
+  st->V = V;
+  st->n_pix = pix;
+  st->n_tiles = tiles;
+  st->tile_w = tw;
+  st->tile_h = th;
+  st->stage = ctx->stage;
+  st->idx_bits = 1;
+  while ((1ll << st->idx_bits) < n) ++st->idx_bits;
+  st->view_bits = 0;
+  while ((1 << st->view_bits) < V) ++st->view_bits;
+  RasterArgs a;
+  fill_args(st, a);
+  a.prof = ProfHook();
+  const bool prof = ctx->prof_on;
+  ctx->prof_on = false;
+  const unsigned long long l0 = g_launches;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaMemcpyAsync(st->d_cams, ctx->h_wcams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(ctx->d_losscams, lc, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(loss, 0, sizeof(float), s);
+  raster_forward(a, rgb, depth, &st->list_sorted, &st->inst_sorted, s);
+  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, lam, dr, dd, loss, ctx->num_sms, s);
+  raster_backward(a, st->inst_sorted, dr, dd, grads->data, grads->stride, dL_dpose, s);
+  const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  ctx->prof_on = prof;
+  ctx->win_kernels = g_launches - l0;
+  g_launches = l0;  // capture launches nothing; replays are counted in dcg_window_run
+  if (ce != cudaSuccess || !graph) return fail(ctx, DCG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+  if (ctx->win_exec) cudaGraphExecDestroy(ctx->win_exec);
+  ctx->win_exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&ctx->win_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return fail(ctx, DCG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ie));
+  ctx->win_V = V;
+  for (int v = 0; v < V; ++v) {
+    ctx->win_W[v] = cams[v].W;
+    ctx->win_H[v] = cams[v].H;
+  }
+  ctx->win_launch[0] = tw;
+  ctx->win_launch[1] = th;
+  ctx->win_launch[2] = ctx->stage;
+  st->valid = true;
+  st->gen++;
+  CK(cudaEventRecord(ctx->ev_win, s));
+  return DCG_OK;
+}
+
+dcg_status dcg_window_run(dcg_ctx* ctx, const dcg_camera* cams, int32_t V, void* stream) {
+  if (!ctx) return DCG_ERR_ARG;
+  if (!ctx->win_exec) return fail(ctx, DCG_ERR_STATE, "no captured window");
+  dcg_status cs = check_cams(ctx, cams, V);
+  if (cs != DCG_OK) return cs;
+  if (V != ctx->win_V) return fail(ctx, DCG_ERR_ARG, "view count differs from the capture");
+  for (int v = 0; v < V; ++v)
+    if (cams[v].W != ctx->win_W[v] || cams[v].H != ctx->win_H[v])
+      return fail(ctx, DCG_ERR_ARG, "image size differs from the capture");
+  if (ctx->tile_w != ctx->win_launch[0] || ctx->tile_h != ctx->win_launch[1] || ctx->stage != ctx->win_launch[2])
+    return fail(ctx, DCG_ERR_ARG, "launch shape changed since the capture");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaEventSynchronize(ctx->ev_win));  // the previous replay has read the camera staging
+  int64_t pix = 0;
+  int tiles = 0;
+  fill_devcams(cams, V, ctx->win_launch[0], ctx->win_launch[1], ctx->h_wcams, &pix, &tiles);
+  CK(cudaGraphLaunch(ctx->win_exec, s));
+  CK(cudaEventRecord(ctx->ev_win, s));
+  g_launches += ctx->win_kernels;
+  ctx->st0->gen++;
+  return DCG_OK;
+}
+
+int64_t dcg_state_generation(const dcg_render_state* st) { return st ? st->gen : -1; }
 
 dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams, int32_t V,
                         float* rgb, float* depth, const float* dr, const float* dd, dcg_gaussians* grads, int32_t reps,

@@ -23,6 +23,7 @@
 //                         per block in shared memory, then vector atomics
 //   9. k_preprocess_bwd   one thread per Gaussian, all views: chain rule to the
 //                         parameters (written once) and the pose twist of each view
+#include <algorithm>
 #include <cstdio>
 
 #include "device_scan.cuh"
@@ -183,9 +184,10 @@ __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, flo
 // ============================================================================
 // 1. preprocess
 // ============================================================================
+template <int DEG>
 __global__ void __launch_bounds__(256) k_preprocess_fwd(RasterArgs a) {
   const long long n = a.n;
-  const int D = (a.deg + 1) * (a.deg + 1);
+  constexpr int D = (DEG + 1) * (DEG + 1);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float* g = a.g;
     const long long S = a.stride;
@@ -261,11 +263,12 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(RasterArgs a) {
       const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
       dx *= il; dy *= il; dz *= il;
       float Y[16];
-      sh_basis(a.deg, dx, dy, dz, Y);
+      sh_basis(DEG, dx, dy, dz, Y);
       float col[3];
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.f;
+#pragma unroll
         for (int k = 0; k < D; ++k) acc += g[(11 + 3 * k + ch) * S + i] * Y[k];
         col[ch] = fmaxf(acc + 0.5f, 0.f);
       }
@@ -735,11 +738,17 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
 // ============================================================================
 // 9. preprocess backward
 // ============================================================================
-__global__ void __launch_bounds__(256) k_preprocess_bwd(RasterArgs a, float* __restrict__ out, long long ostride,
-                                                        float* __restrict__ dpose) {
+// 128 threads per block; the SH-coefficient gradients (3 (DEG+1)^2 per
+// Gaussian, summed over views) are accumulated in the thread's own column of
+// shared memory instead of registers.
+constexpr int kPreBwdThreads = 128;
+template <int DEG>
+__global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs a, float* __restrict__ out,
+                                                                   long long ostride, float* __restrict__ dpose) {
   const long long n = a.n;
-  const int D = (a.deg + 1) * (a.deg + 1);
-  const int F = 11 + 3 * D;
+  constexpr int D = (DEG + 1) * (DEG + 1);
+  __shared__ float s_gsh[3 * D][kPreBwdThreads];
+  float* gsh_col = &s_gsh[0][threadIdx.x];  // element k at gsh_col[k * kPreBwdThreads]
   const long long S = a.stride;
   // one pass over all threads of the grid; lanes past n still join the warp reductions
   const long long n_round = ((n + 31) / 32) * 32;
@@ -747,9 +756,8 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(RasterArgs a, float* __r
     const bool live = i < n;
     const float* g = a.g;
     float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.f;
-    float gsh[48];
 #pragma unroll
-    for (int k = 0; k < 48; ++k) gsh[k] = 0.f;
+    for (int k = 0; k < 3 * D; ++k) gsh_col[k * kPreBwdThreads] = 0.f;
     float mx = 0, my = 0, mz = 0, sc[3] = {1, 1, 1}, qn[4] = {1, 0, 0, 0}, qlen = 1.f, R[9], M[9], opac = 0.5f;
     float S00 = 0, S01 = 0, S02 = 0, S11 = 0, S12 = 0, S22 = 0;
     if (live) {
@@ -868,23 +876,28 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(RasterArgs a, float* __r
         const float il = 1.f / dist;
         dx *= il; dy *= il; dz *= il;
         float Y[16];
-        sh_basis(a.deg, dx, dy, dz, Y);
+        sh_basis(DEG, dx, dy, dz, Y);
         float wsum[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
+          float shc[D];
           float acc = 0.f;
-          for (int k = 0; k < D; ++k) acc += g[(11 + 3 * k + ch) * S + i] * Y[k];
-          if (acc + 0.5f < 0.f) continue;  // clamped channel
-          const float gc = dcol[ch];
+#pragma unroll
           for (int k = 0; k < D; ++k) {
-            gsh[3 * k + ch] += gc * Y[k];
-            wsum[k] += gc * g[(11 + 3 * k + ch) * S + i];
+            shc[k] = g[(11 + 3 * k + ch) * S + i];
+            acc += shc[k] * Y[k];
+          }
+          const float gc = (acc + 0.5f < 0.f) ? 0.f : dcol[ch];  // no gradient through a clamped channel
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            gsh_col[(3 * k + ch) * kPreBwdThreads] += gc * Y[k];
+            wsum[k] += gc * shc[k];
           }
         }
         float gdir[3] = {0, 0, 0};
-        sh_grad_acc(a.deg, dx, dy, dz, wsum, gdir);
+        sh_grad_acc(DEG, dx, dy, dz, wsum, gdir);
         const float dd = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
         const float gmu_sh[3] = {(gdir[0] - dx * dd) * il, (gdir[1] - dy * dd) * il, (gdir[2] - dz * dd) * il};
         // mean: t = W mu + t_cw
@@ -951,8 +964,8 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(RasterArgs a, float* __r
     out[8 * ostride + i] = gq[2];
     out[9 * ostride + i] = gq[3];
     out[10 * ostride + i] = go;
-    for (int k = 0; k < 3 * D; ++k) out[(11 + k) * ostride + i] = gsh[k];
-    (void)F;
+#pragma unroll
+    for (int k = 0; k < 3 * D; ++k) out[(11 + k) * ostride + i] = gsh_col[k * kPreBwdThreads];
   }
 }
 
@@ -998,7 +1011,13 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   const long long pairs = (long long)a.V * a.n;
   a.prof(PH_PRE_FWD, true, st);
   if (a.n > 0) {
-    k_preprocess_fwd<<<grid_for(a.n, a.num_sms), 256, 0, st>>>(a);
+    const int gr = grid_for(a.n, a.num_sms);
+    switch (a.deg) {
+      case 0: k_preprocess_fwd<0><<<gr, 256, 0, st>>>(a); break;
+      case 1: k_preprocess_fwd<1><<<gr, 256, 0, st>>>(a); break;
+      case 2: k_preprocess_fwd<2><<<gr, 256, 0, st>>>(a); break;
+      default: k_preprocess_fwd<3><<<gr, 256, 0, st>>>(a); break;
+    }
     count_launch();
   }
   a.prof(PH_PRE_FWD, false, st);
@@ -1041,7 +1060,13 @@ void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb
   a.prof(PH_BLEND_BWD, false, st);
   a.prof(PH_PRE_BWD, true, st);
   if (a.n > 0) {
-    k_preprocess_bwd<<<grid_for(a.n, a.num_sms), 256, 0, st>>>(a, grads, g_stride, dL_dpose);
+    const int gr = (int)std::min<long long>((a.n + kPreBwdThreads - 1) / kPreBwdThreads, (long long)a.num_sms * 16);
+    switch (a.deg) {
+      case 0: k_preprocess_bwd<0><<<gr, kPreBwdThreads, 0, st>>>(a, grads, g_stride, dL_dpose); break;
+      case 1: k_preprocess_bwd<1><<<gr, kPreBwdThreads, 0, st>>>(a, grads, g_stride, dL_dpose); break;
+      case 2: k_preprocess_bwd<2><<<gr, kPreBwdThreads, 0, st>>>(a, grads, g_stride, dL_dpose); break;
+      default: k_preprocess_bwd<3><<<gr, kPreBwdThreads, 0, st>>>(a, grads, g_stride, dL_dpose); break;
+    }
     count_launch();
   }
   a.prof(PH_PRE_BWD, false, st);

@@ -83,6 +83,11 @@ _SIGS = {
     "dcg_state_evals": (ctypes.c_int, [_P, ctypes.POINTER(_I64), _P]),
     "dcg_profile_read": (ctypes.c_int, [_P, _P, _P]),
     "dcg_launch_count": (ctypes.c_uint64, []),
+    "dcg_window_capture": (ctypes.c_int, [_P, ctypes.POINTER(dcg_gaussians), _I64, ctypes.POINTER(dcg_camera), _I32,
+                                          _P, _P, _P, _P, ctypes.c_float, _P, _P, _P, ctypes.POINTER(dcg_gaussians),
+                                          _P, _P]),
+    "dcg_window_run": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _I32, _P]),
+    "dcg_state_generation": (_I64, [_P]),
     "dcg_cull_chunks_noalloc": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(dcg_camera),
                                                _I32, _P, _P, _P, _P]),
 }
@@ -350,3 +355,20 @@ def dcg_cull_chunks_noalloc(coords, chunk_size: float, dfar: float, cams, mask_o
                                        len(cams), ptr(mask_out), ptr(list_out), ptr(n_out), stream_ptr(stream))
     if st != DCG_OK:
         raise DcgError(st, "dcg_cull_chunks_noalloc failed")
+
+
+def dcg_window_capture(ctx, g: dcg_gaussians, n: int, cams, rgb, depth, tgt_rgb, tgt_depth, lam, dL_drgb, dL_ddepth,
+                       loss, grads: dcg_gaussians, dL_dpose=None, stream=None):
+    arr = make_cameras(cams)
+    check(ctx, lib().dcg_window_capture(ctx, ctypes.byref(g), n, arr, len(cams), ptr(rgb), ptr(depth), ptr(tgt_rgb),
+                                        ptr(tgt_depth), float(lam), ptr(dL_drgb), ptr(dL_ddepth), ptr(loss),
+                                        ctypes.byref(grads), ptr(dL_dpose), stream_ptr(stream)))
+
+
+def dcg_window_run(ctx, cams, stream=None):
+    arr = make_cameras(cams)
+    check(ctx, lib().dcg_window_run(ctx, arr, len(cams), stream_ptr(stream)))
+
+
+def dcg_state_generation(state) -> int:
+    return int(lib().dcg_state_generation(state))

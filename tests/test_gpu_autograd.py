@@ -1,0 +1,126 @@
+"""torch.autograd.Function around the renderer: central finite differences of
+the L1 RGB + 0.1 L1 depth loss on 64 sampled parameters of the indoor room
+(FP32 renders, h = 1e-3), the pose twist, recompute == stored, and equality
+with the direct C-ABI backward."""
+import numpy as np
+import pytest
+
+from paper_2511_23030_b300 import dcg, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(n=500_000):
+    import torch
+
+    from paper_2511_23030_b300.autograd import Renderer
+
+    sc = synth.room_indoor(0, n=n, n_steps=1)
+    P, cam = sc["params"], sc["cams"][0]
+    params = torch.from_numpy(np.ascontiguousarray(P.T)).cuda()
+    tr = torch.from_numpy(sc["target_rgb"][0].reshape(-1)).cuda()
+    td = torch.from_numpy(sc["target_depth"][0].reshape(-1)).cuda()
+    r = Renderer(3, n, max_views=1, max_pixels=cam.W * cam.H)
+    return sc, cam, params, tr, td, r
+
+
+def _loss(rgb, depth, tr, td):
+    P = depth.numel()
+    return (rgb.double() - tr.double()).abs().sum() / (3 * P) + 0.1 * (depth.double() - td.double()).abs().sum() / P
+
+
+def test_autograd_matches_finite_differences():
+    import torch
+
+    from paper_2511_23030_b300.autograd import render
+
+    sc, cam, params, tr, td, r = _setup()
+    try:
+        p = params.clone().requires_grad_(True)
+        xi = torch.zeros(1, 6, device="cuda", requires_grad=True)
+        rgb, depth = render(r, p, xi, [cam])
+        L = _loss(rgb, depth, tr, td)
+        L.backward()
+        g = p.grad.detach().cpu().numpy()
+        rng = np.random.default_rng(0)
+        # sample 64 (component, Gaussian) entries among the visible, non-negligible ones
+        mag = np.abs(g)
+        cand = np.argwhere(mag > np.quantile(mag[mag > 0], 0.9))
+        pick = cand[rng.choice(len(cand), 64, replace=False)]
+        errs = []
+        with torch.no_grad():
+            for c, i in pick:
+                h = 1e-3
+                old = params[c, i].item()
+                params[c, i] = old + h
+                Lp = _loss(*render(r, params, xi.detach(), [cam]), tr, td).item()
+                params[c, i] = old - h
+                Lm = _loss(*render(r, params, xi.detach(), [cam]), tr, td).item()
+                params[c, i] = old
+                fd = (Lp - Lm) / (2 * h)
+                errs.append(abs(fd - g[c, i]) / abs(g[c, i]))
+        errs = np.array(errs)
+        assert np.median(errs) < 1e-2, errs
+        assert (errs < 5e-2).sum() >= 60, errs
+        # pose twist: Tcw <- exp(xi^) Tcw
+        from scipy.linalg import expm
+
+        gx = xi.grad.detach().cpu().numpy()[0]
+        T0 = np.asarray(cam.Tcw, np.float64)
+        for k in range(6):
+            h = 1e-4 if k >= 3 else 1e-3
+            Ls = []
+            for sgn in (1, -1):
+                e = np.zeros(6)
+                e[k] = sgn * h
+                X = np.zeros((4, 4))
+                w = e[3:]
+                X[:3, :3] = [[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]]
+                X[:3, 3] = e[:3]
+                c2 = synth.Camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.W, cam.H, (expm(X) @ T0).astype(np.float32),
+                                  cam.znear, cam.zfar)
+                with torch.no_grad():
+                    Ls.append(_loss(*render(r, params, xi.detach(), [c2]), tr, td).item())
+            fd = (Ls[0] - Ls[1]) / (2 * h)
+            assert abs(fd - gx[k]) <= 5e-2 * abs(gx[k]) + 1e-6, (k, fd, gx[k])
+    finally:
+        r.close()
+
+
+def test_recompute_equals_stored_and_direct_call():
+    import torch
+
+    from paper_2511_23030_b300.autograd import render
+
+    sc, cam, params, tr, td, r = _setup(n=100_000)
+    try:
+        grads = []
+        for recompute, interleave in ((False, False), (True, False), (False, True)):
+            r.recompute = recompute
+            p = params.clone().requires_grad_(True)
+            xi = torch.zeros(1, 6, device="cuda", requires_grad=True)
+            rgb, depth = render(r, p, xi, [cam])
+            if interleave:  # another forward overwrites the state: the backward must recompute
+                other = params.clone()
+                other[0] += 0.5
+                render(r, other, xi.detach(), [cam])
+            _loss(rgb, depth, tr, td).backward()
+            grads.append((p.grad.clone(), xi.grad.clone()))
+        for gp, gx in grads[1:]:
+            assert ((gp - grads[0][0]).norm() / grads[0][0].norm()).item() <= 1e-5
+            assert ((gx - grads[0][1]).norm() / grads[0][1].norm()).item() <= 1e-5
+        # the direct C-ABI backward with the same seed
+        r.recompute = False
+        p = params.clone().requires_grad_(True)
+        rgb, depth = render(r, p, torch.zeros(1, 6, device="cuda"), [cam])
+        seed_r = torch.randn_like(rgb)
+        seed_d = torch.randn_like(depth)
+        (rgb * seed_r).sum().add((depth * seed_d).sum()).backward()
+        g2 = torch.zeros_like(params)
+        dcg.dcg_render_fwd(r.ctx, dcg.gaussians(params, 3), params.shape[1], [cam], torch.empty_like(rgb),
+                           torch.empty_like(depth), r.state)
+        dcg.dcg_render_bwd(r.ctx, seed_r, seed_d, dcg.gaussians(g2, 3), None, r.state)
+        dcg.dcg_sync(r.ctx)
+        assert ((p.grad - g2).norm() / g2.norm()).item() <= 1e-5
+    finally:
+        r.close()
