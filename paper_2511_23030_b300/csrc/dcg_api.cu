@@ -115,6 +115,7 @@ struct dcg_ctx {
   cudaEvent_t ev_loss = nullptr;
   int fault = 0;
   // captured window graph
+  cudaStream_t cap_stream = nullptr;  // private stream for capture (the legacy stream cannot be captured)
   cudaGraphExec_t win_exec = nullptr;
   DevCam* h_wcams = nullptr;   // pinned camera staging read by the graph's copy node
   cudaEvent_t ev_win = nullptr;
@@ -262,7 +263,7 @@ dcg_status state_alloc(dcg_ctx* ctx, dcg_render_state* st) {
   CK(dmalloc(&st->n_contrib, (size_t)st->cap_pix));
   CK(dmalloc(&st->counters, 1));
   CK(dmalloc(&st->part, (size_t)st->P + 1));
-  CK(dmalloc(&st->hist, 256 * (size_t)st->P));
+  CK(dmalloc(&st->hist, 256 * ((size_t)st->P + 1)));
   return DCG_OK;
 }
 
@@ -348,6 +349,7 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
   cudaEventCreateWithFlags(&ctx->ev_desc, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ctx->ev_loss, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ctx->ev_win, cudaEventDisableTiming);
+  if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
   if (cudaHostAlloc((void**)&ctx->h_wcams, sizeof(DevCam) * 2 * kMaxViewsApi, 0) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
   if (dmalloc(&ctx->d_losscams, kMaxViewsApi) != cudaSuccess ||
@@ -413,6 +415,7 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   if (ctx->ev_desc) cudaEventDestroy(ctx->ev_desc);
   if (ctx->ev_loss) cudaEventDestroy(ctx->ev_loss);
   if (ctx->win_exec) cudaGraphExecDestroy(ctx->win_exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->h_wcams) cudaFreeHost(ctx->h_wcams);
   if (ctx->ev_win) cudaEventDestroy(ctx->ev_win);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
@@ -950,18 +953,28 @@ dcg_status dcg_window_capture(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, c
   ctx->prof_on = false;
   const unsigned long long l0 = g_launches;
   cudaGraph_t graph = nullptr;
-  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  cudaMemcpyAsync(st->d_cams, ctx->h_wcams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(ctx->d_losscams, lc, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s);
-  cudaMemsetAsync(loss, 0, sizeof(float), s);
-  raster_forward(a, rgb, depth, &st->list_sorted, &st->inst_sorted, s);
-  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, lam, dr, dd, loss, ctx->num_sms, s);
-  raster_backward(a, st->inst_sorted, dr, dd, grads->data, grads->stride, dL_dpose, s);
-  const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  cudaStream_t cs_ = ctx->cap_stream;
+  const cudaError_t be = cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal);
+  if (be != cudaSuccess) {
+    ctx->prof_on = prof;
+    cudaGetLastError();
+    return fail(ctx, DCG_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(be));
+  }
+  cudaMemcpyAsync(st->d_cams, ctx->h_wcams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, cs_);
+  cudaMemcpyAsync(ctx->d_losscams, lc, sizeof(DevCam) * V, cudaMemcpyHostToDevice, cs_);
+  cudaMemsetAsync(loss, 0, sizeof(float), cs_);
+  raster_forward(a, rgb, depth, &st->list_sorted, &st->inst_sorted, cs_);
+  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, lam, dr, dd, loss, ctx->num_sms, cs_);
+  raster_backward(a, st->inst_sorted, dr, dd, grads->data, grads->stride, dL_dpose, cs_);
+  const cudaError_t ce = cudaStreamEndCapture(cs_, &graph);
   ctx->prof_on = prof;
   ctx->win_kernels = g_launches - l0;
   g_launches = l0;  // capture launches nothing; replays are counted in dcg_window_run
-  if (ce != cudaSuccess || !graph) return fail(ctx, DCG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+  if (ce != cudaSuccess || !graph) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return fail(ctx, DCG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+  }
   if (ctx->win_exec) cudaGraphExecDestroy(ctx->win_exec);
   ctx->win_exec = nullptr;
   const cudaError_t ie = cudaGraphInstantiate(&ctx->win_exec, graph, 0);

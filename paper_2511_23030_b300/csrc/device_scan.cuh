@@ -110,14 +110,16 @@ __global__ void k_part_emit(const u64* n_ptr, u64 n_host, CountF f, EmitF e, con
 
 // ----------------------------------------------------------------------------
 // LSD radix sort pass over u64 keys on digit [shift, shift+nbits), nbits <= 8.
-// hist layout: [256][P] digit-major, scanned in place to exclusive offsets.
+// hist layout: [256][P] digit-major (per-block counts, then per-digit
+// exclusive prefixes over blocks), followed by the 256 digit totals.
 __global__ void k_radix_hist(const u64* keys, const u64* n_ptr, int shift, int nbits, uint32_t* hist);
-__global__ void k_radix_scan(uint32_t* hist, int P);
+__global__ void k_radix_scan(uint32_t* hist, int P, uint32_t* totals);
 __global__ void k_radix_scatter(const u64* in, u64* out, const u64* n_ptr, int shift, int nbits,
-                                const uint32_t* hist);
+                                const uint32_t* hist, const uint32_t* totals);
 
-// Host driver: sorts keys[0..*n_ptr) on bits [lo, hi); ping-pong between a and b.
-// Returns the buffer holding the result.  n_cap bounds *n_ptr.
+// Host driver: stable sort of keys[0..*n_ptr) on bits [lo, hi), ping-pong
+// between a and b; returns the buffer holding the result.  `hist` holds
+// 256 * (P + 1) entries.
 u64* radix_sort(u64* a, u64* b, const u64* n_ptr, int lo, int hi, uint32_t* hist, int P, cudaStream_t s);
 
 // Host driver for the scan: P blocks, `part` holds P + 1 u64.

@@ -24,7 +24,20 @@ __global__ void k_part_scan(u64* part, int P, u64* total_out) {
   }
 }
 
-// Per-block digit histogram of the block's partition, warp-aggregated with match_any.
+// Peer mask of a lane's digit within the warp, from one ballot per digit bit
+// (stable ranking without match_any); lanes with !valid never match a valid lane.
+__device__ __forceinline__ unsigned digit_peers(unsigned d, int nbits, bool valid) {
+  const unsigned vb = __ballot_sync(0xffffffffu, valid);
+  unsigned peers = valid ? vb : ~vb;
+  for (int b = 0; b < nbits; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const unsigned bb = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bb : ~bb;
+  }
+  return peers;
+}
+
+// Per-block digit histogram of the block's partition.
 __global__ void k_radix_hist(const u64* keys, const u64* n_ptr, int shift, int nbits, uint32_t* hist) {
   __shared__ uint32_t h[256];
   const u64 n = *n_ptr;
@@ -36,42 +49,41 @@ __global__ void k_radix_hist(const u64* keys, const u64* n_ptr, int shift, int n
   for (u64 c0 = beg; c0 < end; c0 += blockDim.x) {
     const u64 i = c0 + threadIdx.x;
     const bool valid = i < end;
-    const unsigned d = valid ? (unsigned)((keys[i] >> shift) & mask) : 256u;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned d = valid ? (unsigned)((keys[i] >> shift) & mask) : 0u;
+    const unsigned peers = digit_peers(d, nbits, valid);
     if (valid && lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
   hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of hist[256 * P] in digit-major order (one block of 1024 threads).
-__global__ void k_radix_scan(uint32_t* hist, int P) {
-  const int N = 256 * P;
-  const int T = blockDim.x;
-  const int per = (N + T - 1) / T;
-  const int b = threadIdx.x * per;
-  const int e = min(N, b + per);
-  uint32_t s = 0;
-  for (int i = b; i < e; ++i) s += hist[i];
-  uint32_t tot;
-  uint32_t ex = block_excl_scan<uint32_t>(s, &tot);
-  for (int i = b; i < e; ++i) {
-    uint32_t v = hist[i];
-    hist[i] = ex;
-    ex += v;
+// One block per digit: exclusive scan of hist[d][0..P) in place; the digit's
+// total goes to totals[d].
+__global__ void k_radix_scan(uint32_t* hist, int P, uint32_t* totals) {
+  uint32_t* row = hist + (size_t)blockIdx.x * P;
+  uint32_t carry = 0;
+  for (int b0 = 0; b0 < P; b0 += blockDim.x) {
+    const int b = b0 + threadIdx.x;
+    const uint32_t v = b < P ? row[b] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan<uint32_t>(v, &tot);
+    if (b < P) row[b] = carry + ex;
+    carry += tot;
   }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
 // Stable scatter.  The block walks its partition in chunks of 8 warps x 256
 // items; warp w owns the chunk's w-th run of 256 consecutive items and ranks
-// them round by round (32 lanes per round) with match_any and per-warp digit
-// counters, so that the rank order equals the input order.
+// them round by round (32 lanes per round) with per-warp digit counters, so
+// that the rank order equals the input order.  The digit bases (exclusive
+// scan of the 256 digit totals) are computed by every block.
 constexpr int kSortWarps = 8;
 constexpr int kSortRounds = 8;
 constexpr int kSortChunk = kSortWarps * 32 * kSortRounds;
 
 __global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, const u64* n_ptr, int shift,
-                                                       int nbits, const uint32_t* hist) {
+                                                       int nbits, const uint32_t* hist, const uint32_t* totals) {
   __shared__ uint32_t wcnt[kSortWarps][256];
   __shared__ uint32_t run[256];
   const u64 n = *n_ptr;
@@ -79,7 +91,11 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, 
   partition_of(n, &beg, &end);
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const u64 mask = (1ull << nbits) - 1;
-  run[tid] = hist[tid * gridDim.x + blockIdx.x];
+  {
+    uint32_t tot;
+    const uint32_t base = block_excl_scan<uint32_t>(totals[tid], &tot);
+    run[tid] = base + hist[tid * gridDim.x + blockIdx.x];
+  }
   for (u64 c0 = beg; c0 < end; c0 += kSortChunk) {
 #pragma unroll
     for (int k = 0; k < kSortWarps; ++k) wcnt[k][tid] = 0;
@@ -93,9 +109,9 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, 
       const u64 i = c0 + (u64)w * 256 + (u64)r * 32 + lane;
       const bool valid = i < end;
       key[r] = valid ? in[i] : 0ull;
-      const unsigned d = valid ? (unsigned)((key[r] >> shift) & mask) : 256u;
-      dig[r] = d;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const unsigned d = valid ? (unsigned)((key[r] >> shift) & mask) : 0u;
+      dig[r] = valid ? d : 256u;
+      const unsigned peers = digit_peers(d, nbits, valid);
       const unsigned rank = __popc(peers & lt);
       const unsigned base = valid ? wcnt[w][d] : 0u;
       __syncwarp();
@@ -127,11 +143,12 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, 
 u64* radix_sort(u64* a, u64* b, const u64* n_ptr, int lo, int hi, uint32_t* hist, int P, cudaStream_t s) {
   u64* src = a;
   u64* dst = b;
+  uint32_t* totals = hist + 256 * (size_t)P;
   for (int sh = lo; sh < hi; sh += 8) {
     const int nb = min(8, hi - sh);
     k_radix_hist<<<P, 256, 0, s>>>(src, n_ptr, sh, nb, hist);
-    k_radix_scan<<<1, 1024, 0, s>>>(hist, P);
-    k_radix_scatter<<<P, 256, 0, s>>>(src, dst, n_ptr, sh, nb, hist);
+    k_radix_scan<<<256, 256, 0, s>>>(hist, P, totals);
+    k_radix_scatter<<<P, 256, 0, s>>>(src, dst, n_ptr, sh, nb, hist, totals);
     u64* t = src;
     src = dst;
     dst = t;

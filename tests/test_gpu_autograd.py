@@ -47,21 +47,35 @@ def test_autograd_matches_finite_differences():
         mag = np.abs(g)
         cand = np.argwhere(mag > np.quantile(mag[mag > 0], 0.9))
         pick = cand[rng.choice(len(cand), 64, replace=False)]
-        errs = []
+        names = ["mean"] * 3 + ["log_scale"] * 3 + ["quat"] * 4 + ["opacity"] + ["sh"] * 48
+
+        def fd_at(c, i, h):
+            old = params[c, i].item()
+            params[c, i] = old + h
+            Lp = _loss(*render(r, params, xi.detach(), [cam]), tr, td).item()
+            params[c, i] = old - h
+            Lm = _loss(*render(r, params, xi.detach(), [cam]), tr, td).item()
+            params[c, i] = old
+            return (Lp - Lm) / (2 * h)
+
+        # The loss is piecewise smooth: L1 kinks and the alpha / support /
+        # transmittance cut-offs make it jump where a pixel crosses one.  A
+        # difference quotient that straddles a jump is not a derivative; such
+        # samples show up as disagreeing quotients at h and 2h and are set aside.
+        errs, kinds, skipped = [], [], 0
         with torch.no_grad():
             for c, i in pick:
-                h = 1e-3
-                old = params[c, i].item()
-                params[c, i] = old + h
-                Lp = _loss(*render(r, params, xi.detach(), [cam]), tr, td).item()
-                params[c, i] = old - h
-                Lm = _loss(*render(r, params, xi.detach(), [cam]), tr, td).item()
-                params[c, i] = old
-                fd = (Lp - Lm) / (2 * h)
-                errs.append(abs(fd - g[c, i]) / abs(g[c, i]))
+                f1, f2 = fd_at(c, i, 1e-3), fd_at(c, i, 2e-3)
+                if abs(f1 - f2) > 0.02 * max(abs(f1), abs(f2)):
+                    skipped += 1
+                    continue
+                errs.append(abs(f1 - g[c, i]) / abs(g[c, i]))
+                kinds.append(names[c])
         errs = np.array(errs)
-        assert np.median(errs) < 1e-2, errs
-        assert (errs < 5e-2).sum() >= 60, errs
+        report = sorted(zip(errs.round(5).tolist(), kinds), reverse=True)[:8]
+        assert skipped <= 16, (skipped, report)
+        assert np.median(errs) < 1e-2, report
+        assert (errs < 2e-2).mean() >= 0.95, report
         # pose twist: Tcw <- exp(xi^) Tcw
         from scipy.linalg import expm
 
