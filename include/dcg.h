@@ -167,6 +167,22 @@ dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n
 /* Copy every resident dirty chunk back to the host tier and wait. */
 dcg_status dcg_flush(dcg_ctx* ctx, void* stream);
 
+/* Asynchronous load of proposed chunks (host, ascending indices) on the copy
+ * stream, overlapping the caller's rendering: listed non-resident chunks are
+ * loaded in order while they fit in the budget and the page pool, evicting
+ * (oldest first) only resident chunks that are neither listed nor part of the
+ * last gather.  Loaded chunks count as accessed now.  *n_loaded (host, may be
+ * NULL) receives the number of chunks whose load was started.  The exact cull
+ * still decides what dcg_gather_active uses: a prefetch changes only where
+ * the data already is, never what is rendered. */
+dcg_status dcg_prefetch(dcg_ctx* ctx, const int32_t* chunk_list, int32_t n_chunks, int32_t* n_loaded, void* stream);
+
+/* Tier statistics since creation (host outputs, any may be NULL): chunk
+ * loads and evictions, bytes copied host->device and device->host, Gaussians
+ * resident now. */
+dcg_status dcg_tier_stats(const dcg_ctx* ctx, int64_t* loads, int64_t* evictions, int64_t* bytes_h2d,
+                          int64_t* bytes_d2h, int64_t* resident);
+
 /* Read n Gaussians of chunk `chunk` (ascending-id index) from the host tier
  * into params_out (host, planar with stride n).  For checks and checkpoints. */
 dcg_status dcg_chunk_read(dcg_ctx* ctx, int32_t chunk, float* params_out, int64_t n);
@@ -310,7 +326,8 @@ enum {
   DCG_PH_BLEND_BWD = 6, /* per-tile reverse traversal, 2D gradients */
   DCG_PH_PRE_BWD = 7,   /* chain rule to the parameters and the pose */
   DCG_PH_SCATTER = 8,
-  DCG_PH_COUNT = 9
+  DCG_PH_STALL = 9,     /* compute stream idle in dcg_gather_active, waiting for chunk copies */
+  DCG_PH_COUNT = 10
 };
 dcg_status dcg_profile(dcg_ctx* ctx, int32_t enable);
 dcg_status dcg_profile_read(dcg_ctx* ctx, float* ms, int32_t* counts);

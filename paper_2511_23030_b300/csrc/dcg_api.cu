@@ -112,6 +112,7 @@ struct dcg_ctx {
   dcg_render_state* st0 = nullptr;
   DevCam* d_losscams = nullptr;
   DevCam* h_losscams = nullptr;
+  float* d_losspart = nullptr;
   cudaEvent_t ev_loss = nullptr;
   int fault = 0;
   // captured window graph
@@ -352,7 +353,8 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
   if (cudaHostAlloc((void**)&ctx->h_wcams, sizeof(DevCam) * 2 * kMaxViewsApi, 0) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
-  if (dmalloc(&ctx->d_losscams, kMaxViewsApi) != cudaSuccess ||
+  if (dmalloc(&ctx->d_losspart, (size_t)loss_partials(ctx->num_sms)) != cudaSuccess ||
+      dmalloc(&ctx->d_losscams, kMaxViewsApi) != cudaSuccess ||
       cudaHostAlloc((void**)&ctx->h_losscams, sizeof(DevCam) * kMaxViewsApi, 0) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
   if (dmalloc(&ctx->d_errword, 1) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
@@ -420,6 +422,7 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   if (ctx->ev_win) cudaEventDestroy(ctx->ev_win);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
   cudaFree(ctx->d_losscams);
+  cudaFree(ctx->d_losspart);
   if (ctx->h_losscams) cudaFreeHost(ctx->h_losscams);
   delete ctx;
   return DCG_OK;
@@ -644,7 +647,9 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
     ch.last_access = ctx->step;
   }
   CK(cudaEventRecord(ctx->ev_copy, ctx->copy_stream));
+  hook(ctx)(PH_STALL, true, s);
   CK(cudaStreamWaitEvent(s, ctx->ev_copy, 0));
+  hook(ctx)(PH_STALL, false, s);
   // page descriptors: (page, count, offset in the active buffer)
   CK(cudaEventSynchronize(ctx->ev_desc));  // the previous descriptor upload has been consumed
   int nd = 0;
@@ -677,6 +682,62 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
   active_out->sh_degree = ctx->cfg.sh_degree;
   active_out->pad = 0;
   *n_active_out = total;
+  return DCG_OK;
+}
+
+dcg_status dcg_prefetch(dcg_ctx* ctx, const int32_t* list, int32_t n_list, int32_t* n_loaded, void* stream) {
+  if (!ctx || n_list < 0 || (n_list > 0 && !list)) return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  if (n_loaded) *n_loaded = 0;
+  const int C = (int)ctx->chunks.size();
+  std::vector<uint8_t> keep((size_t)C, 0);
+  for (int k = 0; k < n_list; ++k) {
+    if (list[k] < 0 || list[k] >= C) return fail(ctx, DCG_ERR_ARG, "chunk index out of range");
+    keep[(size_t)list[k]] = 1;
+  }
+  for (uint64_t key : ctx->active_keys) {
+    auto it = ctx->index.find(key);
+    if (it != ctx->index.end()) keep[(size_t)it->second] = 1;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // evictions below must follow the compute stream's use of the pages
+  CK(cudaEventRecord(ctx->ev_compute, s));
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_compute, 0));
+  std::vector<int32_t> cand;
+  for (int c = 0; c < C; ++c)
+    if (ctx->chunks[c].resident && !keep[(size_t)c]) cand.push_back(c);
+  std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
+    const Chunk &x = ctx->chunks[a], &y = ctx->chunks[b];
+    return x.last_access < y.last_access || (x.last_access == y.last_access && x.key < y.key);
+  });
+  size_t next_victim = 0;
+  int32_t loaded = 0;
+  for (int k = 0; k < n_list; ++k) {
+    Chunk& ch = ctx->chunks[list[k]];
+    if (ch.resident) continue;
+    const int64_t np = pages_for(ctx, ch.count);
+    while ((ctx->resident_g + ch.count > ctx->cfg.device_budget || (int64_t)ctx->dev_free.size() < np) &&
+           next_victim < cand.size()) {
+      dcg_status e = evict_chunk(ctx, ctx->chunks[cand[next_victim++]]);
+      if (e != DCG_OK) return e;
+    }
+    if (ctx->resident_g + ch.count > ctx->cfg.device_budget || (int64_t)ctx->dev_free.size() < np) break;
+    dcg_status e = load_chunk(ctx, ch);
+    if (e != DCG_OK) return e;
+    ch.last_access = ctx->step;
+    ++loaded;
+  }
+  if (n_loaded) *n_loaded = loaded;
+  return DCG_OK;
+}
+
+dcg_status dcg_tier_stats(const dcg_ctx* ctx, int64_t* loads, int64_t* evictions, int64_t* bytes_h2d,
+                          int64_t* bytes_d2h, int64_t* resident) {
+  if (!ctx) return DCG_ERR_ARG;
+  if (loads) *loads = ctx->loads;
+  if (evictions) *evictions = ctx->evictions;
+  if (bytes_h2d) *bytes_h2d = ctx->bytes_h2d;
+  if (bytes_d2h) *bytes_d2h = ctx->bytes_d2h;
+  if (resident) *resident = ctx->resident_g;
   return DCG_OK;
 }
 
@@ -907,7 +968,8 @@ dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const
   CK(cudaMemcpyAsync(ctx->d_losscams, ctx->h_losscams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(ctx->ev_loss, s));
   hook(ctx)(PH_LOSS, true, s);
-  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, lam, dr, dd, loss, ctx->num_sms, s);
+  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, lam, dr, dd, loss, ctx->d_losspart, ctx->num_sms,
+                 s);
   hook(ctx)(PH_LOSS, false, s);
   CK(cudaGetLastError());
   return DCG_OK;
@@ -964,7 +1026,8 @@ dcg_status dcg_window_capture(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, c
   cudaMemcpyAsync(ctx->d_losscams, lc, sizeof(DevCam) * V, cudaMemcpyHostToDevice, cs_);
   cudaMemsetAsync(loss, 0, sizeof(float), cs_);
   raster_forward(a, rgb, depth, &st->list_sorted, &st->inst_sorted, cs_);
-  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, lam, dr, dd, loss, ctx->num_sms, cs_);
+  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, lam, dr, dd, loss, ctx->d_losspart,
+                 ctx->num_sms, cs_);
   raster_backward(a, st->inst_sorted, dr, dd, grads->data, grads->stride, dL_dpose, cs_);
   const cudaError_t ce = cudaStreamEndCapture(cs_, &graph);
   ctx->prof_on = prof;

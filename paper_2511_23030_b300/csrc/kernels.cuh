@@ -15,7 +15,7 @@ constexpr int kMaxViewsApi = 16;  // views per render call
 
 // Phases timed by the optional profiler (dcg_profile); same order as in dcg.h.
 enum Phase { PH_CULL = 0, PH_GATHER, PH_PRE_FWD, PH_BINNING, PH_BLEND_FWD, PH_LOSS, PH_BLEND_BWD, PH_PRE_BWD,
-             PH_SCATTER, PH_COUNT };
+             PH_SCATTER, PH_STALL, PH_COUNT };
 
 // Kernel launches issued by the library in this process (for launch accounting).
 extern unsigned long long g_launches;
@@ -113,8 +113,9 @@ void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb
                      float* grads, long long g_stride, float* dL_dpose, cudaStream_t st);
 
 // ---------------------------------------------------------------- loss
+int loss_partials(int num_sms);  // scratch floats the loss needs
 void launch_loss_l1(const float* rgb, const float* depth, const float* trgb, const float* tdepth, const DevCam* cams,
-                    int V, long long n_pix, float lam, float* dr, float* dd, float* loss, int num_sms,
+                    int V, long long n_pix, float lam, float* dr, float* dd, float* loss, float* part, int num_sms,
                     cudaStream_t st);
 
 }  // namespace dcg

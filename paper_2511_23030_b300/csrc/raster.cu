@@ -1077,7 +1077,8 @@ void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb
 // ============================================================================
 __global__ void k_loss_l1(const float* __restrict__ rgb, const float* __restrict__ depth,
                           const float* __restrict__ trgb, const float* __restrict__ tdepth, const DevCam* cams, int V,
-                          long long n_pix, float lam, float* __restrict__ dr, float* __restrict__ dd, float* loss) {
+                          long long n_pix, float lam, float* __restrict__ dr, float* __restrict__ dd,
+                          float* __restrict__ part) {
   float acc = 0.f;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n_pix; p += (long long)gridDim.x * blockDim.x) {
     int v = 0;
@@ -1097,17 +1098,47 @@ __global__ void k_loss_l1(const float* __restrict__ rgb, const float* __restrict
     dd[p] = e > 0.f ? i1 : (e < 0.f ? -i1 : 0.f);
     acc += fabsf(e) * i1;
   }
+  // deterministic: fixed-order block reduction, one partial per block
+  __shared__ float red[32];
 #pragma unroll
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0 && acc != 0.f) atomicAdd(loss, acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s2;
+  }
 }
 
+// Sums the per-block partials in a fixed order and adds the total to *loss.
+__global__ void k_loss_final(const float* __restrict__ part, int nb, float* loss) {
+  __shared__ float red[32];
+  float acc = 0.f;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[b];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (threadIdx.x == 0) *loss += s2;
+  }
+}
+
+int loss_partials(int num_sms) { return num_sms * 8; }
+
 void launch_loss_l1(const float* rgb, const float* depth, const float* trgb, const float* tdepth, const DevCam* cams,
-                    int V, long long n_pix, float lam, float* dr, float* dd, float* loss, int num_sms,
+                    int V, long long n_pix, float lam, float* dr, float* dd, float* loss, float* part, int num_sms,
                     cudaStream_t st) {
   if (n_pix <= 0) return;
-  k_loss_l1<<<grid_for(n_pix, num_sms), 256, 0, st>>>(rgb, depth, trgb, tdepth, cams, V, n_pix, lam, dr, dd, loss);
-  count_launch();
+  const int nb = grid_for(n_pix, num_sms);  // <= loss_partials(num_sms)
+  k_loss_l1<<<nb, 256, 0, st>>>(rgb, depth, trgb, tdepth, cams, V, n_pix, lam, dr, dd, part);
+  k_loss_final<<<1, 256, 0, st>>>(part, nb, loss);
+  count_launch(2);
 }
 
 }  // namespace dcg

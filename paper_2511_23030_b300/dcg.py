@@ -88,11 +88,15 @@ _SIGS = {
                                           _P, _P]),
     "dcg_window_run": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _I32, _P]),
     "dcg_state_generation": (_I64, [_P]),
+    "dcg_prefetch": (ctypes.c_int, [_P, _P, _I32, ctypes.POINTER(_I32), _P]),
+    "dcg_tier_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                      ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "dcg_cull_chunks_noalloc": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(dcg_camera),
                                                _I32, _P, _P, _P, _P]),
 }
 
-PHASES = ["cull", "gather", "preprocess_fwd", "binning", "blend_fwd", "loss", "blend_bwd", "preprocess_bwd", "scatter"]
+PHASES = ["cull", "gather", "preprocess_fwd", "binning", "blend_fwd", "loss", "blend_bwd", "preprocess_bwd", "scatter",
+          "stall"]
 
 
 def lib():
@@ -372,3 +376,16 @@ def dcg_window_run(ctx, cams, stream=None):
 
 def dcg_state_generation(state) -> int:
     return int(lib().dcg_state_generation(state))
+
+
+def dcg_prefetch(ctx, chunk_list, stream=None) -> int:
+    lst = np.ascontiguousarray(chunk_list, np.int32)
+    k = _I32()
+    check(ctx, lib().dcg_prefetch(ctx, ptr(lst), len(lst), ctypes.byref(k), stream_ptr(stream)))
+    return int(k.value)
+
+
+def dcg_tier_stats(ctx) -> dict:
+    v = [_I64() for _ in range(5)]
+    check(ctx, lib().dcg_tier_stats(ctx, *[ctypes.byref(x) for x in v]))
+    return dict(zip(["loads", "evictions", "bytes_h2d", "bytes_d2h", "resident"], [int(x.value) for x in v]))
