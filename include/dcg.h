@@ -177,6 +177,12 @@ dcg_status dcg_flush(dcg_ctx* ctx, void* stream);
  * the data already is, never what is rendered. */
 dcg_status dcg_prefetch(dcg_ctx* ctx, const int32_t* chunk_list, int32_t n_chunks, int32_t* n_loaded, void* stream);
 
+/* Chunks whose cube lies within `radius` of point `p` (host, 3 floats),
+ * optionally only non-resident ones; ascending indices into list_out (host,
+ * capacity dcg_chunk_count), count into *n_out.  Host query, synchronous. */
+dcg_status dcg_chunks_near(const dcg_ctx* ctx, const float* p, float radius, int32_t only_nonresident,
+                           int32_t* list_out, int32_t* n_out);
+
 /* Tier statistics since creation (host outputs, any may be NULL): chunk
  * loads and evictions, bytes copied host->device and device->host, Gaussians
  * resident now. */

@@ -730,6 +730,26 @@ dcg_status dcg_prefetch(dcg_ctx* ctx, const int32_t* list, int32_t n_list, int32
   return DCG_OK;
 }
 
+dcg_status dcg_chunks_near(const dcg_ctx* ctx, const float* p, float radius, int32_t only_nonresident,
+                           int32_t* list_out, int32_t* n_out) {
+  if (!ctx || !p || !list_out || !n_out) return DCG_ERR_ARG;
+  const double s = ctx->cfg.chunk_size, r2 = (double)radius * radius;
+  int32_t k = 0;
+  for (size_t c = 0; c < ctx->chunks.size(); ++c) {
+    const Chunk& ch = ctx->chunks[c];
+    if (only_nonresident && ch.resident) continue;
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double lo = ch.c[a] * s - 0.5 * s, hi = ch.c[a] * s + 0.5 * s;
+      const double e = p[a] < lo ? lo - p[a] : (p[a] > hi ? p[a] - hi : 0.0);
+      d2 += e * e;
+    }
+    if (d2 <= r2) list_out[k++] = (int32_t)c;
+  }
+  *n_out = k;
+  return DCG_OK;
+}
+
 dcg_status dcg_tier_stats(const dcg_ctx* ctx, int64_t* loads, int64_t* evictions, int64_t* bytes_h2d,
                           int64_t* bytes_d2h, int64_t* resident) {
   if (!ctx) return DCG_ERR_ARG;

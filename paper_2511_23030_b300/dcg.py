@@ -89,6 +89,7 @@ _SIGS = {
     "dcg_window_run": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _I32, _P]),
     "dcg_state_generation": (_I64, [_P]),
     "dcg_prefetch": (ctypes.c_int, [_P, _P, _I32, ctypes.POINTER(_I32), _P]),
+    "dcg_chunks_near": (ctypes.c_int, [_P, _P, ctypes.c_float, _I32, _P, ctypes.POINTER(_I32)]),
     "dcg_mlp_create": (ctypes.c_int, [_I32, ctypes.POINTER(_P)]),
     "dcg_mlp_destroy": (ctypes.c_int, [_P]),
     "dcg_mlp_num_params": (_I32, []),
@@ -455,3 +456,12 @@ def dcg_mlp_features(pose_hist: np.ndarray, coords, chunk_size, cand, n_cand, n_
 def dcg_mlp_gather_rows(x, y, perm, n, x_out, y_out, stream=None):
     _mlp_check(lib().dcg_mlp_gather_rows(ptr(x), ptr(y), ptr(perm), n, ptr(x_out), ptr(y_out), stream_ptr(stream)),
                "dcg_mlp_gather_rows")
+
+
+def dcg_chunks_near(ctx, p, radius: float, only_nonresident: bool = False) -> np.ndarray:
+    C = dcg_chunk_count(ctx)
+    out = np.zeros(max(C, 1), np.int32)
+    k = _I32()
+    pp = np.ascontiguousarray(p, np.float32)
+    check(ctx, lib().dcg_chunks_near(ctx, ptr(pp), float(radius), int(only_nonresident), ptr(out), ctypes.byref(k)))
+    return out[: k.value].copy()
