@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--stage", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="batched timing only (no plain/e2e/CPU legs), for profilers")
+    ap.add_argument("--workload", default="window", choices=["window", "corridor"])
+    ap.add_argument("--length", type=float, default=2000.0, help="corridor: metres of road (1 m per frame)")
+    ap.add_argument("--per-m", type=int, default=8000, help="corridor: Gaussians per metre (40M per 5 km)")
     ap.add_argument("--cpu-pixels", type=int, default=48, help="oracle sample: pixels per sampled view")
     return ap.parse_args()
 
@@ -370,8 +373,98 @@ def run_reference(args, rank, world):
                                         "d2h_bytes_per_step": 0}}
 
 
+def run_corridor(args):
+    """Out-of-core mapping along a driving corridor (1241x376 views, 8 m chunks,
+    device budget 15 % of the map, pinned host tier), one keyframe per metre:
+    cull, gather, render fwd, L1 loss, bwd, scatter, then a prefetch proposal:
+    none, constant-velocity extrapolation, or the learned MLP (trained here on
+    a different drive with samples the mapper generates from its exact cull)."""
+    import torch
+
+    from oracle import mlp as orc_mlp  # seeded initial weights only
+    from paper_2511_23030_b300 import build, dcg, prefetch, synth
+
+    build.build()
+    zfar, s = 60.0, 8.0
+    W, H = 1241, 376
+    t0 = time.perf_counter()
+    # training drive (seed 1): chunk layout only, sparse Gaussians
+    xy, head = synth.corridor_path(1, 3000.0)
+    Ptr = synth.corridor_gaussians(np.random.default_rng(6), xy, head, 40, deg=0)
+    cams_tr = synth.corridor_cameras(xy, head, W=W, H=H)
+    for c in cams_tr:
+        c.zfar = zfar
+    ctx = dcg.dcg_create(dcg.config(sh_degree=0, max_active=Ptr.shape[0], max_views=1, max_pixels=W * H,
+                                    chunk_size=s, device_budget=Ptr.shape[0], host_capacity=Ptr.shape[0], dfar=zfar,
+                                    max_chunks=16384, page_gaussians=256))
+    dcg.dcg_chunk_table_update(ctx, torch.from_numpy(np.ascontiguousarray(Ptr.T)).cuda(), Ptr.shape[0])
+    X, y, n, pos = prefetch.make_dataset(ctx, cams_tr, s, 1.5 * zfar, max_samples=200_000)
+    pm = prefetch.PrefetchMLP(max_batch=4096)
+    dcg.dcg_mlp_set_params(pm.m, orc_mlp.init_params(0))
+    t1 = time.perf_counter()
+    losses = prefetch.train(pm, X, y, n, epochs=6, batch=2048, lr=1e-3)
+    t_train = time.perf_counter() - t1
+    dcg.dcg_destroy(ctx)
+    del X, y
+    # evaluation drive (seed 0)
+    xy, head = synth.corridor_path(0, args.length)
+    P = synth.corridor_gaussians(np.random.default_rng(5), xy, head, args.per_m, deg=3)
+    cams = synth.corridor_cameras(xy, head, W=W, H=H)
+    for c in cams:
+        c.zfar = zfar
+    N, F = P.shape
+    budget = int(0.15 * N)
+    Pt = torch.from_numpy(np.ascontiguousarray(P.T))
+    del P
+    t_gen = time.perf_counter() - t0
+    out = {"workload": "corridor", "metric": "out-of-core mapping Mpix/s, stall and hidden chunk-load share",
+           "unit": UNIT, "config": {"length_m": args.length, "gaussians": N, "view": f"{W}x{H}", "chunk_m": s,
+                                    "budget_gaussians": budget, "frames": len(cams)},
+           "train": {"samples": n, "positive_frac": round(pos, 4), "loss_per_epoch": [round(v, 4) for v in losses],
+                     "seconds": round(t_train, 2)}, "setup_seconds": round(t_gen, 1), "modes": {}}
+    for mode in ("none", "cv", "mlp"):
+        ctx = dcg.dcg_create(dcg.config(sh_degree=3, max_active=budget, max_views=1, max_pixels=W * H, chunk_size=s,
+                                        device_budget=budget, host_capacity=N, dfar=zfar, max_chunks=16384,
+                                        page_gaussians=512, max_instances=64 << 20))
+        g_t = Pt.cuda()
+        dcg.dcg_chunk_table_update(ctx, g_t, N)
+        del g_t
+        torch.cuda.empty_cache()
+        pm.bind(ctx)
+        rgb = torch.zeros(3 * W * H, device="cuda")
+        depth = torch.zeros(W * H, device="cuda")
+        dr, dd = torch.zeros_like(rgb), torch.zeros_like(depth)
+        trgb = torch.rand(3 * W * H, device="cuda")
+        tdep = torch.rand(W * H, device="cuda") * 30
+        loss = torch.zeros(1, device="cuda")
+        grads_t = torch.zeros((synth.n_fields(3), budget), device="cuda")
+        grads = dcg.gaussians(grads_t, 3)
+
+        def render(g, na, cam):
+            dcg.dcg_render_fwd(ctx, g, na, [cam], rgb, depth)
+            dcg.dcg_loss_l1(ctx, rgb, depth, trgb, tdep, [cam], 0.1, dr, dd, loss)
+            dcg.dcg_render_bwd(ctx, dr, dd, grads, None)
+
+        r = prefetch.run_corridor(ctx, cams, mode, s, 1.5 * zfar, pm=pm, render=render)
+        dcg.dcg_sync(ctx)
+        r["ms_per_step"] = round(r["ms"] / r["steps"], 4)
+        r["value"] = round(W * H * r["steps"] / (r["ms"] / 1e3) / 1e6, 2)
+        r["io_frac"] = round(r["stall_ms"] / r["ms"], 4)
+        r["hidden_load_frac"] = round(r["hidden_load_frac"], 4)
+        out["modes"][mode] = r
+        dcg.dcg_destroy(ctx)
+    none_stall = out["modes"]["none"]["stall_ms"]
+    for mode in ("cv", "mlp"):
+        out["modes"][mode]["stall_hidden_vs_none"] = round(1 - out["modes"][mode]["stall_ms"] / max(none_stall, 1e-9), 4)
+    pm.close()
+    return out
+
+
 def main():
     args = parse()
+    if args.workload == "corridor":
+        print(json.dumps(run_corridor(args)))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:

@@ -153,10 +153,12 @@ def constant_velocity_cams(cams, t, ahead=(5, 10, 15, 20)):
     return out
 
 
-def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = None, threshold=0.5, render=None):
+def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = None, threshold=0.3, render=None,
+                 warm=1):
     """Map along `cams` one keyframe per step: cull, gather (synchronous loads
     of missing chunks), `render(g, n, cam)`, scatter, then propose prefetches
-    ('none' | 'cv' | 'mlp').  Returns per-run statistics."""
+    ('none' | 'cv' | 'mlp').  The first `warm` steps (the cold start, which no
+    predictor can see coming) are run but not counted.  Returns statistics."""
     import torch
 
     info = dcg.dcg_chunk_info(ctx)
@@ -169,6 +171,11 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for t, cam in enumerate(cams):
+        if t == warm:
+            torch.cuda.synchronize()
+            dcg.dcg_profile_read(ctx)
+            hits = misses = wasted = hit_g = miss_g = 0
+            e0.record()
         lst = dcg.dcg_cull_chunks(ctx, [cam])
         res = dcg.dcg_chunk_info(ctx)["resident"].astype(bool)
         for c in lst:
@@ -211,6 +218,6 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
     prof = dcg.dcg_profile_read(ctx)
     dcg.dcg_profile(ctx, False)
     wasted += len(pending)
-    return {"mode": mode, "steps": len(cams), "ms": e0.elapsed_time(e1), "stall_ms": prof["stall"][0],
+    return {"mode": mode, "steps": len(cams) - warm, "ms": e0.elapsed_time(e1), "stall_ms": prof["stall"][0],
             "hits": hits, "misses": misses, "wasted_prefetches": wasted,
             "hidden_load_frac": hit_g / max(hit_g + miss_g, 1), "tier": dcg.dcg_tier_stats(ctx)}
