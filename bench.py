@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="batched timing only (no plain/e2e/CPU legs), for profilers")
     ap.add_argument("--workload", default="window", choices=["window", "corridor"])
+    ap.add_argument("--bwd", default="warp", choices=["warp", "slots"], help="backward gradient accumulation")
     ap.add_argument("--length", type=float, default=2000.0, help="corridor: metres of road (1 m per frame)")
     ap.add_argument("--per-m", type=int, default=8000, help="corridor: Gaussians per metre (40M per 5 km)")
     ap.add_argument("--cpu-pixels", type=int, default=48, help="oracle sample: pixels per sampled view")
@@ -128,7 +129,8 @@ def run_ours(args, rank, world):
     F = P.shape[1]
     npix = sum(c.W * c.H for c in cams)
     cfg = dcg.config(sh_degree=deg, max_active=n_all + 1024, max_views=8, max_pixels=npix, max_instances=160 << 20,
-                     chunk_size=sc["chunk_size"], device_budget=6_000_000, host_capacity=n_all + 1024, dfar=60.0)
+                     chunk_size=sc["chunk_size"], device_budget=6_000_000, host_capacity=n_all + 1024, dfar=60.0,
+                     flags=1 if args.bwd == "slots" else 0)
     ctx = dcg.dcg_create(cfg)
     stream = torch.cuda.current_stream()
     g_t = torch.from_numpy(np.ascontiguousarray(P.T)).cuda()
@@ -269,7 +271,8 @@ def run_ours(args, rank, world):
         "config": {"workload": "keyframe window: 8 views (4x1200x680, 2x640x480, 2x320x240) = 4,032,000 px over "
                                f"{n_all} Gaussians (SH3, FP32) in 64 chunks of 4 m",
                    "gaussians": n_all, "views": 8, "pixels": npix, "tile": f"{tile[0]}x{tile[1]}", "stage": stage,
-                   "autotune": tune, "l2": "inputs larger than L2 (parameters 472 MB per step)",
+                   "autotune": tune, "bwd_accumulation": args.bwd,
+                   "l2": "inputs larger than L2 (parameters 472 MB per step)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "batched_direct_calls_ms_per_step": round(sum(v[0] for v in prof.values()) / K, 4),
         "plain": {"value": round(mpix_p, 2), "unit": UNIT, "ms_per_step": round(ms_p / K_p, 4),

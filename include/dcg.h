@@ -86,7 +86,8 @@ typedef struct {
   int32_t stage;           /* default Gaussians staged per block batch: 64..256 */
   float dfar;              /* distance filter of the chunk cull, metres */
   int32_t page_gaussians;  /* Gaussians per device/host page (power of two) */
-  int32_t flags;           /* reserved, 0 */
+  int32_t flags;           /* bit 0: backward blend accumulates per-lane shared slots instead of
+                              reducing each Gaussian across the warp (same result); others 0 */
 } dcg_config;
 
 /* Fill *cfg with defaults (s = 4 m, degree 3, budget 6 M, 8 views ...). */

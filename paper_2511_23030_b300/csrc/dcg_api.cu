@@ -881,6 +881,7 @@ static void fill_args(dcg_render_state* st, RasterArgs& a) {
   a.errword = ctx->d_errword;
   a.num_sms = ctx->num_sms;
   a.prof = hook(ctx);
+  a.bwd_slots = (ctx->cfg.flags & 1) ? 1 : 0;
 }
 
 static void fill_devcams(const dcg_camera* cams, int V, int tw, int th, DevCam* out, int64_t* pix_out,

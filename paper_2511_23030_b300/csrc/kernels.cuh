@@ -102,6 +102,7 @@ struct RasterArgs {
   int P;
   unsigned* errword;
   int num_sms;
+  int bwd_slots;  // 1: backward accumulates per-lane slots instead of warp reductions
   ProfHook prof;
 };
 

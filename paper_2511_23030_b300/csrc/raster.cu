@@ -368,18 +368,28 @@ struct TileLayout {
   static_assert(WPR * (TH / WY) == 8, "eight warp blocks per tile");
 };
 
-// Does the box |x - u| <= ex, |y - v| <= ey (coordinates relative to the
-// warp block origin) meet the warp block [0, 7] x [0, WY-1]?  ex, ey come from
-// the FP32 conic the blend uses, slightly enlarged so that the test never
-// drops a Gaussian the per-pixel support test q <= 9 would keep:
-// Sigma'_xx = C / (A C - B^2) = -2 C' log2e / (4 A' C' - B'^2), same for yy.
+// Can Gaussian (conic cn, centre (ub, vb) relative to the warp block origin)
+// reach the support test p >= kPMin at some pixel of the warp block
+// [0, 7] x [0, WY-1]?  p(dx, dy) = A' dx^2 + B' dx dy + C' dy^2 is concave
+// (A', C' < 0); its maximum over the block rectangle is 0 if the centre is
+// inside, else it lies on an edge, where the 1D maximiser is clamped to the
+// edge.  A small margin keeps the test conservative against FP32 rounding.
 template <int WY>
 __device__ __forceinline__ bool meets_block(float ub, float vb, float4 cn) {
-  const float den = 4.f * cn.x * cn.z - cn.y * cn.y;
-  const float sxx = -2.f * kLog2e * cn.z / den, syy = -2.f * kLog2e * cn.x / den;
-  const float ex = 3.001f * sqrtf(fmaxf(sxx, 0.f)) + 0.01f;
-  const float ey = 3.001f * sqrtf(fmaxf(syy, 0.f)) + 0.01f;
-  return ub + ex >= 0.f && ub - ex <= 7.f && vb + ey >= 0.f && vb - ey <= (float)(WY - 1);
+  const float X0 = -ub, X1 = 7.f - ub, Y0 = -vb, Y1 = (float)(WY - 1) - vb;
+  if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
+  const float A = cn.x, B = cn.y, C = cn.z;
+  const float ky = -0.5f * B / C, kx = -0.5f * B / A;  // argmax of dy (resp. dx) for a fixed dx (dy)
+  float best;
+  {
+    const float dy0 = fminf(fmaxf(ky * X0, Y0), Y1), dy1 = fminf(fmaxf(ky * X1, Y0), Y1);
+    best = fmaxf(X0 * (A * X0 + B * dy0) + C * dy0 * dy0, X1 * (A * X1 + B * dy1) + C * dy1 * dy1);
+  }
+  {
+    const float dx0 = fminf(fmaxf(kx * Y0, X0), X1), dx1 = fminf(fmaxf(kx * Y1, X0), X1);
+    best = fmaxf(best, fmaxf(A * dx0 * dx0 + Y0 * (B * dx0 + C * Y0), A * dx1 * dx1 + Y1 * (B * dx1 + C * Y1)));
+  }
+  return best >= kPMin * 1.001f - 1e-3f;
 }
 
 // Forward blend.  One block per tile (taken from a device queue); each of
@@ -735,6 +745,194 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
   }
 }
 
+// Backward variant without per-Gaussian warp reductions: every lane adds its
+// own contribution to a private slot of a block-shared accumulator
+// [segment Gaussian][component][lane] (shared-memory atomics, since warps of
+// the block may touch the same Gaussian); at the end of each segment of
+// kSlotSeg Gaussians the block sums the 32 slots (rotated to avoid bank
+// conflicts), zeroes them, and issues the global vector atomics.
+constexpr int kSlotSeg = 64;
+constexpr size_t kSlotSmem = sizeof(float) * kSlotSeg * 10 * 32;
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_blend_bwd_slots(RasterArgs a, const u64* __restrict__ inst,
+                                                         const float* __restrict__ dL_drgb,
+                                                         const float* __restrict__ dL_ddepth) {
+  using L = TileLayout<TW, TH>;
+  constexpr int PPT = L::PPT;
+  extern __shared__ float s_slot[];  // [kSlotSeg][10][32]
+  __shared__ float2 s_xy[8][32];
+  __shared__ float4 s_con[8][32];
+  __shared__ float4 s_col[8][32];
+  __shared__ unsigned s_rel[8][32];
+  __shared__ float s_sum[kSlotSeg][10];
+  __shared__ unsigned s_tile;
+  __shared__ unsigned s_maxlast;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int bx0 = (w % L::WPR) * 8, by0 = (w / L::WPR) * L::WY;
+  const int lx = bx0 + (lane & 7);
+  const int ly = by0 + (lane >> 3);
+  const unsigned lt = lanemask_lt();
+  for (int e = tid; e < kSlotSeg * 10 * 32; e += 256) s_slot[e] = 0.f;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      s_tile = atomicAdd(&a.counters->tile_queue_bwd, 1u);
+      s_maxlast = 0;
+    }
+    __syncthreads();
+    const unsigned gt = s_tile;
+    if (gt >= (unsigned)a.n_tiles) break;
+    const int v = view_of_tile(a.cams, a.V, gt);
+    const DevCam& c = a.cams[v];
+    const int W = c.W, H = c.H;
+    const int local = (int)gt - c.tile_base;
+    const int ty = local / c.ntx, tx = local - ty * c.ntx;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const float x0f = (float)x0, y0f = (float)y0;
+    const long long P = (long long)W * H;
+    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Sr[PPT], Sg[PPT], Sb[PPT], Sd[PPT];
+    uint32_t last[PPT];
+    const int px = x0 + lx;
+    uint32_t mylast = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int py = y0 + ly + 4 * k;
+      last[k] = 0;
+      T[k] = 0.f;
+      gr[k] = gg[k] = gb[k] = gd[k] = 0.f;
+      if (px < W && py < H) {
+        const long long pix = (long long)py * W + px;
+        T[k] = a.T_final[c.pix_off + pix];
+        last[k] = a.n_contrib[c.pix_off + pix];
+        gr[k] = dL_drgb[3 * c.pix_off + pix];
+        gg[k] = dL_drgb[3 * c.pix_off + P + pix];
+        gb[k] = dL_drgb[3 * c.pix_off + 2 * P + pix];
+        gd[k] = dL_ddepth[c.pix_off + pix];
+      }
+      Sr[k] = Sg[k] = Sb[k] = Sd[k] = 0.f;
+      mylast = max(mylast, last[k]);
+    }
+    const int warplast = (int)__reduce_max_sync(0xffffffffu, mylast);
+    if (lane == 0) atomicMax(&s_maxlast, (unsigned)warplast);
+    __syncthreads();
+    const int maxlast = (int)s_maxlast;
+    const uint2 rg = a.ranges[gt];
+    for (int send = maxlast; send > 0; send -= kSlotSeg) {
+      const int sbeg = max(0, send - kSlotSeg);
+      for (int hi = min(send, warplast); hi > sbeg; hi -= 32) {
+        const int rel = hi - 1 - lane;
+        bool pass = false;
+        float ul = 0.f, vl = 0.f;
+        float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
+        unsigned vi = 0;
+        if (rel >= sbeg) {
+          vi = (unsigned)inst[rg.x + rel];
+          const float4 r0 = a.rec[3ull * vi + 0];
+          cn = a.rec[3ull * vi + 1];
+          ul = df_sub_round(r0.x, r0.z, x0f);
+          vl = df_sub_round(r0.y, r0.w, y0f);
+          pass = meets_block<L::WY>(ul - (float)bx0, vl - (float)by0, cn);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (pass) {
+          const int slot = __popc(m & lt);
+          s_xy[w][slot] = make_float2(ul, vl);
+          s_con[w][slot] = cn;
+          s_col[w][slot] = a.rec[3ull * vi + 2];
+          s_rel[w][slot] = (unsigned)rel;
+        }
+        __syncwarp();
+        const int cnt = __popc(m);
+        for (int j = 0; j < cnt; ++j) {
+          const int r = (int)s_rel[w][j];
+          const float2 xy = s_xy[w][j];
+          const float4 cq = s_con[w][j];
+          const float dx = __fsub_rn((float)lx, xy.x);
+          const float sx = __fmul_rn(dx, __fmul_rn(cq.x, dx));
+          const float bx = __fmul_rn(cq.y, dx);
+          float acc[10];
+#pragma unroll
+          for (int q = 0; q < 10; ++q) acc[q] = 0.f;
+          bool any = false;
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            if (r < (int)last[k]) {
+              const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
+              const float p = blend_power(sx, bx, cq.z, dy);
+              if (p >= kPMin) {
+                const float G = ex2_approx(p);
+                const float araw = __fmul_rn(cq.w, G);
+                const float al = fminf(kAlphaMax, araw);
+                if (al >= kAlphaMin) {
+                  any = true;
+                  const float4 cl = s_col[w][j];
+                  T[k] = __fdividef(T[k], 1.f - al);
+                  const float wgt = al * T[k];
+                  acc[6] += wgt * gr[k];
+                  acc[7] += wgt * gg[k];
+                  acc[8] += wgt * gb[k];
+                  acc[9] += wgt * gd[k];
+                  const float dal = T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] +
+                                            (cl.w - Sd[k]) * gd[k]);
+                  Sr[k] = al * cl.x + (1.f - al) * Sr[k];
+                  Sg[k] = al * cl.y + (1.f - al) * Sg[k];
+                  Sb[k] = al * cl.z + (1.f - al) * Sb[k];
+                  Sd[k] = al * cl.w + (1.f - al) * Sd[k];
+                  if (araw < kAlphaMax) {
+                    acc[5] += dal * G;
+                    const float dp = dal * cq.w * G * kLn2;
+                    acc[2] += dp * dx * dx;
+                    acc[3] += dp * dx * dy;
+                    acc[4] += dp * dy * dy;
+                    acc[0] -= dp * (2.f * cq.x * dx + cq.y * dy);
+                    acc[1] -= dp * (cq.y * dx + 2.f * cq.z * dy);
+                  }
+                }
+              }
+            }
+          }
+          if (any) {
+            float* sl = s_slot + (size_t)(r - sbeg) * 320 + lane;
+#pragma unroll
+            for (int q = 0; q < 10; ++q) atomicAdd(sl + 32 * q, acc[q]);
+          }
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      const int cnt_seg = send - sbeg;
+      for (int e = tid; e < cnt_seg * 10; e += 256) {
+        float* sl = s_slot + (size_t)e * 32;
+        float acc = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          const int kk = (k + tid) & 31;
+          acc += sl[kk];
+          sl[kk] = 0.f;
+        }
+        (&s_sum[0][0])[e] = acc;
+      }
+      __syncthreads();
+      for (int j = tid; j < cnt_seg; j += 256) {
+        const float* q = s_sum[j];
+        const float4 g0 = make_float4(q[0], q[1], q[2], q[3]);
+        const float4 g1 = make_float4(q[4], q[5], q[6], q[7]);
+        const bool n0 = g0.x != 0.f || g0.y != 0.f || g0.z != 0.f || g0.w != 0.f;
+        const bool n1 = g1.x != 0.f || g1.y != 0.f || g1.z != 0.f || g1.w != 0.f;
+        const bool n2 = q[8] != 0.f || q[9] != 0.f;
+        if (n0 || n1 || n2) {
+          float4* gp = a.grad2d + 3ull * (unsigned)inst[rg.x + sbeg + j];
+          if (n0) atomicAdd(gp + 0, g0);
+          if (n1) atomicAdd(gp + 1, g1);
+          if (n2) atomicAdd(reinterpret_cast<float2*>(gp + 2), make_float2(q[8], q[9]));
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // ============================================================================
 // 9. preprocess backward
 // ============================================================================
@@ -987,6 +1185,17 @@ static void blend_bwd_launch(RasterArgs& a, const u64* inst, const float* dr, co
   k_blend_bwd<TW, TH, STAGE><<<grid, 256, 0, st>>>(a, inst, dr, dd);
 }
 
+template <int TW, int TH>
+static void blend_bwd_slots_launch(RasterArgs& a, const u64* inst, const float* dr, const float* dd, cudaStream_t st) {
+  static int occ = -1;
+  if (occ < 0) {
+    cudaFuncSetAttribute(k_blend_bwd_slots<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlotSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_bwd_slots<TW, TH>, 256, kSlotSmem);
+  }
+  const int grid = max(1, min(a.n_tiles, a.num_sms * max(occ, 1)));
+  k_blend_bwd_slots<TW, TH><<<grid, 256, kSlotSmem, st>>>(a, inst, dr, dd);
+}
+
 #define DCG_STAGES(TW, TH, CALL)                  \
   switch (a.stage) {                              \
     case 64: CALL(TW, TH, 64); break;             \
@@ -1053,9 +1262,15 @@ void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb
   cudaMemsetAsync(&a.counters->tile_queue_bwd, 0, sizeof(unsigned), st);
   if (dL_dpose) cudaMemsetAsync(dL_dpose, 0, sizeof(float) * 6 * a.V, st);
   a.prof(PH_BLEND_BWD, true, st);
+  if (a.bwd_slots) {
+    if (a.tile_w == 32 && a.tile_h == 32) blend_bwd_slots_launch<32, 32>(a, inst_sorted, dL_drgb, dL_ddepth, st);
+    else if (a.tile_w == 32 && a.tile_h == 16) blend_bwd_slots_launch<32, 16>(a, inst_sorted, dL_drgb, dL_ddepth, st);
+    else blend_bwd_slots_launch<16, 16>(a, inst_sorted, dL_drgb, dL_ddepth, st);
+  } else {
 #define BWD_CALL(TW, TH, SG) blend_bwd_launch<TW, TH, SG>(a, inst_sorted, dL_drgb, dL_ddepth, st)
-  DCG_TILES(BWD_CALL)
+    DCG_TILES(BWD_CALL)
 #undef BWD_CALL
+  }
   count_launch();
   a.prof(PH_BLEND_BWD, false, st);
   a.prof(PH_PRE_BWD, true, st);

@@ -50,6 +50,21 @@ def ctx0():
     dcg.dcg_destroy(c)
 
 
+@pytest.fixture(scope="module", params=["warp", "slots"])
+def ctx0b(request):
+    # both gradient-accumulation variants of the backward blend
+    c = make_ctx(deg=0, n_max=100_000, views=8, flags=1 if request.param == "slots" else 0)
+    yield c
+    dcg.dcg_destroy(c)
+
+
+@pytest.fixture(scope="module", params=["warp", "slots"])
+def ctxb(request):
+    c = make_ctx(deg=3, n_max=600_000, views=8, flags=1 if request.param == "slots" else 0)
+    yield c
+    dcg.dcg_destroy(c)
+
+
 def _pix_arrays(rgb_v, depth_v):
     H, W = depth_v.shape
     return rgb_v.reshape(3, -1).T.astype(np.float64), depth_v.reshape(-1).astype(np.float64)
@@ -99,7 +114,8 @@ def test_sort_keys_bit_exact_and_tile_lists_valid(ctx0, orc):
     assert np.array_equal(rect[good, 0], tx0[good])
 
 
-def test_small_view_backward_matches_oracle(ctx0, orc):
+def test_small_view_backward_matches_oracle(ctx0b, orc):
+    ctx0 = ctx0b
     sc = synth.room_small(0)
     P, cam = sc["params"], sc["cams"][0]
     n = P.shape[0]
@@ -128,7 +144,8 @@ def _room_views(n=120_000, n_views=3, seed=1):
     return sc["params"], sc["cams"]
 
 
-def test_room_sh3_sampled_pixels_and_sparse_seed_gradients(ctx, orc):
+def test_room_sh3_sampled_pixels_and_sparse_seed_gradients(ctxb, orc):
+    ctx = ctxb
     P, cams = _room_views(n=60_000, n_views=1, seed=1)
     cam = cams[0]
     n = P.shape[0]
