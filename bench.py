@@ -321,7 +321,7 @@ def roofline(phases, n_act, n_vis, n_inst, n_eval, npix, deg, F, clocks):
 
 
 # ----------------------------------------------------------------------------- CPU baseline (oracle)
-def cpu_baseline(pix_per_view: int, views=None, n_gaussians=2_000_000, seed=0):
+def cpu_baseline(pix_per_view: int, views=None, n_gaussians=2_000_000, seed=0, scene=None):
     """FP64 oracle fwd+bwd on a bounded pixel sample of the window (the whole
     scene is projected for every sampled view)."""
     import oracle
@@ -329,7 +329,7 @@ def cpu_baseline(pix_per_view: int, views=None, n_gaussians=2_000_000, seed=0):
     from paper_2511_23030_b300 import synth
 
     oracle.build()
-    sc = synth.window_scene(0, n=n_gaussians)
+    sc = synth.window_scene(0, n=n_gaussians) if scene is None else scene
     P, cams = sc["params"], sc["cams"]
     views = range(len(cams)) if views is None else views
     rng = np.random.default_rng(seed)
@@ -353,14 +353,18 @@ def cpu_baseline(pix_per_view: int, views=None, n_gaussians=2_000_000, seed=0):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    from paper_2511_23030_b300 import synth
+
     K, W = args.steps, args.warmup
+    sc = synth.window_scene(0, n=args.gaussians)
     views = [5]  # one 640x480 view per step keeps the whole run within minutes
     for _ in range(min(W, 1)):
-        cpu_baseline(8, views=views, n_gaussians=args.gaussians)
+        cpu_baseline(4, views=views, n_gaussians=args.gaussians, scene=sc)
     t0 = time.perf_counter()
     m = 0
-    for _ in range(K):
-        cb = cpu_baseline(16, views=views, n_gaussians=args.gaussians)
+    cb = None
+    for k in range(K):
+        cb = cpu_baseline(16, views=views, n_gaussians=args.gaussians, seed=k, scene=sc)
         m += 16
     dt = time.perf_counter() - t0
     val = m / dt / 1e6

@@ -510,10 +510,11 @@ static void orc_scene(const double* params, int64_t n, int deg, const OrcCam* ca
   sc->F = 11 + 3 * orc_nsh(deg);
   sc->proj.resize((size_t)n);
   sc->vis.clear();
-  for (int64_t i = 0; i < n; ++i) {
-    orc_project(&params[sc->F * i], deg, cam, &sc->proj[(size_t)i]);
+  // every Gaussian is projected independently
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) orc_project(&params[sc->F * i], deg, cam, &sc->proj[(size_t)i]);
+  for (int64_t i = 0; i < n; ++i)
     if (sc->proj[(size_t)i].vis) sc->vis.push_back(i);
-  }
 }
 
 struct OrcEps {

@@ -23,6 +23,8 @@ struct Chunk {
   bool resident = false;
   bool dirty = false;
   int64_t last_access = -1;
+  uint64_t load_seq = 0;         // copy-stream sequence number of the last load
+  cudaEvent_t ev_load = nullptr;  // recorded after the last load's copies
 };
 
 }  // namespace dcg
@@ -92,6 +94,7 @@ struct dcg_ctx {
   std::vector<int32_t> host_free;
   int64_t resident_g = 0;
   int64_t step = 0;
+  uint64_t copy_seq = 0;
   // active buffer
   float* d_active = nullptr;
   int64_t n_active = 0;
@@ -231,6 +234,9 @@ dcg_status load_chunk(dcg_ctx* ctx, Chunk& ch) {
                  cudaMemcpyHostToDevice, ctx->copy_stream));
     ctx->bytes_h2d += cnt * ctx->F * 4;
   }
+  if (!ch.ev_load) CK(cudaEventCreateWithFlags(&ch.ev_load, cudaEventDisableTiming));
+  CK(cudaEventRecord(ch.ev_load, ctx->copy_stream));
+  ch.load_seq = ++ctx->copy_seq;
   ch.resident = true;
   ch.dirty = false;
   ctx->resident_g += ch.count;
@@ -397,6 +403,8 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
     state_free(ctx->st0);
     delete ctx->st0;
   }
+  for (auto& ch : ctx->chunks)
+    if (ch.ev_load) cudaEventDestroy(ch.ev_load);
   cudaFree(ctx->d_errword);
   if (ctx->h_errword) cudaFreeHost(ctx->h_errword);
   cudaFree(ctx->d_coords); cudaFree(ctx->d_vis); cudaFree(ctx->d_list); cudaFree(ctx->d_nlist); cudaFree(ctx->d_cullcams);
@@ -646,9 +654,16 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
     }
     ch.last_access = ctx->step;
   }
-  CK(cudaEventRecord(ctx->ev_copy, ctx->copy_stream));
+  // wait only for the copies the listed chunks need: the copy stream is in
+  // order, so the listed chunk loaded last stands for all of them (prefetches
+  // of chunks not needed yet keep running)
+  const Chunk* newest = nullptr;
+  for (int k = 0; k < n_list; ++k) {
+    const Chunk& ch = ctx->chunks[list[k]];
+    if (ch.ev_load && (!newest || ch.load_seq > newest->load_seq)) newest = &ch;
+  }
   hook(ctx)(PH_STALL, true, s);
-  CK(cudaStreamWaitEvent(s, ctx->ev_copy, 0));
+  if (newest) CK(cudaStreamWaitEvent(s, newest->ev_load, 0));
   hook(ctx)(PH_STALL, false, s);
   // page descriptors: (page, count, offset in the active buffer)
   CK(cudaEventSynchronize(ctx->ev_desc));  // the previous descriptor upload has been consumed
