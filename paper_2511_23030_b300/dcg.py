@@ -354,12 +354,13 @@ def dcg_autotune(ctx, g: dcg_gaussians, n: int, cams, rgb, depth, dL_drgb, dL_dd
                  stream=None):
     arr = make_cameras(cams)
     tw, th, sg = _I32(), _I32(), _I32()
-    ms = np.zeros(15, np.float32)
+    ms = np.zeros(16, np.float32)
     check(ctx, lib().dcg_autotune(ctx, ctypes.byref(g), n, arr, len(cams), ptr(rgb), ptr(depth), ptr(dL_drgb),
                                   ptr(dL_ddepth), ctypes.byref(grads), reps, ctypes.byref(tw), ctypes.byref(th),
                                   ctypes.byref(sg), ptr(ms), stream_ptr(stream)))
     table = {f"{TUNE_TILES[i // 5][0]}x{TUNE_TILES[i // 5][1]}/{TUNE_STAGES[i % 5]}": round(float(ms[i]), 4)
              for i in range(15)}
+    table["16x16/32 (warp per tile)"] = round(float(ms[15]), 4)
     return {"tile": [tw.value, th.value], "stage": sg.value, "ms": table}
 
 

@@ -50,17 +50,20 @@ def ctx0():
     dcg.dcg_destroy(c)
 
 
-@pytest.fixture(scope="module", params=["warp", "slots"])
+BWD_VARIANTS = {"warp": dict(flags=0), "slots": dict(flags=1), "warp_per_tile": dict(flags=0, stage=32)}
+
+
+@pytest.fixture(scope="module", params=list(BWD_VARIANTS))
 def ctx0b(request):
-    # both gradient-accumulation variants of the backward blend
-    c = make_ctx(deg=0, n_max=100_000, views=8, flags=1 if request.param == "slots" else 0)
+    # every blend variant: block per tile with warp reductions or lane slots, warp per tile
+    c = make_ctx(deg=0, n_max=100_000, views=8, **BWD_VARIANTS[request.param])
     yield c
     dcg.dcg_destroy(c)
 
 
-@pytest.fixture(scope="module", params=["warp", "slots"])
+@pytest.fixture(scope="module", params=list(BWD_VARIANTS))
 def ctxb(request):
-    c = make_ctx(deg=3, n_max=600_000, views=8, flags=1 if request.param == "slots" else 0)
+    c = make_ctx(deg=3, n_max=600_000, views=8, **BWD_VARIANTS[request.param])
     yield c
     dcg.dcg_destroy(c)
 
@@ -199,7 +202,7 @@ def test_batched_views_equal_single_views(ctx):
 
 
 @pytest.mark.parametrize("tile,stage", [((16, 16), 64), ((32, 16), 128), ((32, 32), 256), ((16, 16), 192),
-                                        ((32, 32), 96)])
+                                        ((32, 32), 96), ((16, 16), 32)])
 def test_launch_shapes_agree(ctx, tile, stage):
     P, cams = _room_views(n=60_000, n_views=1, seed=4)
     dcg.dcg_set_launch(ctx, 16, 16, 128)
