@@ -83,7 +83,8 @@ typedef struct {
   int64_t max_pixels;      /* total pixels over the views of one render call */
   int64_t max_instances;   /* (view, tile, Gaussian) instances per render call */
   int32_t tile_w, tile_h;  /* default blend tile: 16x16, 32x16 or 32x32 */
-  int32_t stage;           /* default Gaussians staged per block batch: 64..256 */
+  int32_t stage;           /* default Gaussians staged per block batch: 64..256; 32 selects the
+                              warp-per-block blend kernels */
   float dfar;              /* distance filter of the chunk cull, metres */
   int32_t page_gaussians;  /* Gaussians per device/host page (power of two) */
   int32_t flags;           /* bit 0: backward blend accumulates per-lane shared slots instead of
@@ -241,8 +242,10 @@ dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const
 
 /* Blend launch shape used by the next render calls: tile 16x16, 32x16 or
  * 32x32 pixels and 64..256 Gaussians staged per block batch (one block per
- * tile); stage 32 with a 16x16 tile selects the warp-per-tile kernels (one
- * warp owns a tile, 8 pixels per lane).  Results do not depend on it. */
+ * tile, warps of a tile synchronised per batch); stage 32 selects the
+ * warp-per-block kernels (every warp takes one 8-column block of a tile from
+ * a device queue on its own, no block barriers).  Results do not depend on
+ * it (gradients up to FP32 atomic order). */
 dcg_status dcg_set_launch(dcg_ctx* ctx, int32_t tile_w, int32_t tile_h, int32_t stage);
 
 /* Batched keyframe window as one CUDA graph.  dcg_window_capture records,
@@ -266,11 +269,12 @@ int64_t dcg_state_generation(const dcg_render_state* st);
 
 /* Autotuner of the blend launch shape: times render_fwd + render_bwd of this
  * call (default state, `reps` repetitions after one warm-up, CUDA events on
- * `stream`) for every tile {16x16, 32x16, 32x32} x staging depth
- * {64, 96, 128, 192, 256} and for the warp-per-tile kernels (16x16, 32),
- * keeps the fastest as the context's launch shape and returns it.  ms_out
- * (16 floats in that order, may be NULL) receives the mean time of each.  rgb/depth/grads are overwritten; dL_drgb and
- * dL_ddepth are the seeds used for the backward.  Synchronous. */
+ * `stream`) for every tile {16x16, 32x16, 32x32} x stage
+ * {64, 96, 128, 192, 256, 32 (warp-per-block)}, keeps the fastest as the
+ * context's launch shape and returns it.  ms_out (18 floats, tile-major in
+ * that order, may be NULL) receives the mean time of each.  rgb/depth/grads
+ * are overwritten; dL_drgb and dL_ddepth are the seeds used for the
+ * backward.  Synchronous. */
 dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams, int32_t n_views,
                         float* rgb, float* depth, const float* dL_drgb, const float* dL_ddepth, dcg_gaussians* grads,
                         int32_t reps, int32_t* tile_w, int32_t* tile_h, int32_t* stage, float* ms_out, void* stream);

@@ -853,7 +853,7 @@ dcg_status dcg_state_destroy(dcg_render_state* st) {
 }
 
 dcg_status dcg_set_launch(dcg_ctx* ctx, int32_t tw, int32_t th, int32_t stage) {
-  if (!ctx || !valid_tile(tw, th) || !valid_stage(stage) || (stage == 32 && (tw != 16 || th != 16)))
+  if (!ctx || !valid_tile(tw, th) || !valid_stage(stage))
     return fail(ctx, DCG_ERR_ARG, "bad launch shape");
   ctx->tile_w = tw;
   ctx->tile_h = th;
@@ -1125,8 +1125,8 @@ dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const d
   if (!ctx || reps <= 0) return DCG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   static const int tiles[3][2] = {{16, 16}, {32, 16}, {32, 32}};
-  static const int stages[5] = {64, 96, 128, 192, 256};
-  // candidate 16: the warp-per-tile kernels (16x16 tiles, stage code 32)
+  // stage code 32 selects the warp-per-block kernels (no staging segment)
+  static const int stages[6] = {64, 96, 128, 192, 256, 32};
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
@@ -1135,13 +1135,9 @@ dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const d
   const bool prof = ctx->prof_on;
   ctx->prof_on = false;
   dcg_status rc = DCG_OK;
-  for (int t = 0; t < 4 && rc == DCG_OK; ++t)
-    for (int k = 0; k < 5 && rc == DCG_OK; ++k) {
-      if (t == 3 && k > 0) break;
-      if (t == 3)
-        dcg_set_launch(ctx, 16, 16, 32);
-      else
-        dcg_set_launch(ctx, tiles[t][0], tiles[t][1], stages[k]);
+  for (int t = 0; t < 3 && rc == DCG_OK; ++t)
+    for (int k = 0; k < 6 && rc == DCG_OK; ++k) {
+      dcg_set_launch(ctx, tiles[t][0], tiles[t][1], stages[k]);
       float ms = 0.f;
       for (int r = 0; r <= reps && rc == DCG_OK; ++r) {
         if (r == 1) cudaEventRecord(a, s);
@@ -1153,7 +1149,7 @@ dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const d
       cudaEventSynchronize(b);
       cudaEventElapsedTime(&ms, a, b);
       ms /= reps;
-      if (ms_out) ms_out[5 * t + k] = ms;
+      if (ms_out) ms_out[6 * t + k] = ms;
       if (ms < best) {
         best = ms;
         bt = t;
@@ -1164,11 +1160,10 @@ dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const d
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc != DCG_OK) return rc;
-  const int btw = bt == 3 ? 16 : tiles[bt][0], bth = bt == 3 ? 16 : tiles[bt][1], bst = bt == 3 ? 32 : stages[bs];
-  dcg_set_launch(ctx, btw, bth, bst);
-  if (tile_w) *tile_w = btw;
-  if (tile_h) *tile_h = bth;
-  if (stage) *stage = bst;
+  dcg_set_launch(ctx, tiles[bt][0], tiles[bt][1], stages[bs]);
+  if (tile_w) *tile_w = tiles[bt][0];
+  if (tile_h) *tile_h = tiles[bt][1];
+  if (stage) *stage = stages[bs];
   return dcg_sync(ctx, stream);
 }
 

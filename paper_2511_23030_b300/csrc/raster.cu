@@ -379,7 +379,10 @@ __device__ __forceinline__ bool meets_block(float ub, float vb, float4 cn) {
   const float X0 = -ub, X1 = 7.f - ub, Y0 = -vb, Y1 = (float)(WY - 1) - vb;
   if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
   const float A = cn.x, B = cn.y, C = cn.z;
-  const float ky = -0.5f * B / C, kx = -0.5f * B / A;  // argmax of dy (resp. dx) for a fixed dx (dy)
+  // argmax of dy (resp. dx) for a fixed dx (dy); an approximate quotient only
+  // moves the evaluation point slightly inside the rectangle, which the
+  // margin below absorbs
+  const float ky = __fdividef(-0.5f * B, C), kx = __fdividef(-0.5f * B, A);
   float best;
   {
     const float dy0 = fminf(fmaxf(ky * X0, Y0), Y1), dy1 = fminf(fmaxf(ky * X1, Y0), Y1);
@@ -746,76 +749,62 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
 }
 
 // ============================================================================
-// Warp-per-tile blends for 16x16 tiles.  One warp owns a whole tile; lane l
-// holds 8 pixels, one in each 8x4 sub-block b (x = (l & 7) + 8 (b & 1),
-// y = (l >> 3) + 4 (b >> 1)).  The warp walks the tile's list 32 instances at
-// a time, computes for each the set of sub-blocks it can reach (3-sigma box,
-// then the exact ellipse-rectangle test), compacts the survivors and
-// evaluates only the reached sub-blocks.  There is no block-level
-// synchronisation; the backward reduces each Gaussian once per tile and
-// issues its vector atomics directly.  Per-pixel arithmetic is identical to
-// the block-per-tile kernels, so results are too.
-__device__ __forceinline__ unsigned subblock_mask(float ul, float vl, float4 cn) {
-  const float den = 4.f * cn.x * cn.z - cn.y * cn.y;
-  const float sxx = -2.f * kLog2e * cn.z / den, syy = -2.f * kLog2e * cn.x / den;
-  const float ex = 3.001f * sqrtf(fmaxf(sxx, 0.f)) + 0.01f;
-  const float ey = 3.001f * sqrtf(fmaxf(syy, 0.f)) + 0.01f;
-  unsigned xm = 0, ym = 0;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-    if (ul + ex >= (float)(8 * i) && ul - ex <= (float)(8 * i + 7)) xm |= 1u << i;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    if (vl + ey >= (float)(4 * i) && vl - ey <= (float)(4 * i + 3)) ym |= 1u << i;
-  unsigned m = 0;
-#pragma unroll
-  for (int b = 0; b < 8; ++b)
-    if (((xm >> (b & 1)) & (ym >> (b >> 1)) & 1u) && meets_block<4>(ul - (float)(8 * (b & 1)), vl - (float)(4 * (b >> 1)), cn))
-      m |= 1u << b;
-  return m;
-}
-
-constexpr int kWPB = 2;  // warps per block of the warp-per-tile kernels
-
-__global__ void __launch_bounds__(32 * kWPB) k_blend_fwd_w(RasterArgs a, const u64* __restrict__ inst, float* __restrict__ rgb,
-                                                     float* __restrict__ dout) {
-  __shared__ float2 s_xy[kWPB][32];
-  __shared__ float4 s_con[kWPB][32];
-  __shared__ float4 s_col[kWPB][32];
-  __shared__ unsigned s_rel[kWPB][32];
-  __shared__ unsigned char s_m[kWPB][32];
+// Warp-per-block blends.  The per-warp work is that of the block-per-tile
+// kernels (one 8 x WY pixel block of a tile, its own walk of the tile's
+// list), but every warp takes its (tile, block) items from a device queue on
+// its own, so there is no block barrier anywhere: a warp whose pixels finish
+// early moves on at once.  Items are numbered tile-major (8 per tile), so the
+// warps of one SM tend to share a tile's list in L1.  The backward has no
+// tile-shared accumulator: after the warp reduction each of the 10 lanes that
+// hold a component of a Gaussian's 2D gradient adds it to global memory
+// (one red instruction per Gaussian and warp).  Per-pixel arithmetic is that
+// of the block-per-tile kernels, so images are identical.
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_blend_fwd_q(RasterArgs a, const u64* __restrict__ inst,
+                                                     float* __restrict__ rgb, float* __restrict__ dout) {
+  using L = TileLayout<TW, TH>;
+  constexpr int PPT = L::PPT;
+  __shared__ float2 s_xy[8][32];
+  __shared__ float4 s_con[8][32];
+  __shared__ float4 s_col[8][32];
+  __shared__ unsigned s_rel[8][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int lx0 = lane & 7, ly0 = lane >> 3;
   const unsigned lt = lanemask_lt();
+  const unsigned n_items = 8u * (unsigned)a.n_tiles;
   for (;;) {
-    unsigned gt = 0;
-    if (lane == 0) gt = atomicAdd(&a.counters->tile_queue, 1u);
-    gt = __shfl_sync(0xffffffffu, gt, 0);
-    if (gt >= (unsigned)a.n_tiles) break;
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(&a.counters->tile_queue, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    const unsigned gt = item >> 3, wb = item & 7u;
+    const int bx0 = (int)(wb % L::WPR) * 8, by0 = (int)(wb / L::WPR) * L::WY;
+    const int lx = bx0 + (lane & 7);
+    const int ly = by0 + (lane >> 3);
     const int v = view_of_tile(a.cams, a.V, gt);
     const DevCam& c = a.cams[v];
     const int W = c.W, H = c.H;
     const int local = (int)gt - c.tile_base;
     const int ty = local / c.ntx, tx = local - ty * c.ntx;
-    const int x0 = tx * 16, y0 = ty * 16;
+    const int x0 = tx * TW, y0 = ty * TH;
     const float x0f = (float)x0, y0f = (float)y0;
-    float T[8], Tf[8], Cr[8], Cg[8], Cb[8], Dz[8];
-    uint32_t last[8];
+    float T[PPT], Tf[PPT], Cr[PPT], Cg[PPT], Cb[PPT], Dz[PPT];
+    uint32_t last[PPT];
     unsigned ev = 0;
-    unsigned alive = 0;  // sub-blocks with a live pixel (warp-uniform)
+    const int px = x0 + lx;
+    int alive = 0;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int px = x0 + lx0 + 8 * (b & 1), py = y0 + ly0 + 4 * (b >> 1);
-      T[b] = (px < W && py < H) ? 1.f : 0.f;
-      Tf[b] = T[b];
-      Cr[b] = Cg[b] = Cb[b] = Dz[b] = 0.f;
-      last[b] = 0;
-      if (__any_sync(0xffffffffu, T[b] > 0.f)) alive |= 1u << b;
+    for (int k = 0; k < PPT; ++k) {
+      const int py = y0 + ly + 4 * k;
+      T[k] = (px < W && py < H) ? 1.f : 0.f;
+      Tf[k] = T[k];
+      Cr[k] = Cg[k] = Cb[k] = Dz[k] = 0.f;
+      last[k] = 0;
+      alive |= T[k] > 0.f;
     }
     const uint2 rg = a.ranges[gt];
-    for (unsigned b0 = rg.x; b0 < rg.y && alive; b0 += 32) {
+    for (unsigned b0 = rg.x; b0 < rg.y && __any_sync(0xffffffffu, alive); b0 += 32) {
       const unsigned idx = b0 + lane;
-      unsigned m = 0;
+      bool pass = false;
       float ul = 0.f, vl = 0.f;
       float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
       unsigned vi = 0;
@@ -825,49 +814,46 @@ __global__ void __launch_bounds__(32 * kWPB) k_blend_fwd_w(RasterArgs a, const u
         cn = a.rec[3ull * vi + 1];
         ul = df_sub_round(r0.x, r0.z, x0f);
         vl = df_sub_round(r0.y, r0.w, y0f);
-        m = subblock_mask(ul, vl, cn) & alive;
+        pass = meets_block<L::WY>(ul - (float)bx0, vl - (float)by0, cn);
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
-      if (m) {
-        const int slot = __popc(bal & lt);
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) {
+        const int slot = __popc(m & lt);
         s_xy[w][slot] = make_float2(ul, vl);
         s_con[w][slot] = cn;
         s_col[w][slot] = a.rec[3ull * vi + 2];
         s_rel[w][slot] = idx - rg.x;
-        s_m[w][slot] = (unsigned char)m;
       }
       __syncwarp();
-      const int cnt = __popc(bal);
+      const int cnt = __popc(m);
       for (int j = 0; j < cnt; ++j) {
         const float2 xy = s_xy[w][j];
         const float4 cq = s_con[w][j];
-        const unsigned mj = s_m[w][j];
-        const float dxa = __fsub_rn((float)lx0, xy.x), dxb = __fsub_rn((float)(lx0 + 8), xy.x);
-        const float sxa = __fmul_rn(dxa, __fmul_rn(cq.x, dxa)), sxb = __fmul_rn(dxb, __fmul_rn(cq.x, dxb));
-        const float bxa = __fmul_rn(cq.y, dxa), bxb = __fmul_rn(cq.y, dxb);
+        const float dx = __fsub_rn((float)lx, xy.x);
+        const float sx = __fmul_rn(dx, __fmul_rn(cq.x, dx));
+        const float bx = __fmul_rn(cq.y, dx);
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          if (!((mj >> b) & 1u)) continue;
-          if (T[b] > 0.f) {
+        for (int k = 0; k < PPT; ++k) {
+          if (T[k] > 0.f) {
             ++ev;
-            const float dy = __fsub_rn((float)(ly0 + 4 * (b >> 1)), xy.y);
-            const float p = blend_power((b & 1) ? sxb : sxa, (b & 1) ? bxb : bxa, cq.z, dy);
+            const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
+            const float p = blend_power(sx, bx, cq.z, dy);
             if (p >= kPMin) {
               const float al = fminf(kAlphaMax, __fmul_rn(cq.w, ex2_approx(p)));
               if (al >= kAlphaMin) {
-                const float Tn = __fmul_rn(T[b], __fsub_rn(1.f, al));
+                const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, al));
                 if (Tn < kTMin) {
-                  Tf[b] = T[b];
-                  T[b] = 0.f;
+                  Tf[k] = T[k];
+                  T[k] = 0.f;
                 } else {
                   const float4 cl = s_col[w][j];
-                  const float wgt = al * T[b];
-                  Cr[b] += wgt * cl.x;
-                  Cg[b] += wgt * cl.y;
-                  Cb[b] += wgt * cl.z;
-                  Dz[b] += wgt * cl.w;
-                  T[b] = Tn;
-                  last[b] = s_rel[w][j] + 1;
+                  const float wgt = al * T[k];
+                  Cr[k] += wgt * cl.x;
+                  Cg[k] += wgt * cl.y;
+                  Cb[k] += wgt * cl.z;
+                  Dz[k] += wgt * cl.w;
+                  T[k] = Tn;
+                  last[k] = s_rel[w][j] + 1;
                 }
               }
             }
@@ -875,9 +861,9 @@ __global__ void __launch_bounds__(32 * kWPB) k_blend_fwd_w(RasterArgs a, const u
         }
       }
       __syncwarp();
+      alive = 0;
 #pragma unroll
-      for (int b = 0; b < 8; ++b)
-        if (((alive >> b) & 1u) && !__any_sync(0xffffffffu, T[b] > 0.f)) alive &= ~(1u << b);
+      for (int k = 0; k < PPT; ++k) alive |= T[k] > 0.f;
     }
     {
       const unsigned wev = __reduce_add_sync(0xffffffffu, ev);
@@ -885,132 +871,118 @@ __global__ void __launch_bounds__(32 * kWPB) k_blend_fwd_w(RasterArgs a, const u
     }
     const long long P = (long long)W * H;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int px = x0 + lx0 + 8 * (b & 1), py = y0 + ly0 + 4 * (b >> 1);
+    for (int k = 0; k < PPT; ++k) {
+      const int py = y0 + ly + 4 * k;
       if (px < W && py < H) {
         const long long pix = (long long)py * W + px;
-        rgb[3 * c.pix_off + pix] = Cr[b];
-        rgb[3 * c.pix_off + P + pix] = Cg[b];
-        rgb[3 * c.pix_off + 2 * P + pix] = Cb[b];
-        dout[c.pix_off + pix] = Dz[b];
-        a.T_final[c.pix_off + pix] = T[b] > 0.f ? T[b] : Tf[b];
-        a.n_contrib[c.pix_off + pix] = last[b];
+        rgb[3 * c.pix_off + pix] = Cr[k];
+        rgb[3 * c.pix_off + P + pix] = Cg[k];
+        rgb[3 * c.pix_off + 2 * P + pix] = Cb[k];
+        dout[c.pix_off + pix] = Dz[k];
+        a.T_final[c.pix_off + pix] = T[k] > 0.f ? T[k] : Tf[k];
+        a.n_contrib[c.pix_off + pix] = last[k];
       }
     }
   }
 }
 
-__global__ void __launch_bounds__(32 * kWPB) k_blend_bwd_w(RasterArgs a, const u64* __restrict__ inst,
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __restrict__ inst,
                                                      const float* __restrict__ dL_drgb,
                                                      const float* __restrict__ dL_ddepth) {
-  __shared__ float2 s_xy[kWPB][32];
-  __shared__ float4 s_con[kWPB][32];
-  __shared__ float4 s_col[kWPB][32];
-  __shared__ unsigned s_rel[kWPB][32];
-  __shared__ unsigned s_vi[kWPB][32];
-  __shared__ unsigned char s_m[kWPB][32];
+  using L = TileLayout<TW, TH>;
+  constexpr int PPT = L::PPT;
+  __shared__ float2 s_xy[8][32];
+  __shared__ float4 s_con[8][32];
+  __shared__ float4 s_col[8][32];
+  __shared__ unsigned s_rel[8][32];
+  __shared__ unsigned s_vi[8][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int lx0 = lane & 7, ly0 = lane >> 3;
   const unsigned lt = lanemask_lt();
-  // lanes that hold each of the 10 components after warp_sum_transpose<10>
-  int owner[10];
-  {
-    float probe[10];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) probe[q] = 0.f;
-    int comp;
-    bool has;
-    warp_sum_transpose<10>(probe, &comp, &has);
-#pragma unroll
-    for (int q = 0; q < 10; ++q) owner[q] = __ffs(__ballot_sync(0xffffffffu, has && comp == q)) - 1;
-  }
+  const unsigned n_items = 8u * (unsigned)a.n_tiles;
+  float* const g2 = reinterpret_cast<float*>(a.grad2d);
   for (;;) {
-    unsigned gt = 0;
-    if (lane == 0) gt = atomicAdd(&a.counters->tile_queue_bwd, 1u);
-    gt = __shfl_sync(0xffffffffu, gt, 0);
-    if (gt >= (unsigned)a.n_tiles) break;
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(&a.counters->tile_queue_bwd, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    const unsigned gt = item >> 3, wb = item & 7u;
+    const int bx0 = (int)(wb % L::WPR) * 8, by0 = (int)(wb / L::WPR) * L::WY;
+    const int lx = bx0 + (lane & 7);
+    const int ly = by0 + (lane >> 3);
     const int v = view_of_tile(a.cams, a.V, gt);
     const DevCam& c = a.cams[v];
     const int W = c.W, H = c.H;
     const int local = (int)gt - c.tile_base;
     const int ty = local / c.ntx, tx = local - ty * c.ntx;
-    const int x0 = tx * 16, y0 = ty * 16;
+    const int x0 = tx * TW, y0 = ty * TH;
     const float x0f = (float)x0, y0f = (float)y0;
     const long long P = (long long)W * H;
-    float T[8], gr[8], gg[8], gb[8], gd[8], Sr[8], Sg[8], Sb[8], Sd[8];
-    uint32_t last[8];
-    uint32_t sub_last[8];  // warp maximum of `last` per sub-block
-    uint32_t wl = 0;
+    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Sr[PPT], Sg[PPT], Sb[PPT], Sd[PPT];
+    uint32_t last[PPT];
+    const int px = x0 + lx;
+    uint32_t mylast = 0;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int px = x0 + lx0 + 8 * (b & 1), py = y0 + ly0 + 4 * (b >> 1);
-      last[b] = 0;
-      T[b] = 0.f;
-      gr[b] = gg[b] = gb[b] = gd[b] = 0.f;
+    for (int k = 0; k < PPT; ++k) {
+      const int py = y0 + ly + 4 * k;
+      last[k] = 0;
+      T[k] = 0.f;
+      gr[k] = gg[k] = gb[k] = gd[k] = 0.f;
       if (px < W && py < H) {
         const long long pix = (long long)py * W + px;
-        T[b] = a.T_final[c.pix_off + pix];
-        last[b] = a.n_contrib[c.pix_off + pix];
-        gr[b] = dL_drgb[3 * c.pix_off + pix];
-        gg[b] = dL_drgb[3 * c.pix_off + P + pix];
-        gb[b] = dL_drgb[3 * c.pix_off + 2 * P + pix];
-        gd[b] = dL_ddepth[c.pix_off + pix];
+        T[k] = a.T_final[c.pix_off + pix];
+        last[k] = a.n_contrib[c.pix_off + pix];
+        gr[k] = dL_drgb[3 * c.pix_off + pix];
+        gg[k] = dL_drgb[3 * c.pix_off + P + pix];
+        gb[k] = dL_drgb[3 * c.pix_off + 2 * P + pix];
+        gd[k] = dL_ddepth[c.pix_off + pix];
       }
-      Sr[b] = Sg[b] = Sb[b] = Sd[b] = 0.f;
-      sub_last[b] = __reduce_max_sync(0xffffffffu, last[b]);
-      wl = max(wl, sub_last[b]);
+      Sr[k] = Sg[k] = Sb[k] = Sd[k] = 0.f;
+      mylast = max(mylast, last[k]);
     }
+    const int warplast = (int)__reduce_max_sync(0xffffffffu, mylast);
     const uint2 rg = a.ranges[gt];
-    for (int hi = (int)wl; hi > 0; hi -= 32) {
+    for (int hi = warplast; hi > 0; hi -= 32) {
       const int rel = hi - 1 - lane;  // lane 0 takes the largest index: compaction keeps reverse order
-      unsigned m = 0;
+      bool pass = false;
       float ul = 0.f, vl = 0.f;
       float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
       unsigned vi = 0;
       if (rel >= 0) {
-        unsigned live = 0;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) live |= (sub_last[b] > (uint32_t)rel ? 1u : 0u) << b;
-        if (live) {
-          vi = (unsigned)inst[rg.x + rel];
-          const float4 r0 = a.rec[3ull * vi + 0];
-          cn = a.rec[3ull * vi + 1];
-          ul = df_sub_round(r0.x, r0.z, x0f);
-          vl = df_sub_round(r0.y, r0.w, y0f);
-          m = subblock_mask(ul, vl, cn) & live;
-        }
+        vi = (unsigned)inst[rg.x + rel];
+        const float4 r0 = a.rec[3ull * vi + 0];
+        cn = a.rec[3ull * vi + 1];
+        ul = df_sub_round(r0.x, r0.z, x0f);
+        vl = df_sub_round(r0.y, r0.w, y0f);
+        pass = meets_block<L::WY>(ul - (float)bx0, vl - (float)by0, cn);
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
-      if (m) {
-        const int slot = __popc(bal & lt);
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) {
+        const int slot = __popc(m & lt);
         s_xy[w][slot] = make_float2(ul, vl);
         s_con[w][slot] = cn;
         s_col[w][slot] = a.rec[3ull * vi + 2];
         s_rel[w][slot] = (unsigned)rel;
         s_vi[w][slot] = vi;
-        s_m[w][slot] = (unsigned char)m;
       }
       __syncwarp();
-      const int cnt = __popc(bal);
+      const int cnt = __popc(m);
       for (int j = 0; j < cnt; ++j) {
         const int r = (int)s_rel[w][j];
         const float2 xy = s_xy[w][j];
         const float4 cq = s_con[w][j];
-        const unsigned mj = s_m[w][j];
-        const float dxa = __fsub_rn((float)lx0, xy.x), dxb = __fsub_rn((float)(lx0 + 8), xy.x);
-        const float sxa = __fmul_rn(dxa, __fmul_rn(cq.x, dxa)), sxb = __fmul_rn(dxb, __fmul_rn(cq.x, dxb));
-        const float bxa = __fmul_rn(cq.y, dxa), bxb = __fmul_rn(cq.y, dxb);
+        const float dx = __fsub_rn((float)lx, xy.x);
+        const float sx = __fmul_rn(dx, __fmul_rn(cq.x, dx));
+        const float bx = __fmul_rn(cq.y, dx);
         float acc[10];
 #pragma unroll
         for (int q = 0; q < 10; ++q) acc[q] = 0.f;
         bool any = false;
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          if (!((mj >> b) & 1u)) continue;
-          if (r < (int)last[b]) {
-            const float dx = (b & 1) ? dxb : dxa;
-            const float dy = __fsub_rn((float)(ly0 + 4 * (b >> 1)), xy.y);
-            const float p = blend_power((b & 1) ? sxb : sxa, (b & 1) ? bxb : bxa, cq.z, dy);
+        for (int k = 0; k < PPT; ++k) {
+          if (r < (int)last[k]) {
+            const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
+            const float p = blend_power(sx, bx, cq.z, dy);
             if (p >= kPMin) {
               const float G = ex2_approx(p);
               const float araw = __fmul_rn(cq.w, G);
@@ -1018,18 +990,18 @@ __global__ void __launch_bounds__(32 * kWPB) k_blend_bwd_w(RasterArgs a, const u
               if (al >= kAlphaMin) {
                 any = true;
                 const float4 cl = s_col[w][j];
-                T[b] = __fdividef(T[b], 1.f - al);
-                const float wgt = al * T[b];
-                acc[6] += wgt * gr[b];
-                acc[7] += wgt * gg[b];
-                acc[8] += wgt * gb[b];
-                acc[9] += wgt * gd[b];
-                const float dal = T[b] * ((cl.x - Sr[b]) * gr[b] + (cl.y - Sg[b]) * gg[b] + (cl.z - Sb[b]) * gb[b] +
-                                          (cl.w - Sd[b]) * gd[b]);
-                Sr[b] = al * cl.x + (1.f - al) * Sr[b];
-                Sg[b] = al * cl.y + (1.f - al) * Sg[b];
-                Sb[b] = al * cl.z + (1.f - al) * Sb[b];
-                Sd[b] = al * cl.w + (1.f - al) * Sd[b];
+                T[k] = __fdividef(T[k], 1.f - al);
+                const float wgt = al * T[k];
+                acc[6] += wgt * gr[k];
+                acc[7] += wgt * gg[k];
+                acc[8] += wgt * gb[k];
+                acc[9] += wgt * gd[k];
+                const float dal = T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] +
+                                          (cl.w - Sd[k]) * gd[k]);
+                Sr[k] = al * cl.x + (1.f - al) * Sr[k];
+                Sg[k] = al * cl.y + (1.f - al) * Sg[k];
+                Sb[k] = al * cl.z + (1.f - al) * Sb[k];
+                Sd[k] = al * cl.w + (1.f - al) * Sd[k];
                 if (araw < kAlphaMax) {
                   acc[5] += dal * G;
                   const float dp = dal * cq.w * G * kLn2;
@@ -1047,15 +1019,7 @@ __global__ void __launch_bounds__(32 * kWPB) k_blend_bwd_w(RasterArgs a, const u
           int comp;
           bool has;
           const float tot = warp_sum_transpose<10>(acc, &comp, &has);
-          float g[10];
-#pragma unroll
-          for (int q = 0; q < 10; ++q) g[q] = __shfl_sync(0xffffffffu, tot, owner[q]);
-          if (lane < 3) {
-            float4* gp = a.grad2d + 3ull * s_vi[w][j];
-            if (lane == 0) atomicAdd(gp + 0, make_float4(g[0], g[1], g[2], g[3]));
-            else if (lane == 1) atomicAdd(gp + 1, make_float4(g[4], g[5], g[6], g[7]));
-            else atomicAdd(reinterpret_cast<float2*>(gp + 2), make_float2(g[8], g[9]));
-          }
+          if (has && tot != 0.f) atomicAdd(g2 + 12ull * s_vi[w][j] + comp, tot);
         }
       }
       __syncwarp();
@@ -1514,19 +1478,27 @@ static void blend_bwd_slots_launch(RasterArgs& a, const u64* inst, const float* 
   k_blend_bwd_slots<TW, TH><<<grid, 256, kSlotSmem, st>>>(a, inst, dr, dd);
 }
 
-static void blend_w_launch(bool fwd, RasterArgs& a, const u64* inst, float* rgb, float* dout, const float* dr,
+template <int TW, int TH>
+static void blend_q_launch(bool fwd, RasterArgs& a, const u64* inst, float* rgb, float* dout, const float* dr,
                            const float* dd, cudaStream_t st) {
   static int occ_f = -1, occ_b = -1;
   if (occ_f < 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_blend_fwd_w, 32 * kWPB, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_blend_bwd_w, 32 * kWPB, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_blend_fwd_q<TW, TH>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_blend_bwd_q<TW, TH>, 256, 0);
   }
   const int occ = fwd ? occ_f : occ_b;
-  const int grid = max(1, min((a.n_tiles + kWPB - 1) / kWPB, a.num_sms * max(occ, 1)));
+  const int grid = max(1, min(a.n_tiles, a.num_sms * max(occ, 1)));
   if (fwd)
-    k_blend_fwd_w<<<grid, 32 * kWPB, 0, st>>>(a, inst, rgb, dout);
+    k_blend_fwd_q<TW, TH><<<grid, 256, 0, st>>>(a, inst, rgb, dout);
   else
-    k_blend_bwd_w<<<grid, 32 * kWPB, 0, st>>>(a, inst, dr, dd);
+    k_blend_bwd_q<TW, TH><<<grid, 256, 0, st>>>(a, inst, dr, dd);
+}
+
+static void blend_q_dispatch(bool fwd, RasterArgs& a, const u64* inst, float* rgb, float* dout, const float* dr,
+                             const float* dd, cudaStream_t st) {
+  if (a.tile_w == 32 && a.tile_h == 32) blend_q_launch<32, 32>(fwd, a, inst, rgb, dout, dr, dd, st);
+  else if (a.tile_w == 32 && a.tile_h == 16) blend_q_launch<32, 16>(fwd, a, inst, rgb, dout, dr, dd, st);
+  else blend_q_launch<16, 16>(fwd, a, inst, rgb, dout, dr, dd, st);
 }
 
 #define DCG_STAGES(TW, TH, CALL)                  \
@@ -1582,7 +1554,7 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   a.prof(PH_BINNING, false, st);
   a.prof(PH_BLEND_FWD, true, st);
   if (a.stage == 32) {
-    blend_w_launch(true, a, is, rgb, dout, nullptr, nullptr, st);
+    blend_q_dispatch(true, a, is, rgb, dout, nullptr, nullptr, st);
   } else {
 #define FWD_CALL(TW, TH, SG) blend_fwd_launch<TW, TH, SG>(a, is, rgb, dout, st)
     DCG_TILES(FWD_CALL)
@@ -1600,7 +1572,7 @@ void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb
   if (dL_dpose) cudaMemsetAsync(dL_dpose, 0, sizeof(float) * 6 * a.V, st);
   a.prof(PH_BLEND_BWD, true, st);
   if (a.stage == 32) {
-    blend_w_launch(false, a, inst_sorted, nullptr, nullptr, dL_drgb, dL_ddepth, st);
+    blend_q_dispatch(false, a, inst_sorted, nullptr, nullptr, dL_drgb, dL_ddepth, st);
   } else if (a.bwd_slots) {
     if (a.tile_w == 32 && a.tile_h == 32) blend_bwd_slots_launch<32, 32>(a, inst_sorted, dL_drgb, dL_ddepth, st);
     else if (a.tile_w == 32 && a.tile_h == 16) blend_bwd_slots_launch<32, 16>(a, inst_sorted, dL_drgb, dL_ddepth, st);

@@ -76,8 +76,10 @@ __global__ void k_radix_scan(uint32_t* hist, int P, uint32_t* totals) {
 // Stable scatter.  The block walks its partition in chunks of 8 warps x 256
 // items; warp w owns the chunk's w-th run of 256 consecutive items and ranks
 // them round by round (32 lanes per round) with per-warp digit counters, so
-// that the rank order equals the input order.  The digit bases (exclusive
-// scan of the 256 digit totals) are computed by every block.
+// that the rank order equals the input order.  The chunk is then reordered by
+// digit in shared memory and written out as contiguous runs per digit
+// (coalesced stores).  The digit bases (exclusive scan of the 256 digit
+// totals) are computed by every block.
 constexpr int kSortWarps = 8;
 constexpr int kSortRounds = 8;
 constexpr int kSortChunk = kSortWarps * 32 * kSortRounds;
@@ -86,6 +88,8 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, 
                                                        int nbits, const uint32_t* hist, const uint32_t* totals) {
   __shared__ uint32_t wcnt[kSortWarps][256];
   __shared__ uint32_t run[256];
+  __shared__ uint32_t cstart[256];
+  __shared__ u64 stage[kSortChunk];
   const u64 n = *n_ptr;
   u64 beg, end;
   partition_of(n, &beg, &end);
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, 
       pos[r] = base + rank;
     }
     __syncthreads();
-    // exclusive scan across warps for digit `tid`
+    // exclusive scan across warps for digit `tid`, then over digits for the chunk
     uint32_t acc = 0;
 #pragma unroll
     for (int k = 0; k < kSortWarps; ++k) {
@@ -128,11 +132,22 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, 
       wcnt[k][tid] = acc;
       acc += t;
     }
+    {
+      uint32_t tot;
+      cstart[tid] = block_excl_scan<uint32_t>(acc, &tot);
+    }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
       const unsigned d = dig[r];
-      if (d < 256u) out[run[d] + wcnt[w][d] + pos[r]] = key[r];
+      if (d < 256u) stage[cstart[d] + wcnt[w][d] + pos[r]] = key[r];
+    }
+    __syncthreads();
+    const int cnt = (int)min((u64)kSortChunk, end - c0);
+    for (int p = tid; p < cnt; p += 256) {
+      const u64 k = stage[p];
+      const unsigned d = (unsigned)((k >> shift) & mask);
+      out[run[d] + (uint32_t)p - cstart[d]] = k;
     }
     __syncthreads();
     run[tid] += acc;

@@ -347,20 +347,19 @@ def dcg_state_evals(ctx, state=None, stream=None) -> int:
 
 
 TUNE_TILES = [(16, 16), (32, 16), (32, 32)]
-TUNE_STAGES = [64, 96, 128, 192, 256]
+TUNE_STAGES = [64, 96, 128, 192, 256, 32]  # 32: warp-per-block kernels
 
 
 def dcg_autotune(ctx, g: dcg_gaussians, n: int, cams, rgb, depth, dL_drgb, dL_ddepth, grads: dcg_gaussians, reps=3,
                  stream=None):
     arr = make_cameras(cams)
     tw, th, sg = _I32(), _I32(), _I32()
-    ms = np.zeros(16, np.float32)
+    ms = np.zeros(18, np.float32)
     check(ctx, lib().dcg_autotune(ctx, ctypes.byref(g), n, arr, len(cams), ptr(rgb), ptr(depth), ptr(dL_drgb),
                                   ptr(dL_ddepth), ctypes.byref(grads), reps, ctypes.byref(tw), ctypes.byref(th),
                                   ctypes.byref(sg), ptr(ms), stream_ptr(stream)))
-    table = {f"{TUNE_TILES[i // 5][0]}x{TUNE_TILES[i // 5][1]}/{TUNE_STAGES[i % 5]}": round(float(ms[i]), 4)
-             for i in range(15)}
-    table["16x16/32 (warp per tile)"] = round(float(ms[15]), 4)
+    table = {f"{TUNE_TILES[i // 6][0]}x{TUNE_TILES[i // 6][1]}/{TUNE_STAGES[i % 6]}": round(float(ms[i]), 4)
+             for i in range(18)}
     return {"tile": [tw.value, th.value], "stage": sg.value, "ms": table}
 
 

@@ -50,12 +50,12 @@ def ctx0():
     dcg.dcg_destroy(c)
 
 
-BWD_VARIANTS = {"warp": dict(flags=0), "slots": dict(flags=1), "warp_per_tile": dict(flags=0, stage=32)}
+BWD_VARIANTS = {"warp": dict(flags=0), "slots": dict(flags=1), "warp_per_block": dict(flags=0, stage=32)}
 
 
 @pytest.fixture(scope="module", params=list(BWD_VARIANTS))
 def ctx0b(request):
-    # every blend variant: block per tile with warp reductions or lane slots, warp per tile
+    # every blend variant: block per tile with warp reductions or lane slots, warp per block
     c = make_ctx(deg=0, n_max=100_000, views=8, **BWD_VARIANTS[request.param])
     yield c
     dcg.dcg_destroy(c)
@@ -202,7 +202,8 @@ def test_batched_views_equal_single_views(ctx):
 
 
 @pytest.mark.parametrize("tile,stage", [((16, 16), 64), ((32, 16), 128), ((32, 32), 256), ((16, 16), 192),
-                                        ((32, 32), 96), ((16, 16), 32)])
+                                        ((32, 32), 96), ((16, 16), 32), ((32, 16), 32),
+                                        ((32, 32), 32)])
 def test_launch_shapes_agree(ctx, tile, stage):
     P, cams = _room_views(n=60_000, n_views=1, seed=4)
     dcg.dcg_set_launch(ctx, 16, 16, 128)
