@@ -291,11 +291,15 @@ dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, void* stream);
 
 /* Copies of the state's per-tile sorted lists for checks (host outputs; any
  * may be NULL): ranges [n_tiles, 2] (start, end) into ids, ids [n_instances]
- * (view-local Gaussian index), per (view, Gaussian) FP32 depth [n_views * n],
- * tile rectangle [n_views * n, 4] (x0, y0, x1, y1 inclusive; x1 < x0 if culled),
- * per-pixel final transmittance and contributor count.  Synchronises. */
-dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, float* depth, int32_t* rect,
-                          float* T_final, int32_t* n_contrib, void* stream);
+ * (pair index v n + i), masks [n_instances] (bit b: the instance's Gaussian
+ * may reach warp block b of the tile; blocks are 8 pixels wide and
+ * tile_w tile_h / 64 high, numbered row-major), per (view, Gaussian) FP32
+ * depth [n_views * n], 3-sigma tile rectangle [n_views * n, 4] (x0, y0, x1,
+ * y1 inclusive; x1 < x0 if culled), per-pixel final transmittance and
+ * contributor count.  A tile lists the Gaussians whose rectangle covers it
+ * and whose support ellipse reaches its pixel rectangle.  Synchronises. */
+dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, uint8_t* masks, float* depth,
+                          int32_t* rect, float* T_final, int32_t* n_contrib, void* stream);
 
 /* ---------------------------------------------------------------- learned chunk prefetch
  * A small MLP proposes chunks that the next ~20 frames will need, so that

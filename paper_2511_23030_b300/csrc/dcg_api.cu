@@ -285,6 +285,9 @@ void state_free(dcg_render_state* st) {
 }
 
 bool valid_tile(int tw, int th) { return (tw == 16 && th == 16) || (tw == 32 && th == 16) || (tw == 32 && th == 32); }
+// instance keys hold the global tile id in 24 bits
+constexpr int kMaxTiles = 1 << 24;
+
 bool valid_stage(int s) { return s == 32 || s == 64 || s == 96 || s == 128 || s == 192 || s == 256; }
 
 dcg_status check_cams(dcg_ctx* ctx, const dcg_camera* cams, int V) {
@@ -947,7 +950,8 @@ dcg_status dcg_render_fwd(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const
   int tiles = 0;
   CK(cudaEventSynchronize(st->ev_cams));  // staging buffer free again
   fill_devcams(cams, V, tw, th, st->h_cams, &pix, &tiles);
-  if (pix > st->cap_pix || tiles > st->cap_tiles) return fail(ctx, DCG_ERR_CAPACITY, "pixel or tile capacity exceeded");
+  if (pix > st->cap_pix || tiles > st->cap_tiles || tiles > kMaxTiles)
+    return fail(ctx, DCG_ERR_CAPACITY, "pixel or tile capacity exceeded");
   CK(cudaMemcpyAsync(st->d_cams, st->h_cams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(st->ev_cams, s));
   st->g = *g;
@@ -1029,7 +1033,8 @@ dcg_status dcg_window_capture(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, c
   int64_t pix = 0;
   int tiles = 0;
   fill_devcams(cams, V, tw, th, ctx->h_wcams, &pix, &tiles);
-  if (pix > st->cap_pix || tiles > st->cap_tiles) return fail(ctx, DCG_ERR_CAPACITY, "pixel or tile capacity exceeded");
+  if (pix > st->cap_pix || tiles > st->cap_tiles || tiles > kMaxTiles)
+    return fail(ctx, DCG_ERR_CAPACITY, "pixel or tile capacity exceeded");
   // loss cameras (pixel offsets) live in the second half of the staging buffer
   DevCam* lc = ctx->h_wcams + kMaxViewsApi;
   for (int v = 0; v < V; ++v) lc[v] = ctx->h_wcams[v];
@@ -1221,8 +1226,8 @@ dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, void* stream) 
   return DCG_OK;
 }
 
-dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, float* depth, int32_t* rect,
-                          float* T_final, int32_t* n_contrib, void* stream) {
+dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, uint8_t* masks, float* depth,
+                          int32_t* rect, float* T_final, int32_t* n_contrib, void* stream) {
   if (!st || !st->valid) return DCG_ERR_STATE;
   dcg_ctx* ctx = st->ctx;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1232,7 +1237,7 @@ dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids,
   const int64_t K = (int64_t)h.n_inst_c, pairs = (int64_t)st->V * st->n;
   if (ranges) CK(cudaMemcpyAsync(ranges, st->ranges, sizeof(uint2) * st->n_tiles, cudaMemcpyDeviceToHost, s));
   std::vector<u64> inst;
-  if (ids) {
+  if (ids || masks) {
     inst.resize((size_t)K);
     if (K) CK(cudaMemcpyAsync(inst.data(), st->inst_sorted, 8 * (size_t)K, cudaMemcpyDeviceToHost, s));
   }
@@ -1247,6 +1252,8 @@ dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids,
   CK(cudaStreamSynchronize(s));
   if (ids)
     for (int64_t k = 0; k < K; ++k) ids[k] = (uint32_t)(inst[(size_t)k] & 0xffffffffu);
+  if (masks)
+    for (int64_t k = 0; k < K; ++k) masks[k] = (uint8_t)(inst[(size_t)k] >> 56);
   if (rect)
     for (int64_t k = 0; k < pairs; ++k) {
       rect[4 * k + 0] = r[(size_t)k].x;

@@ -163,6 +163,125 @@ __device__ __forceinline__ float blend_power(float sx, float bx, float Cp, float
   return __fmaf_rn(dy, __fmaf_rn(Cp, dy, bx), sx);
 }
 
+// ----------------------------------------------------------------------------
+// Support geometry used by binning.  The support region of a Gaussian is the
+// ellipse p(dx, dy) >= pm around its centre, p = A' dx^2 + B' dx dy + C' dy^2
+// with the pre-scaled conic (A', C' < 0) and pm = kPMin widened by a margin
+// that keeps every decision below conservative against FP32 rounding.  For a
+// fixed dy, dx ranges over s dy +- sqrt((m - k dy^2) / a) with a = -A',
+// s = B' / 2a, k = -C' - B'^2 / 4a > 0 and m = -pm; the ellipse spans
+// |dy| <= sqrt(m / k), and its right-most point has
+// dy* = sign(s) sqrt(m s^2 a / (k (k + s^2 a))) (the left-most point is its
+// mirror image).  The x-extent of the ellipse within a horizontal band
+// [Y0, Y1] is therefore [xL(dyL), xR(dyR)] with dyR, dyL = +-dy* clamped to the
+// band, which makes both the tile span of a tile row and the warp blocks a
+// Gaussian reaches exact (up to the margin).  Every operation is rounded
+// explicitly so the count and emission passes take identical decisions.
+struct SupportEllipse {
+  float ia, s, k, m, dym, dys;  // ia = 1 / a
+};
+
+// Square root from the hardware approximation: a deterministic function of
+// its input (so count and emission agree); its error is covered by the slack
+// in band_extent.
+__device__ __forceinline__ float sqrt_hw(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ SupportEllipse support_of(float4 cn) {
+  SupportEllipse e;
+  e.ia = __frcp_rn(-cn.x);
+  e.s = __fmul_rn(__fmul_rn(cn.y, 0.5f), e.ia);
+  e.k = __fsub_rn(-cn.z, __fmul_rn(__fmul_rn(__fmul_rn(cn.y, cn.y), 0.25f), e.ia));
+  e.m = -(kPMin * 1.001f - 1e-3f);
+  if (!(e.k > 0.f)) {  // not an ellipse (cannot happen for a valid conic): reach nothing
+    e.k = 0.f;
+    e.dym = -1.f;
+    e.dys = 0.f;
+    return e;
+  }
+  e.dym = sqrt_hw(__fmul_rn(e.m, __frcp_rn(e.k)));
+  const float t = __fmul_rn(__fmul_rn(e.s, e.s), __frcp_rn(e.ia));
+  e.dys = copysignf(sqrt_hw(__fmul_rn(__fmul_rn(e.m, t), __frcp_rn(__fmul_rn(e.k, __fadd_rn(e.k, t))))), e.s);
+  return e;
+}
+
+// x-extent [*xl, *xr] (relative to the centre) of the ellipse within the band
+// dy in [Y0, Y1] (relative to the centre); false if the band misses it.
+__device__ __forceinline__ bool band_extent(const SupportEllipse& e, float Y0, float Y1, float* xl, float* xr) {
+  const float lo = fmaxf(Y0, -e.dym), hi = fminf(Y1, e.dym);
+  if (!(lo <= __fadd_rn(hi, 1e-3f))) return false;
+  const float yr = fminf(fmaxf(e.dys, lo), hi), yl = fminf(fmaxf(-e.dys, lo), hi);
+  const float hr = sqrt_hw(fmaxf(__fmul_rn(__fsub_rn(e.m, __fmul_rn(__fmul_rn(e.k, yr), yr)), e.ia), 0.f));
+  const float hl = sqrt_hw(fmaxf(__fmul_rn(__fsub_rn(e.m, __fmul_rn(__fmul_rn(e.k, yl), yl)), e.ia), 0.f));
+  // slack: 1e-3 px plus a relative 1e-5 for the approximate square roots
+  *xr = __fadd_rn(__fmaf_rn(hr, 1.00001f, __fmul_rn(e.s, yr)), 1e-3f);
+  *xl = __fsub_rn(__fmaf_rn(hl, -1.00001f, __fmul_rn(e.s, yl)), 1e-3f);
+  return true;
+}
+
+// Instance keys: bits [0, 32) pair index, [32, 56) global tile, [56, 64) the
+// warp blocks of the tile that the Gaussian reaches (bit b: the 8 x WY pixel
+// block b of TileLayout, row-major).  Only the tile bits are sorted.
+constexpr int kMaskShift = 56;
+constexpr unsigned kTileMask = (1u << 24) - 1u;
+// Rectangles of more tiles than this are emitted whole (every tile).
+constexpr int kTightMax = 1024;
+
+__device__ __forceinline__ bool block_bit(u64 key, int b) { return ((key >> (kMaskShift + b)) & 1ull) != 0ull; }
+
+// Tile row ty of rectangle r: the x-extents of the ellipse in the row's nbr
+// bands of warp blocks (wy pixel rows each) go to bl/br (returned bitmask:
+// bands reached), and the tiles [*j0, *j1] (offsets from the rectangle's
+// first column) covered by their union.  Returns false if the row gets no
+// instance.  Whole rectangles (more than kTightMax tiles) keep every tile.
+__device__ __forceinline__ bool row_span(const SupportEllipse& e, float4 r0, short4 r, int ty, int tw, int th, int wy,
+                                         bool whole, int* j0, int* j1, float* bl, float* br, unsigned* bands) {
+  const int nbr = th / wy;
+  const float vl = df_sub_round(r0.y, r0.w, (float)(ty * th));
+  float xl = 3.0e38f, xr = -3.0e38f;
+  unsigned bm = 0;
+  for (int rb = 0; rb < nbr; ++rb) {
+    const float y0 = __fsub_rn((float)(rb * wy), vl);
+    if (band_extent(e, y0, __fadd_rn(y0, (float)(wy - 1)), &bl[rb], &br[rb])) {
+      bm |= 1u << rb;
+      xl = fminf(xl, bl[rb]);
+      xr = fmaxf(xr, br[rb]);
+    }
+  }
+  *bands = bm;
+  if (whole) {
+    *j0 = 0;
+    *j1 = r.z - r.x;
+    return true;
+  }
+  if (!bm) return false;
+  const float ux = df_sub_round(r0.x, r0.z, (float)(r.x * tw));  // centre relative to the rectangle's left edge
+  const float itw = 1.f / (float)tw;                             // tw is a power of two: exact
+  const float a0 = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(ux, xl), (float)(tw - 1)), itw));
+  const float a1 = floorf(__fmul_rn(__fadd_rn(ux, xr), itw));
+  *j0 = (int)fminf(fmaxf(a0, 0.f), 32767.f);
+  *j1 = (int)fmaxf(fminf(a1, (float)(r.z - r.x)), -1.f);
+  return *j0 <= *j1;
+}
+
+// Tiles of the rectangle r that the Gaussian reaches (the emission pass
+// emits exactly these).
+__device__ __forceinline__ uint32_t tight_count(float4 r0, float4 cn, short4 r, int tw, int th, int wy) {
+  const bool whole = (r.z - r.x + 1) * (r.w - r.y + 1) > kTightMax;
+  const SupportEllipse e = support_of(cn);
+  uint32_t k = 0;
+  float bl[4], br[4];
+  unsigned bands;
+  for (int ty = r.y; ty <= r.w; ++ty) {
+    int j0, j1;
+    if (row_span(e, r0, r, ty, tw, th, wy, whole, &j0, &j1, bl, br, &bands)) k += (uint32_t)(j1 - j0 + 1);
+  }
+  return k;
+}
+
 // FP32 camera depth in the fixed order ((R20 mx + R21 my) + R22 mz) + t2.
 __device__ __forceinline__ float cam_depth(const DevCam& c, float mx, float my, float mz) {
   return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.R[6], mx), __fmul_rn(c.R[7], my)), __fmul_rn(c.R[8], mz)), c.t[2]);
@@ -254,10 +373,14 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(RasterArgs a) {
       }
       const int tx0 = (int)px0 / a.tile_w, tx1 = (int)px1 / a.tile_w;
       const int ty0 = (int)py0 / a.tile_h, ty1 = (int)py1 / a.tile_h;
-      a.touched[vi] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-      a.rect[vi] = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
+      const short4 rc = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
+      a.rect[vi] = rc;
       const float idet = 1.f / det;
       const float A = cc * idet, B = -cb * idet, Cn = ca * idet;
+      const float4 r0 = make_float4(ud.hi, vd.hi, ud.lo, vd.lo);
+      const float4 cn = make_float4(-0.5f * kLog2e * A, -kLog2e * B, -0.5f * kLog2e * Cn, opac);
+      // tiles of the rectangle that the support ellipse reaches
+      a.touched[vi] = tight_count(r0, cn, rc, a.tile_w, a.tile_h, a.tile_w * a.tile_h / 64);
       // colour: SH of the direction from the camera centre
       float dx = mx - c.C[0], dy = my - c.C[1], dz = mz - c.C[2];
       const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
@@ -272,8 +395,8 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(RasterArgs a) {
         for (int k = 0; k < D; ++k) acc += g[(11 + 3 * k + ch) * S + i] * Y[k];
         col[ch] = fmaxf(acc + 0.5f, 0.f);
       }
-      a.rec[3 * vi + 0] = make_float4(ud.hi, vd.hi, ud.lo, vd.lo);
-      a.rec[3 * vi + 1] = make_float4(-0.5f * kLog2e * A, -kLog2e * B, -0.5f * kLog2e * Cn, opac);
+      a.rec[3 * vi + 0] = r0;
+      a.rec[3 * vi + 1] = cn;
       a.rec[3 * vi + 2] = make_float4(col[0], col[1], col[2], z);
       a.grad2d[3 * vi + 0] = make_float4(0.f, 0.f, 0.f, 0.f);
       a.grad2d[3 * vi + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -311,12 +434,18 @@ struct InstCount {
   int ib;
   __device__ u64 operator()(u64 s) const { return touched[pair_of_key(list[s], ib, n)]; }
 };
+// One thread per visible pair (in depth order) writes its instances: the
+// tiles of its rectangle that the support ellipse reaches (row spans, the
+// same as the count in k_preprocess_fwd), each with the mask of the warp
+// blocks the ellipse reaches.
 struct InstEmit {
   const u64* list;
   const short4* rect;
+  const float4* rec;
   const DevCam* cams;
   long long n;
   int ib;
+  int tw, th, wpr, wy;
   u64* inst;
   u64 cap;
   __device__ void operator()(u64 s, u64 off, u64) const {
@@ -324,14 +453,47 @@ struct InstEmit {
     const u64 vi = pair_of_key(key, ib, n);
     const int v = (int)(key >> (31 + ib));
     const short4 r = rect[vi];
+    const float4 r0 = rec[3 * vi + 0], cn = rec[3 * vi + 1];
+    const bool whole = (r.z - r.x + 1) * (r.w - r.y + 1) > kTightMax;
+    const SupportEllipse e = support_of(cn);
     const u64 base = (u64)cams[v].tile_base;
     const int ntx = cams[v].ntx;
+    const int nbr = th / wy;  // rows of warp blocks per tile (2 or 4)
     u64 o = off;
-    for (int ty = r.y; ty <= r.w; ++ty)
-      for (int tx = r.x; tx <= r.z; ++tx, ++o)
-        if (o < cap) inst[o] = ((base + (u64)ty * ntx + tx) << 32) | vi;
+    for (int ty = r.y; ty <= r.w; ++ty) {
+      int j0, j1;
+      float bl[4], br[4];
+      unsigned bands;
+      if (!row_span(e, r0, r, ty, tw, th, wy, whole, &j0, &j1, bl, br, &bands)) continue;
+      for (int j = j0; j <= j1; ++j) {
+        const int tx = r.x + j;
+        const float ul = df_sub_round(r0.x, r0.z, (float)(tx * tw));
+        unsigned mask = 0;
+        for (int rb = 0; rb < nbr; ++rb) {
+          if (!((bands >> rb) & 1u)) continue;
+          for (int c = 0; c < wpr; ++c) {
+            const float x0 = __fsub_rn((float)(8 * c), ul);
+            if (bl[rb] <= __fadd_rn(x0, 7.f) && br[rb] >= x0) mask |= 1u << (rb * wpr + c);
+          }
+        }
+        if (o < cap) inst[o] = ((u64)mask << kMaskShift) | ((base + (u64)ty * ntx + tx) << 32) | vi;
+        ++o;
+      }
+    }
   }
 };
+
+struct InstOffset {
+  u64* off;
+  __device__ void operator()(u64 s, u64 o, u64) const { off[s] = o; }
+};
+
+// Runs an emission functor for items [0, *n_ptr) at precomputed offsets.
+template <class EmitF>
+__global__ void __launch_bounds__(256) k_emit_at(const u64* n_ptr, const u64* off, EmitF e) {
+  const u64 n = *n_ptr;
+  for (u64 s = blockIdx.x * (u64)blockDim.x + threadIdx.x; s < n; s += (u64)gridDim.x * blockDim.x) e(s, off[s], 0);
+}
 
 __global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
   const u64 k = c->n_inst;
@@ -342,9 +504,9 @@ __global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
 __global__ void k_ranges(const u64* __restrict__ inst, const u64* n_ptr, uint2* __restrict__ ranges) {
   const u64 K = *n_ptr;
   for (u64 k = blockIdx.x * (u64)blockDim.x + threadIdx.x; k < K; k += (u64)gridDim.x * blockDim.x) {
-    const unsigned t = (unsigned)(inst[k] >> 32);
-    if (k == 0 || (unsigned)(inst[k - 1] >> 32) != t) ranges[t].x = (unsigned)k;
-    if (k + 1 == K || (unsigned)(inst[k + 1] >> 32) != t) ranges[t].y = (unsigned)(k + 1);
+    const unsigned t = (unsigned)(inst[k] >> 32) & kTileMask;
+    if (k == 0 || ((unsigned)(inst[k - 1] >> 32) & kTileMask) != t) ranges[t].x = (unsigned)k;
+    if (k + 1 == K || ((unsigned)(inst[k + 1] >> 32) & kTileMask) != t) ranges[t].y = (unsigned)(k + 1);
   }
 }
 
@@ -367,33 +529,6 @@ struct TileLayout {
   static constexpr int WPR = TW / 8;     // warp blocks per tile row
   static_assert(WPR * (TH / WY) == 8, "eight warp blocks per tile");
 };
-
-// Can Gaussian (conic cn, centre (ub, vb) relative to the warp block origin)
-// reach the support test p >= kPMin at some pixel of the warp block
-// [0, 7] x [0, WY-1]?  p(dx, dy) = A' dx^2 + B' dx dy + C' dy^2 is concave
-// (A', C' < 0); its maximum over the block rectangle is 0 if the centre is
-// inside, else it lies on an edge, where the 1D maximiser is clamped to the
-// edge.  A small margin keeps the test conservative against FP32 rounding.
-template <int WY>
-__device__ __forceinline__ bool meets_block(float ub, float vb, float4 cn) {
-  const float X0 = -ub, X1 = 7.f - ub, Y0 = -vb, Y1 = (float)(WY - 1) - vb;
-  if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
-  const float A = cn.x, B = cn.y, C = cn.z;
-  // argmax of dy (resp. dx) for a fixed dx (dy); an approximate quotient only
-  // moves the evaluation point slightly inside the rectangle, which the
-  // margin below absorbs
-  const float ky = __fdividef(-0.5f * B, C), kx = __fdividef(-0.5f * B, A);
-  float best;
-  {
-    const float dy0 = fminf(fmaxf(ky * X0, Y0), Y1), dy1 = fminf(fmaxf(ky * X1, Y0), Y1);
-    best = fmaxf(X0 * (A * X0 + B * dy0) + C * dy0 * dy0, X1 * (A * X1 + B * dy1) + C * dy1 * dy1);
-  }
-  {
-    const float dx0 = fminf(fmaxf(kx * Y0, X0), X1), dx1 = fminf(fmaxf(kx * Y1, X0), X1);
-    best = fmaxf(best, fmaxf(A * dx0 * dx0 + Y0 * (B * dx0 + C * Y0), A * dx1 * dx1 + Y1 * (B * dx1 + C * Y1)));
-  }
-  return best >= kPMin * 1.001f - 1e-3f;
-}
 
 // Forward blend.  One block per tile (taken from a device queue); each of
 // its 8 warps owns an 8 x WY pixel block and walks the tile's depth-sorted
@@ -447,22 +582,18 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
     for (unsigned b0 = rg.x; b0 < rg.y && __any_sync(0xffffffffu, alive); b0 += 32) {
       const unsigned idx = b0 + lane;
       bool pass = false;
-      float ul = 0.f, vl = 0.f;
-      float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
       unsigned vi = 0;
       if (idx < rg.y) {
-        vi = (unsigned)inst[idx];
-        const float4 r0 = a.rec[3ull * vi + 0];
-        cn = a.rec[3ull * vi + 1];
-        ul = df_sub_round(r0.x, r0.z, x0f);
-        vl = df_sub_round(r0.y, r0.w, y0f);
-        pass = meets_block<L::WY>(ul - (float)bx0, vl - (float)by0, cn);
+        const u64 key = inst[idx];
+        vi = (unsigned)key;
+        pass = block_bit(key, w);
       }
       const unsigned m = __ballot_sync(0xffffffffu, pass);
       if (pass) {
+        const float4 r0 = a.rec[3ull * vi + 0];
         const int slot = __popc(m & lt);
-        s_xy[w][slot] = make_float2(ul, vl);
-        s_con[w][slot] = cn;
+        s_xy[w][slot] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+        s_con[w][slot] = a.rec[3ull * vi + 1];
         s_col[w][slot] = a.rec[3ull * vi + 2];
         s_rel[w][slot] = idx - rg.x;
       }
@@ -650,22 +781,18 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
       for (int hi = min(send, warplast); hi > sbeg; hi -= 32) {
         const int rel = hi - 1 - lane;  // lane 0 takes the largest index: compaction keeps reverse order
         bool pass = false;
-        float ul = 0.f, vl = 0.f;
-        float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
         unsigned vi = 0;
         if (rel >= sbeg) {
-          vi = (unsigned)inst[rg.x + rel];
-          const float4 r0 = a.rec[3ull * vi + 0];
-          cn = a.rec[3ull * vi + 1];
-          ul = df_sub_round(r0.x, r0.z, x0f);
-          vl = df_sub_round(r0.y, r0.w, y0f);
-          pass = meets_block<L::WY>(ul - (float)bx0, vl - (float)by0, cn);
+          const u64 key = inst[rg.x + rel];
+          vi = (unsigned)key;
+          pass = block_bit(key, w);
         }
         const unsigned m = __ballot_sync(0xffffffffu, pass);
         if (pass) {
+          const float4 r0 = a.rec[3ull * vi + 0];
           const int slot = __popc(m & lt);
-          s_xy[w][slot] = make_float2(ul, vl);
-          s_con[w][slot] = cn;
+          s_xy[w][slot] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+          s_con[w][slot] = a.rec[3ull * vi + 1];
           s_col[w][slot] = a.rec[3ull * vi + 2];
           s_rel[w][slot] = (unsigned)rel;
         }
@@ -805,22 +932,18 @@ __global__ void __launch_bounds__(256) k_blend_fwd_q(RasterArgs a, const u64* __
     for (unsigned b0 = rg.x; b0 < rg.y && __any_sync(0xffffffffu, alive); b0 += 32) {
       const unsigned idx = b0 + lane;
       bool pass = false;
-      float ul = 0.f, vl = 0.f;
-      float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
       unsigned vi = 0;
       if (idx < rg.y) {
-        vi = (unsigned)inst[idx];
-        const float4 r0 = a.rec[3ull * vi + 0];
-        cn = a.rec[3ull * vi + 1];
-        ul = df_sub_round(r0.x, r0.z, x0f);
-        vl = df_sub_round(r0.y, r0.w, y0f);
-        pass = meets_block<L::WY>(ul - (float)bx0, vl - (float)by0, cn);
+        const u64 key = inst[idx];
+        vi = (unsigned)key;
+        pass = block_bit(key, wb);
       }
       const unsigned m = __ballot_sync(0xffffffffu, pass);
       if (pass) {
+        const float4 r0 = a.rec[3ull * vi + 0];
         const int slot = __popc(m & lt);
-        s_xy[w][slot] = make_float2(ul, vl);
-        s_con[w][slot] = cn;
+        s_xy[w][slot] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+        s_con[w][slot] = a.rec[3ull * vi + 1];
         s_col[w][slot] = a.rec[3ull * vi + 2];
         s_rel[w][slot] = idx - rg.x;
       }
@@ -945,22 +1068,18 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
     for (int hi = warplast; hi > 0; hi -= 32) {
       const int rel = hi - 1 - lane;  // lane 0 takes the largest index: compaction keeps reverse order
       bool pass = false;
-      float ul = 0.f, vl = 0.f;
-      float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
       unsigned vi = 0;
       if (rel >= 0) {
-        vi = (unsigned)inst[rg.x + rel];
-        const float4 r0 = a.rec[3ull * vi + 0];
-        cn = a.rec[3ull * vi + 1];
-        ul = df_sub_round(r0.x, r0.z, x0f);
-        vl = df_sub_round(r0.y, r0.w, y0f);
-        pass = meets_block<L::WY>(ul - (float)bx0, vl - (float)by0, cn);
+        const u64 key = inst[rg.x + rel];
+        vi = (unsigned)key;
+        pass = block_bit(key, wb);
       }
       const unsigned m = __ballot_sync(0xffffffffu, pass);
       if (pass) {
+        const float4 r0 = a.rec[3ull * vi + 0];
         const int slot = __popc(m & lt);
-        s_xy[w][slot] = make_float2(ul, vl);
-        s_con[w][slot] = cn;
+        s_xy[w][slot] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+        s_con[w][slot] = a.rec[3ull * vi + 1];
         s_col[w][slot] = a.rec[3ull * vi + 2];
         s_rel[w][slot] = (unsigned)rel;
         s_vi[w][slot] = vi;
@@ -1105,22 +1224,18 @@ __global__ void __launch_bounds__(256) k_blend_bwd_slots(RasterArgs a, const u64
       for (int hi = min(send, warplast); hi > sbeg; hi -= 32) {
         const int rel = hi - 1 - lane;
         bool pass = false;
-        float ul = 0.f, vl = 0.f;
-        float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
         unsigned vi = 0;
         if (rel >= sbeg) {
-          vi = (unsigned)inst[rg.x + rel];
-          const float4 r0 = a.rec[3ull * vi + 0];
-          cn = a.rec[3ull * vi + 1];
-          ul = df_sub_round(r0.x, r0.z, x0f);
-          vl = df_sub_round(r0.y, r0.w, y0f);
-          pass = meets_block<L::WY>(ul - (float)bx0, vl - (float)by0, cn);
+          const u64 key = inst[rg.x + rel];
+          vi = (unsigned)key;
+          pass = block_bit(key, w);
         }
         const unsigned m = __ballot_sync(0xffffffffu, pass);
         if (pass) {
+          const float4 r0 = a.rec[3ull * vi + 0];
           const int slot = __popc(m & lt);
-          s_xy[w][slot] = make_float2(ul, vl);
-          s_con[w][slot] = cn;
+          s_xy[w][slot] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+          s_con[w][slot] = a.rec[3ull * vi + 1];
           s_col[w][slot] = a.rec[3ull * vi + 2];
           s_rel[w][slot] = (unsigned)rel;
         }
@@ -1541,16 +1656,22 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
                  &a.counters->n_vis, st);
   const int lbits = 31 + a.view_bits;
   u64* ls = radix_sort(a.list_a, a.list_b, &a.counters->n_vis, a.idx_bits, a.idx_bits + lbits, a.hist, a.P, st);
-  part_scan_emit(&a.counters->n_vis, 0, InstCount{ls, a.touched, a.n, a.idx_bits},
-                 InstEmit{ls, a.rect, a.cams, a.n, a.idx_bits, a.inst_a, (u64)a.cap_inst}, a.part, a.P,
+  // instance offsets by an ordered scan (the free list buffer holds them),
+  // then the emission itself, one thread per visible pair with no barriers
+  u64* offs = ls == a.list_a ? a.list_b : a.list_a;
+  part_scan_emit(&a.counters->n_vis, 0, InstCount{ls, a.touched, a.n, a.idx_bits}, InstOffset{offs}, a.part, a.P,
                  &a.counters->n_inst, st);
+  k_emit_at<<<a.num_sms * 8, 256, 0, st>>>(&a.counters->n_vis, offs,
+                                           InstEmit{ls, a.rect, a.rec, a.cams, a.n, a.idx_bits, a.tile_w, a.tile_h,
+                                                    a.tile_w / 8, a.tile_w * a.tile_h / 64, a.inst_a,
+                                                    (u64)a.cap_inst});
   k_clamp_inst<<<1, 1, 0, st>>>(a.counters, (u64)a.cap_inst, a.errword);
   int tb = 1;
   while ((1ll << tb) < (long long)a.n_tiles) ++tb;
   u64* is = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, 32, 32 + tb, a.hist, a.P, st);
   cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)max(a.n_tiles, 1), st);
   k_ranges<<<a.num_sms * 4, 256, 0, st>>>(is, &a.counters->n_inst_c, a.ranges);
-  count_launch(6 + 3 * ((lbits + 7) / 8) + 3 * ((tb + 7) / 8) + 2);
+  count_launch(7 + 3 * ((lbits + 7) / 8) + 3 * ((tb + 7) / 8) + 2);
   a.prof(PH_BINNING, false, st);
   a.prof(PH_BLEND_FWD, true, st);
   if (a.stage == 32) {

@@ -75,7 +75,7 @@ _SIGS = {
                                    _P]),
     "dcg_set_launch": (ctypes.c_int, [_P, _I32, _I32, _I32]),
     "dcg_state_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
-    "dcg_state_read": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "dcg_state_read": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "dcg_profile": (ctypes.c_int, [_P, _I32]),
     "dcg_autotune": (ctypes.c_int, [_P, ctypes.POINTER(dcg_gaussians), _I64, ctypes.POINTER(dcg_camera), _I32, _P, _P,
                                     _P, _P, ctypes.POINTER(dcg_gaussians), _I32, ctypes.POINTER(_I32),
@@ -309,19 +309,21 @@ def dcg_state_stats(ctx, state=None, stream=None):
 
 
 def dcg_state_read(ctx, state, n_views, n, n_pix, stream=None):
-    """Returns dict(ranges [T,2] u32, ids [K] u32, depth [V*n] f32, rect [V*n,4] i32, T [P], n_contrib [P])."""
+    """Returns dict(ranges [T,2] u32, ids [K] u32, masks [K] u8, depth [V*n] f32, rect [V*n,4] i32, T [P],
+    n_contrib [P])."""
     nv, K, T = dcg_state_stats(ctx, state, stream)
     ranges = np.zeros((T, 2), np.uint32)
     ids = np.zeros(max(K, 1), np.uint32)
+    masks = np.zeros(max(K, 1), np.uint8)
     depth = np.zeros(max(n_views * n, 1), np.float32)
     rect = np.zeros((max(n_views * n, 1), 4), np.int32)
     Tf = np.zeros(max(n_pix, 1), np.float32)
     nc = np.zeros(max(n_pix, 1), np.int32)
     st = state if state is not None else dcg_default_state(ctx)
-    check(ctx, lib().dcg_state_read(st, ptr(ranges), ptr(ids), ptr(depth), ptr(rect), ptr(Tf), ptr(nc),
+    check(ctx, lib().dcg_state_read(st, ptr(ranges), ptr(ids), ptr(masks), ptr(depth), ptr(rect), ptr(Tf), ptr(nc),
                                     stream_ptr(stream)))
-    return dict(ranges=ranges, ids=ids[:K], depth=depth[: n_views * n], rect=rect[: n_views * n], T=Tf[:n_pix],
-                n_contrib=nc[:n_pix], n_visible=nv)
+    return dict(ranges=ranges, ids=ids[:K], masks=masks[:K], depth=depth[: n_views * n], rect=rect[: n_views * n],
+                T=Tf[:n_pix], n_contrib=nc[:n_pix], n_visible=nv)
 
 
 def dcg_profile(ctx, enable: bool):

@@ -93,20 +93,43 @@ def test_sort_keys_bit_exact_and_tile_lists_valid(ctx0, orc):
     st = dcg.dcg_state_read(ctx0, None, 1, n, cam.W * cam.H)
     z32 = orc.depth_f32(P[:, :3], cam)
     assert np.array_equal(st["depth"].view(np.uint32), z32.view(np.uint32))
-    # per tile: exactly the Gaussians whose rectangle covers it, in (depth bits, index) order
+    # per tile: the Gaussians whose rectangle covers it, in (depth bits, index) order, less those
+    # whose support ellipse misses the tile.  What is left out must miss it: q > 9 at every pixel of
+    # the tile by the oracle's FP64 conic.  Block masks likewise: a cleared bit means q > 9 at every
+    # pixel of that 8 x 4 block.
+    pr = orc.project(P, 0, cam)
     rect = st["rect"]
     vis = rect[:, 2] >= rect[:, 0]
     ntx = (cam.W + 15) // 16
-    ranges, ids = st["ranges"], st["ids"]
+    ranges, ids, masks = st["ranges"], st["ids"], st["masks"]
     zb = st["depth"].view(np.uint32)
+    by, bx = np.mgrid[0:4, 0:8]
+
+    def q_at(g, xs, ys):
+        dx, dy = xs - pr["u"][g], ys - pr["v"][g]
+        return pr["A"][g] * dx * dx + 2.0 * pr["B"][g] * dx * dy + pr["C"][g] * dy * dy
+
+    dropped = kept = 0
     for t in range(ranges.shape[0]):
         ty, tx = divmod(t, ntx)
         lst = ids[ranges[t, 0]:ranges[t, 1]]
+        msk = masks[ranges[t, 0]:ranges[t, 1]]
         want = np.nonzero(vis & (rect[:, 0] <= tx) & (rect[:, 2] >= tx) & (rect[:, 1] <= ty) & (rect[:, 3] >= ty))[0]
         want = want[np.lexsort((want, zb[want]))]
-        assert np.array_equal(lst, want), t
+        assert np.array_equal(lst, want[np.isin(want, lst)]), t  # an ordered subsequence
+        for g in want[~np.isin(want, lst)]:
+            ys, xs = np.mgrid[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16]
+            assert q_at(g, xs, ys).min() > 9.0, (t, g)
+            dropped += 1
+        for g, m in zip(lst, msk):
+            for b in range(8):
+                if not (m >> b) & 1:
+                    xs = 16 * tx + 8 * (b % 2) + bx
+                    ys = 16 * ty + 4 * (b // 2) + by
+                    assert q_at(g, xs, ys).min() > 9.0, (t, g, b)
+            kept += 1
+    assert kept > 0 and dropped > 0
     # rectangles agree with the oracle's FP64 extents except within rounding of a pixel boundary
-    pr = orc.project(P, 0, cam)
     x0 = np.floor(pr["u"] - pr["ex"])
     x1 = np.ceil(pr["u"] + pr["ex"])
     near = (np.abs(pr["u"] - pr["ex"] - np.round(pr["u"] - pr["ex"])) < 1e-4) | (
