@@ -8,7 +8,8 @@
 //                         projection, 2D conic, 3-sigma tile rectangle and SH
 //                         colour are written as one 48-byte record.
 //   2. compaction         ordered scan over pairs -> keys (view, depth, index)
-//   3. depth sort         stable LSD radix sort on (view, depth bits)
+//   3. depth sort         stable LSD radix sort on the depth bits (the view
+//                         bits ride along; the tile sort separates views)
 //   4. instance emission  ordered scan of tiles-touched in depth order; each
 //                         instance is (global tile id, pair index)
 //   5. tile sort          stable LSD radix sort on the tile id only: the depth
@@ -834,13 +835,16 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
                   Sb[k] = al * cl.z + (1.f - al) * Sb[k];
                   Sd[k] = al * cl.w + (1.f - al) * Sd[k];
                   if (araw < kAlphaMax) {
-                    acc[5] += dal * G;
-                    const float dp = dal * cq.w * G * kLn2;
-                    acc[2] += dp * dx * dx;
-                    acc[3] += dp * dx * dy;
-                    acc[4] += dp * dy * dy;
-                    acc[0] -= dp * (2.f * cq.x * dx + cq.y * dy);
-                    acc[1] -= dp * (cq.y * dx + 2.f * cq.z * dy);
+                    // moments of dL/dalpha * G; the conic and opacity factors are applied per
+                    // Gaussian in k_preprocess_bwd
+                    const float gG = dal * G;
+                    const float gx = gG * dx, gy = gG * dy;
+                    acc[5] += gG;
+                    acc[0] += gx;
+                    acc[1] += gy;
+                    acc[2] += gx * dx;
+                    acc[3] += gx * dy;
+                    acc[4] += gy * dy;
                   }
                 }
               }
@@ -1122,13 +1126,16 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
                 Sb[k] = al * cl.z + (1.f - al) * Sb[k];
                 Sd[k] = al * cl.w + (1.f - al) * Sd[k];
                 if (araw < kAlphaMax) {
-                  acc[5] += dal * G;
-                  const float dp = dal * cq.w * G * kLn2;
-                  acc[2] += dp * dx * dx;
-                  acc[3] += dp * dx * dy;
-                  acc[4] += dp * dy * dy;
-                  acc[0] -= dp * (2.f * cq.x * dx + cq.y * dy);
-                  acc[1] -= dp * (cq.y * dx + 2.f * cq.z * dy);
+                  // moments of dL/dalpha * G; the conic and opacity factors are applied per
+                  // Gaussian in k_preprocess_bwd
+                  const float gG = dal * G;
+                  const float gx = gG * dx, gy = gG * dy;
+                  acc[5] += gG;
+                  acc[0] += gx;
+                  acc[1] += gy;
+                  acc[2] += gx * dx;
+                  acc[3] += gx * dy;
+                  acc[4] += gy * dy;
                 }
               }
             }
@@ -1277,13 +1284,16 @@ __global__ void __launch_bounds__(256) k_blend_bwd_slots(RasterArgs a, const u64
                   Sb[k] = al * cl.z + (1.f - al) * Sb[k];
                   Sd[k] = al * cl.w + (1.f - al) * Sd[k];
                   if (araw < kAlphaMax) {
-                    acc[5] += dal * G;
-                    const float dp = dal * cq.w * G * kLn2;
-                    acc[2] += dp * dx * dx;
-                    acc[3] += dp * dx * dy;
-                    acc[4] += dp * dy * dy;
-                    acc[0] -= dp * (2.f * cq.x * dx + cq.y * dy);
-                    acc[1] -= dp * (cq.y * dx + 2.f * cq.z * dy);
+                    // moments of dL/dalpha * G; the conic and opacity factors are applied per
+                    // Gaussian in k_preprocess_bwd
+                    const float gG = dal * G;
+                    const float gx = gG * dx, gy = gG * dy;
+                    acc[5] += gG;
+                    acc[0] += gx;
+                    acc[1] += gy;
+                    acc[2] += gx * dx;
+                    acc[3] += gx * dy;
+                    acc[4] += gy * dy;
                   }
                 }
               }
@@ -1409,9 +1419,15 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
         const float cc = T1[0] * ST1[0] + T1[1] * ST1[1] + T1[2] * ST1[2] + kDilate;
         const float det = ca * cc - cb * cb;
         const float id = 1.f / det, id2 = id * id;
-        // 2D gradients: du, dv, dA', dB', dC', do, dr, dg, db, dz
-        const float du = g0.x, dv = g0.y;
-        const float dA = g0.z * (-0.5f * kLog2e), dB = g0.w * (-kLog2e), dC = g1.x * (-0.5f * kLog2e);
+        // The blends accumulate, over the pixels, moments of g = dL/dalpha * G:
+        // (sum g dx, sum g dy, sum g dx^2, sum g dx dy, sum g dy^2, sum g), with
+        // dx = x - u, and the colour and depth sums.  Since alpha = o 2^p and
+        // p = A' dx^2 + B' dx dy + C' dy^2, dL/dp = o ln2 g per pixel.
+        const float fo = opac * kLn2;
+        const float Ap = -0.5f * kLog2e * cc * id, Bp = kLog2e * cb * id, Cp = -0.5f * kLog2e * ca * id;
+        const float du = -fo * (2.f * Ap * g0.x + Bp * g0.y), dv = -fo * (Bp * g0.x + 2.f * Cp * g0.y);
+        // gradients of the unscaled conic entries (A' = -A log2(e) / 2, B' = -B log2(e), C' = -C log2(e) / 2)
+        const float dA = fo * g0.z * (-0.5f * kLog2e), dB = fo * g0.w * (-kLog2e), dC = fo * g1.x * (-0.5f * kLog2e);
         const float dop = g1.y;
         const float dcol[3] = {g1.z, g1.w, g2.x};
         const float dzz = g2.y;
@@ -1654,7 +1670,9 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   // compaction into depth keys
   part_scan_emit(nullptr, (u64)pairs, VisCount{a.touched}, VisEmit{a.depth, a.list_a, a.n, a.idx_bits}, a.part, a.P,
                  &a.counters->n_vis, st);
-  const int lbits = 31 + a.view_bits;
+  // Only the 31 depth bits are sorted: the view bits above them ride along,
+  // since the stable tile sort below separates the views anyway.
+  const int lbits = 31;
   u64* ls = radix_sort(a.list_a, a.list_b, &a.counters->n_vis, a.idx_bits, a.idx_bits + lbits, a.hist, a.P, st);
   // instance offsets by an ordered scan (the free list buffer holds them),
   // then the emission itself, one thread per visible pair with no barriers
