@@ -14,7 +14,8 @@
 //                         instance is (global tile id, pair index)
 //   5. tile sort          stable LSD radix sort on the tile id only: the depth
 //                         order inside a tile survives from step 3
-//   6. ranges             [start, end) per tile
+//   6. ranges + masks     [start, end) per tile; each instance gets the mask
+//                         of the tile's warp blocks its Gaussian reaches
 //   7. k_blend_fwd        persistent blocks take tiles from a device queue,
 //                         stage records in shared memory, blend front to back
 // Backward:
@@ -233,32 +234,20 @@ constexpr int kTightMax = 1024;
 
 __device__ __forceinline__ bool block_bit(u64 key, int b) { return ((key >> (kMaskShift + b)) & 1ull) != 0ull; }
 
-// Tile row ty of rectangle r: the x-extents of the ellipse in the row's nbr
-// bands of warp blocks (wy pixel rows each) go to bl/br (returned bitmask:
-// bands reached), and the tiles [*j0, *j1] (offsets from the rectangle's
-// first column) covered by their union.  Returns false if the row gets no
-// instance.  Whole rectangles (more than kTightMax tiles) keep every tile.
-__device__ __forceinline__ bool row_span(const SupportEllipse& e, float4 r0, short4 r, int ty, int tw, int th, int wy,
-                                         bool whole, int* j0, int* j1, float* bl, float* br, unsigned* bands) {
-  const int nbr = th / wy;
-  const float vl = df_sub_round(r0.y, r0.w, (float)(ty * th));
-  float xl = 3.0e38f, xr = -3.0e38f;
-  unsigned bm = 0;
-  for (int rb = 0; rb < nbr; ++rb) {
-    const float y0 = __fsub_rn((float)(rb * wy), vl);
-    if (band_extent(e, y0, __fadd_rn(y0, (float)(wy - 1)), &bl[rb], &br[rb])) {
-      bm |= 1u << rb;
-      xl = fminf(xl, bl[rb]);
-      xr = fmaxf(xr, br[rb]);
-    }
-  }
-  *bands = bm;
+// Tiles [*j0, *j1] (offsets from the rectangle's first column) of tile row
+// ty of rectangle r that the ellipse reaches; false if none.  Whole
+// rectangles (more than kTightMax tiles) keep every tile.
+// r0 = (u_hi, v_hi, u_lo, v_lo).
+__device__ __forceinline__ bool row_span(const SupportEllipse& e, float4 r0, short4 r, int ty, int tw, int th,
+                                         bool whole, int* j0, int* j1) {
   if (whole) {
     *j0 = 0;
     *j1 = r.z - r.x;
     return true;
   }
-  if (!bm) return false;
+  const float vl = df_sub_round(r0.y, r0.w, (float)(ty * th));
+  float xl, xr;
+  if (!band_extent(e, -vl, __fsub_rn((float)(th - 1), vl), &xl, &xr)) return false;
   const float ux = df_sub_round(r0.x, r0.z, (float)(r.x * tw));  // centre relative to the rectangle's left edge
   const float itw = 1.f / (float)tw;                             // tw is a power of two: exact
   const float a0 = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(ux, xl), (float)(tw - 1)), itw));
@@ -270,17 +259,32 @@ __device__ __forceinline__ bool row_span(const SupportEllipse& e, float4 r0, sho
 
 // Tiles of the rectangle r that the Gaussian reaches (the emission pass
 // emits exactly these).
-__device__ __forceinline__ uint32_t tight_count(float4 r0, float4 cn, short4 r, int tw, int th, int wy) {
+__device__ __forceinline__ uint32_t tight_count(float4 r0, float4 cn, short4 r, int tw, int th) {
   const bool whole = (r.z - r.x + 1) * (r.w - r.y + 1) > kTightMax;
   const SupportEllipse e = support_of(cn);
   uint32_t k = 0;
-  float bl[4], br[4];
-  unsigned bands;
   for (int ty = r.y; ty <= r.w; ++ty) {
     int j0, j1;
-    if (row_span(e, r0, r, ty, tw, th, wy, whole, &j0, &j1, bl, br, &bands)) k += (uint32_t)(j1 - j0 + 1);
+    if (row_span(e, r0, r, ty, tw, th, whole, &j0, &j1)) k += (uint32_t)(j1 - j0 + 1);
   }
   return k;
+}
+
+// Warp blocks (8 x wy pixels, wpr per row, nbr rows) of a tile that the
+// ellipse reaches; (ul, vl) is its centre relative to the tile origin.
+__device__ __forceinline__ unsigned tile_block_mask(const SupportEllipse& e, float ul, float vl, int wpr, int wy,
+                                                    int nbr) {
+  unsigned mask = 0;
+  for (int rb = 0; rb < nbr; ++rb) {
+    float xl, xr;
+    const float y0 = __fsub_rn((float)(rb * wy), vl);
+    if (!band_extent(e, y0, __fadd_rn(y0, (float)(wy - 1)), &xl, &xr)) continue;
+    for (int c = 0; c < wpr; ++c) {
+      const float x0 = __fsub_rn((float)(8 * c), ul);
+      if (xl <= __fadd_rn(x0, 7.f) && xr >= x0) mask |= 1u << (rb * wpr + c);
+    }
+  }
+  return mask;
 }
 
 // FP32 camera depth in the fixed order ((R20 mx + R21 my) + R22 mz) + t2.
@@ -381,7 +385,7 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(RasterArgs a) {
       const float4 r0 = make_float4(ud.hi, vd.hi, ud.lo, vd.lo);
       const float4 cn = make_float4(-0.5f * kLog2e * A, -kLog2e * B, -0.5f * kLog2e * Cn, opac);
       // tiles of the rectangle that the support ellipse reaches
-      a.touched[vi] = tight_count(r0, cn, rc, a.tile_w, a.tile_h, a.tile_w * a.tile_h / 64);
+      a.touched[vi] = tight_count(r0, cn, rc, a.tile_w, a.tile_h);
       // colour: SH of the direction from the camera centre
       float dx = mx - c.C[0], dy = my - c.C[1], dz = mz - c.C[2];
       const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
@@ -437,8 +441,8 @@ struct InstCount {
 };
 // One thread per visible pair (in depth order) writes its instances: the
 // tiles of its rectangle that the support ellipse reaches (row spans, the
-// same as the count in k_preprocess_fwd), each with the mask of the warp
-// blocks the ellipse reaches.
+// same as the count in k_preprocess_fwd).  Block masks are added after the
+// tile sort (k_ranges_masks).
 struct InstEmit {
   const u64* list;
   const short4* rect;
@@ -446,7 +450,7 @@ struct InstEmit {
   const DevCam* cams;
   long long n;
   int ib;
-  int tw, th, wpr, wy;
+  int tw, th;
   u64* inst;
   u64 cap;
   __device__ void operator()(u64 s, u64 off, u64) const {
@@ -459,27 +463,13 @@ struct InstEmit {
     const SupportEllipse e = support_of(cn);
     const u64 base = (u64)cams[v].tile_base;
     const int ntx = cams[v].ntx;
-    const int nbr = th / wy;  // rows of warp blocks per tile (2 or 4)
     u64 o = off;
     for (int ty = r.y; ty <= r.w; ++ty) {
       int j0, j1;
-      float bl[4], br[4];
-      unsigned bands;
-      if (!row_span(e, r0, r, ty, tw, th, wy, whole, &j0, &j1, bl, br, &bands)) continue;
-      for (int j = j0; j <= j1; ++j) {
-        const int tx = r.x + j;
-        const float ul = df_sub_round(r0.x, r0.z, (float)(tx * tw));
-        unsigned mask = 0;
-        for (int rb = 0; rb < nbr; ++rb) {
-          if (!((bands >> rb) & 1u)) continue;
-          for (int c = 0; c < wpr; ++c) {
-            const float x0 = __fsub_rn((float)(8 * c), ul);
-            if (bl[rb] <= __fadd_rn(x0, 7.f) && br[rb] >= x0) mask |= 1u << (rb * wpr + c);
-          }
-        }
-        if (o < cap) inst[o] = ((u64)mask << kMaskShift) | ((base + (u64)ty * ntx + tx) << 32) | vi;
-        ++o;
-      }
+      if (!row_span(e, r0, r, ty, tw, th, whole, &j0, &j1)) continue;
+      const u64 row = base + (u64)ty * ntx + (u64)r.x;
+      for (int j = j0; j <= j1; ++j, ++o)
+        if (o < cap) inst[o] = ((row + (u64)j) << 32) | vi;
     }
   }
 };
@@ -502,12 +492,29 @@ __global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
   if (k > cap) atomicOr(errword, ERRW_CAPACITY_BIT);
 }
 
-__global__ void k_ranges(const u64* __restrict__ inst, const u64* n_ptr, uint2* __restrict__ ranges) {
+// Per-tile ranges [start, end) of the sorted instances, and each instance
+// copied to `out` with the mask of the tile's warp blocks its Gaussian
+// reaches in bits [56, 64) (one thread per instance).
+__global__ void k_ranges_masks(const u64* __restrict__ inst, const u64* n_ptr, uint2* __restrict__ ranges,
+                               u64* __restrict__ out, const float4* __restrict__ rec, const DevCam* __restrict__ cams,
+                               int V, int tw, int th) {
   const u64 K = *n_ptr;
+  const int wpr = tw / 8, wy = tw * th / 64, nbr = th / wy;
   for (u64 k = blockIdx.x * (u64)blockDim.x + threadIdx.x; k < K; k += (u64)gridDim.x * blockDim.x) {
-    const unsigned t = (unsigned)(inst[k] >> 32) & kTileMask;
+    const u64 key = inst[k];
+    const unsigned t = (unsigned)(key >> 32) & kTileMask;
     if (k == 0 || ((unsigned)(inst[k - 1] >> 32) & kTileMask) != t) ranges[t].x = (unsigned)k;
     if (k + 1 == K || ((unsigned)(inst[k + 1] >> 32) & kTileMask) != t) ranges[t].y = (unsigned)(k + 1);
+    int v = 0;
+    while (v + 1 < V && (int)t >= cams[v + 1].tile_base) ++v;
+    const DevCam& c = cams[v];
+    const int local = (int)t - c.tile_base;
+    const int ty = local / c.ntx, tx = local - ty * c.ntx;
+    const unsigned vi = (unsigned)key;
+    const float4 r0 = rec[3ull * vi + 0], cn = rec[3ull * vi + 1];
+    const unsigned m = tile_block_mask(support_of(cn), df_sub_round(r0.x, r0.z, (float)(tx * tw)),
+                                       df_sub_round(r0.y, r0.w, (float)(ty * th)), wpr, wy, nbr);
+    out[k] = key | ((u64)m << kMaskShift);
   }
 }
 
@@ -1679,16 +1686,17 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   u64* offs = ls == a.list_a ? a.list_b : a.list_a;
   part_scan_emit(&a.counters->n_vis, 0, InstCount{ls, a.touched, a.n, a.idx_bits}, InstOffset{offs}, a.part, a.P,
                  &a.counters->n_inst, st);
-  k_emit_at<<<a.num_sms * 8, 256, 0, st>>>(&a.counters->n_vis, offs,
-                                           InstEmit{ls, a.rect, a.rec, a.cams, a.n, a.idx_bits, a.tile_w, a.tile_h,
-                                                    a.tile_w / 8, a.tile_w * a.tile_h / 64, a.inst_a,
-                                                    (u64)a.cap_inst});
+  k_emit_at<<<a.num_sms * 8, 256, 0, st>>>(
+      &a.counters->n_vis, offs,
+      InstEmit{ls, a.rect, a.rec, a.cams, a.n, a.idx_bits, a.tile_w, a.tile_h, a.inst_a, (u64)a.cap_inst});
   k_clamp_inst<<<1, 1, 0, st>>>(a.counters, (u64)a.cap_inst, a.errword);
   int tb = 1;
   while ((1ll << tb) < (long long)a.n_tiles) ++tb;
-  u64* is = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, 32, 32 + tb, a.hist, a.P, st);
+  u64* sorted = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, 32, 32 + tb, a.hist, a.P, st);
+  u64* is = sorted == a.inst_a ? a.inst_b : a.inst_a;  // sorted instances with block masks
   cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)max(a.n_tiles, 1), st);
-  k_ranges<<<a.num_sms * 4, 256, 0, st>>>(is, &a.counters->n_inst_c, a.ranges);
+  k_ranges_masks<<<a.num_sms * 8, 256, 0, st>>>(sorted, &a.counters->n_inst_c, a.ranges, is, a.rec, a.cams, a.V,
+                                                 a.tile_w, a.tile_h);
   count_launch(7 + 3 * ((lbits + 7) / 8) + 3 * ((tb + 7) / 8) + 2);
   a.prof(PH_BINNING, false, st);
   a.prof(PH_BLEND_FWD, true, st);
