@@ -89,6 +89,9 @@ typedef struct {
   int32_t page_gaussians;  /* Gaussians per device/host page (power of two) */
   int32_t flags;           /* bit 0: backward blend accumulates per-lane shared slots instead of
                               reducing each Gaussian across the warp (same result); others 0 */
+  int32_t with_moments;    /* 1: every Gaussian stores its Adam moments m and v beside its
+                              parameters (pages, host tier and active buffer hold 3 F components);
+                              0 (default): parameters only */
 } dcg_config;
 
 /* Fill *cfg with defaults (s = 4 m, degree 3, budget 6 M, 8 views ...). */
@@ -194,6 +197,37 @@ dcg_status dcg_tier_stats(const dcg_ctx* ctx, int64_t* loads, int64_t* evictions
 /* Read n Gaussians of chunk `chunk` (ascending-id index) from the host tier
  * into params_out (host, planar with stride n).  For checks and checkpoints. */
 dcg_status dcg_chunk_read(dcg_ctx* ctx, int32_t chunk, float* params_out, int64_t n);
+
+/* Adam moments of chunk `chunk` as last written to the host tier (m_out and
+ * v_out host, planar with stride n, n = the chunk's count; fresh Gaussians
+ * start at zero).  Contexts with with_moments only (DCG_ERR_ARG otherwise). */
+dcg_status dcg_chunk_read_moments(dcg_ctx* ctx, int32_t chunk, float* m_out, float* v_out, int64_t n);
+
+/* ---------------------------------------------------------------- optimizer
+ * The paper optimises the parameters of the active chunks against the loss
+ * of Eq. 2-4 (Sec. III-E "Optimization") and keeps optimizer state per
+ * Gaussian (Sec. III-F resets it after a loop closure).  With with_moments,
+ * the Adam moments travel with their Gaussians: dcg_gather_active copies
+ * them into the active buffer beside the parameters, dcg_scatter_back and
+ * evictions write them back. */
+
+/* Views of the active set's moments (library-owned device memory, planar
+ * like the parameters, in the order of the last dcg_gather_active; valid
+ * until dcg_destroy).  DCG_ERR_ARG without with_moments. */
+dcg_status dcg_active_moments(dcg_ctx* ctx, dcg_gaussians* m, dcg_gaussians* v);
+
+/* One Adam step (Kingma & Ba, bias-corrected) over the n Gaussians of the
+ * gathered active set, in place on `params` (dev, usually the active view
+ * from dcg_gather_active) and the active moments, with gradients `grads`
+ * (dev, planar):
+ *   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+ *   p <- p - lr[c] / (1 - b1^step) * m / (sqrt(v) / sqrt(1 - b2^step) + eps)
+ * lr: host, F learning rates, one per component.  step >= 1 counts the steps
+ * taken so far including this one.  Errors: DCG_ERR_ARG (hyper-parameters,
+ * degree, strides, no moments), DCG_ERR_STATE (n differs from the gathered
+ * set).  Stream-ordered; call dcg_scatter_back afterwards to keep the result. */
+dcg_status dcg_adam_step(dcg_ctx* ctx, const dcg_gaussians* params, const dcg_gaussians* grads, int64_t n,
+                         const float* lr, float beta1, float beta2, float eps, int64_t step, void* stream);
 
 /* ---------------------------------------------------------------- rendering
  * Differentiable rasterisation of RGB and depth (Sec. III-E: the selected

@@ -163,42 +163,43 @@ void launch_cull(const int32_t* coords, int C, const dcg_camera* cams, int V, fl
 }
 
 // ----------------------------------------------------------------------------
-// Page copies.  A page holds page_g Gaussians component-major:
-// component c of slot j at page[c * page_g + j].  desc[3d .. 3d+2] =
-// (page index, count, offset in the active buffer).
-__global__ void k_gather_pages(const float* __restrict__ pool, long long page_g, int F,
+// Page copies.  A page holds page_g Gaussians component-major with Fp
+// components: component c of slot j at page[c * page_g + j].
+// desc[3d .. 3d+2] = (page index, count, offset in the active buffer).
+// Components [c0, c0 + nc) of each page map to rows 0 .. nc-1 of `active`.
+__global__ void k_gather_pages(const float* __restrict__ pool, long long page_g, int Fp, int c0, int nc,
                                const long long* __restrict__ desc, float* __restrict__ active, long long stride) {
   const long long d = blockIdx.x;
   const long long page = desc[3 * d], cnt = desc[3 * d + 1], off = desc[3 * d + 2];
-  const float* src = pool + page * page_g * F;
-  for (int c = blockIdx.y; c < F; c += gridDim.y) {
+  const float* src = pool + page * page_g * Fp + (long long)c0 * page_g;
+  for (int c = blockIdx.y; c < nc; c += gridDim.y) {
     const float* s = src + (long long)c * page_g;
     float* t = active + (long long)c * stride + off;
     for (long long j = threadIdx.x; j < cnt; j += blockDim.x) t[j] = s[j];
   }
 }
 
-__global__ void k_scatter_pages(float* __restrict__ pool, long long page_g, int F,
+__global__ void k_scatter_pages(float* __restrict__ pool, long long page_g, int Fp, int c0, int nc,
                                 const long long* __restrict__ desc, const float* __restrict__ active,
                                 long long stride) {
   const long long d = blockIdx.x;
   const long long page = desc[3 * d], cnt = desc[3 * d + 1], off = desc[3 * d + 2];
-  float* dst = pool + page * page_g * F;
-  for (int c = blockIdx.y; c < F; c += gridDim.y) {
+  float* dst = pool + page * page_g * Fp + (long long)c0 * page_g;
+  for (int c = blockIdx.y; c < nc; c += gridDim.y) {
     float* t = dst + (long long)c * page_g;
     const float* s = active + (long long)c * stride + off;
     for (long long j = threadIdx.x; j < cnt; j += blockDim.x) t[j] = s[j];
   }
 }
 
-void launch_page_copy(bool gather, float* pool, long long page_g, int F, const long long* desc, int nd,
+void launch_page_copy(bool gather, float* pool, long long page_g, int Fp, int c0, int nc, const long long* desc, int nd,
                       float* active, long long stride, cudaStream_t st) {
-  if (nd <= 0) return;
-  dim3 grid(nd, F < 16 ? F : 16);
+  if (nd <= 0 || nc <= 0) return;
+  dim3 grid(nd, nc < 16 ? nc : 16);
   if (gather)
-    k_gather_pages<<<grid, 256, 0, st>>>(pool, page_g, F, desc, active, stride);
+    k_gather_pages<<<grid, 256, 0, st>>>(pool, page_g, Fp, c0, nc, desc, active, stride);
   else
-    k_scatter_pages<<<grid, 256, 0, st>>>(pool, page_g, F, desc, active, stride);
+    k_scatter_pages<<<grid, 256, 0, st>>>(pool, page_g, Fp, c0, nc, desc, active, stride);
   count_launch();
 }
 

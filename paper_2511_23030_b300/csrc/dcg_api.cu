@@ -64,7 +64,8 @@ struct dcg_render_state {
 
 struct dcg_ctx {
   dcg_config cfg{};
-  int F = 0;
+  int F = 0;   // parameter components per Gaussian
+  int Fs = 0;  // stored components per Gaussian: F, or 3 F with the Adam moments (m then v)
   int device = 0;
   int num_sms = 148;
   std::string err;
@@ -197,7 +198,7 @@ cudaError_t page_copy(dcg_ctx* ctx, float* dst, const float* src, int64_t cnt, c
   if (cnt <= 0) return cudaSuccess;
   const size_t pitch = (size_t)ctx->page_g * 4;
   if (cnt == ctx->page_g) return cudaMemcpyAsync(dst, src, (size_t)ctx->page_floats * 4, kind, s);
-  return cudaMemcpy2DAsync(dst, pitch, src, pitch, (size_t)cnt * 4, (size_t)ctx->F, kind, s);
+  return cudaMemcpy2DAsync(dst, pitch, src, pitch, (size_t)cnt * 4, (size_t)ctx->Fs, kind, s);
 }
 
 int64_t pages_for(dcg_ctx* ctx, int64_t count) { return (count + ctx->page_g - 1) / ctx->page_g; }
@@ -209,7 +210,7 @@ dcg_status evict_chunk(dcg_ctx* ctx, Chunk& ch) {
       const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - (int64_t)p * ctx->page_g);
       CK(page_copy(ctx, host_page(ctx, ch.host_pages[p]), dev_page(ctx, ch.dev_pages[p]), cnt,
                    cudaMemcpyDeviceToHost, ctx->copy_stream));
-      ctx->bytes_d2h += cnt * ctx->F * 4;
+      ctx->bytes_d2h += cnt * ctx->Fs * 4;
     }
     ch.dirty = false;
   }
@@ -232,7 +233,7 @@ dcg_status load_chunk(dcg_ctx* ctx, Chunk& ch) {
     const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - p * ctx->page_g);
     CK(page_copy(ctx, dev_page(ctx, ch.dev_pages[(size_t)p]), host_page(ctx, ch.host_pages[(size_t)p]), cnt,
                  cudaMemcpyHostToDevice, ctx->copy_stream));
-    ctx->bytes_h2d += cnt * ctx->F * 4;
+    ctx->bytes_h2d += cnt * ctx->Fs * 4;
   }
   if (!ch.ev_load) CK(cudaEventCreateWithFlags(&ch.ev_load, cudaEventDisableTiming));
   CK(cudaEventRecord(ch.ev_load, ctx->copy_stream));
@@ -335,18 +336,19 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
       c.max_chunks <= 0 || c.max_views <= 0 || c.max_views > kMaxViewsApi || c.max_active <= 0 || c.max_pixels <= 0 ||
       c.max_instances <= 0 || c.max_instances >= (1ll << 32) || c.page_gaussians <= 0 ||
       (c.page_gaussians & (c.page_gaussians - 1)) != 0 || !valid_tile(c.tile_w, c.tile_h) || !valid_stage(c.stage) ||
-      (int64_t)c.max_views * c.max_active >= (1ll << 32))
+      (int64_t)c.max_views * c.max_active >= (1ll << 32) || (c.with_moments != 0 && c.with_moments != 1))
     bad = DCG_ERR_ARG;
   if (bad != DCG_OK) {
     delete ctx;
     return bad;
   }
   ctx->F = 11 + 3 * nsh(c.sh_degree);
+  ctx->Fs = c.with_moments ? 3 * ctx->F : ctx->F;
   ctx->tile_w = c.tile_w;
   ctx->tile_h = c.tile_h;
   ctx->stage = c.stage;
   ctx->page_g = c.page_gaussians;
-  ctx->page_floats = ctx->page_g * ctx->F;
+  ctx->page_floats = ctx->page_g * ctx->Fs;
   auto cleanup_fail = [&](dcg_status s) {
     dcg_destroy(ctx);
     return s;
@@ -387,7 +389,7 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
   for (int64_t p = ctx->dev_pages - 1; p >= 0; --p) ctx->dev_free.push_back((int32_t)p);
   for (int64_t p = ctx->host_pages - 1; p >= 0; --p) ctx->host_free.push_back((int32_t)p);
   // active buffer and page descriptors
-  if (dmalloc(&ctx->d_active, (size_t)ctx->F * c.max_active) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
+  if (dmalloc(&ctx->d_active, (size_t)ctx->Fs * c.max_active) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
   ctx->max_desc = ctx->dev_pages;
   if (dmalloc(&ctx->d_desc, 3 * (size_t)ctx->max_desc) != cudaSuccess ||
       cudaHostAlloc((void**)&ctx->h_desc, sizeof(long long) * 3 * (size_t)ctx->max_desc, 0) != cudaSuccess)
@@ -551,6 +553,7 @@ dcg_status dcg_chunk_table_update(dcg_ctx* ctx, const float* params, int64_t str
       }
       float* page = host_page(ctx, ch.host_pages[(size_t)p]);
       for (int f = 0; f < F; ++f) page[(int64_t)f * ctx->page_g + j] = ctx->h_stage[(int64_t)f * n + i];
+      for (int f = F; f < ctx->Fs; ++f) page[(int64_t)f * ctx->page_g + j] = 0.f;  // fresh Adam moments
       ch.count++;
     }
   }
@@ -689,7 +692,8 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
   if (nd > 0) CK(cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(long long) * 3 * nd, cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(ctx->ev_desc, s));
   hook(ctx)(PH_GATHER, true, s);
-  launch_page_copy(true, ctx->d_pool, ctx->page_g, ctx->F, ctx->d_desc, nd, ctx->d_active, ctx->cfg.max_active, s);
+  launch_page_copy(true, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->Fs, ctx->d_desc, nd, ctx->d_active,
+                   ctx->cfg.max_active, s);
   hook(ctx)(PH_GATHER, false, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev_compute, s));
@@ -791,7 +795,16 @@ dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n
       return fail(ctx, DCG_ERR_STATE, "a gathered chunk is no longer resident");
   }
   hook(ctx)(PH_SCATTER, true, s);
-  launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->F, ctx->d_desc, ctx->n_desc, active->data, active->stride, s);
+  if (active->data == ctx->d_active && active->stride == ctx->cfg.max_active) {
+    launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->Fs, ctx->d_desc, ctx->n_desc, ctx->d_active,
+                     ctx->cfg.max_active, s);
+  } else {  // parameters from the caller's buffer, moments from the active buffer
+    launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->F, ctx->d_desc, ctx->n_desc, active->data,
+                     active->stride, s);
+    if (ctx->Fs > ctx->F)
+      launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, ctx->F, ctx->Fs - ctx->F, ctx->d_desc, ctx->n_desc,
+                       ctx->d_active + (size_t)ctx->F * ctx->cfg.max_active, ctx->cfg.max_active, s);
+  }
   hook(ctx)(PH_SCATTER, false, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev_compute, s));
@@ -810,7 +823,7 @@ dcg_status dcg_flush(dcg_ctx* ctx, void* stream) {
       const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - (int64_t)p * ctx->page_g);
       CK(page_copy(ctx, host_page(ctx, ch.host_pages[p]), dev_page(ctx, ch.dev_pages[p]), cnt, cudaMemcpyDeviceToHost,
                    ctx->copy_stream));
-      ctx->bytes_d2h += cnt * ctx->F * 4;
+      ctx->bytes_d2h += cnt * ctx->Fs * 4;
     }
     ch.dirty = false;
   }
@@ -828,6 +841,67 @@ dcg_status dcg_chunk_read(dcg_ctx* ctx, int32_t chunk, float* out, int64_t n) {
     const float* page = host_page(ctx, ch.host_pages[(size_t)p]);
     for (int f = 0; f < ctx->F; ++f) out[(int64_t)f * n + i] = page[(int64_t)f * ctx->page_g + j];
   }
+  return DCG_OK;
+}
+
+dcg_status dcg_chunk_read_moments(dcg_ctx* ctx, int32_t chunk, float* m_out, float* v_out, int64_t n) {
+  if (!ctx || chunk < 0 || chunk >= (int32_t)ctx->chunks.size() || !m_out || !v_out)
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  if (ctx->Fs == ctx->F) return fail(ctx, DCG_ERR_ARG, "the context stores no optimizer moments");
+  const Chunk& ch = ctx->chunks[chunk];
+  if (n != ch.count) return fail(ctx, DCG_ERR_ARG, "n must equal the chunk's count");
+  CK(cudaStreamSynchronize(ctx->copy_stream));
+  const int F = ctx->F;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t p = i / ctx->page_g, j = i - p * ctx->page_g;
+    const float* page = host_page(ctx, ch.host_pages[(size_t)p]);
+    for (int f = 0; f < F; ++f) {
+      m_out[(int64_t)f * n + i] = page[(int64_t)(F + f) * ctx->page_g + j];
+      v_out[(int64_t)f * n + i] = page[(int64_t)(2 * F + f) * ctx->page_g + j];
+    }
+  }
+  return DCG_OK;
+}
+
+// ---------------------------------------------------------------- optimizer
+dcg_status dcg_active_moments(dcg_ctx* ctx, dcg_gaussians* m, dcg_gaussians* v) {
+  if (!ctx || !m || !v) return DCG_ERR_ARG;
+  if (ctx->Fs == ctx->F) return fail(ctx, DCG_ERR_ARG, "the context stores no optimizer moments");
+  const int64_t S = ctx->cfg.max_active;
+  m->data = ctx->d_active + (size_t)ctx->F * S;
+  v->data = ctx->d_active + (size_t)2 * ctx->F * S;
+  m->stride = v->stride = S;
+  m->sh_degree = v->sh_degree = ctx->cfg.sh_degree;
+  m->pad = v->pad = 0;
+  return DCG_OK;
+}
+
+dcg_status dcg_adam_step(dcg_ctx* ctx, const dcg_gaussians* params, const dcg_gaussians* grads, int64_t n,
+                         const float* lr, float beta1, float beta2, float eps, int64_t step, void* stream) {
+  if (!ctx || !params || !grads || !lr || !params->data || !grads->data) return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  if (ctx->Fs == ctx->F) return fail(ctx, DCG_ERR_ARG, "the context stores no optimizer moments");
+  if (!ctx->active_valid || n != ctx->n_active) return fail(ctx, DCG_ERR_STATE, "n must equal the gathered active set");
+  if (params->sh_degree != ctx->cfg.sh_degree || grads->sh_degree != ctx->cfg.sh_degree || params->stride < n ||
+      grads->stride < n)
+    return fail(ctx, DCG_ERR_ARG, "degree or stride does not match the active set");
+  if (step < 1 || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return fail(ctx, DCG_ERR_ARG, "bad Adam hyper-parameters");
+  const int F = ctx->F;
+  if (F > kAdamMaxF) return fail(ctx, DCG_ERR_ARG, "too many components");
+  AdamArgs aa{};
+  const double bc1 = 1.0 - std::pow((double)beta1, (double)step), bc2 = 1.0 - std::pow((double)beta2, (double)step);
+  for (int c = 0; c < F; ++c) {
+    if (!std::isfinite(lr[c])) return fail(ctx, DCG_ERR_ARG, "learning rate not finite");
+    aa.step[c] = (float)(lr[c] / bc1);
+  }
+  aa.beta1 = beta1;
+  aa.beta2 = beta2;
+  aa.isb2 = (float)(1.0 / std::sqrt(bc2));
+  aa.eps = eps;
+  const int64_t S = ctx->cfg.max_active;
+  launch_adam(params->data, params->stride, grads->data, grads->stride, ctx->d_active + (size_t)F * S,
+              ctx->d_active + (size_t)2 * F * S, S, n, F, aa, ctx->num_sms, (cudaStream_t)stream);
+  CK(cudaGetLastError());
   return DCG_OK;
 }
 

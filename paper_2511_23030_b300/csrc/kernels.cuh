@@ -39,8 +39,17 @@ void launch_chunk_keys(const float* means, long long row, long long col, long lo
                        unsigned* errword, int num_sms, cudaStream_t st);
 void launch_cull(const int32_t* coords, int C, const dcg_camera* cams, int V, float s, float dfar, uint8_t* mask,
                  uint8_t* vis, int32_t* list, int32_t* n, cudaStream_t st);
-void launch_page_copy(bool gather, float* pool, long long page_g, int F, const long long* desc, int nd,
+void launch_page_copy(bool gather, float* pool, long long page_g, int Fp, int c0, int nc, const long long* desc, int nd,
                       float* active, long long stride, cudaStream_t st);
+
+// ---------------------------------------------------------------- optim.cu
+constexpr int kAdamMaxF = 64;
+struct AdamArgs {
+  float step[kAdamMaxF];  // lr_c / (1 - beta1^t) per component
+  float beta1, beta2, isb2, eps;  // isb2 = 1 / sqrt(1 - beta2^t)
+};
+void launch_adam(float* p, long long ps, const float* g, long long gs, float* m, float* v, long long ms, long long n,
+                 int F, const AdamArgs& aa, int num_sms, cudaStream_t st);
 
 // ---------------------------------------------------------------- raster
 // Per-view camera constants (built on the host from dcg_camera).

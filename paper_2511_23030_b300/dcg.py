@@ -42,7 +42,8 @@ class dcg_config(ctypes.Structure):
                 ("host_capacity", ctypes.c_int64), ("max_chunks", ctypes.c_int32), ("max_views", ctypes.c_int32),
                 ("max_active", ctypes.c_int64), ("max_pixels", ctypes.c_int64), ("max_instances", ctypes.c_int64),
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("stage", ctypes.c_int32),
-                ("dfar", ctypes.c_float), ("page_gaussians", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("dfar", ctypes.c_float), ("page_gaussians", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("with_moments", ctypes.c_int32)]
 
 
 _lib = None
@@ -102,6 +103,10 @@ _SIGS = {
     "dcg_mlp_gather_rows": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P, _P]),
     "dcg_tier_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "dcg_chunk_read_moments": (ctypes.c_int, [_P, _I32, _P, _P, _I64]),
+    "dcg_active_moments": (ctypes.c_int, [_P, _P, _P]),
+    "dcg_adam_step": (ctypes.c_int, [_P, _P, _P, _I64, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I64,
+                                     _P]),
     "dcg_cull_chunks_noalloc": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(dcg_camera),
                                                _I32, _P, _P, _P, _P]),
 }
@@ -264,6 +269,29 @@ def dcg_chunk_read(ctx, chunk: int, n: int, F: int) -> np.ndarray:
     out = np.zeros((F, n), np.float32)
     check(ctx, lib().dcg_chunk_read(ctx, chunk, ptr(out), n))
     return out
+
+
+def dcg_chunk_read_moments(ctx, chunk: int, n: int, F: int):
+    """Adam moments (m, v) of a chunk from the host tier, each [F, n] float32."""
+    m = np.zeros((F, n), np.float32)
+    v = np.zeros((F, n), np.float32)
+    check(ctx, lib().dcg_chunk_read_moments(ctx, chunk, ptr(m), ptr(v), n))
+    return m, v
+
+
+def dcg_active_moments(ctx):
+    """Views (m, v) of the active set's Adam moments (library-owned)."""
+    m, v = dcg_gaussians(), dcg_gaussians()
+    check(ctx, lib().dcg_active_moments(ctx, ctypes.byref(m), ctypes.byref(v)))
+    return m, v
+
+
+def dcg_adam_step(ctx, params: dcg_gaussians, grads: dcg_gaussians, n: int, lr, beta1=0.9, beta2=0.999, eps=1e-15,
+                  step=1, stream=None):
+    """One Adam step over the gathered active set; lr: one learning rate per component (F values)."""
+    lr_a = np.ascontiguousarray(np.asarray(lr, np.float32).reshape(-1))
+    check(ctx, lib().dcg_adam_step(ctx, ctypes.byref(params), ctypes.byref(grads), n, ptr(lr_a), float(beta1),
+                                   float(beta2), float(eps), int(step), stream_ptr(stream)))
 
 
 def dcg_state_create(ctx):

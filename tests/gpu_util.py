@@ -24,13 +24,14 @@ def planar(params_aos: np.ndarray, stride: int | None = None):
 
 
 def make_ctx(deg=3, n_max=600_000, views=8, pixels=None, inst=1 << 24, chunk=4.0, budget=None, host=None,
-             tile=(16, 16), stage=128, dfar=100.0, page=2048, max_chunks=8192, flags=0):
+             tile=(16, 16), stage=128, dfar=100.0, page=2048, max_chunks=8192, flags=0, moments=0):
     pixels = 8 * 1241 * 376 if pixels is None else pixels
     budget = n_max if budget is None else budget
     host = n_max if host is None else host
     cfg = dcg.config(sh_degree=deg, max_active=n_max, max_views=views, max_pixels=pixels, max_instances=inst,
                      chunk_size=chunk, device_budget=budget, host_capacity=host, tile_w=tile[0], tile_h=tile[1],
-                     stage=stage, dfar=dfar, page_gaussians=page, max_chunks=max_chunks, flags=flags)
+                     stage=stage, dfar=dfar, page_gaussians=page, max_chunks=max_chunks, flags=flags,
+                     with_moments=moments)
     return dcg.dcg_create(cfg)
 
 
