@@ -293,6 +293,9 @@ def run_ours(args, rank, world):
     return out
 
 
+LAMBDA_S = 0.2  # weight of the SSIM term of Eq. 3 in the training leg (the 3DGS value)
+
+
 def lr_per_component(F: int):
     """3DGS-style learning rates per parameter component (means, log-scales, quaternion,
     opacity logit, SH DC, SH rest)."""
@@ -305,8 +308,8 @@ def lr_per_component(F: int):
 
 def train_leg(args, sc, cfg, tile, stage, trgb, tdep, rgb, depth, dr, dd, loss, grads, grads_t, dpose, npix, K, W):
     """The whole training step of the window with Adam moments stored per Gaussian (they are
-    gathered and scattered with the parameters): cull, gather, [fwd, loss, bwd: graph], Adam,
-    scatter.  Also times the Adam kernel alone against the HBM roofline."""
+    gathered and scattered with the parameters): cull, gather, [fwd, loss of Eq. 2-4 with the SSIM
+    term, bwd: graph], Adam, scatter.  Also times the Adam kernel and the loss alone."""
     import torch
 
     from paper_2511_23030_b300 import dcg
@@ -329,7 +332,8 @@ def train_leg(args, sc, cfg, tile, stage, trgb, tdep, rgb, depth, dr, dd, loss, 
             lst = dcg.dcg_cull_chunks(ctx, cams)
             g, n = dcg.dcg_gather_active(ctx, lst)
             if st["n"] != n:
-                dcg.dcg_window_capture(ctx, g, n, cams, rgb, depth, trgb, tdep, lam, dr, dd, loss, grads, dpose)
+                dcg.dcg_window_capture(ctx, g, n, cams, rgb, depth, trgb, tdep, lam, dr, dd, loss, grads, dpose,
+                                       lambda_s=LAMBDA_S)
                 st["n"] = n
             dcg.dcg_window_run(ctx, cams)
             st["t"] += 1
@@ -357,10 +361,21 @@ def train_leg(args, sc, cfg, tile, stage, trgb, tdep, rgb, depth, dr, dd, loss, 
         a1.record(stream)
         torch.cuda.synchronize()
         ms_adam = a0.elapsed_time(a1) / reps
+        # the loss of Eq. 2-4 with and without its SSIM term
+        ms_loss = {}
+        for ls in (0.0, LAMBDA_S):
+            a0.record(stream)
+            for _ in range(reps):
+                dcg.dcg_loss(ctx, rgb, depth, trgb, tdep, cams, ls, lam, dr, dd, loss)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms_loss[ls] = a0.elapsed_time(a1) / reps
         hbm, _, src = peaks()
         gbs = 28.0 * F * n / (ms_adam / 1e3) / 1e9  # read p, g, m, v; write p, m, v (FP32)
         return {"value": round(npix / (ms / 1e3) / 1e6, 2), "unit": UNIT, "ms_per_step": round(ms, 4),
                 "optimizer": "Adam, moments stored per Gaussian in the chunks (3 F floats per Gaussian)",
+                "loss": f"Eq. 2-4: lambda_s {LAMBDA_S} (SSIM, 11x11 Gaussian window), lambda_depth {lam}",
+                "loss_ms": round(ms_loss[LAMBDA_S], 4), "loss_l1_only_ms": round(ms_loss[0.0], 4),
                 "adam_ms": round(ms_adam, 4), "adam_roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm,
                                                                  "unit": "GB/s", "frac": round(gbs / hbm, 4),
                                                                  "bytes_per_launch": int(28 * F * n),

@@ -274,6 +274,19 @@ dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const
                        const float* tgt_depth, const dcg_camera* cams, int32_t n_views, float lambda_depth,
                        float* dL_drgb, float* dL_ddepth, float* loss, void* stream);
 
+/* The loss of Eq. 2-4 with the SSIM term of Eq. 3, summed over views:
+ *   L = sum_v [ (1 - lambda_s) mean|C - C_gt| + lambda_s (1 - SSIM(C, C_gt))
+ *               + lambda_depth mean|D - D_gt| ],
+ * SSIM with an 11 x 11 Gaussian window (sigma 1.5), C1 = 0.01^2,
+ * C2 = 0.03^2, zero padding, averaged over pixels and channels (the 3DGS
+ * form; the paper does not define it further).  Writes dL/dC and dL/dD
+ * (dev, layouts as rgb / depth) and adds L to *loss (dev, caller zeroes).
+ * lambda_s in [0, 1]; 0 gives dcg_loss_l1.  DCG_ERR_CAPACITY if the views
+ * need more 16x16 SSIM tiles than max_pixels / 16 + 64 max_views + 64. */
+dcg_status dcg_loss(dcg_ctx* ctx, const float* rgb, const float* depth, const float* tgt_rgb, const float* tgt_depth,
+                    const dcg_camera* cams, int32_t n_views, float lambda_s, float lambda_depth, float* dL_drgb,
+                    float* dL_ddepth, float* loss, void* stream);
+
 /* Blend launch shape used by the next render calls: tile 16x16, 32x16 or
  * 32x32 pixels and 64..256 Gaussians staged per block batch (one block per
  * tile, warps of a tile synchronised per batch); stage 32 selects the
@@ -283,8 +296,9 @@ dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const
 dcg_status dcg_set_launch(dcg_ctx* ctx, int32_t tile_w, int32_t tile_h, int32_t stage);
 
 /* Batched keyframe window as one CUDA graph.  dcg_window_capture records,
- * on `stream`, the forward render of all n_views views of `g`, the L1 loss
- * of Eq. 2-4 against tgt_rgb / tgt_depth (lambda_depth for depth), and the
+ * on `stream`, the forward render of all n_views views of `g`, the loss of
+ * Eq. 2-4 against tgt_rgb / tgt_depth (as dcg_loss with lambda_s and
+ * lambda_depth), and the
  * backward to `grads` and dL_dpose, with every item count read from device
  * memory, and instantiates the graph (replacing a previous one).
  * dcg_window_run replays it on `stream` with the camera poses and
@@ -293,7 +307,7 @@ dcg_status dcg_set_launch(dcg_ctx* ctx, int32_t tile_w, int32_t tile_h, int32_t 
  * zeroed by the graph.  The render state used is the context's default one. */
 dcg_status dcg_window_capture(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams,
                               int32_t n_views, float* rgb, float* depth, const float* tgt_rgb, const float* tgt_depth,
-                              float lambda_depth, float* dL_drgb, float* dL_ddepth, float* loss,
+                              float lambda_depth, float lambda_s, float* dL_drgb, float* dL_ddepth, float* loss,
                               dcg_gaussians* grads, float* dL_dpose, void* stream);
 dcg_status dcg_window_run(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views, void* stream);
 

@@ -117,6 +117,12 @@ struct dcg_ctx {
   DevCam* d_losscams = nullptr;
   DevCam* h_losscams = nullptr;
   float* d_losspart = nullptr;
+  // SSIM term: 16 x 16 tile tables (host staging: [0, 16) for dcg_loss, [16, 32) for the window graph)
+  DevCam* d_ssimcams = nullptr;
+  DevCam* d_wssimcams = nullptr;
+  DevCam* h_ssimcams = nullptr;
+  float* d_ssimpart = nullptr;
+  int64_t cap_ssim_tiles = 0;
   cudaEvent_t ev_loss = nullptr;
   int fault = 0;
   // captured window graph
@@ -368,6 +374,12 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
       dmalloc(&ctx->d_losscams, kMaxViewsApi) != cudaSuccess ||
       cudaHostAlloc((void**)&ctx->h_losscams, sizeof(DevCam) * kMaxViewsApi, 0) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
+  ctx->cap_ssim_tiles = c.max_pixels / 16 + 64 * (int64_t)c.max_views + 64;
+  if (dmalloc(&ctx->d_ssimcams, kMaxViewsApi) != cudaSuccess || dmalloc(&ctx->d_wssimcams, kMaxViewsApi) != cudaSuccess ||
+      dmalloc(&ctx->d_ssimpart, 3 * (size_t)ctx->cap_ssim_tiles) != cudaSuccess ||
+      cudaHostAlloc((void**)&ctx->h_ssimcams, sizeof(DevCam) * 2 * kMaxViewsApi, 0) != cudaSuccess)
+    return cleanup_fail(DCG_ERR_OOM);
+  if (ssim_init() != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
   if (dmalloc(&ctx->d_errword, 1) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
   cudaMemset(ctx->d_errword, 0, sizeof(unsigned));
   if (cudaHostAlloc((void**)&ctx->h_errword, sizeof(unsigned), 0) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
@@ -437,6 +449,10 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   cudaFree(ctx->d_losscams);
   cudaFree(ctx->d_losspart);
   if (ctx->h_losscams) cudaFreeHost(ctx->h_losscams);
+  cudaFree(ctx->d_ssimcams);
+  cudaFree(ctx->d_wssimcams);
+  cudaFree(ctx->d_ssimpart);
+  if (ctx->h_ssimcams) cudaFreeHost(ctx->h_ssimcams);
   delete ctx;
   return DCG_OK;
 }
@@ -1064,13 +1080,34 @@ dcg_status dcg_render_bwd(dcg_ctx* ctx, dcg_render_state* st, const float* dL_dr
   return DCG_OK;
 }
 
-dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const float* trgb, const float* tdepth,
-                       const dcg_camera* cams, int32_t V, float lam, float* dr, float* dd, float* loss, void* stream) {
+// 16 x 16 tiles of the views for the SSIM kernel; returns the tile count.
+static int64_t fill_ssim_cams(const dcg_camera* cams, int V, DevCam* out) {
+  const int t = ssim_tile();
+  int64_t pix = 0, tiles = 0;
+  for (int v = 0; v < V; ++v) {
+    DevCam& d = out[v];
+    std::memset(&d, 0, sizeof(d));
+    d.W = cams[v].W;
+    d.H = cams[v].H;
+    d.pix_off = pix;
+    d.ntx = (d.W + t - 1) / t;
+    d.nty = (d.H + t - 1) / t;
+    d.tile_base = (int)tiles;
+    pix += (int64_t)d.W * d.H;
+    tiles += (int64_t)d.ntx * d.nty;
+  }
+  return tiles;
+}
+
+static dcg_status loss_impl(dcg_ctx* ctx, const float* rgb, const float* depth, const float* trgb, const float* tdepth,
+                            const dcg_camera* cams, int32_t V, float lambda_s, float lam, float* dr, float* dd,
+                            float* loss, void* stream) {
   if (!ctx || !rgb || !depth || !trgb || !tdepth || !dr || !dd || !loss) return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  if (!(lambda_s >= 0.f && lambda_s <= 1.f) || !std::isfinite(lam)) return fail(ctx, DCG_ERR_ARG, "bad loss weights");
   dcg_status cs = check_cams(ctx, cams, V);
   if (cs != DCG_OK) return cs;
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaEventSynchronize(ctx->ev_loss));  // staging buffer free again
+  CK(cudaEventSynchronize(ctx->ev_loss));  // staging buffers free again
   int64_t pix = 0;
   for (int v = 0; v < V; ++v) {
     DevCam& d = ctx->h_losscams[v];
@@ -1080,23 +1117,39 @@ dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const
     d.pix_off = pix;
     pix += (int64_t)cams[v].W * cams[v].H;
   }
+  const int64_t tiles = lambda_s > 0.f ? fill_ssim_cams(cams, V, ctx->h_ssimcams) : 0;
+  if (tiles > ctx->cap_ssim_tiles) return fail(ctx, DCG_ERR_CAPACITY, "SSIM tile capacity exceeded");
   CK(cudaMemcpyAsync(ctx->d_losscams, ctx->h_losscams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s));
+  if (tiles) CK(cudaMemcpyAsync(ctx->d_ssimcams, ctx->h_ssimcams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(ctx->ev_loss, s));
   hook(ctx)(PH_LOSS, true, s);
-  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, lam, dr, dd, loss, ctx->d_losspart, ctx->num_sms,
-                 s);
+  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, 1.f - lambda_s, lam, dr, dd, loss,
+                 ctx->d_losspart, ctx->num_sms, s);
+  if (tiles) launch_ssim(rgb, trgb, ctx->d_ssimcams, V, (int)tiles, lambda_s, dr, loss, ctx->d_ssimpart, s);
   hook(ctx)(PH_LOSS, false, s);
   CK(cudaGetLastError());
   return DCG_OK;
 }
 
+dcg_status dcg_loss_l1(dcg_ctx* ctx, const float* rgb, const float* depth, const float* trgb, const float* tdepth,
+                       const dcg_camera* cams, int32_t V, float lam, float* dr, float* dd, float* loss, void* stream) {
+  return loss_impl(ctx, rgb, depth, trgb, tdepth, cams, V, 0.f, lam, dr, dd, loss, stream);
+}
+
+dcg_status dcg_loss(dcg_ctx* ctx, const float* rgb, const float* depth, const float* trgb, const float* tdepth,
+                    const dcg_camera* cams, int32_t V, float lambda_s, float lambda_depth, float* dr, float* dd,
+                    float* loss, void* stream) {
+  return loss_impl(ctx, rgb, depth, trgb, tdepth, cams, V, lambda_s, lambda_depth, dr, dd, loss, stream);
+}
+
 dcg_status dcg_window_capture(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const dcg_camera* cams, int32_t V,
-                              float* rgb, float* depth, const float* trgb, const float* tdepth, float lam, float* dr,
-                              float* dd, float* loss, dcg_gaussians* grads, float* dL_dpose, void* stream) {
+                              float* rgb, float* depth, const float* trgb, const float* tdepth, float lam,
+                              float lambda_s, float* dr, float* dd, float* loss, dcg_gaussians* grads, float* dL_dpose,
+                              void* stream) {
   if (!ctx) return DCG_ERR_ARG;
   dcg_render_state* st = ctx->st0;
   if (!g || n < 0 || (n > 0 && !g->data) || g->stride < n || !rgb || !depth || !trgb || !tdepth || !dr || !dd ||
-      !loss || !grads || grads->stride < n || grads->sh_degree != g->sh_degree)
+      !loss || !grads || grads->stride < n || grads->sh_degree != g->sh_degree || !(lambda_s >= 0.f && lambda_s <= 1.f))
     return fail(ctx, DCG_ERR_ARG, "bad arguments");
   dcg_status cs = check_cams(ctx, cams, V);
   if (cs != DCG_OK) return cs;
@@ -1112,6 +1165,9 @@ dcg_status dcg_window_capture(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, c
   // loss cameras (pixel offsets) live in the second half of the staging buffer
   DevCam* lc = ctx->h_wcams + kMaxViewsApi;
   for (int v = 0; v < V; ++v) lc[v] = ctx->h_wcams[v];
+  DevCam* sc = ctx->h_ssimcams + kMaxViewsApi;
+  const int64_t stiles = lambda_s > 0.f ? fill_ssim_cams(cams, V, sc) : 0;
+  if (stiles > ctx->cap_ssim_tiles) return fail(ctx, DCG_ERR_CAPACITY, "SSIM tile capacity exceeded");
   st->g = *g;
   st->n = n;
   st->V = V;
@@ -1140,10 +1196,12 @@ dcg_status dcg_window_capture(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, c
   }
   cudaMemcpyAsync(st->d_cams, ctx->h_wcams, sizeof(DevCam) * V, cudaMemcpyHostToDevice, cs_);
   cudaMemcpyAsync(ctx->d_losscams, lc, sizeof(DevCam) * V, cudaMemcpyHostToDevice, cs_);
+  if (stiles) cudaMemcpyAsync(ctx->d_wssimcams, sc, sizeof(DevCam) * V, cudaMemcpyHostToDevice, cs_);
   cudaMemsetAsync(loss, 0, sizeof(float), cs_);
   raster_forward(a, rgb, depth, &st->list_sorted, &st->inst_sorted, cs_);
-  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, lam, dr, dd, loss, ctx->d_losspart,
-                 ctx->num_sms, cs_);
+  launch_loss_l1(rgb, depth, trgb, tdepth, ctx->d_losscams, V, pix, 1.f - lambda_s, lam, dr, dd, loss,
+                 ctx->d_losspart, ctx->num_sms, cs_);
+  if (stiles) launch_ssim(rgb, trgb, ctx->d_wssimcams, V, (int)stiles, lambda_s, dr, loss, ctx->d_ssimpart, cs_);
   raster_backward(a, st->inst_sorted, dr, dd, grads->data, grads->stride, dL_dpose, cs_);
   const cudaError_t ce = cudaStreamEndCapture(cs_, &graph);
   ctx->prof_on = prof;

@@ -125,7 +125,12 @@ void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb
 // ---------------------------------------------------------------- loss
 int loss_partials(int num_sms);  // scratch floats the loss needs
 void launch_loss_l1(const float* rgb, const float* depth, const float* trgb, const float* tdepth, const DevCam* cams,
-                    int V, long long n_pix, float lam, float* dr, float* dd, float* loss, float* part, int num_sms,
-                    cudaStream_t st);
+                    int V, long long n_pix, float wimg, float lam, float* dr, float* dd, float* loss, float* part,
+                    int num_sms, cudaStream_t st);
+// loss.cu: SSIM term (16 x 16 tiles of the views in `cams`: W, H, pix_off, ntx, tile_base)
+int ssim_tile();
+cudaError_t ssim_init();
+void launch_ssim(const float* rgb, const float* trgb, const DevCam* cams, int V, int n_tiles, float lam_s, float* dr,
+                 float* loss, float* part, cudaStream_t st);
 
 }  // namespace dcg

@@ -1746,11 +1746,12 @@ void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb
 }
 
 // ============================================================================
-// L1 loss of Eq. 2-4 (image L1 part and depth L1), per view means
+// L1 parts of Eq. 2-4 (image L1 with weight wimg = 1 - lambda_s, depth L1
+// with weight lambda_depth), per view means
 // ============================================================================
 __global__ void k_loss_l1(const float* __restrict__ rgb, const float* __restrict__ depth,
                           const float* __restrict__ trgb, const float* __restrict__ tdepth, const DevCam* cams, int V,
-                          long long n_pix, float lam, float* __restrict__ dr, float* __restrict__ dd,
+                          long long n_pix, float wimg, float lam, float* __restrict__ dr, float* __restrict__ dd,
                           float* __restrict__ part) {
   float acc = 0.f;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n_pix; p += (long long)gridDim.x * blockDim.x) {
@@ -1759,7 +1760,7 @@ __global__ void k_loss_l1(const float* __restrict__ rgb, const float* __restrict
     const long long off = cams[v].pix_off;
     const long long P = (long long)cams[v].W * cams[v].H;
     const long long l = p - off;
-    const float i3 = 1.f / (3.f * (float)P), i1 = lam / (float)P;
+    const float i3 = wimg / (3.f * (float)P), i1 = lam / (float)P;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       const long long k = 3 * off + ch * P + l;
@@ -1805,11 +1806,11 @@ __global__ void k_loss_final(const float* __restrict__ part, int nb, float* loss
 int loss_partials(int num_sms) { return num_sms * 8; }
 
 void launch_loss_l1(const float* rgb, const float* depth, const float* trgb, const float* tdepth, const DevCam* cams,
-                    int V, long long n_pix, float lam, float* dr, float* dd, float* loss, float* part, int num_sms,
-                    cudaStream_t st) {
+                    int V, long long n_pix, float wimg, float lam, float* dr, float* dd, float* loss, float* part,
+                    int num_sms, cudaStream_t st) {
   if (n_pix <= 0) return;
   const int nb = grid_for(n_pix, num_sms);  // <= loss_partials(num_sms)
-  k_loss_l1<<<nb, 256, 0, st>>>(rgb, depth, trgb, tdepth, cams, V, n_pix, lam, dr, dd, part);
+  k_loss_l1<<<nb, 256, 0, st>>>(rgb, depth, trgb, tdepth, cams, V, n_pix, wimg, lam, dr, dd, part);
   k_loss_final<<<1, 256, 0, st>>>(part, nb, loss);
   count_launch(2);
 }

@@ -85,8 +85,10 @@ _SIGS = {
     "dcg_profile_read": (ctypes.c_int, [_P, _P, _P]),
     "dcg_launch_count": (ctypes.c_uint64, []),
     "dcg_window_capture": (ctypes.c_int, [_P, ctypes.POINTER(dcg_gaussians), _I64, ctypes.POINTER(dcg_camera), _I32,
-                                          _P, _P, _P, _P, ctypes.c_float, _P, _P, _P, ctypes.POINTER(dcg_gaussians),
-                                          _P, _P]),
+                                          _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P,
+                                          ctypes.POINTER(dcg_gaussians), _P, _P]),
+    "dcg_loss": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(dcg_camera), _I32, ctypes.c_float, ctypes.c_float,
+                                _P, _P, _P, _P]),
     "dcg_window_run": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _I32, _P]),
     "dcg_state_generation": (_I64, [_P]),
     "dcg_prefetch": (ctypes.c_int, [_P, _P, _I32, ctypes.POINTER(_I32), _P]),
@@ -321,6 +323,12 @@ def dcg_loss_l1(ctx, rgb, depth, tgt_rgb, tgt_depth, cams, lam, dL_drgb, dL_ddep
                                  float(lam), ptr(dL_drgb), ptr(dL_ddepth), ptr(loss), stream_ptr(stream)))
 
 
+def dcg_loss(ctx, rgb, depth, tgt_rgb, tgt_depth, cams, lambda_s, lambda_depth, dL_drgb, dL_ddepth, loss, stream=None):
+    arr = make_cameras(cams)
+    check(ctx, lib().dcg_loss(ctx, ptr(rgb), ptr(depth), ptr(tgt_rgb), ptr(tgt_depth), arr, len(cams), float(lambda_s),
+                              float(lambda_depth), ptr(dL_drgb), ptr(dL_ddepth), ptr(loss), stream_ptr(stream)))
+
+
 def dcg_set_launch(ctx, tile_w: int, tile_h: int, stage: int):
     check(ctx, lib().dcg_set_launch(ctx, tile_w, tile_h, stage))
 
@@ -403,11 +411,11 @@ def dcg_cull_chunks_noalloc(coords, chunk_size: float, dfar: float, cams, mask_o
 
 
 def dcg_window_capture(ctx, g: dcg_gaussians, n: int, cams, rgb, depth, tgt_rgb, tgt_depth, lam, dL_drgb, dL_ddepth,
-                       loss, grads: dcg_gaussians, dL_dpose=None, stream=None):
+                       loss, grads: dcg_gaussians, dL_dpose=None, stream=None, lambda_s=0.0):
     arr = make_cameras(cams)
     check(ctx, lib().dcg_window_capture(ctx, ctypes.byref(g), n, arr, len(cams), ptr(rgb), ptr(depth), ptr(tgt_rgb),
-                                        ptr(tgt_depth), float(lam), ptr(dL_drgb), ptr(dL_ddepth), ptr(loss),
-                                        ctypes.byref(grads), ptr(dL_dpose), stream_ptr(stream)))
+                                        ptr(tgt_depth), float(lam), float(lambda_s), ptr(dL_drgb), ptr(dL_ddepth),
+                                        ptr(loss), ctypes.byref(grads), ptr(dL_dpose), stream_ptr(stream)))
 
 
 def dcg_window_run(ctx, cams, stream=None):

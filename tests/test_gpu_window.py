@@ -26,15 +26,16 @@ def _buffers(cams, F, n):
                 pose=z(6 * len(cams)))
 
 
-def _direct(ctx, g, n, cams, b, trgb, tdep, lam, deg):
+def _direct(ctx, g, n, cams, b, trgb, tdep, lam, deg, lam_s):
     b["loss"].zero_()
     dcg.dcg_render_fwd(ctx, g, n, cams, b["rgb"], b["depth"])
-    dcg.dcg_loss_l1(ctx, b["rgb"], b["depth"], trgb, tdep, cams, lam, b["dr"], b["dd"], b["loss"])
+    dcg.dcg_loss(ctx, b["rgb"], b["depth"], trgb, tdep, cams, lam_s, lam, b["dr"], b["dd"], b["loss"])
     dcg.dcg_render_bwd(ctx, b["dr"], b["dd"], dcg.gaussians(b["grads"], deg), b["pose"])
     dcg.dcg_sync(ctx)
 
 
-def test_window_graph_equals_direct_calls():
+@pytest.mark.parametrize("lam_s", [0.0, 0.2])
+def test_window_graph_equals_direct_calls(lam_s):
     import torch
 
     P, cams, sc = _scene()
@@ -49,7 +50,7 @@ def test_window_graph_equals_direct_calls():
                                 .astype(np.float32)).cuda()
         a, b = _buffers(cams, F, n), _buffers(cams, F, n)
         dcg.dcg_window_capture(ctx, g, n, cams, a["rgb"], a["depth"], trgb, tdep, 0.1, a["dr"], a["dd"], a["loss"],
-                               dcg.gaussians(a["grads"], 3), a["pose"])
+                               dcg.gaussians(a["grads"], 3), a["pose"], lambda_s=lam_s)
         rng = np.random.default_rng(3)
         for it in range(3):
             if it:
@@ -60,7 +61,7 @@ def test_window_graph_equals_direct_calls():
             dcg.dcg_window_run(ctx, cams)
             dcg.dcg_sync(ctx)
             ra = {k: v.clone() for k, v in a.items()}
-            _direct(ctx, g, n, cams, b, trgb, tdep, 0.1, 3)
+            _direct(ctx, g, n, cams, b, trgb, tdep, 0.1, 3, lam_s)
             assert torch.equal(ra["rgb"], b["rgb"]) and torch.equal(ra["depth"], b["depth"])
             assert torch.equal(ra["dr"], b["dr"]) and torch.equal(ra["dd"], b["dd"])
             assert abs(ra["loss"].item() - b["loss"].item()) <= 1e-6 * abs(b["loss"].item())
