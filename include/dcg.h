@@ -229,6 +229,39 @@ dcg_status dcg_active_moments(dcg_ctx* ctx, dcg_gaussians* m, dcg_gaussians* v);
 dcg_status dcg_adam_step(dcg_ctx* ctx, const dcg_gaussians* params, const dcg_gaussians* grads, int64_t n,
                          const float* lr, float beta1, float beta2, float eps, int64_t step, void* stream);
 
+/* ---------------------------------------------------------------- loop closure
+ * Sec. III-F "Cross-Chunk Transformation" and "Chunk Redistribution". */
+
+/* Corrects the map after a loop closure.  kf: the K affected keyframes
+ * (1 <= K <= 16) with their poses before the correction; corr (host,
+ * [K][16] row-major) the correction of each keyframe, a rigid transform
+ * (typically Tcw_new^-1 Tcw_old).  The chunks that keyframe k's frustum cull
+ * keeps (pose before the correction) are batch-loaded together (their union
+ * must fit the device budget: DCG_ERR_BUDGET otherwise, the table is then
+ * unchanged; the paper's keyframe-by-keyframe fallback is not provided).  A
+ * Gaussian of such a chunk whose centre projects into keyframe k's image
+ * (znear < z <= zfar, 0 <= u < W, 0 <= v < H; FP32, one rounding per
+ * operation) moves rigidly with it: x' = C_k x, q' = q(C_k) (x) q (SH
+ * coefficients and scales unchanged); a Gaussian seen by several keyframes
+ * moves with the first of them only (the global transformation mask).
+ * Then chunk ids (Eq. 5/6) are recomputed for the loaded Gaussians and those
+ * whose chunk changed are redistributed: a chunk keeps its remaining
+ * Gaussians in stored order and receives incoming ones after them in gather
+ * order; chunks are created as needed (emptied chunks stay, with count 0).
+ * Optimizer moments travel with their Gaussians.  Chunk indices may change
+ * (new chunks keep the table in ascending key order) and the active set is
+ * invalidated.  n_transformed / n_moved (host, may be NULL): Gaussians moved
+ * rigidly / moved to another chunk.  DCG_ERR_KEY_RANGE if a corrected position
+ * leaves the Eq. 6 range (table unchanged).  Synchronous. */
+dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* corr, int32_t K, int64_t* n_transformed,
+                            int64_t* n_moved, void* stream);
+
+/* Post-correction reset of Sec. III-F for the gathered active set: opacity
+ * capped at max_opacity (logit <- min(logit, logit(max_opacity))) and, with
+ * with_moments, the Adam moments zeroed.  params: the active view (dev).
+ * DCG_ERR_STATE if n differs from the gathered set.  Stream-ordered. */
+dcg_status dcg_reset_active(dcg_ctx* ctx, const dcg_gaussians* params, int64_t n, float max_opacity, void* stream);
+
 /* ---------------------------------------------------------------- rendering
  * Differentiable rasterisation of RGB and depth (Sec. III-E: the selected
  * Gaussians are rasterised into RGB and depth images; Eq. 4 needs the depth)

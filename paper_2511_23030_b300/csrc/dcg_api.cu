@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <string>
 #include <unordered_map>
@@ -123,6 +124,11 @@ struct dcg_ctx {
   DevCam* h_ssimcams = nullptr;
   float* d_ssimpart = nullptr;
   int64_t cap_ssim_tiles = 0;
+  // loop closure: per-keyframe cull masks, chunk segments of the active set, keyframes
+  uint8_t* d_lcmask = nullptr;
+  long long* d_lcseg = nullptr;
+  int* d_lcsegc = nullptr;
+  LcView* d_lcview = nullptr;
   cudaEvent_t ev_loss = nullptr;
   int fault = 0;
   // captured window graph
@@ -380,6 +386,10 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
       cudaHostAlloc((void**)&ctx->h_ssimcams, sizeof(DevCam) * 2 * kMaxViewsApi, 0) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
   if (ssim_init() != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
+  if (dmalloc(&ctx->d_lcmask, (size_t)kMaxViewsApi * c.max_chunks) != cudaSuccess ||
+      dmalloc(&ctx->d_lcseg, (size_t)c.max_chunks) != cudaSuccess ||
+      dmalloc(&ctx->d_lcsegc, (size_t)c.max_chunks) != cudaSuccess || dmalloc(&ctx->d_lcview, kMaxViewsApi) != cudaSuccess)
+    return cleanup_fail(DCG_ERR_OOM);
   if (dmalloc(&ctx->d_errword, 1) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
   cudaMemset(ctx->d_errword, 0, sizeof(unsigned));
   if (cudaHostAlloc((void**)&ctx->h_errword, sizeof(unsigned), 0) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
@@ -449,6 +459,10 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   cudaFree(ctx->d_losscams);
   cudaFree(ctx->d_losspart);
   if (ctx->h_losscams) cudaFreeHost(ctx->h_losscams);
+  cudaFree(ctx->d_lcmask);
+  cudaFree(ctx->d_lcseg);
+  cudaFree(ctx->d_lcsegc);
+  cudaFree(ctx->d_lcview);
   cudaFree(ctx->d_ssimcams);
   cudaFree(ctx->d_wssimcams);
   cudaFree(ctx->d_ssimpart);
@@ -917,6 +931,323 @@ dcg_status dcg_adam_step(dcg_ctx* ctx, const dcg_gaussians* params, const dcg_ga
   const int64_t S = ctx->cfg.max_active;
   launch_adam(params->data, params->stride, grads->data, grads->stride, ctx->d_active + (size_t)F * S,
               ctx->d_active + (size_t)2 * F * S, S, n, F, aa, ctx->num_sms, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return DCG_OK;
+}
+
+// ---------------------------------------------------------------- loop closure
+// Unit quaternion (w, x, y, z) of a rotation matrix (row-major), Shepperd's method.
+static void rot_to_quat(const double R[9], double q[4]) {
+  const double tr = R[0] + R[4] + R[8];
+  if (tr > 0.0) {
+    const double s = 2.0 * std::sqrt(1.0 + tr);
+    q[0] = 0.25 * s;
+    q[1] = (R[7] - R[5]) / s;
+    q[2] = (R[2] - R[6]) / s;
+    q[3] = (R[3] - R[1]) / s;
+  } else if (R[0] > R[4] && R[0] > R[8]) {
+    const double s = 2.0 * std::sqrt(1.0 + R[0] - R[4] - R[8]);
+    q[0] = (R[7] - R[5]) / s;
+    q[1] = 0.25 * s;
+    q[2] = (R[1] + R[3]) / s;
+    q[3] = (R[2] + R[6]) / s;
+  } else if (R[4] > R[8]) {
+    const double s = 2.0 * std::sqrt(1.0 + R[4] - R[0] - R[8]);
+    q[0] = (R[2] - R[6]) / s;
+    q[1] = (R[1] + R[3]) / s;
+    q[2] = 0.25 * s;
+    q[3] = (R[5] + R[7]) / s;
+  } else {
+    const double s = 2.0 * std::sqrt(1.0 + R[8] - R[0] - R[4]);
+    q[0] = (R[3] - R[1]) / s;
+    q[1] = (R[2] + R[6]) / s;
+    q[2] = (R[5] + R[7]) / s;
+    q[3] = 0.25 * s;
+  }
+  const double l = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int k = 0; k < 4; ++k) q[k] /= l;
+}
+
+// Appends Gaussian j of the planar host rows (`rows` components, stride
+// `stride`) to chunk ch in the host tier; components >= rows are zeroed.
+static void append_host_row(dcg_ctx* ctx, Chunk& ch, const float* src, int64_t stride, int64_t j, int rows) {
+  const int64_t slot = ch.count;
+  const int64_t p = slot / ctx->page_g, o = slot - p * ctx->page_g;
+  if (p >= (int64_t)ch.host_pages.size()) {
+    ch.host_pages.push_back(ctx->host_free.back());
+    ctx->host_free.pop_back();
+  }
+  float* page = host_page(ctx, ch.host_pages[(size_t)p]);
+  for (int f = 0; f < rows; ++f) page[(int64_t)f * ctx->page_g + o] = src[(int64_t)f * stride + j];
+  for (int f = rows; f < ctx->Fs; ++f) page[(int64_t)f * ctx->page_g + o] = 0.f;
+  ch.count++;
+}
+
+static Chunk make_chunk(uint64_t k) {
+  Chunk ch;
+  ch.key = k;
+  const int64_t m = (1 << 21) - 1;
+  ch.c[0] = (int32_t)((int64_t)((k >> 42) & m) - (1 << 20));
+  ch.c[1] = (int32_t)((int64_t)((k >> 21) & m) - (1 << 20));
+  ch.c[2] = (int32_t)((int64_t)(k & m) - (1 << 20));
+  return ch;
+}
+
+dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* corr, int32_t K, int64_t* n_transformed,
+                            int64_t* n_moved, void* stream) {
+  if (!ctx || !kf || !corr || K <= 0 || K > kMaxViewsApi) return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  for (int k = 0; k < K; ++k) {
+    const dcg_camera& c = kf[k];
+    if (c.W <= 0 || c.H <= 0 || !(c.fx > 0.f) || !(c.fy > 0.f) || !(c.znear > 0.f) || !(c.zfar > c.znear))
+      return fail(ctx, DCG_ERR_ARG, "bad keyframe camera");
+    for (int e = 0; e < 16; ++e)
+      if (!std::isfinite(corr[16 * k + e])) return fail(ctx, DCG_ERR_ARG, "correction not finite");
+  }
+  if (n_transformed) *n_transformed = 0;
+  if (n_moved) *n_moved = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int C = (int)ctx->chunks.size();
+  if (C == 0) return DCG_OK;
+  // 1. frustum cull of every affected keyframe (pose before the correction)
+  std::memcpy(ctx->h_cullcams, kf, sizeof(dcg_camera) * K);
+  CK(cudaMemcpyAsync(ctx->d_cullcams, ctx->h_cullcams, sizeof(dcg_camera) * K, cudaMemcpyHostToDevice, s));
+  launch_cull(ctx->d_coords, C, ctx->d_cullcams, K, ctx->cfg.chunk_size, ctx->cfg.dfar, ctx->d_lcmask, ctx->d_vis,
+              ctx->d_list, ctx->d_nlist, s);
+  CK(cudaGetLastError());
+  int32_t nl = 0;
+  CK(cudaMemcpyAsync(&nl, ctx->d_nlist, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int32_t> list((size_t)nl);
+  if (nl) CK(cudaMemcpy(list.data(), ctx->d_list, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost));
+  if (nl == 0) return DCG_OK;
+  // 2. batch-load the union (DCG_ERR_BUDGET if it does not fit)
+  dcg_gaussians g{};
+  int64_t n = 0;
+  dcg_status gs = dcg_gather_active(ctx, list.data(), nl, &g, &n, stream);
+  if (gs != DCG_OK) return gs;
+  std::vector<long long> seg((size_t)nl);
+  std::vector<int> segc((size_t)nl);
+  std::vector<uint64_t> segkey((size_t)nl);
+  {
+    long long off = 0;
+    for (int k = 0; k < nl; ++k) {
+      seg[(size_t)k] = off;
+      segc[(size_t)k] = list[(size_t)k];
+      segkey[(size_t)k] = ctx->chunks[list[(size_t)k]].key;
+      off += ctx->chunks[list[(size_t)k]].count;
+    }
+  }
+  std::vector<LcView> views((size_t)K);
+  for (int k = 0; k < K; ++k) {
+    const dcg_camera& c = kf[k];
+    LcView& v = views[(size_t)k];
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) v.R[3 * r + q] = c.Tcw[4 * r + q];
+      v.t[r] = c.Tcw[4 * r + 3];
+      for (int q = 0; q < 4; ++q) v.C[4 * r + q] = corr[16 * k + 4 * r + q];
+    }
+    v.fx = c.fx; v.fy = c.fy; v.cx = c.cx; v.cy = c.cy; v.znear = c.znear; v.zfar = c.zfar; v.W = c.W; v.H = c.H;
+    double Rd[9], qd[4];
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) Rd[3 * r + q] = corr[16 * k + 4 * r + q];
+    rot_to_quat(Rd, qd);
+    for (int q = 0; q < 4; ++q) v.q[q] = (float)qd[q];
+  }
+  CK(cudaMemcpyAsync(ctx->d_lcseg, seg.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->d_lcsegc, segc.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->d_lcview, views.data(), sizeof(LcView) * K, cudaMemcpyHostToDevice, s));
+  // 3. rigid correction under the global mask, then chunk ids of the result (Eq. 5/6)
+  dcg_render_state* st = ctx->st0;
+  uint32_t* d_flags = st->touched;  // render scratch, at least max_active entries
+  u64* d_keys = st->list_a;
+  const int64_t S = ctx->cfg.max_active;
+  launch_loop_transform(ctx->d_active, S, n, ctx->d_lcseg, ctx->d_lcsegc, nl, ctx->d_lcmask, C, ctx->d_lcview, K,
+                        d_flags, ctx->num_sms, s);
+  launch_chunk_keys(ctx->d_active, 1, S, n, ctx->cfg.chunk_size, d_keys, ctx->d_errword, ctx->num_sms, s);
+  CK(cudaGetLastError());
+  std::vector<uint32_t> flags((size_t)n);
+  std::vector<uint64_t> keys((size_t)n);
+  if (n) {
+    CK(cudaMemcpyAsync(flags.data(), d_flags, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(keys.data(), d_keys, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  }
+  dcg_status es = dcg_sync(ctx, stream);  // a corrected position outside the key range stops here, table unchanged
+  if (es != DCG_OK) {
+    ctx->active_valid = false;
+    return es;
+  }
+  // 4. redistribution: a chunk keeps its remaining Gaussians in stored order
+  // and receives incoming ones after them, in gather order
+  int64_t nt = 0, nm = 0;
+  std::vector<std::vector<int64_t>> stay((size_t)nl);
+  std::map<uint64_t, std::vector<int64_t>> incoming;
+  for (int k = 0, i = 0; k < nl; ++k) {
+    const int64_t end = k + 1 < nl ? seg[(size_t)k + 1] : n;
+    for (; i < end; ++i) {
+      nt += flags[(size_t)i] != 0u;
+      if (keys[(size_t)i] == segkey[(size_t)k]) {
+        stay[(size_t)k].push_back(i);
+      } else {
+        incoming[keys[(size_t)i]].push_back(i);
+        ++nm;
+      }
+    }
+  }
+  if (n_transformed) *n_transformed = nt;
+  if (n_moved) *n_moved = nm;
+  if (nm == 0) return dcg_scatter_back(ctx, &g, n, stream);
+  std::vector<long long> perm;
+  perm.reserve((size_t)n);
+  std::vector<int64_t> newcount((size_t)nl);
+  for (int k = 0; k < nl; ++k) {
+    perm.insert(perm.end(), stay[(size_t)k].begin(), stay[(size_t)k].end());
+    auto it = incoming.find(segkey[(size_t)k]);
+    if (it != incoming.end()) {
+      perm.insert(perm.end(), it->second.begin(), it->second.end());
+      newcount[(size_t)k] = (int64_t)(stay[(size_t)k].size() + it->second.size());
+      incoming.erase(it);
+    } else {
+      newcount[(size_t)k] = (int64_t)stay[(size_t)k].size();
+    }
+  }
+  const int64_t n_kept = (int64_t)perm.size();  // Gaussians staying on the device (gathered chunks)
+  std::vector<std::pair<uint64_t, int64_t>> outside;  // (key, count) of targets that were not gathered
+  for (auto& kv : incoming) {
+    perm.insert(perm.end(), kv.second.begin(), kv.second.end());
+    outside.emplace_back(kv.first, (int64_t)kv.second.size());
+  }
+  // capacity checks before anything changes
+  int64_t dev_need = 0, dev_have = 0, host_need = 0, host_have = 0, new_chunks = 0;
+  for (int k = 0; k < nl; ++k) {
+    const Chunk& ch = ctx->chunks[list[(size_t)k]];
+    dev_need += pages_for(ctx, newcount[(size_t)k]);
+    dev_have += (int64_t)ch.dev_pages.size();
+    host_need += pages_for(ctx, newcount[(size_t)k]);
+    host_have += (int64_t)ch.host_pages.size();
+  }
+  for (auto& o : outside) {
+    auto it = ctx->index.find(o.first);
+    if (it == ctx->index.end()) {
+      ++new_chunks;
+      host_need += pages_for(ctx, o.second);
+    } else {
+      const Chunk& ch = ctx->chunks[it->second];
+      host_need += pages_for(ctx, ch.count + o.second) - (int64_t)ch.host_pages.size();
+    }
+  }
+  if (dev_need - dev_have > (int64_t)ctx->dev_free.size()) return fail(ctx, DCG_ERR_BUDGET, "device page pool exhausted");
+  if (host_need - host_have > (int64_t)ctx->host_free.size()) return fail(ctx, DCG_ERR_CAPACITY, "host tier full");
+  if ((int64_t)ctx->chunks.size() + new_chunks > ctx->cfg.max_chunks)
+    return fail(ctx, DCG_ERR_CAPACITY, "chunk table full");
+  // permuted copy of the active rows (parameters and moments)
+  const int Fs = ctx->Fs;
+  float* d_tmp = nullptr;
+  long long* d_perm = nullptr;
+  CK(cudaMallocAsync((void**)&d_tmp, sizeof(float) * (size_t)Fs * (size_t)n, s));
+  CK(cudaMallocAsync((void**)&d_perm, sizeof(long long) * (size_t)n, s));
+  CK(cudaMemcpyAsync(d_perm, perm.data(), sizeof(long long) * (size_t)n, cudaMemcpyHostToDevice, s));
+  launch_permute_rows(ctx->d_active, S, d_tmp, n, d_perm, n, Fs, ctx->num_sms, s);
+  // gathered chunks: new counts and pages, content written from the permuted rows
+  CK(cudaEventSynchronize(ctx->ev_desc));
+  int nd = 0;
+  int64_t off = 0;
+  for (int k = 0; k < nl; ++k) {
+    Chunk& ch = ctx->chunks[list[(size_t)k]];
+    const int64_t nc = newcount[(size_t)k];
+    const size_t np = (size_t)pages_for(ctx, nc);
+    while (ch.dev_pages.size() < np) {
+      ch.dev_pages.push_back(ctx->dev_free.back());
+      ctx->dev_free.pop_back();
+    }
+    while (ch.dev_pages.size() > np) {
+      ctx->dev_free.push_back(ch.dev_pages.back());
+      ch.dev_pages.pop_back();
+    }
+    while (ch.host_pages.size() < np) {
+      ch.host_pages.push_back(ctx->host_free.back());
+      ctx->host_free.pop_back();
+    }
+    while (ch.host_pages.size() > np) {
+      ctx->host_free.push_back(ch.host_pages.back());
+      ch.host_pages.pop_back();
+    }
+    ctx->resident_g += nc - ch.count;
+    ch.count = nc;
+    ch.dirty = true;
+    for (size_t p = 0; p < np; ++p) {
+      const int64_t cnt = std::min<int64_t>(ctx->page_g, nc - (int64_t)p * ctx->page_g);
+      ctx->h_desc[3 * nd + 0] = ch.dev_pages[p];
+      ctx->h_desc[3 * nd + 1] = cnt;
+      ctx->h_desc[3 * nd + 2] = off;
+      off += cnt;
+      ++nd;
+    }
+  }
+  if (nd > 0) CK(cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(long long) * 3 * nd, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(ctx->ev_desc, s));
+  launch_page_copy(false, ctx->d_pool, ctx->page_g, Fs, 0, Fs, ctx->d_desc, nd, d_tmp, n, s);
+  CK(cudaGetLastError());
+  // Gaussians leaving for chunks that were not gathered: appended in the host tier
+  const int64_t n_out = n - n_kept;
+  if (n_out > 0) {
+    if (n_out * Fs > ctx->stage_cap) {
+      if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+      ctx->h_stage = nullptr;
+      ctx->stage_cap = 0;
+      CK(cudaHostAlloc((void**)&ctx->h_stage, sizeof(float) * (size_t)(n_out * Fs), 0));
+      ctx->stage_cap = n_out * Fs;
+    }
+    CK(cudaMemcpy2DAsync(ctx->h_stage, (size_t)n_out * 4, d_tmp + n_kept, (size_t)n * 4, (size_t)n_out * 4, (size_t)Fs,
+                         cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaFreeAsync(d_perm, s));
+  CK(cudaFreeAsync(d_tmp, s));
+  CK(cudaStreamSynchronize(s));
+  if (n_out > 0) {
+    bool added = false;
+    int64_t j = 0;
+    for (auto& o : outside) {
+      auto it = ctx->index.find(o.first);
+      if (it == ctx->index.end()) {
+        ctx->chunks.push_back(make_chunk(o.first));
+        ctx->index[o.first] = (int32_t)ctx->chunks.size() - 1;
+        added = true;
+        it = ctx->index.find(o.first);
+      }
+      Chunk& ch = ctx->chunks[it->second];
+      if (ch.resident) {  // write back and drop: the next gather reloads the whole chunk
+        CK(cudaEventRecord(ctx->ev_compute, s));
+        CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_compute, 0));
+        dcg_status e = evict_chunk(ctx, ch);
+        if (e != DCG_OK) return e;
+        ctx->evictions--;
+        CK(cudaStreamSynchronize(ctx->copy_stream));
+      }
+      for (int64_t q = 0; q < o.second; ++q, ++j) append_host_row(ctx, ch, ctx->h_stage, n_out, j, Fs);
+    }
+    if (added) {
+      std::sort(ctx->chunks.begin(), ctx->chunks.end(), [](const Chunk& a, const Chunk& b) { return a.key < b.key; });
+      ctx->index.clear();
+      for (size_t k = 0; k < ctx->chunks.size(); ++k) ctx->index[ctx->chunks[k].key] = (int32_t)k;
+      dcg_status us = upload_coords(ctx);
+      if (us != DCG_OK) return us;
+    }
+  }
+  ctx->active_valid = false;  // the caller gathers again
+  return DCG_OK;
+}
+
+dcg_status dcg_reset_active(dcg_ctx* ctx, const dcg_gaussians* params, int64_t n, float max_opacity, void* stream) {
+  if (!ctx || !params || !params->data || !(max_opacity > 0.f && max_opacity < 1.f))
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  if (!ctx->active_valid || n != ctx->n_active) return fail(ctx, DCG_ERR_STATE, "n must equal the gathered active set");
+  if (params->sh_degree != ctx->cfg.sh_degree || params->stride < n) return fail(ctx, DCG_ERR_ARG, "bad layout");
+  cudaStream_t s = (cudaStream_t)stream;
+  const float cap = (float)std::log((double)max_opacity / (1.0 - (double)max_opacity));
+  launch_cap_rows(params->data + 10 * params->stride, n, cap, ctx->num_sms, s);
+  if (ctx->Fs > ctx->F)
+    CK(cudaMemset2DAsync(ctx->d_active + (size_t)ctx->F * ctx->cfg.max_active, (size_t)ctx->cfg.max_active * 4, 0,
+                         (size_t)n * 4, (size_t)(ctx->Fs - ctx->F), s));
   CK(cudaGetLastError());
   return DCG_OK;
 }

@@ -42,6 +42,24 @@ void launch_cull(const int32_t* coords, int C, const dcg_camera* cams, int V, fl
 void launch_page_copy(bool gather, float* pool, long long page_g, int Fp, int c0, int nc, const long long* desc, int nd,
                       float* active, long long stride, cudaStream_t st);
 
+// ---------------------------------------------------------------- loopclosure.cu
+// One affected keyframe: pose before the correction (world -> camera), its
+// intrinsics and image, the correction x' = C x (3 x 4 row-major) and the
+// rotation of C as a unit quaternion (w, x, y, z).
+struct LcView {
+  float R[9], t[3];
+  float fx, fy, cx, cy, znear, zfar;
+  int W, H;
+  float C[12];
+  float q[4];
+};
+void launch_loop_transform(float* act, long long stride, long long n, const long long* seg_off, const int* seg_chunk,
+                           int nseg, const uint8_t* mask, int C, const LcView* kf, int K, uint32_t* flags, int num_sms,
+                           cudaStream_t st);
+void launch_permute_rows(const float* src, long long sstride, float* dst, long long dstride, const long long* perm,
+                         long long n, int rows, int num_sms, cudaStream_t st);
+void launch_cap_rows(float* row, long long n, float cap, int num_sms, cudaStream_t st);
+
 // ---------------------------------------------------------------- optim.cu
 constexpr int kAdamMaxF = 64;
 struct AdamArgs {

@@ -1,0 +1,104 @@
+// Loop-closure correction of the gathered chunks (Sec. III-F "Cross-Chunk
+// Transformation"): each Gaussian of a chunk that an affected keyframe's
+// frustum cull keeps, and whose centre projects into that keyframe's image
+// (pose before the correction), moves rigidly with the keyframe,
+//   x' = R_k x + t_k,   q' = q_k (x) q   (Hamilton product),
+// where (R_k, t_k) is the keyframe's correction and q_k its rotation as a unit
+// quaternion.  A Gaussian seen by several keyframes moves with the first of
+// them only (the global transformation mask).  The camera transform, the
+// projection and the corrected position are evaluated in FP32 with one
+// rounding per operation in a fixed order, so that the visibility decision
+// and the chunk ids recomputed from the result (Eq. 5/6) are reproducible.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace dcg {
+
+__device__ __forceinline__ float dot3_rn(const float* r, float x, float y, float z, float t) {
+  return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r[0], x), __fmul_rn(r[1], y)), __fmul_rn(r[2], z)), t);
+}
+
+__global__ void k_loop_transform(float* __restrict__ act, long long stride, long long n,
+                                 const long long* __restrict__ seg_off, const int* __restrict__ seg_chunk, int nseg,
+                                 const uint8_t* __restrict__ mask, int C, const LcView* __restrict__ kf, int K,
+                                 uint32_t* __restrict__ flags) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    // chunk of active Gaussian i: the last segment starting at or before i
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (seg_off[mid] <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    const int c = seg_chunk[lo];
+    const float x = act[0 * stride + i], y = act[1 * stride + i], z = act[2 * stride + i];
+    uint32_t f = 0;
+    for (int k = 0; k < K; ++k) {
+      if (!mask[(long long)k * C + c]) continue;
+      const LcView& v = kf[k];
+      const float tx = dot3_rn(v.R + 0, x, y, z, v.t[0]);
+      const float ty = dot3_rn(v.R + 3, x, y, z, v.t[1]);
+      const float tz = dot3_rn(v.R + 6, x, y, z, v.t[2]);
+      if (!(tz > v.znear && tz <= v.zfar)) continue;
+      const float u = __fadd_rn(__fmul_rn(v.fx, __fdiv_rn(tx, tz)), v.cx);
+      const float w = __fadd_rn(__fmul_rn(v.fy, __fdiv_rn(ty, tz)), v.cy);
+      if (!(u >= 0.f && u < (float)v.W && w >= 0.f && w < (float)v.H)) continue;
+      act[0 * stride + i] = dot3_rn(v.C + 0, x, y, z, v.C[3]);
+      act[1 * stride + i] = dot3_rn(v.C + 4, x, y, z, v.C[7]);
+      act[2 * stride + i] = dot3_rn(v.C + 8, x, y, z, v.C[11]);
+      const float a0 = v.q[0], a1 = v.q[1], a2 = v.q[2], a3 = v.q[3];
+      const float b0 = act[6 * stride + i], b1 = act[7 * stride + i], b2 = act[8 * stride + i], b3 = act[9 * stride + i];
+      act[6 * stride + i] = a0 * b0 - a1 * b1 - a2 * b2 - a3 * b3;
+      act[7 * stride + i] = a0 * b1 + a1 * b0 + a2 * b3 - a3 * b2;
+      act[8 * stride + i] = a0 * b2 - a1 * b3 + a2 * b0 + a3 * b1;
+      act[9 * stride + i] = a0 * b3 + a1 * b2 - a2 * b1 + a3 * b0;
+      f = (uint32_t)k + 1u;
+      break;
+    }
+    flags[i] = f;
+  }
+}
+
+// dst[c][j] = src[c][perm[j]] for c < rows, j < n (planar rows).
+__global__ void k_permute_rows(const float* __restrict__ src, long long sstride, float* __restrict__ dst,
+                               long long dstride, const long long* __restrict__ perm, long long n, int rows) {
+  for (int c = blockIdx.y; c < rows; c += gridDim.y)
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+      dst[(long long)c * dstride + j] = src[(long long)c * sstride + perm[j]];
+}
+
+// Opacity reset of Sec. III-F: logit <- min(logit, cap) for rows [0, n).
+__global__ void k_cap_rows(float* __restrict__ row, long long n, float cap) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    row[j] = fminf(row[j], cap);
+}
+
+void launch_loop_transform(float* act, long long stride, long long n, const long long* seg_off, const int* seg_chunk,
+                           int nseg, const uint8_t* mask, int C, const LcView* kf, int K, uint32_t* flags, int num_sms,
+                           cudaStream_t st) {
+  if (n <= 0) return;
+  const long long blocks = (n + 255) / 256;
+  k_loop_transform<<<(int)std::min<long long>(blocks, (long long)num_sms * 8), 256, 0, st>>>(act, stride, n, seg_off,
+                                                                                           seg_chunk, nseg, mask, C,
+                                                                                           kf, K, flags);
+  count_launch();
+}
+
+void launch_permute_rows(const float* src, long long sstride, float* dst, long long dstride, const long long* perm,
+                         long long n, int rows, int num_sms, cudaStream_t st) {
+  if (n <= 0 || rows <= 0) return;
+  const long long blocks = (n + 255) / 256;
+  dim3 grid((unsigned)std::min<long long>(blocks, (long long)num_sms * 4), (unsigned)std::min(rows, 16));
+  k_permute_rows<<<grid, 256, 0, st>>>(src, sstride, dst, dstride, perm, n, rows);
+  count_launch();
+}
+
+void launch_cap_rows(float* row, long long n, float cap, int num_sms, cudaStream_t st) {
+  if (n <= 0) return;
+  const long long blocks = (n + 255) / 256;
+  k_cap_rows<<<(int)std::min<long long>(blocks, (long long)num_sms * 8), 256, 0, st>>>(row, n, cap);
+  count_launch();
+}
+
+}  // namespace dcg

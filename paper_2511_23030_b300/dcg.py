@@ -109,6 +109,9 @@ _SIGS = {
     "dcg_active_moments": (ctypes.c_int, [_P, _P, _P]),
     "dcg_adam_step": (ctypes.c_int, [_P, _P, _P, _I64, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I64,
                                      _P]),
+    "dcg_loop_closure": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _P, _I32, ctypes.POINTER(_I64),
+                                        ctypes.POINTER(_I64), _P]),
+    "dcg_reset_active": (ctypes.c_int, [_P, _P, _I64, ctypes.c_float, _P]),
     "dcg_cull_chunks_noalloc": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(dcg_camera),
                                                _I32, _P, _P, _P, _P]),
 }
@@ -294,6 +297,20 @@ def dcg_adam_step(ctx, params: dcg_gaussians, grads: dcg_gaussians, n: int, lr, 
     lr_a = np.ascontiguousarray(np.asarray(lr, np.float32).reshape(-1))
     check(ctx, lib().dcg_adam_step(ctx, ctypes.byref(params), ctypes.byref(grads), n, ptr(lr_a), float(beta1),
                                    float(beta2), float(eps), int(step), stream_ptr(stream)))
+
+
+def dcg_loop_closure(ctx, keyframes, corrections, stream=None):
+    """Loop-closure correction; corrections: K rigid 4x4 transforms. Returns (n_transformed, n_moved)."""
+    arr = make_cameras(keyframes)
+    C = np.ascontiguousarray(np.asarray(corrections, np.float32).reshape(len(keyframes), 16))
+    nt, nm = _I64(), _I64()
+    check(ctx, lib().dcg_loop_closure(ctx, arr, ptr(C), len(keyframes), ctypes.byref(nt), ctypes.byref(nm),
+                                      stream_ptr(stream)))
+    return int(nt.value), int(nm.value)
+
+
+def dcg_reset_active(ctx, params: dcg_gaussians, n: int, max_opacity=0.01, stream=None):
+    check(ctx, lib().dcg_reset_active(ctx, ctypes.byref(params), n, float(max_opacity), stream_ptr(stream)))
 
 
 def dcg_state_create(ctx):

@@ -1,0 +1,134 @@
+"""Loop-closure correction and chunk redistribution on the GPU against the
+reference: the same Gaussians move, to the same chunks, in the same order,
+with their optimizer moments."""
+import numpy as np
+import pytest
+
+from oracle import loopclosure as lc
+from paper_2511_23030_b300 import dcg, synth
+
+from gpu_util import make_ctx, planar
+
+pytestmark = pytest.mark.gpu
+
+N = 64_000
+QUAT = [6, 7, 8, 9]
+
+
+def _rot(axis, deg):
+    a = np.deg2rad(deg)
+    c, s = np.cos(a), np.sin(a)
+    R = {"x": [[1, 0, 0], [0, c, -s], [0, s, c]], "z": [[c, -s, 0], [s, c, 0], [0, 0, 1]]}[axis]
+    return np.asarray(R)
+
+
+def _corr(axis, deg, t):
+    C = np.eye(4)
+    C[:3, :3] = _rot(axis, deg)
+    C[:3, 3] = t
+    return C.astype(np.float32)
+
+
+def _setup(budget=None):
+    import torch
+
+    sc = synth.window_scene(0, n=N, deg=1)
+    ctx = make_ctx(deg=1, n_max=N, chunk=sc["chunk_size"], budget=budget, host=N, page=512, dfar=60.0, moments=1)
+    dcg.dcg_chunk_table_update(ctx, planar(sc["params"]), N)
+    F = sc["params"].shape[1]
+    if budget is None:  # give the moments non-zero values
+        g, n = dcg.dcg_gather_active(ctx, np.arange(dcg.dcg_chunk_count(ctx), dtype=np.int32))
+        grad = torch.sin(3.0 * dcg.active_tensor(g, n, F)).contiguous()
+        dcg.dcg_adam_step(ctx, g, dcg.gaussians(grad, 1), n, np.full(F, 1e-3, np.float32), step=1)
+        dcg.dcg_scatter_back(ctx, g, n)
+    dcg.dcg_flush(ctx)
+    return ctx, sc, F
+
+
+def _read_all(ctx, F):
+    info = dcg.dcg_chunk_info(ctx)
+    out = {}
+    for c, k in enumerate(info["keys"]):
+        cnt = int(info["counts"][c])
+        p = dcg.dcg_chunk_read(ctx, c, cnt, F)
+        m, v = dcg.dcg_chunk_read_moments(ctx, c, cnt, F)
+        out[int(k)] = np.concatenate([p, m, v]).T.copy()
+    return out
+
+
+def _same(after, want):
+    assert sorted(after) == sorted(want)
+    for k in want:
+        a, w = after[k], want[k]
+        assert a.shape == w.shape, k
+        cols = [c for c in range(a.shape[1]) if c not in QUAT]
+        assert np.array_equal(a[:, cols], w[:, cols]), k
+        qa, qw = a[:, QUAT].astype(np.float64), w[:, QUAT].astype(np.float64)
+        err = np.minimum(np.abs(qa - qw).max(1), np.abs(qa + qw).max(1))  # q and -q are one rotation
+        assert (err <= 2e-6 * np.abs(qw).max(1) + 1e-30).all(), k
+
+
+def test_loop_closure_matches_reference():
+    ctx, sc, F = _setup()
+    try:
+        kfs = [sc["cams"][0], sc["cams"][3]]
+        corrs = [_corr("z", 2.0, (0.8, -0.4, 0.3)), _corr("x", 1.5, (-0.6, 0.5, 0.2))]
+        before = _read_all(ctx, F)
+        nt, nm = dcg.dcg_loop_closure(ctx, kfs, corrs)
+        dcg.dcg_flush(ctx)
+        after = _read_all(ctx, F)
+        want, wt, wm = lc.loop_closure(before, sc["chunk_size"], 60.0, kfs, corrs)
+        assert (nt, nm) == (wt, wm) and nt > 1000 and nm > 100
+        _same(after, want)
+        # the corrected map renders
+        import torch
+
+        g, n = dcg.dcg_gather_active(ctx, np.arange(dcg.dcg_chunk_count(ctx), dtype=np.int32))
+        c = sc["cams"][0]
+        rgb, depth = torch.zeros(3 * c.W * c.H, device="cuda"), torch.zeros(c.W * c.H, device="cuda")
+        dcg.dcg_render_fwd(ctx, g, n, [c], rgb, depth)
+        dcg.dcg_sync(ctx)
+        assert n == N and float(rgb.abs().sum()) > 0
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
+def test_identity_correction_changes_nothing_and_budget_error_leaves_the_table():
+    ctx, sc, F = _setup()
+    try:
+        before = _read_all(ctx, F)
+        nt, nm = dcg.dcg_loop_closure(ctx, [sc["cams"][1]], [np.eye(4, dtype=np.float32)])
+        dcg.dcg_flush(ctx)
+        assert nt > 0 and nm == 0
+        after = _read_all(ctx, F)
+        assert sorted(after) == sorted(before)
+        assert all(np.array_equal(after[k], before[k]) for k in before)
+    finally:
+        dcg.dcg_destroy(ctx)
+    small, sc, F = _setup(budget=N // 16)
+    try:
+        before = _read_all(small, F)
+        with pytest.raises(dcg.DcgError) as e:
+            dcg.dcg_loop_closure(small, sc["cams"][:4], [_corr("z", 1.0, (0.1, 0, 0))] * 4)
+        assert e.value.status == 4
+        after = _read_all(small, F)
+        assert all(np.array_equal(after[k], before[k]) for k in before)
+    finally:
+        dcg.dcg_destroy(small)
+
+
+def test_reset_active_caps_opacity_and_zeroes_moments():
+    ctx, sc, F = _setup()
+    try:
+        g, n = dcg.dcg_gather_active(ctx, np.arange(4, dtype=np.int32))
+        p0 = dcg.active_tensor(g, n, F).cpu().numpy().copy()
+        dcg.dcg_reset_active(ctx, g, n, 0.01)
+        dcg.dcg_sync(ctx)
+        p1 = dcg.active_tensor(g, n, F).cpu().numpy()
+        cap = np.float32(np.log(0.01 / 0.99))
+        assert np.array_equal(p1[10], np.minimum(p0[10], cap))
+        assert np.array_equal(np.delete(p1, 10, 0), np.delete(p0, 10, 0))
+        m, v = dcg.dcg_active_moments(ctx)
+        assert not dcg.active_tensor(m, n, F).any() and not dcg.active_tensor(v, n, F).any()
+    finally:
+        dcg.dcg_destroy(ctx)
