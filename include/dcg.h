@@ -262,6 +262,36 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
  * DCG_ERR_STATE if n differs from the gathered set.  Stream-ordered. */
 dcg_status dcg_reset_active(dcg_ctx* ctx, const dcg_gaussians* params, int64_t n, float max_opacity, void* stream);
 
+/* ---------------------------------------------------------------- LoG sampling (Sec. III-B, Eq. 1) */
+
+/* Sampling probability of Eq. 1 for one view and the pixels it samples:
+ * P_s = max(P_L - P~, 0) with P_L, P~ the norms over the three channels of
+ * the Laplacian-of-Gaussian responses of `image` and of `rendered` (dev,
+ * [3][H][W] each).  The paper leaves the operator open; here: sigma 1 on a
+ * 7 x 7 support as g2(dx) g(dy) + g(dx) g2(dy) (g the normalised Gaussian,
+ * g2 its second derivative shifted to sum 0), the nearest edge pixel repeated
+ * outside the image.  Pixel p = y W + x is sampled iff
+ * u[p] < min(1, kappa P_s(p)) (u: dev [H W], the caller's uniform numbers in
+ * [0, 1)).  ps_out (dev [H W], may be NULL) receives P_s; idx_out (dev,
+ * max_out entries) the sampled pixels in ascending order, *n_out (host)
+ * their number (DCG_ERR_CAPACITY if more than max_out, the first max_out are
+ * written).  H W <= max_pixels.  Synchronous. */
+dcg_status dcg_log_sample(dcg_ctx* ctx, const float* image, const float* rendered, int32_t W, int32_t H, float kappa,
+                          const float* u, float* ps_out, int32_t* idx_out, int32_t max_out, int32_t* n_out,
+                          void* stream);
+
+/* New Gaussians at n sampled pixels idx (dev) of a view with camera `cam`:
+ * centre at depth[p] (dev [H W], metres along the optical axis, > 0) on the
+ * pixel's ray, log-scale log(depth / fx) on all three axes (one pixel
+ * footprint), identity rotation, the given opacity logit, SH DC
+ * (image[p] - 0.5) / Y00 from the pixel colour (dev [3][H][W]) and the other
+ * coefficients 0, written planar to params_out (dev, [F][stride], stride >= n)
+ * for dcg_chunk_table_update.  The paper places sampled Gaussians at depths
+ * from its depth networks (Sec. III-B); those are outside this library. */
+dcg_status dcg_backproject(dcg_ctx* ctx, const int32_t* idx, int32_t n, const float* depth, const float* image,
+                           const dcg_camera* cam, float opacity_logit, float* params_out, int64_t stride,
+                           void* stream);
+
 /* ---------------------------------------------------------------- rendering
  * Differentiable rasterisation of RGB and depth (Sec. III-E: the selected
  * Gaussians are rasterised into RGB and depth images; Eq. 4 needs the depth)

@@ -129,6 +129,9 @@ struct dcg_ctx {
   long long* d_lcseg = nullptr;
   int* d_lcsegc = nullptr;
   LcView* d_lcview = nullptr;
+  // LoG sampling: per-pixel flags, sample count
+  uint32_t* d_lsflags = nullptr;
+  u64* d_lscount = nullptr;
   cudaEvent_t ev_loss = nullptr;
   int fault = 0;
   // captured window graph
@@ -380,6 +383,9 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
       dmalloc(&ctx->d_losscams, kMaxViewsApi) != cudaSuccess ||
       cudaHostAlloc((void**)&ctx->h_losscams, sizeof(DevCam) * kMaxViewsApi, 0) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
+  if (dmalloc(&ctx->d_lsflags, (size_t)c.max_pixels) != cudaSuccess || dmalloc(&ctx->d_lscount, 1) != cudaSuccess)
+    return cleanup_fail(DCG_ERR_OOM);
+  if (log_init() != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
   ctx->cap_ssim_tiles = c.max_pixels / 16 + 64 * (int64_t)c.max_views + 64;
   if (dmalloc(&ctx->d_ssimcams, kMaxViewsApi) != cudaSuccess || dmalloc(&ctx->d_wssimcams, kMaxViewsApi) != cudaSuccess ||
       dmalloc(&ctx->d_ssimpart, 3 * (size_t)ctx->cap_ssim_tiles) != cudaSuccess ||
@@ -459,6 +465,8 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   cudaFree(ctx->d_losscams);
   cudaFree(ctx->d_losspart);
   if (ctx->h_losscams) cudaFreeHost(ctx->h_losscams);
+  cudaFree(ctx->d_lsflags);
+  cudaFree(ctx->d_lscount);
   cudaFree(ctx->d_lcmask);
   cudaFree(ctx->d_lcseg);
   cudaFree(ctx->d_lcsegc);
@@ -1248,6 +1256,50 @@ dcg_status dcg_reset_active(dcg_ctx* ctx, const dcg_gaussians* params, int64_t n
   if (ctx->Fs > ctx->F)
     CK(cudaMemset2DAsync(ctx->d_active + (size_t)ctx->F * ctx->cfg.max_active, (size_t)ctx->cfg.max_active * 4, 0,
                          (size_t)n * 4, (size_t)(ctx->Fs - ctx->F), s));
+  CK(cudaGetLastError());
+  return DCG_OK;
+}
+
+// ---------------------------------------------------------------- LoG sampling
+static LcView view_of(const dcg_camera& c) {
+  LcView v{};
+  for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 3; ++q) v.R[3 * r + q] = c.Tcw[4 * r + q];
+    v.t[r] = c.Tcw[4 * r + 3];
+  }
+  v.fx = c.fx; v.fy = c.fy; v.cx = c.cx; v.cy = c.cy; v.znear = c.znear; v.zfar = c.zfar; v.W = c.W; v.H = c.H;
+  return v;
+}
+
+dcg_status dcg_log_sample(dcg_ctx* ctx, const float* image, const float* rendered, int32_t W, int32_t H, float kappa,
+                          const float* u, float* ps_out, int32_t* idx_out, int32_t max_out, int32_t* n_out,
+                          void* stream) {
+  if (!ctx || !image || !rendered || !u || !idx_out || !n_out || W <= 0 || H <= 0 || max_out < 0 || !(kappa >= 0.f) ||
+      !std::isfinite(kappa))
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  if ((int64_t)W * H > ctx->cfg.max_pixels || (int64_t)W * H >= (1ll << 31))
+    return fail(ctx, DCG_ERR_CAPACITY, "image larger than max_pixels");
+  cudaStream_t s = (cudaStream_t)stream;
+  dcg_render_state* st = ctx->st0;
+  launch_log_sample(image, rendered, W, H, kappa, u, ps_out, ctx->d_lsflags, idx_out, max_out, st->part, st->P,
+                    ctx->d_lscount, s);
+  CK(cudaGetLastError());
+  u64 cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, ctx->d_lscount, sizeof(u64), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *n_out = (int32_t)std::min<u64>(cnt, (u64)max_out);
+  if (cnt > (u64)max_out) return fail(ctx, DCG_ERR_CAPACITY, "more samples than max_out");
+  return DCG_OK;
+}
+
+dcg_status dcg_backproject(dcg_ctx* ctx, const int32_t* idx, int32_t n, const float* depth, const float* image,
+                           const dcg_camera* cam, float opacity_logit, float* params_out, int64_t stride,
+                           void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!idx || !depth || !image || !params_out)) || !cam || stride < n)
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  if (cam->W <= 0 || cam->H <= 0 || !(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(ctx, DCG_ERR_ARG, "bad camera");
+  launch_backproject(idx, n, depth, image, cam->W, cam->H, view_of(*cam), opacity_logit, ctx->F, params_out, stride,
+                     ctx->num_sms, (cudaStream_t)stream);
   CK(cudaGetLastError());
   return DCG_OK;
 }

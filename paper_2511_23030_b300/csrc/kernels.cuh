@@ -60,6 +60,15 @@ void launch_permute_rows(const float* src, long long sstride, float* dst, long l
                          long long n, int rows, int num_sms, cudaStream_t st);
 void launch_cap_rows(float* row, long long n, float cap, int num_sms, cudaStream_t st);
 
+// ---------------------------------------------------------------- sampling.cu
+cudaError_t log_init();
+void launch_log_sample(const float* img, const float* ren, int W, int H, float kappa, const float* u, float* ps_out,
+                       uint32_t* flags, int32_t* idx_out, long long cap, u64* part, int Pb, u64* count,
+                       cudaStream_t st);
+void launch_backproject(const int32_t* idx, long long n, const float* depth, const float* img, int W, int H,
+                        const LcView& cam, float logit, int F, float* out, long long stride, int num_sms,
+                        cudaStream_t st);
+
 // ---------------------------------------------------------------- optim.cu
 constexpr int kAdamMaxF = 64;
 struct AdamArgs {

@@ -112,6 +112,10 @@ _SIGS = {
     "dcg_loop_closure": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _P, _I32, ctypes.POINTER(_I64),
                                         ctypes.POINTER(_I64), _P]),
     "dcg_reset_active": (ctypes.c_int, [_P, _P, _I64, ctypes.c_float, _P]),
+    "dcg_log_sample": (ctypes.c_int, [_P, _P, _P, _I32, _I32, ctypes.c_float, _P, _P, _P, _I32, ctypes.POINTER(_I32),
+                                      _P]),
+    "dcg_backproject": (ctypes.c_int, [_P, _P, _I32, _P, _P, ctypes.POINTER(dcg_camera), ctypes.c_float, _P, _I64,
+                                       _P]),
     "dcg_cull_chunks_noalloc": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(dcg_camera),
                                                _I32, _P, _P, _P, _P]),
 }
@@ -311,6 +315,20 @@ def dcg_loop_closure(ctx, keyframes, corrections, stream=None):
 
 def dcg_reset_active(ctx, params: dcg_gaussians, n: int, max_opacity=0.01, stream=None):
     check(ctx, lib().dcg_reset_active(ctx, ctypes.byref(params), n, float(max_opacity), stream_ptr(stream)))
+
+
+def dcg_log_sample(ctx, image, rendered, W: int, H: int, kappa: float, u, idx_out, ps_out=None, stream=None) -> int:
+    """Eq. 1 penalty sampling of one view; returns the number of sampled pixels written to idx_out."""
+    n = _I32()
+    check(ctx, lib().dcg_log_sample(ctx, ptr(image), ptr(rendered), W, H, float(kappa), ptr(u), ptr(ps_out),
+                                    ptr(idx_out), idx_out.numel(), ctypes.byref(n), stream_ptr(stream)))
+    return int(n.value)
+
+
+def dcg_backproject(ctx, idx, n: int, depth, image, cam, opacity_logit: float, params_out, stream=None):
+    arr = make_cameras([cam])
+    check(ctx, lib().dcg_backproject(ctx, ptr(idx), n, ptr(depth), ptr(image), arr, float(opacity_logit),
+                                     ptr(params_out), params_out.stride(0), stream_ptr(stream)))
 
 
 def dcg_state_create(ctx):

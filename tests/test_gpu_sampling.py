@@ -1,0 +1,84 @@
+"""LoG penalty sampling of Eq. 1 and back-projection against the references;
+sampled Gaussians enter the chunk table."""
+import numpy as np
+import pytest
+
+from oracle import logsample as ls
+from paper_2511_23030_b300 import dcg, synth
+
+from gpu_util import make_ctx, render, planar
+
+pytestmark = pytest.mark.gpu
+
+
+def _images(W, H, seed):
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    base = np.stack([0.5 + 0.4 * np.sin(0.3 * x + 0.2 * y), 0.5 + 0.4 * np.cos(0.25 * y), 0.3 + 0.002 * x])
+    img = base + (rng.uniform(0, 1, (3, H, W)) < 0.05) * 0.5  # sparse bright details
+    ren = base + 0.1 * rng.normal(size=(3, H, W))
+    return np.clip(img, 0, 1).astype(np.float32), np.clip(ren, 0, 1).astype(np.float32)
+
+
+@pytest.mark.parametrize("W,H", [(100, 70), (37, 23), (16, 16)])
+def test_penalty_and_samples_match_reference(W, H):
+    import torch
+
+    img, ren = _images(W, H, W)
+    u = np.random.default_rng(1).uniform(0, 1, W * H).astype(np.float32)
+    ctx = make_ctx(deg=0, n_max=1000, views=1, pixels=W * H)
+    try:
+        ti, tr, tu = (torch.from_numpy(a.reshape(-1)).cuda() for a in (img, ren, u))
+        ps = torch.zeros(W * H, device="cuda")
+        idx = torch.zeros(W * H, dtype=torch.int32, device="cuda")
+        n = dcg.dcg_log_sample(ctx, ti, tr, W, H, 3.0, tu, idx, ps_out=ps)
+        want = ls.penalty(img, ren).reshape(-1)
+        got = ps.cpu().numpy().astype(np.float64)
+        assert np.abs(got - want).max() <= 1e-5 * want.max() + 1e-6
+        got_idx = set(idx[:n].cpu().numpy().tolist())
+        assert list(idx[:n].cpu().numpy()) == sorted(got_idx)  # ascending
+        ref_idx = set(ls.sample(want, u, 3.0).tolist())
+        # decisions may differ only where u is within rounding of the threshold
+        amb = set(np.nonzero(np.abs(u - np.minimum(1.0, 3.0 * want)) <= 1e-5)[0].tolist())
+        assert (got_idx ^ ref_idx) <= amb and len(got_idx) > 0
+        # capacity: fewer slots than samples
+        small = torch.zeros(max(1, n // 2), dtype=torch.int32, device="cuda")
+        with pytest.raises(dcg.DcgError) as e:
+            dcg.dcg_log_sample(ctx, ti, tr, W, H, 3.0, tu, small)
+        assert e.value.status == 6
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
+def test_backprojection_and_insertion_into_chunks():
+    import torch
+
+    sc = synth.room_small(0)
+    P, cam = sc["params"], sc["cams"][0]
+    W, H = cam.W, cam.H
+    ctx = make_ctx(deg=0, n_max=20_000, views=1, pixels=W * H, chunk=1.0, host=40_000)
+    try:
+        # the input image is the full scene, the current map holds half of it
+        _, _, img, dep = render(ctx, P, 0, [cam])
+        _, _, ren, _ = render(ctx, P[::2].copy(), 0, [cam])
+        u = torch.from_numpy(np.random.default_rng(2).uniform(0, 1, W * H).astype(np.float32)).cuda()
+        idx = torch.zeros(W * H, dtype=torch.int32, device="cuda")
+        n = dcg.dcg_log_sample(ctx, img, ren, W, H, 20.0, u, idx)
+        assert n > 10
+        # depths where the full scene rendered something
+        d = dep.clone()
+        d[d <= 0.05] = 1.0
+        F = 11 + 3
+        out = torch.zeros((F, n), device="cuda")
+        dcg.dcg_backproject(ctx, idx, n, d, img, cam, 0.0, out)
+        dcg.dcg_sync(ctx)
+        want = ls.backproject(idx[:n].cpu().numpy(), d.cpu().numpy(), img.cpu().numpy().reshape(3, H, W), cam, 0.0, F)
+        got = out.T.cpu().numpy().astype(np.float64)
+        assert np.allclose(got, want, rtol=2e-6, atol=2e-6)
+        # into the chunk table: the map grows by the sampled Gaussians
+        dcg.dcg_chunk_table_update(ctx, planar(P), P.shape[0])
+        dcg.dcg_chunk_table_update(ctx, out, n)
+        info = dcg.dcg_chunk_info(ctx)
+        assert int(info["counts"].sum()) == P.shape[0] + n
+    finally:
+        dcg.dcg_destroy(ctx)
