@@ -395,10 +395,12 @@ dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const d
 dcg_status dcg_state_stats(dcg_render_state* st, int64_t* n_visible, int64_t* n_instances, int64_t* n_tiles,
                            void* stream);
 
-/* Pixel-Gaussian evaluations performed by the last forward blend of `st`:
- * (pixel, Gaussian) pairs whose support test ran while the pixel was still
- * blending (the unit of the blend's arithmetic).  Synchronises `stream`. */
-dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, void* stream);
+/* Work of the last forward blend of `st`: *n_eval (pixel, Gaussian) pairs
+ * whose support test ran while the pixel was still blending (depends on the
+ * kernel's culling), *n_blend (may be NULL) pairs actually composited
+ * (alpha >= 1/255, before termination: the method's own unit of blending
+ * work, independent of the kernel).  Synchronises `stream`. */
+dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, int64_t* n_blend, void* stream);
 
 /* Copies of the state's per-tile sorted lists for checks (host outputs; any
  * may be NULL): ranges [n_tiles, 2] (start, end) into ids, ids [n_instances]

@@ -268,7 +268,7 @@ dcg_status state_alloc(dcg_ctx* ctx, dcg_render_state* st) {
   st->cap_inst = c.max_instances;
   st->cap_pix = c.max_pixels;
   st->cap_tiles = c.max_pixels / 16 + 64 * (int64_t)c.max_views + 64;  // generous bound incl. ragged edges
-  st->P = ctx->num_sms * 4;
+  st->P = ctx->num_sms * 8;  // partitions of the scans and sorts: 8 per SM keep enough loads in flight
   CK(dmalloc(&st->d_cams, kMaxViewsApi));
   CK(cudaHostAlloc((void**)&st->h_cams, sizeof(DevCam) * kMaxViewsApi, cudaHostAllocDefault));
   CK(cudaEventCreateWithFlags(&st->ev_cams, cudaEventDisableTiming));
@@ -1731,13 +1731,14 @@ dcg_status dcg_state_stats(dcg_render_state* st, int64_t* n_visible, int64_t* n_
   return DCG_OK;
 }
 
-dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, void* stream) {
+dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, int64_t* n_blend, void* stream) {
   if (!st || !n_eval) return DCG_ERR_ARG;
   dcg_ctx* ctx = st->ctx;
   DevCounters h;
   CK(cudaMemcpyAsync(&h, st->counters, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   *n_eval = (int64_t)h.n_eval;
+  if (n_blend) *n_blend = (int64_t)h.n_blend;
   return DCG_OK;
 }
 

@@ -99,6 +99,7 @@ struct DevCounters {
   u64 n_inst;   // instances requested (> capacity means overflow)
   u64 n_inst_c; // instances kept (min with capacity)
   u64 n_eval;   // pixel-Gaussian evaluations of the forward blend
+  u64 n_blend;  // pixel-Gaussian pairs the forward blend composited (alpha >= 1/255, before termination)
   unsigned tile_queue;
   unsigned tile_queue_bwd;
   unsigned pad[8];

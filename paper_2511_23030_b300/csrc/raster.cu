@@ -309,7 +309,7 @@ __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, flo
 // 1. preprocess
 // ============================================================================
 template <int DEG>
-__global__ void __launch_bounds__(256) k_preprocess_fwd(RasterArgs a) {
+__global__ void __launch_bounds__(256, 3) k_preprocess_fwd(RasterArgs a) {
   const long long n = a.n;
   constexpr int D = (DEG + 1) * (DEG + 1);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
     const float x0f = (float)x0, y0f = (float)y0;
     float T[PPT], Tf[PPT], Cr[PPT], Cg[PPT], Cb[PPT], Dz[PPT];
     uint32_t last[PPT];
-    unsigned ev = 0;  // evaluations of (live pixel, Gaussian) pairs by this thread
+    unsigned ev = 0, nb = 0;  // evaluations of (live pixel, Gaussian) pairs by this thread
     const int px = x0 + lx;
     int alive = 0;
 #pragma unroll
@@ -635,6 +635,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
                   Dz[k] += wgt * cl.w;
                   T[k] = Tn;
                   last[k] = s_rel[w][j] + 1;
+                  ++nb;
                 }
               }
             }
@@ -647,8 +648,9 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
       for (int k = 0; k < PPT; ++k) alive |= T[k] > 0.f;
     }
     {
-      const unsigned wev = __reduce_add_sync(0xffffffffu, ev);
+      const unsigned wev = __reduce_add_sync(0xffffffffu, ev), wnb = __reduce_add_sync(0xffffffffu, nb);
       if (lane == 0 && wev) atomicAdd(&a.counters->n_eval, (unsigned long long)wev);
+      if (lane == 0 && wnb) atomicAdd(&a.counters->n_blend, (unsigned long long)wnb);
     }
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
@@ -927,7 +929,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd_q(RasterArgs a, const u64* __
     const float x0f = (float)x0, y0f = (float)y0;
     float T[PPT], Tf[PPT], Cr[PPT], Cg[PPT], Cb[PPT], Dz[PPT];
     uint32_t last[PPT];
-    unsigned ev = 0;
+    unsigned ev = 0, nb = 0;
     const int px = x0 + lx;
     int alive = 0;
 #pragma unroll
@@ -988,6 +990,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd_q(RasterArgs a, const u64* __
                   Dz[k] += wgt * cl.w;
                   T[k] = Tn;
                   last[k] = s_rel[w][j] + 1;
+                  ++nb;
                 }
               }
             }
@@ -1000,8 +1003,9 @@ __global__ void __launch_bounds__(256) k_blend_fwd_q(RasterArgs a, const u64* __
       for (int k = 0; k < PPT; ++k) alive |= T[k] > 0.f;
     }
     {
-      const unsigned wev = __reduce_add_sync(0xffffffffu, ev);
+      const unsigned wev = __reduce_add_sync(0xffffffffu, ev), wnb = __reduce_add_sync(0xffffffffu, nb);
       if (lane == 0 && wev) atomicAdd(&a.counters->n_eval, (unsigned long long)wev);
+      if (lane == 0 && wnb) atomicAdd(&a.counters->n_blend, (unsigned long long)wnb);
     }
     const long long P = (long long)W * H;
 #pragma unroll

@@ -37,8 +37,13 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d, int nbits, bool vali
   return peers;
 }
 
-// Per-block digit histogram of the block's partition.
-__global__ void k_radix_hist(const u64* keys, const u64* n_ptr, int shift, int nbits, uint32_t* hist) {
+// Per-block digit histogram of the block's partition.  Each thread loads
+// kHistUnroll keys (strided by the block size) before ranking them, so that
+// several loads are in flight per thread.
+constexpr int kHistUnroll = 4;
+
+__global__ void __launch_bounds__(256) k_radix_hist(const u64* keys, const u64* n_ptr, int shift, int nbits,
+                                                    uint32_t* hist) {
   __shared__ uint32_t h[256];
   const u64 n = *n_ptr;
   u64 beg, end;
@@ -46,12 +51,22 @@ __global__ void k_radix_hist(const u64* keys, const u64* n_ptr, int shift, int n
   h[threadIdx.x] = 0;
   __syncthreads();
   const u64 mask = (1ull << nbits) - 1;
-  for (u64 c0 = beg; c0 < end; c0 += blockDim.x) {
-    const u64 i = c0 + threadIdx.x;
-    const bool valid = i < end;
-    const unsigned d = valid ? (unsigned)((keys[i] >> shift) & mask) : 0u;
-    const unsigned peers = digit_peers(d, nbits, valid);
-    if (valid && lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  const unsigned lane = lane_id();
+  for (u64 c0 = beg; c0 < end; c0 += (u64)kHistUnroll * blockDim.x) {
+    u64 k[kHistUnroll];
+#pragma unroll
+    for (int r = 0; r < kHistUnroll; ++r) {
+      const u64 i = c0 + (u64)r * blockDim.x + threadIdx.x;
+      k[r] = i < end ? keys[i] : 0ull;
+    }
+#pragma unroll
+    for (int r = 0; r < kHistUnroll; ++r) {
+      const u64 i = c0 + (u64)r * blockDim.x + threadIdx.x;
+      const bool valid = i < end;
+      const unsigned d = valid ? (unsigned)((k[r] >> shift) & mask) : 0u;
+      const unsigned peers = digit_peers(d, nbits, valid);
+      if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
   }
   __syncthreads();
   hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
@@ -108,11 +123,16 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, 
     uint32_t pos[kSortRounds];
     unsigned dig[kSortRounds];
     const unsigned lt = lanemask_lt();
+    // all loads of the chunk first (several in flight per thread), then the ranking
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+      const u64 i = c0 + (u64)w * 256 + (u64)r * 32 + lane;
+      key[r] = i < end ? in[i] : 0ull;
+    }
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
       const u64 i = c0 + (u64)w * 256 + (u64)r * 32 + lane;
       const bool valid = i < end;
-      key[r] = valid ? in[i] : 0ull;
       const unsigned d = valid ? (unsigned)((key[r] >> shift) & mask) : 0u;
       dig[r] = valid ? d : 256u;
       const unsigned peers = digit_peers(d, nbits, valid);

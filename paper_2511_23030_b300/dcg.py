@@ -81,7 +81,7 @@ _SIGS = {
     "dcg_autotune": (ctypes.c_int, [_P, ctypes.POINTER(dcg_gaussians), _I64, ctypes.POINTER(dcg_camera), _I32, _P, _P,
                                     _P, _P, ctypes.POINTER(dcg_gaussians), _I32, ctypes.POINTER(_I32),
                                     ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P, _P]),
-    "dcg_state_evals": (ctypes.c_int, [_P, ctypes.POINTER(_I64), _P]),
+    "dcg_state_evals": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
     "dcg_profile_read": (ctypes.c_int, [_P, _P, _P]),
     "dcg_launch_count": (ctypes.c_uint64, []),
     "dcg_window_capture": (ctypes.c_int, [_P, ctypes.POINTER(dcg_gaussians), _I64, ctypes.POINTER(dcg_camera), _I32,
@@ -412,11 +412,12 @@ def dcg_launch_count() -> int:
     return int(lib().dcg_launch_count())
 
 
-def dcg_state_evals(ctx, state=None, stream=None) -> int:
-    v = _I64()
+def dcg_state_evals(ctx, state=None, stream=None):
+    """(evaluations, composited pairs) of the last forward blend."""
+    v, b = _I64(), _I64()
     st = state if state is not None else dcg_default_state(ctx)
-    check(ctx, lib().dcg_state_evals(st, ctypes.byref(v), stream_ptr(stream)))
-    return int(v.value)
+    check(ctx, lib().dcg_state_evals(st, ctypes.byref(v), ctypes.byref(b), stream_ptr(stream)))
+    return int(v.value), int(b.value)
 
 
 TUNE_TILES = [(16, 16), (32, 16), (32, 32)]
