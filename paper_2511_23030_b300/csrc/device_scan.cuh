@@ -69,13 +69,25 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total) {
 //   CountF: u64 operator()(u64 i) const   -- items item i produces
 //   EmitF : void operator()(u64 i, u64 offset, u64 count) const
 // part[0..P) partial sums, part[P] total.
+// Items per thread per step of the partition walks (several loads in flight).
+constexpr int kScanItems = 4;
+
 template <class CountF>
 __global__ void k_part_reduce(const u64* n_ptr, u64 n_host, CountF f, u64* part) {
   const u64 n = n_ptr ? *n_ptr : n_host;
   u64 beg, end;
   partition_of(n, &beg, &end);
   u64 acc = 0;
-  for (u64 i = beg + threadIdx.x; i < end; i += blockDim.x) acc += f(i);
+  for (u64 c0 = beg; c0 < end; c0 += (u64)kScanItems * blockDim.x) {
+    u64 v[kScanItems];
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+      const u64 i = c0 + (u64)r * blockDim.x + threadIdx.x;
+      v[r] = i < end ? f(i) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) acc += v[r];
+  }
   __shared__ u64 red[32];
 #pragma unroll
   for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -92,18 +104,30 @@ __global__ void k_part_reduce(const u64* n_ptr, u64 n_host, CountF f, u64* part)
 // Single block: exclusive scan of part[0..P) in place, total to part[P] and *total_out.
 __global__ void k_part_scan(u64* part, int P, u64* total_out);
 
+// Emission in item order: each step covers kScanItems * blockDim items, thread
+// t the consecutive items [c0 + kScanItems t, c0 + kScanItems (t + 1)).
 template <class CountF, class EmitF>
 __global__ void k_part_emit(const u64* n_ptr, u64 n_host, CountF f, EmitF e, const u64* part) {
   const u64 n = n_ptr ? *n_ptr : n_host;
   u64 beg, end;
   partition_of(n, &beg, &end);
   u64 base = part[blockIdx.x];
-  for (u64 c0 = beg; c0 < end; c0 += blockDim.x) {
-    const u64 i = c0 + threadIdx.x;
-    const u64 cnt = i < end ? f(i) : 0;
+  for (u64 c0 = beg; c0 < end; c0 += (u64)kScanItems * blockDim.x) {
+    const u64 i0 = c0 + (u64)kScanItems * threadIdx.x;
+    u64 cnt[kScanItems];
+    u64 sum = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+      cnt[r] = i0 + r < end ? f(i0 + r) : 0;
+      sum += cnt[r];
+    }
     u64 tot;
-    const u64 off = block_excl_scan<u64>(cnt, &tot);
-    if (i < end && cnt) e(i, base + off, cnt);
+    u64 off = base + block_excl_scan<u64>(sum, &tot);
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+      if (cnt[r]) e(i0 + r, off, cnt[r]);
+      off += cnt[r];
+    }
     base += tot;
   }
 }

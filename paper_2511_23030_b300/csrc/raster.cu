@@ -11,11 +11,10 @@
 //   3. depth sort         stable LSD radix sort on the depth bits (the view
 //                         bits ride along; the tile sort separates views)
 //   4. instance emission  ordered scan of tiles-touched in depth order; each
-//                         instance is (global tile id, pair index)
+//                         instance is (warp-block mask, global tile id, pair)
 //   5. tile sort          stable LSD radix sort on the tile id only: the depth
 //                         order inside a tile survives from step 3
-//   6. ranges + masks     [start, end) per tile; each instance gets the mask
-//                         of the tile's warp blocks its Gaussian reaches
+//   6. ranges             [start, end) per tile
 //   7. k_blend_fwd        persistent blocks take tiles from a device queue,
 //                         stage records in shared memory, blend front to back
 // Backward:
@@ -270,18 +269,29 @@ __device__ __forceinline__ uint32_t tight_count(float4 r0, float4 cn, short4 r, 
   return k;
 }
 
-// Warp blocks (8 x wy pixels, wpr per row, nbr rows) of a tile that the
-// ellipse reaches; (ul, vl) is its centre relative to the tile origin.
-__device__ __forceinline__ unsigned tile_block_mask(const SupportEllipse& e, float ul, float vl, int wpr, int wy,
-                                                    int nbr) {
+// x-extents of the ellipse in the nbr bands of warp blocks (wy pixel rows
+// each) of a tile row; vl is the centre relative to the row's top.  Returns
+// the bitmask of bands the ellipse reaches.
+__device__ __forceinline__ unsigned block_bands(const SupportEllipse& e, float vl, int wy, int nbr, float* bl,
+                                                float* br) {
+  unsigned bands = 0;
+  for (int rb = 0; rb < nbr; ++rb) {
+    const float y0 = __fsub_rn((float)(rb * wy), vl);
+    if (band_extent(e, y0, __fadd_rn(y0, (float)(wy - 1)), &bl[rb], &br[rb])) bands |= 1u << rb;
+  }
+  return bands;
+}
+
+// Warp blocks (8 columns each, wpr per row) of one tile of that row that the
+// ellipse reaches; ul is the centre relative to the tile's left edge.
+__device__ __forceinline__ unsigned tile_block_mask(unsigned bands, const float* bl, const float* br, float ul,
+                                                    int wpr, int nbr) {
   unsigned mask = 0;
   for (int rb = 0; rb < nbr; ++rb) {
-    float xl, xr;
-    const float y0 = __fsub_rn((float)(rb * wy), vl);
-    if (!band_extent(e, y0, __fadd_rn(y0, (float)(wy - 1)), &xl, &xr)) continue;
+    if (!((bands >> rb) & 1u)) continue;
     for (int c = 0; c < wpr; ++c) {
       const float x0 = __fsub_rn((float)(8 * c), ul);
-      if (xl <= __fadd_rn(x0, 7.f) && xr >= x0) mask |= 1u << (rb * wpr + c);
+      if (bl[rb] <= __fadd_rn(x0, 7.f) && br[rb] >= x0) mask |= 1u << (rb * wpr + c);
     }
   }
   return mask;
@@ -441,8 +451,8 @@ struct InstCount {
 };
 // One thread per visible pair (in depth order) writes its instances: the
 // tiles of its rectangle that the support ellipse reaches (row spans, the
-// same as the count in k_preprocess_fwd).  Block masks are added after the
-// tile sort (k_ranges_masks).
+// same as the count in k_preprocess_fwd), each with the mask of the tile's
+// warp blocks the ellipse reaches (band extents once per tile row).
 struct InstEmit {
   const u64* list;
   const short4* rect;
@@ -463,13 +473,19 @@ struct InstEmit {
     const SupportEllipse e = support_of(cn);
     const u64 base = (u64)cams[v].tile_base;
     const int ntx = cams[v].ntx;
+    const int wy = tw * th / 64, wpr = tw / 8, nbr = th / wy;
     u64 o = off;
     for (int ty = r.y; ty <= r.w; ++ty) {
       int j0, j1;
       if (!row_span(e, r0, r, ty, tw, th, whole, &j0, &j1)) continue;
+      float bl[4], br[4];
+      const unsigned bands = block_bands(e, df_sub_round(r0.y, r0.w, (float)(ty * th)), wy, nbr, bl, br);
       const u64 row = base + (u64)ty * ntx + (u64)r.x;
-      for (int j = j0; j <= j1; ++j, ++o)
-        if (o < cap) inst[o] = ((row + (u64)j) << 32) | vi;
+      for (int j = j0; j <= j1; ++j, ++o) {
+        const float ul = df_sub_round(r0.x, r0.z, (float)((r.x + j) * tw));
+        const u64 m = tile_block_mask(bands, bl, br, ul, wpr, nbr);
+        if (o < cap) inst[o] = (m << kMaskShift) | ((row + (u64)j) << 32) | vi;
+      }
     }
   }
 };
@@ -492,29 +508,13 @@ __global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
   if (k > cap) atomicOr(errword, ERRW_CAPACITY_BIT);
 }
 
-// Per-tile ranges [start, end) of the sorted instances, and each instance
-// copied to `out` with the mask of the tile's warp blocks its Gaussian
-// reaches in bits [56, 64) (one thread per instance).
-__global__ void k_ranges_masks(const u64* __restrict__ inst, const u64* n_ptr, uint2* __restrict__ ranges,
-                               u64* __restrict__ out, const float4* __restrict__ rec, const DevCam* __restrict__ cams,
-                               int V, int tw, int th) {
+// Per-tile ranges [start, end) of the sorted instances.
+__global__ void k_ranges(const u64* __restrict__ inst, const u64* n_ptr, uint2* __restrict__ ranges) {
   const u64 K = *n_ptr;
-  const int wpr = tw / 8, wy = tw * th / 64, nbr = th / wy;
   for (u64 k = blockIdx.x * (u64)blockDim.x + threadIdx.x; k < K; k += (u64)gridDim.x * blockDim.x) {
-    const u64 key = inst[k];
-    const unsigned t = (unsigned)(key >> 32) & kTileMask;
+    const unsigned t = (unsigned)(inst[k] >> 32) & kTileMask;
     if (k == 0 || ((unsigned)(inst[k - 1] >> 32) & kTileMask) != t) ranges[t].x = (unsigned)k;
     if (k + 1 == K || ((unsigned)(inst[k + 1] >> 32) & kTileMask) != t) ranges[t].y = (unsigned)(k + 1);
-    int v = 0;
-    while (v + 1 < V && (int)t >= cams[v + 1].tile_base) ++v;
-    const DevCam& c = cams[v];
-    const int local = (int)t - c.tile_base;
-    const int ty = local / c.ntx, tx = local - ty * c.ntx;
-    const unsigned vi = (unsigned)key;
-    const float4 r0 = rec[3ull * vi + 0], cn = rec[3ull * vi + 1];
-    const unsigned m = tile_block_mask(support_of(cn), df_sub_round(r0.x, r0.z, (float)(tx * tw)),
-                                       df_sub_round(r0.y, r0.w, (float)(ty * th)), wpr, wy, nbr);
-    out[k] = key | ((u64)m << kMaskShift);
   }
 }
 
@@ -1696,11 +1696,9 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   k_clamp_inst<<<1, 1, 0, st>>>(a.counters, (u64)a.cap_inst, a.errword);
   int tb = 1;
   while ((1ll << tb) < (long long)a.n_tiles) ++tb;
-  u64* sorted = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, 32, 32 + tb, a.hist, a.P, st);
-  u64* is = sorted == a.inst_a ? a.inst_b : a.inst_a;  // sorted instances with block masks
+  u64* is = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, 32, 32 + tb, a.hist, a.P, st);
   cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)max(a.n_tiles, 1), st);
-  k_ranges_masks<<<a.num_sms * 8, 256, 0, st>>>(sorted, &a.counters->n_inst_c, a.ranges, is, a.rec, a.cams, a.V,
-                                                 a.tile_w, a.tile_h);
+  k_ranges<<<a.num_sms * 8, 256, 0, st>>>(is, &a.counters->n_inst_c, a.ranges);
   count_launch(7 + 3 * ((lbits + 7) / 8) + 3 * ((tb + 7) / 8) + 2);
   a.prof(PH_BINNING, false, st);
   a.prof(PH_BLEND_FWD, true, st);
