@@ -36,14 +36,36 @@ constexpr float kC2 = 0.03f * 0.03f;
 
 __constant__ float c_win[2 * kR + 1];
 
+// Sliding window of 2R+1 taps over a run of `RUN` outputs: out[o] for
+// o < RUN from in[0 .. RUN + 2R), all in registers.
+template <int RUN>
+__device__ __forceinline__ void win_run(const float (&in)[RUN + 2 * kR], float (&out)[RUN]) {
+#pragma unroll
+  for (int o = 0; o < RUN; ++o) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k <= 2 * kR; ++k) acc += c_win[k] * in[o + k];
+    out[o] = acc;
+  }
+}
+
+constexpr int kRunH = 13;  // outputs per thread in the forward horizontal pass (26 = 2 x 13)
+constexpr int kRunV = 13;  // outputs per thread in the forward vertical pass
+constexpr int kRunBH = 8;  // outputs per thread in the backward horizontal pass (half a row)
+constexpr int kRunBV = 4;  // outputs per thread in the backward vertical pass (a quarter column)
+
 __global__ void __launch_bounds__(256) k_ssim(const float* __restrict__ rgb, const float* __restrict__ trgb,
                                               const DevCam* __restrict__ cams, int V, float lam_s,
                                               float* __restrict__ dr, float* __restrict__ part) {
   __shared__ float sx[kA][kA + 1], sy[kA][kA + 1];
   __shared__ float h[5][kA][kG + 1];
-  __shared__ float g3[3][kG][kG + 1];
-  __shared__ float hb[3][kG][kT + 1];
+  // vertical-pass statistics st[0..4]; after the S pass st[0..2] hold the g
+  // maps and the backward horizontal pass writes hb over st[3..4]
+  __shared__ float st_raw[5 * kG * (kG + 1)];
   __shared__ float red[8];
+  float(*st)[kG][kG + 1] = reinterpret_cast<float(*)[kG][kG + 1]>(st_raw);
+  float(*hb)[kG][kT + 1] = reinterpret_cast<float(*)[kG][kT + 1]>(st_raw + 3 * kG * (kG + 1));
+  static_assert(3 * kG * (kT + 1) <= 2 * kG * (kG + 1), "hb fits over st[3..4]");
   const int tid = threadIdx.x;
   const int gt = blockIdx.x, ch = blockIdx.y;
   int v = 0;
@@ -66,41 +88,54 @@ __global__ void __launch_bounds__(256) k_ssim(const float* __restrict__ rgb, con
     sy[r][q] = in ? Y[k] : 0.f;
   }
   __syncthreads();
-  // horizontal window pass: rows 0..35, columns 0..25 of the S region
-  for (int i = tid; i < kA * kG; i += 256) {
-    const int r = i / kG, q = i - r * kG;
-    float m0 = 0.f, m1 = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  // horizontal pass: item = (row, half of the 26 columns, group); groups:
+  // 0 -> (x, x^2), 1 -> (y, y^2), 2 -> x y
+  for (int it = tid; it < kA * 2 * 3; it += 256) {
+    const int grp = it / (kA * 2), rem = it - grp * (kA * 2), r = rem >> 1, q0 = (rem & 1) * kRunH;
+    float a[kRunH + 2 * kR], o1[kRunH], o2[kRunH];
+    if (grp == 0) {
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float wk = c_win[k], a = sx[r][q + k], b = sy[r][q + k];
-      m0 += wk * a;
-      m1 += wk * b;
-      s0 += wk * (a * a);
-      s1 += wk * (b * b);
-      s2 += wk * (a * b);
+      for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = sx[r][q0 + k];
+    } else if (grp == 1) {
+#pragma unroll
+      for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = sy[r][q0 + k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = sx[r][q0 + k] * sy[r][q0 + k];
     }
-    h[0][r][q] = m0;
-    h[1][r][q] = m1;
-    h[2][r][q] = s0;
-    h[3][r][q] = s1;
-    h[4][r][q] = s2;
+    win_run<kRunH>(a, o1);
+    if (grp < 2) {
+#pragma unroll
+      for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = a[k] * a[k];
+      win_run<kRunH>(a, o2);
+    }
+    float* d1 = grp == 0 ? &h[0][r][q0] : (grp == 1 ? &h[1][r][q0] : &h[4][r][q0]);
+    float* d2 = grp == 0 ? &h[2][r][q0] : &h[3][r][q0];
+#pragma unroll
+    for (int o = 0; o < kRunH; ++o) d1[o] = o1[o];
+    if (grp < 2) {
+#pragma unroll
+      for (int o = 0; o < kRunH; ++o) d2[o] = o2[o];
+    }
   }
   __syncthreads();
-  // vertical pass, S and the g maps on the 26 x 26 region
+  // vertical pass: item = (statistic, column, half of the 26 rows)
+  for (int it = tid; it < 5 * kG * 2; it += 256) {
+    const int sidx = it / (kG * 2), rem = it - sidx * (kG * 2), q = rem >> 1, r0 = (rem & 1) * kRunV;
+    float a[kRunV + 2 * kR], o[kRunV];
+#pragma unroll
+    for (int k = 0; k < kRunV + 2 * kR; ++k) a[k] = h[sidx][r0 + k][q];
+    win_run<kRunV>(a, o);
+#pragma unroll
+    for (int k = 0; k < kRunV; ++k) st[sidx][r0 + k][q] = o[k];
+  }
+  __syncthreads();
+  // S and the g maps on the 26 x 26 region (g written over the statistics)
   const float coef = -lam_s / (3.f * (float)P);
   float acc = 0.f;
   for (int i = tid; i < kG * kG; i += 256) {
     const int r = i / kG, q = i - r * kG;
-    float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
-#pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float wk = c_win[k];
-      mx += wk * h[0][r + k][q];
-      my += wk * h[1][r + k][q];
-      xx += wk * h[2][r + k][q];
-      yy += wk * h[3][r + k][q];
-      xy += wk * h[4][r + k][q];
-    }
+    const float mx = st[0][r][q], my = st[1][r][q], xx = st[2][r][q], yy = st[3][r][q], xy = st[4][r][q];
     const int px = ax + kR + q, py = ay + kR + r;
     const bool in = px >= 0 && px < W && py >= 0 && py < H;
     float gmu = 0.f, gxx = 0.f, gxy = 0.f;
@@ -115,41 +150,42 @@ __global__ void __launch_bounds__(256) k_ssim(const float* __restrict__ rgb, con
       gxy = 2.f * cs * iA2;
       if (r >= kR && r < kR + kT && q >= kR && q < kR + kT) acc += S;
     }
-    g3[0][r][q] = gmu;
-    g3[1][r][q] = gxx;
-    g3[2][r][q] = gxy;
+    st[0][r][q] = gmu;  // each thread rewrites only its own position
+    st[1][r][q] = gxx;
+    st[2][r][q] = gxy;
   }
   __syncthreads();
-  // backward horizontal pass: rows 0..25, output columns 0..15
-  for (int i = tid; i < kG * kT; i += 256) {
-    const int r = i / kT, q = i - r * kT;
-    float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+  // backward horizontal pass: item = (g map, row, half of the 16 output columns)
+  constexpr int kSegH = kT / kRunBH;
+  for (int it = tid; it < 3 * kG * kSegH; it += 256) {
+    const int m = it / (kG * kSegH), rem = it - m * (kG * kSegH), r = rem / kSegH, q0 = (rem - r * kSegH) * kRunBH;
+    float a[kRunBH + 2 * kR], o[kRunBH];
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float wk = c_win[k];
-      b0 += wk * g3[0][r][q + k];
-      b1 += wk * g3[1][r][q + k];
-      b2 += wk * g3[2][r][q + k];
-    }
-    hb[0][r][q] = b0;
-    hb[1][r][q] = b1;
-    hb[2][r][q] = b2;
+    for (int k = 0; k < kRunBH + 2 * kR; ++k) a[k] = st[m][r][q0 + k];
+    win_run<kRunBH>(a, o);
+#pragma unroll
+    for (int k = 0; k < kRunBH; ++k) hb[m][r][q0 + k] = o[k];
+  }
+  __syncthreads();
+  // backward vertical pass: item = (g map, column, quarter of the 16 output rows);
+  // the window sums on the tile go to h[m] rows 0..15
+  constexpr int kSegV = kT / kRunBV;
+  for (int it = tid; it < 3 * kT * kSegV; it += 256) {
+    const int m = it / (kT * kSegV), rem = it - m * (kT * kSegV), q = rem / kSegV, r0 = (rem - q * kSegV) * kRunBV;
+    float a[kRunBV + 2 * kR], o[kRunBV];
+#pragma unroll
+    for (int k = 0; k < kRunBV + 2 * kR; ++k) a[k] = hb[m][r0 + k][q];
+    win_run<kRunBV>(a, o);
+#pragma unroll
+    for (int k = 0; k < kRunBV; ++k) h[m][r0 + k][q] = o[k];
   }
   __syncthreads();
   {
     const int r = tid / kT, q = tid - r * kT;  // 256 threads = one output pixel each
-    float b0 = 0.f, b1 = 0.f, b2 = 0.f;
-#pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float wk = c_win[k];
-      b0 += wk * hb[0][r + k][q];
-      b1 += wk * hb[1][r + k][q];
-      b2 += wk * hb[2][r + k][q];
-    }
     const int px = tx * kT + q, py = ty * kT + r;
     if (px < W && py < H) {
       const float x = sx[r + 2 * kR][q + 2 * kR], y = sy[r + 2 * kR][q + 2 * kR];
-      D[(long long)py * W + px] += b0 + 2.f * x * b1 + y * b2;
+      D[(long long)py * W + px] += h[0][r][q] + 2.f * x * h[1][r][q] + y * h[2][r][q];
     }
   }
   // loss partial of this block: -lambda_s / (3 P) * sum S (fixed-order reduction)
