@@ -46,6 +46,23 @@ def visibility(ctx, cams):
     return out
 
 
+class _Ready:
+    def __init__(self, p):
+        self.p = p
+
+    def result(self):
+        return self.p
+
+
+class _Pending:
+    def __init__(self, ev, buf, n):
+        self.ev, self.buf, self.n = ev, buf, n
+
+    def result(self):
+        self.ev.synchronize()
+        return self.buf[: self.n].numpy().copy()
+
+
 class PrefetchMLP:
     """The MLP plus feature buffers; `bind(ctx)` points it at a chunk table."""
 
@@ -71,6 +88,29 @@ class PrefetchMLP:
         if self.m is not None:
             dcg.dcg_mlp_destroy(self.m)
             self.m = None
+
+    def score_async(self, ph, cand, chunk_size, stream):
+        """Launch the scoring of `cand` on `stream` (features, MLP, copy of the
+        probabilities to pinned memory); `.result()` of the returned handle
+        waits for that stream only.  One batch (len(cand) <= max_batch)."""
+        import torch
+
+        n = len(cand)
+        if n == 0 or n > self.max_batch:
+            return _Ready(self.score(ph, cand, chunk_size))
+        rows = (n + 63) // 64 * 64
+        if getattr(self, "prob_h", None) is None:
+            self.prob_h = torch.zeros(self.max_batch).pin_memory()
+            self.cand_h = torch.zeros(self.max_batch, dtype=torch.int32).pin_memory()
+        self.cand_h[:n] = torch.from_numpy(np.ascontiguousarray(cand, np.int32))
+        with torch.cuda.stream(stream):
+            self.cand[:n].copy_(self.cand_h[:n], non_blocking=True)
+            dcg.dcg_mlp_features(ph, self.coords, chunk_size, self.cand, n, rows, self.x, stream=stream)
+            dcg.dcg_mlp_forward(self.m, self.x, rows, self.prob, stream=stream)
+            self.prob_h[:n].copy_(self.prob[:n], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return _Pending(ev, self.prob_h, n)
 
     def score(self, ph, cand, chunk_size):
         import torch
@@ -168,6 +208,7 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
     hit_g = miss_g = 0
     dcg.dcg_profile(ctx, True)
     dcg.dcg_profile_read(ctx)
+    side = torch.cuda.Stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for t, cam in enumerate(cams):
@@ -188,21 +229,26 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
                 hit_g += int(counts[c])
                 pending.discard(int(c))
         g, n = dcg.dcg_gather_active(ctx, lst)
-        if render is not None:
-            render(g, n, cam)
-        dcg.dcg_scatter_back(ctx, g, n)
+        # proposals for the coming frames are computed on a side stream while
+        # this frame renders (they depend only on poses and residency)
         prop = []
+        pending_scores = None
         if mode == "mlp":
             cand = dcg.dcg_chunks_near(ctx, cam_centre(cam), radius, only_nonresident=True)
-            p = pm.score(pose_history(cams, t), cand, chunk_size)
-            order = np.argsort(-p, kind="stable")
-            prop = [int(cand[i]) for i in order if p[i] > threshold]
+            pending_scores = pm.score_async(pose_history(cams, t), cand, chunk_size, side)
         elif mode == "cv":
             fut = set()
             for fc in constant_velocity_cams(cams, t):
-                fut.update(int(c) for c in dcg.dcg_cull_chunks(ctx, [fc]))
+                fut.update(int(c) for c in dcg.dcg_cull_chunks(ctx, [fc], stream=side))
             res = dcg.dcg_chunk_info(ctx)["resident"].astype(bool)
             prop = sorted(c for c in fut if not res[c])
+        if render is not None:
+            render(g, n, cam)
+        dcg.dcg_scatter_back(ctx, g, n)
+        if pending_scores is not None:
+            p = pending_scores.result()
+            order = np.argsort(-p, kind="stable")
+            prop = [int(cand[i]) for i in order if p[i] > threshold]
         if prop:
             before = dcg.dcg_chunk_info(ctx)["resident"].astype(bool)
             dcg.dcg_prefetch(ctx, prop)
