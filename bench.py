@@ -113,6 +113,17 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (every rank gets it); identity on one rank."""
+    if world <= 1:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------- our implementation
 def run_ours(args, rank, world):
     import torch
@@ -230,17 +241,15 @@ def run_ours(args, rank, world):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         ms = e0.elapsed_time(e1)
         launches = dcg.dcg_launch_count() - l0
         prof = None
         if profile:
             prof = dcg.dcg_profile_read(ctx)
             dcg.dcg_profile(ctx, False)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, launches, prof
+        return max_over_ranks(ms, world, "cuda"), launches, prof
 
     K, W = args.steps, args.warmup
     # per-phase device times of the direct (uncaptured) calls; the graph replays the same kernels
@@ -508,7 +517,6 @@ def run_corridor(args):
     a different drive with samples the mapper generates from its exact cull)."""
     import torch
 
-    from oracle import mlp as orc_mlp  # seeded initial weights only
     from paper_2511_23030_b300 import build, dcg, prefetch, synth
 
     build.build()
@@ -527,7 +535,7 @@ def run_corridor(args):
     dcg.dcg_chunk_table_update(ctx, torch.from_numpy(np.ascontiguousarray(Ptr.T)).cuda(), Ptr.shape[0])
     X, y, n, pos = prefetch.make_dataset(ctx, cams_tr, s, 1.5 * zfar, max_samples=200_000)
     pm = prefetch.PrefetchMLP(max_batch=4096)
-    dcg.dcg_mlp_set_params(pm.m, orc_mlp.init_params(0))
+    dcg.dcg_mlp_set_params(pm.m, synth.mlp_init_params(0))
     t1 = time.perf_counter()
     losses = prefetch.train(pm, X, y, n, epochs=6, batch=2048, lr=1e-3)
     t_train = time.perf_counter() - t1

@@ -52,19 +52,6 @@ def gelu_grad(x):
     return 0.5 * (1.0 + erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
 
 
-def init_params(seed=0):
-    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases (seeded input)."""
-    rng = np.random.default_rng(seed)
-    d = {}
-    for name, shp in SIZES:
-        if name.startswith("b"):
-            d[name] = np.zeros(shp)
-        else:
-            fan_in = shp[0]
-            d[name] = rng.uniform(-1, 1, shp) / math.sqrt(fan_in)
-    return pack(d).astype(np.float32)
-
-
 def forward(flat, x, bf16_storage=True):
     p = unpack(flat)
     q = bf16 if bf16_storage else (lambda a: np.asarray(a, np.float64))

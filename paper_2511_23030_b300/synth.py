@@ -275,3 +275,23 @@ def pixel_sample(rng: np.random.Generator, W: int, H: int, m: int) -> np.ndarray
     """m distinct pixel coordinates (x, y) as int32 [m, 2]."""
     idx = rng.choice(W * H, size=min(m, W * H), replace=False)
     return np.stack([idx % W, idx // W], 1).astype(np.int32)
+
+
+# Parameter layout of the chunk-prefetch MLP (128 -> 256 -> 256 -> 256 -> 1):
+# W1[128][256] b1 W2[256][256] b2 W3[256][256] b3 w4[256] b4, row-major.
+MLP_SIZES = [("W1", (128, 256)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)),
+             ("b3", (256,)), ("w4", (256,)), ("b4", (1,))]
+
+
+def mlp_init_params(seed: int = 0) -> np.ndarray:
+    """Seeded initial weights of the prefetch MLP (flat float32 in the layout
+    above): uniform in +-1/sqrt(fan_in), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shp in MLP_SIZES:
+        if name.startswith("b"):
+            parts.append(np.zeros(shp))
+        else:
+            parts.append(rng.uniform(-1, 1, shp) / np.sqrt(shp[0]))
+    return np.concatenate([p.reshape(-1) for p in parts]).astype(np.float32)
+

@@ -55,7 +55,7 @@ def test_forward_grads_and_adam_match_reference():
 
     rng = np.random.default_rng(1)
     B = 256
-    P = mlp.init_params(2)
+    P = synth.mlp_init_params(2)
     P[mlp.N_PARAMS - 1] = 0.1
     xb, x64 = _bf16_tensor(rng.normal(0, 1, (B, mlp.N_IN)))
     y = (rng.uniform(size=B) < 0.3).astype(np.float32)
@@ -110,7 +110,7 @@ def test_training_reduces_loss_on_a_learnable_rule():
     yt = torch.from_numpy(y).cuda()
     m = dcg.dcg_mlp_create(B)
     try:
-        dcg.dcg_mlp_set_params(m, mlp.init_params(5))
+        dcg.dcg_mlp_set_params(m, synth.mlp_init_params(5))
         losses = []
         for epoch in range(6):
             tot = torch.zeros(1, device="cuda")

@@ -40,9 +40,8 @@ def test_prefetch_hides_loads_and_never_changes_images():
     try:
         X, y, n, pos = prefetch.make_dataset(ctx_tr, cams_tr, 8.0, 1.5 * ZFAR, max_samples=40_000)
         assert n > 20_000 and 0.05 < pos < 0.95
-        from oracle import mlp as orc_mlp
 
-        dcg.dcg_mlp_set_params(pm.m, orc_mlp.init_params(0))
+        dcg.dcg_mlp_set_params(pm.m, synth.mlp_init_params(0))
         losses = prefetch.train(pm, X, y, n, epochs=5, batch=1024, lr=1e-3)
         assert losses[-1] < 0.7 * losses[0], losses
         dcg.dcg_destroy(ctx_tr)

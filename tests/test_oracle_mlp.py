@@ -6,6 +6,8 @@ import math
 import numpy as np
 import pytest
 
+from paper_2511_23030_b300 import synth
+
 
 def test_gelu_and_bce_against_library_forms():
     from scipy.special import log_expit, ndtr
@@ -29,7 +31,7 @@ def test_mlp_gradient_finite_differences():
     from oracle import mlp
 
     rng = np.random.default_rng(0)
-    P = mlp.init_params(1).astype(np.float64)
+    P = synth.mlp_init_params(1).astype(np.float64)
     P += rng.normal(0, 0.01, P.shape)  # non-zero biases too
     x = rng.normal(0, 1, (8, mlp.N_IN))
     y = (rng.uniform(size=8) < 0.5).astype(np.float64)
