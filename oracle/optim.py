@@ -2,8 +2,8 @@
 
 The paper optimises the Gaussian parameters of the chunks in VRAM against the
 loss of Eq. 2-4 (Sec. III-E "Optimization") and keeps optimizer state per
-Gaussian (Sec. III-F resets "the Gaussian opacity and optimizer states" of
-merged regions after a loop closure).  The optimizer is Adam (Kingma & Ba,
+Gaussian (after a loop closure, Sec. III-F clears that state, and lowers the
+opacity, where separately built parts of the map meet).  The optimizer is Adam (Kingma & Ba,
 "Adam: A Method for Stochastic Optimization", Algorithm 1) with its bias
 correction written in the equivalent form
 
