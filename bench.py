@@ -217,13 +217,56 @@ def run_ours(args, rank, world):
             dcg.dcg_scatter_back(ctx, g, n)
         return n
 
-    def step_e2e():
-        trgb.copy_(trgb_h, non_blocking=True)
-        tdep.copy_(tdep_h, non_blocking=True)
-        step_batched()
-        loss_h.copy_(loss, non_blocking=True)
-        stream.synchronize()
-        return float(loss_h.item())
+    # End to end through the public API: every step copies its targets from
+    # pinned host memory and reads its loss back.  The copy for step t+1 runs on
+    # a copy stream as soon as step t's loss has read the target buffer, i.e.
+    # under step t's backward and step t+1's forward; the loss of each step is
+    # copied to its own pinned slot and read after the run.
+    copy_stream = torch.cuda.Stream()
+    ev_free, ev_ready = torch.cuda.Event(), torch.cuda.Event()
+    loss_slots = {}
+
+    def issue_targets():
+        copy_stream.wait_event(ev_free)
+        with torch.cuda.stream(copy_stream):
+            trgb.copy_(trgb_h, non_blocking=True)
+            tdep.copy_(tdep_h, non_blocking=True)
+            ev_ready.record(copy_stream)
+
+    def step_e2e(t, last):
+        lst = dcg.dcg_cull_chunks(ctx, cams)
+        g, n = dcg.dcg_gather_active(ctx, lst)
+        dcg.dcg_render_fwd(ctx, g, n, cams, rgb, depth)
+        stream.wait_event(ev_ready)
+        loss.zero_()
+        dcg.dcg_loss_l1(ctx, rgb, depth, trgb, tdep, cams, lam, dr, dd, loss)
+        ev_free.record(stream)
+        if not last:
+            issue_targets()
+        dcg.dcg_render_bwd(ctx, dr, dd, grads, dpose)
+        dcg.dcg_scatter_back(ctx, g, n)
+        loss_slots["buf"][t: t + 1].copy_(loss, non_blocking=True)
+        return n
+
+    def timed_e2e(k, w):
+        loss_slots["buf"] = torch.zeros(max(k, w) + 1).pin_memory()
+        for rep, steps in ((0, w), (1, k)):
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            ev_free.record(stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            issue_targets()
+            for t in range(steps):
+                step_e2e(t, t == steps - 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+        losses = loss_slots["buf"][:k].numpy()
+        assert np.isfinite(losses).all() and (losses > 0).all()
+        return max_over_ranks(e0.elapsed_time(e1), world, "cuda")
 
     def timed(fn, k, w, profile=False):
         for _ in range(w):
@@ -264,7 +307,7 @@ def run_ours(args, rank, world):
             ms_p, ms_e = ms_b * K_p / K * 8, ms_b
         else:
             ms_p, launches_p, _ = timed(step_plain, K_p, max(1, W // 2))
-            ms_e, _, _ = timed(step_e2e, K, 2)
+            ms_e = timed_e2e(K, 2)
     clocks = clk.summary()
     dcg.dcg_sync(ctx)
 
