@@ -160,16 +160,27 @@ dcg_status dcg_cull_chunks(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views
  * ones are copied back to the host tier.  Active order: listed chunks in
  * ascending id, each in stored order.  *active_out receives a view of the
  * active buffer (stride = max_active), *n_active_out its size.
+ * When the last call on the active buffer was a dcg_scatter_back of the
+ * buffer itself and the list names the same chunks (all still resident), the
+ * buffer is handed out again without a copy (it already holds their stored
+ * values); otherwise a deferred write-back is completed first.
  * DCG_ERR_BUDGET if the listed chunks alone exceed the budget. */
 dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* chunk_list, int32_t n_chunks,
                              dcg_gaussians* active_out, int64_t* n_active_out, void* stream);
 
 /* Inverse of the last dcg_gather_active: copy `active` (dev, planar, n must
  * equal the gathered count) back into the resident chunks and mark them
- * dirty, so that an eviction writes them to the host tier. */
+ * dirty, so that an eviction writes them to the host tier.  When `active` is
+ * the library's own active buffer the copy is deferred (write-back): from
+ * then on the buffer is the stored value of the gathered chunks, and writes
+ * to it reach the map, until the library copies it into the chunk pages, which
+ * it does before anything else reads, moves or replaces them (a gather of a
+ * different list, dcg_flush, dcg_chunk_table_update, dcg_loop_closure).
+ * A caller buffer is copied at once (the moments from the active buffer). */
 dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n, void* stream);
 
-/* Copy every resident dirty chunk back to the host tier and wait. */
+/* Complete a deferred write-back of the active buffer, copy every resident
+ * dirty chunk back to the host tier and wait. */
 dcg_status dcg_flush(dcg_ctx* ctx, void* stream);
 
 /* Asynchronous load of proposed chunks (host, chunk indices in the order to load) on the copy

@@ -102,6 +102,12 @@ struct dcg_ctx {
   int64_t n_active = 0;
   std::vector<uint64_t> active_keys;
   bool active_valid = false;
+  // The active buffer as a write-back copy of the listed chunks: active_fresh
+  // means a scatter_back of the buffer itself made it the chunks' stored value
+  // (a gather of the same list hands it out again), active_dirty that the copy
+  // into the device pages is still deferred.
+  bool active_fresh = false;
+  bool active_dirty = false;
   long long* d_desc = nullptr;
   long long* h_desc = nullptr;
   int64_t max_desc = 0;
@@ -220,6 +226,8 @@ int64_t pages_for(dcg_ctx* ctx, int64_t count) { return (count + ctx->page_g - 1
 
 dcg_status evict_chunk(dcg_ctx* ctx, Chunk& ch) {
   if (!ch.resident) return DCG_OK;
+  if (ctx->active_dirty && std::find(ctx->active_keys.begin(), ctx->active_keys.end(), ch.key) != ctx->active_keys.end())
+    return fail(ctx, DCG_ERR_STATE, "eviction of an active chunk before its write-back");
   if (ch.dirty) {
     for (size_t p = 0; p < ch.dev_pages.size(); ++p) {
       const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - (int64_t)p * ctx->page_g);
@@ -319,6 +327,19 @@ dcg_status check_cams(dcg_ctx* ctx, const dcg_camera* cams, int V) {
 }  // namespace
 
 extern "C" {
+
+// Copies a deferred scatter_back of the active buffer into the device pages
+// (on stream s, before anything reads, evicts or rewrites those pages).
+dcg_status writeback_active(dcg_ctx* ctx, cudaStream_t s) {
+  if (!ctx->active_dirty) return DCG_OK;
+  ctx->active_dirty = false;
+  if (!ctx->active_valid) return DCG_OK;
+  launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->Fs, ctx->d_desc, ctx->n_desc, ctx->d_active,
+                   ctx->cfg.max_active, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev_compute, s));
+  return DCG_OK;
+}
 
 void dcg_config_default(dcg_config* c) {
   std::memset(c, 0, sizeof(*c));
@@ -511,6 +532,11 @@ dcg_status dcg_chunk_table_update(dcg_ctx* ctx, const float* params, int64_t str
   if (n == 0) return DCG_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const int F = ctx->F;
+  {
+    dcg_status wb = writeback_active(ctx, s);
+    if (wb != DCG_OK) return wb;
+    ctx->active_fresh = false;  // chunks may grow: the next gather copies again
+  }
   if (n > ctx->keys_cap) {
     cudaFree(ctx->d_keys);
     if (ctx->h_keys) cudaFreeHost(ctx->h_keys);
@@ -658,6 +684,24 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
   if (total > ctx->cfg.device_budget || total > ctx->cfg.max_active)
     return fail(ctx, DCG_ERR_BUDGET, "visible chunks exceed the device budget");
   if (ctx->fault == 2) return fail(ctx, DCG_ERR_BUDGET, "injected budget failure");
+  // the active buffer already holds exactly these chunks: hand it out again
+  bool reuse = ctx->active_valid && ctx->active_fresh && (size_t)n_list == ctx->active_keys.size();
+  for (int k = 0; reuse && k < n_list; ++k)
+    reuse = ctx->chunks[list[k]].key == ctx->active_keys[(size_t)k] && ctx->chunks[list[k]].resident;
+  if (reuse) {
+    ctx->step++;
+    for (int k = 0; k < n_list; ++k) ctx->chunks[list[k]].last_access = ctx->step;
+    active_out->data = ctx->d_active;
+    active_out->stride = ctx->cfg.max_active;
+    active_out->sh_degree = ctx->cfg.sh_degree;
+    active_out->pad = 0;
+    *n_active_out = ctx->n_active;
+    return DCG_OK;
+  }
+  {
+    dcg_status wb = writeback_active(ctx, s);
+    if (wb != DCG_OK) return wb;
+  }
   ctx->step++;
   // LRU eviction (Sec. III-E): oldest first, ties by id, the fewest chunks that make room
   int64_t deficit_g = ctx->resident_g + incoming - ctx->cfg.device_budget;
@@ -737,6 +781,7 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
   CK(cudaEventRecord(ctx->ev_compute, s));
   ctx->n_active = total;
   ctx->active_valid = true;
+  ctx->active_fresh = false;  // only a scatter_back of this buffer makes it reusable
   active_out->data = ctx->d_active;
   active_out->stride = ctx->cfg.max_active;
   active_out->sh_degree = ctx->cfg.sh_degree;
@@ -834,9 +879,12 @@ dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n
   }
   hook(ctx)(PH_SCATTER, true, s);
   if (active->data == ctx->d_active && active->stride == ctx->cfg.max_active) {
-    launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->Fs, ctx->d_desc, ctx->n_desc, ctx->d_active,
-                     ctx->cfg.max_active, s);
+    // the active buffer itself: the copy to the pages is deferred (write-back)
+    ctx->active_dirty = true;
+    ctx->active_fresh = true;
   } else {  // parameters from the caller's buffer, moments from the active buffer
+    ctx->active_dirty = false;
+    ctx->active_fresh = false;
     launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->F, ctx->d_desc, ctx->n_desc, active->data,
                      active->stride, s);
     if (ctx->Fs > ctx->F)
@@ -853,6 +901,10 @@ dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n
 dcg_status dcg_flush(dcg_ctx* ctx, void* stream) {
   if (!ctx) return DCG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  {
+    dcg_status wb = writeback_active(ctx, s);
+    if (wb != DCG_OK) return wb;
+  }
   CK(cudaEventRecord(ctx->ev_compute, s));
   CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_compute, 0));
   for (Chunk& ch : ctx->chunks) {
@@ -1028,7 +1080,12 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   std::vector<int32_t> list((size_t)nl);
   if (nl) CK(cudaMemcpy(list.data(), ctx->d_list, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost));
   if (nl == 0) return DCG_OK;
-  // 2. batch-load the union (DCG_ERR_BUDGET if it does not fit)
+  // 2. batch-load the union (DCG_ERR_BUDGET if it does not fit); a deferred
+  // write-back goes to the pages first, as the transform below works in place
+  {
+    dcg_status wb = writeback_active(ctx, s);
+    if (wb != DCG_OK) return wb;
+  }
   dcg_gaussians g{};
   int64_t n = 0;
   dcg_status gs = dcg_gather_active(ctx, list.data(), nl, &g, &n, stream);
@@ -1242,6 +1299,8 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
     }
   }
   ctx->active_valid = false;  // the caller gathers again
+  ctx->active_fresh = false;
+  ctx->active_dirty = false;
   return DCG_OK;
 }
 

@@ -193,3 +193,55 @@ def test_budget_error_when_visible_exceeds_budget():
         assert e.value.status == 4
     finally:
         dcg.dcg_destroy(ctx)
+
+
+def test_deferred_write_back_of_the_active_set(orc):
+    """scatter_back of the library's own active buffer defers the copy into the
+    chunk pages: the same list is handed out again as is, and the deferred copy
+    lands before an eviction or a flush saves the chunks."""
+    probe, _ = _window_table()
+    info = dcg.dcg_chunk_info(probe)
+    dcg.dcg_destroy(probe)
+    counts = info["counts"]
+    A, B = np.arange(0, 10, dtype=np.int32), np.arange(30, 46, dtype=np.int32)
+    assert counts[B].sum() >= counts[A].sum()
+    budget = int(counts[B].sum()) + 1  # gathering B evicts every other chunk
+    ctx, sc = _window_table(budget=budget, page=256)
+    try:
+        P = sc["params"]
+        F = P.shape[1]
+        _, keys, _ = orc.chunk_keys(P[:, :3], sc["chunk_size"])
+
+        def rows(lst):
+            return np.concatenate([P[keys == info["keys"][c]] for c in lst])
+
+        g, n = dcg.dcg_gather_active(ctx, A)
+        dcg.active_tensor(g, n, F).mul_(3.0)
+        g, n = dcg.dcg_gather_active(ctx, A)  # no scatter_back in between: copied again
+        assert np.array_equal(_read_active(g, n, F), rows(A))
+        dcg.active_tensor(g, n, F).mul_(2.0)
+        dcg.dcg_scatter_back(ctx, g, n)
+        before = dcg.dcg_tier_stats(ctx)
+        g2, n2 = dcg.dcg_gather_active(ctx, A)  # handed out as is
+        assert (g2.data, n2) == (g.data, n) and dcg.dcg_tier_stats(ctx) == before
+        want = rows(A) * np.float32(2.0)
+        assert np.array_equal(_read_active(g, n, F), want)
+        dcg.active_tensor(g, n, F).add_(1.0)
+        dcg.dcg_scatter_back(ctx, g, n)
+        want = want + np.float32(1.0)
+        g, n = dcg.dcg_gather_active(ctx, B)  # write-back, then A is evicted to the host tier
+        assert not dcg.dcg_chunk_info(ctx)["resident"][A].any()
+        assert np.array_equal(_read_active(g, n, F), rows(B))
+        g, n = dcg.dcg_gather_active(ctx, A)  # reloaded from the host tier
+        assert np.array_equal(_read_active(g, n, F), want)
+        dcg.active_tensor(g, n, F).add_(1.0)
+        dcg.dcg_scatter_back(ctx, g, n)
+        want = want + np.float32(1.0)
+        dcg.dcg_flush(ctx)
+        off = 0
+        for c in A:
+            cnt = int(counts[c])
+            assert np.array_equal(dcg.dcg_chunk_read(ctx, int(c), cnt, F).T, want[off: off + cnt])
+            off += cnt
+    finally:
+        dcg.dcg_destroy(ctx)
