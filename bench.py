@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="batched timing only (no plain/e2e/CPU legs), for profilers")
     ap.add_argument("--workload", default="window", choices=["window", "corridor"])
     ap.add_argument("--bwd", default="warp", choices=["warp", "slots"], help="backward gradient accumulation")
-    ap.add_argument("--length", type=float, default=2000.0, help="corridor: metres of road (1 m per frame)")
+    ap.add_argument("--length", type=float, default=5000.0, help="corridor: metres of road (1 m per frame)")
     ap.add_argument("--per-m", type=int, default=8000, help="corridor: Gaussians per metre (40M per 5 km)")
     ap.add_argument("--cpu-pixels", type=int, default=48, help="oracle sample: pixels per sampled view")
     return ap.parse_args()
@@ -554,7 +554,8 @@ def run_reference(args, rank, world):
 
 def run_corridor(args):
     """Out-of-core mapping along a driving corridor (1241x376 views, 8 m chunks,
-    device budget 15 % of the map, pinned host tier), one keyframe per metre:
+    5 km and 40 M Gaussians by default, device budget 15 % of the map capped
+    at 6 M Gaussians, pinned host tier), one keyframe per metre:
     cull, gather, render fwd, L1 loss, bwd, scatter, then a prefetch proposal:
     none, constant-velocity extrapolation, or the learned MLP (trained here on
     a different drive with samples the mapper generates from its exact cull)."""
@@ -591,7 +592,7 @@ def run_corridor(args):
     for c in cams:
         c.zfar = zfar
     N, F = P.shape
-    budget = int(0.15 * N)
+    budget = min(6_000_000, int(0.15 * N))  # device active set: 6 M Gaussians on the 5 km drive
     Pt = torch.from_numpy(np.ascontiguousarray(P.T))
     del P
     t_gen = time.perf_counter() - t0
@@ -623,6 +624,7 @@ def run_corridor(args):
             dcg.dcg_loss_l1(ctx, rgb, depth, trgb, tdep, [cam], 0.1, dr, dd, loss)
             dcg.dcg_render_bwd(ctx, dr, dd, grads, None)
 
+        out["config"]["chunks"] = dcg.dcg_chunk_count(ctx)
         r = prefetch.run_corridor(ctx, cams, mode, s, 1.5 * zfar, pm=pm, render=render)
         dcg.dcg_sync(ctx)
         r["ms_per_step"] = round(r["ms"] / r["steps"], 4)
