@@ -79,12 +79,12 @@ typedef struct {
   int64_t host_capacity;   /* Gaussians the pinned host tier (stand-in for disk) can hold */
   int32_t max_chunks;      /* chunk table capacity */
   int32_t max_views;       /* views per render call (<= 16) */
-  int64_t max_active;      /* Gaussians per render call / active buffer */
+  int64_t max_active;      /* Gaussians per render call / active buffer; max_views max_active <= 2^28 */
   int64_t max_pixels;      /* total pixels over the views of one render call */
   int64_t max_instances;   /* (view, tile, Gaussian) instances per render call */
   int32_t tile_w, tile_h;  /* default blend tile: 16x16, 32x16 or 32x32 */
   int32_t stage;           /* default Gaussians staged per block batch: 64..256; 32 selects the
-                              warp-per-block blend kernels */
+                              warp-per-block blend kernels, 16 the half-warp-per-half-block ones */
   float dfar;              /* distance filter of the chunk cull, metres */
   int32_t page_gaussians;  /* Gaussians per device/host page (power of two) */
   int32_t flags;           /* bit 0: backward blend accumulates per-lane shared slots instead of
@@ -365,8 +365,10 @@ dcg_status dcg_loss(dcg_ctx* ctx, const float* rgb, const float* depth, const fl
  * 32x32 pixels and 64..256 Gaussians staged per block batch (one block per
  * tile, warps of a tile synchronised per batch); stage 32 selects the
  * warp-per-block kernels (every warp takes one 8-column block of a tile from
- * a device queue on its own, no block barriers).  Results do not depend on
- * it (gradients up to FP32 atomic order). */
+ * a device queue on its own, no block barriers), stage 16 the half-warp
+ * kernels (as 32, but the two half-warps walk separate lists for the two
+ * 4-column halves of the block).  Results do not depend on it (gradients up
+ * to FP32 atomic order). */
 dcg_status dcg_set_launch(dcg_ctx* ctx, int32_t tile_w, int32_t tile_h, int32_t stage);
 
 /* Batched keyframe window as one CUDA graph.  dcg_window_capture records,
@@ -392,8 +394,8 @@ int64_t dcg_state_generation(const dcg_render_state* st);
 /* Autotuner of the blend launch shape: times render_fwd + render_bwd of this
  * call (default state, `reps` repetitions after one warm-up, CUDA events on
  * `stream`) for every tile {16x16, 32x16, 32x32} x stage
- * {64, 96, 128, 192, 256, 32 (warp-per-block)}, keeps the fastest as the
- * context's launch shape and returns it.  ms_out (18 floats, tile-major in
+ * {64, 96, 128, 192, 256, 32 (warp-per-block), 16 (half-warp)}, keeps the
+ * fastest as the context's launch shape and returns it.  ms_out (21 floats, tile-major in
  * that order, may be NULL) receives the mean time of each.  rgb/depth/grads
  * are overwritten; dL_drgb and dL_ddepth are the seeds used for the
  * backward.  Synchronous. */
@@ -415,14 +417,15 @@ dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, int64_t* n_ble
 
 /* Copies of the state's per-tile sorted lists for checks (host outputs; any
  * may be NULL): ranges [n_tiles, 2] (start, end) into ids, ids [n_instances]
- * (pair index v n + i), masks [n_instances] (bit b: the instance's Gaussian
- * may reach warp block b of the tile; blocks are 8 pixels wide and
- * tile_w tile_h / 64 high, numbered row-major), per (view, Gaussian) FP32
+ * (pair index v n + i), masks [n_instances] (bit 2 b + h: the instance's
+ * Gaussian may reach the left (h = 0) or right (h = 1) 4-pixel-wide half of
+ * warp block b of the tile; blocks are 8 pixels wide and tile_w tile_h / 64
+ * high, numbered row-major), per (view, Gaussian) FP32
  * depth [n_views * n], 3-sigma tile rectangle [n_views * n, 4] (x0, y0, x1,
  * y1 inclusive; x1 < x0 if culled), per-pixel final transmittance and
  * contributor count.  A tile lists the Gaussians whose rectangle covers it
  * and whose support ellipse reaches its pixel rectangle.  Synchronises. */
-dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, uint8_t* masks, float* depth,
+dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, uint16_t* masks, float* depth,
                           int32_t* rect, float* T_final, int32_t* n_contrib, void* stream);
 
 /* ---------------------------------------------------------------- learned chunk prefetch

@@ -309,10 +309,10 @@ void state_free(dcg_render_state* st) {
 }
 
 bool valid_tile(int tw, int th) { return (tw == 16 && th == 16) || (tw == 32 && th == 16) || (tw == 32 && th == 32); }
-// instance keys hold the global tile id in 24 bits
-constexpr int kMaxTiles = 1 << 24;
+// instance keys hold the global tile id in 20 bits (and the pair index in 28)
+constexpr int kMaxTiles = 1 << 20;
 
-bool valid_stage(int s) { return s == 32 || s == 64 || s == 96 || s == 128 || s == 192 || s == 256; }
+bool valid_stage(int s) { return s == 16 || s == 32 || s == 64 || s == 96 || s == 128 || s == 192 || s == 256; }
 
 dcg_status check_cams(dcg_ctx* ctx, const dcg_camera* cams, int V) {
   if (!cams || V <= 0 || V > ctx->cfg.max_views || V > kMaxViewsApi) return fail(ctx, DCG_ERR_ARG, "bad views");
@@ -372,7 +372,7 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
       c.max_chunks <= 0 || c.max_views <= 0 || c.max_views > kMaxViewsApi || c.max_active <= 0 || c.max_pixels <= 0 ||
       c.max_instances <= 0 || c.max_instances >= (1ll << 32) || c.page_gaussians <= 0 ||
       (c.page_gaussians & (c.page_gaussians - 1)) != 0 || !valid_tile(c.tile_w, c.tile_h) || !valid_stage(c.stage) ||
-      (int64_t)c.max_views * c.max_active >= (1ll << 32) || (c.with_moments != 0 && c.with_moments != 1))
+      (int64_t)c.max_views * c.max_active > (1ll << 28) || (c.with_moments != 0 && c.with_moments != 1))
     bad = DCG_ERR_ARG;
   if (bad != DCG_OK) {
     delete ctx;
@@ -1704,8 +1704,9 @@ dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const d
   if (!ctx || reps <= 0) return DCG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   static const int tiles[3][2] = {{16, 16}, {32, 16}, {32, 32}};
-  // stage code 32 selects the warp-per-block kernels (no staging segment)
-  static const int stages[6] = {64, 96, 128, 192, 256, 32};
+  // stage codes 32 and 16 select the warp-per-block and half-warp kernels (no staging segment)
+  constexpr int NS = 7;
+  static const int stages[NS] = {64, 96, 128, 192, 256, 32, 16};
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
@@ -1715,7 +1716,7 @@ dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const d
   ctx->prof_on = false;
   dcg_status rc = DCG_OK;
   for (int t = 0; t < 3 && rc == DCG_OK; ++t)
-    for (int k = 0; k < 6 && rc == DCG_OK; ++k) {
+    for (int k = 0; k < NS && rc == DCG_OK; ++k) {
       dcg_set_launch(ctx, tiles[t][0], tiles[t][1], stages[k]);
       float ms = 0.f;
       for (int r = 0; r <= reps && rc == DCG_OK; ++r) {
@@ -1728,7 +1729,7 @@ dcg_status dcg_autotune(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const d
       cudaEventSynchronize(b);
       cudaEventElapsedTime(&ms, a, b);
       ms /= reps;
-      if (ms_out) ms_out[6 * t + k] = ms;
+      if (ms_out) ms_out[NS * t + k] = ms;
       if (ms < best) {
         best = ms;
         bt = t;
@@ -1801,7 +1802,7 @@ dcg_status dcg_state_evals(dcg_render_state* st, int64_t* n_eval, int64_t* n_ble
   return DCG_OK;
 }
 
-dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, uint8_t* masks, float* depth,
+dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids, uint16_t* masks, float* depth,
                           int32_t* rect, float* T_final, int32_t* n_contrib, void* stream) {
   if (!st || !st->valid) return DCG_ERR_STATE;
   dcg_ctx* ctx = st->ctx;
@@ -1826,9 +1827,9 @@ dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids,
   if (n_contrib) CK(cudaMemcpyAsync(n_contrib, st->n_contrib, 4 * (size_t)st->n_pix, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (ids)
-    for (int64_t k = 0; k < K; ++k) ids[k] = (uint32_t)(inst[(size_t)k] & 0xffffffffu);
+    for (int64_t k = 0; k < K; ++k) ids[k] = (uint32_t)(inst[(size_t)k] & ((1ull << 28) - 1));
   if (masks)
-    for (int64_t k = 0; k < K; ++k) masks[k] = (uint8_t)(inst[(size_t)k] >> 56);
+    for (int64_t k = 0; k < K; ++k) masks[k] = (uint16_t)(inst[(size_t)k] >> 48);
   if (rect)
     for (int64_t k = 0; k < pairs; ++k) {
       rect[4 * k + 0] = r[(size_t)k].x;

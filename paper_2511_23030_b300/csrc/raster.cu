@@ -223,15 +223,21 @@ __device__ __forceinline__ bool band_extent(const SupportEllipse& e, float Y0, f
   return true;
 }
 
-// Instance keys: bits [0, 32) pair index, [32, 56) global tile, [56, 64) the
-// warp blocks of the tile that the Gaussian reaches (bit b: the 8 x WY pixel
-// block b of TileLayout, row-major).  Only the tile bits are sorted.
-constexpr int kMaskShift = 56;
-constexpr unsigned kTileMask = (1u << 24) - 1u;
+// Instance keys: bits [0, 28) pair index, [28, 48) global tile, [48, 64) the
+// half blocks of the tile that the Gaussian reaches (bit 2 b + h: the left
+// (h = 0) or right (h = 1) 4 x WY half of the 8 x WY warp block b of
+// TileLayout, blocks row-major).  Only the tile bits are sorted.
+constexpr int kPairBits = 28;
+constexpr u64 kPairMask = (1ull << kPairBits) - 1ull;
+constexpr int kTileShift = 28;
+constexpr unsigned kTileMask = (1u << 20) - 1u;
+constexpr int kMaskShift = 48;
 // Rectangles of more tiles than this are emitted whole (every tile).
 constexpr int kTightMax = 1024;
 
-__device__ __forceinline__ bool block_bit(u64 key, int b) { return ((key >> (kMaskShift + b)) & 1ull) != 0ull; }
+__device__ __forceinline__ unsigned half_bits(u64 key, int b) { return (unsigned)(key >> (kMaskShift + 2 * b)) & 3u; }
+__device__ __forceinline__ bool block_bit(u64 key, int b) { return half_bits(key, b) != 0u; }
+__device__ __forceinline__ unsigned pair_of_inst(u64 key) { return (unsigned)(key & kPairMask); }
 
 // Tiles [*j0, *j1] (offsets from the rectangle's first column) of tile row
 // ty of rectangle r that the ellipse reaches; false if none.  Whole
@@ -282,16 +288,22 @@ __device__ __forceinline__ unsigned block_bands(const SupportEllipse& e, float v
   return bands;
 }
 
-// Warp blocks (8 columns each, wpr per row) of one tile of that row that the
-// ellipse reaches; ul is the centre relative to the tile's left edge.
+// Half blocks (4 columns each, 2 wpr per row) of one tile of that row that
+// the ellipse reaches; ul is the centre relative to the tile's left edge.
+// Bit 2 (rb wpr + c / 2) + (c & 1) for half column c of band rb: the half
+// columns [ceil((ul + bl - 3) / 4), floor((ul + br) / 4)] of each band (the
+// extents carry 1e-3 px of slack, more than the rounding here).
 __device__ __forceinline__ unsigned tile_block_mask(unsigned bands, const float* bl, const float* br, float ul,
                                                     int wpr, int nbr) {
   unsigned mask = 0;
+  const float cmax = (float)(2 * wpr - 1);
   for (int rb = 0; rb < nbr; ++rb) {
     if (!((bands >> rb) & 1u)) continue;
-    for (int c = 0; c < wpr; ++c) {
-      const float x0 = __fsub_rn((float)(8 * c), ul);
-      if (bl[rb] <= __fadd_rn(x0, 7.f) && br[rb] >= x0) mask |= 1u << (rb * wpr + c);
+    const float c0 = fmaxf(ceilf((ul + bl[rb] - 3.f) * 0.25f), 0.f);
+    const float c1 = fminf(floorf((ul + br[rb]) * 0.25f), cmax);
+    if (c0 <= c1) {
+      const unsigned run = (2u << (int)c1) - (1u << (int)c0);  // bits c0..c1
+      mask |= run << (2 * rb * wpr);
     }
   }
   return mask;
@@ -484,7 +496,7 @@ struct InstEmit {
       for (int j = j0; j <= j1; ++j, ++o) {
         const float ul = df_sub_round(r0.x, r0.z, (float)((r.x + j) * tw));
         const u64 m = tile_block_mask(bands, bl, br, ul, wpr, nbr);
-        if (o < cap) inst[o] = (m << kMaskShift) | ((row + (u64)j) << 32) | vi;
+        if (o < cap) inst[o] = (m << kMaskShift) | ((row + (u64)j) << kTileShift) | vi;
       }
     }
   }
@@ -512,9 +524,9 @@ __global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
 __global__ void k_ranges(const u64* __restrict__ inst, const u64* n_ptr, uint2* __restrict__ ranges) {
   const u64 K = *n_ptr;
   for (u64 k = blockIdx.x * (u64)blockDim.x + threadIdx.x; k < K; k += (u64)gridDim.x * blockDim.x) {
-    const unsigned t = (unsigned)(inst[k] >> 32) & kTileMask;
-    if (k == 0 || ((unsigned)(inst[k - 1] >> 32) & kTileMask) != t) ranges[t].x = (unsigned)k;
-    if (k + 1 == K || ((unsigned)(inst[k + 1] >> 32) & kTileMask) != t) ranges[t].y = (unsigned)(k + 1);
+    const unsigned t = (unsigned)(inst[k] >> kTileShift) & kTileMask;
+    if (k == 0 || ((unsigned)(inst[k - 1] >> kTileShift) & kTileMask) != t) ranges[t].x = (unsigned)k;
+    if (k + 1 == K || ((unsigned)(inst[k + 1] >> kTileShift) & kTileMask) != t) ranges[t].y = (unsigned)(k + 1);
   }
 }
 
@@ -593,7 +605,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
       unsigned vi = 0;
       if (idx < rg.y) {
         const u64 key = inst[idx];
-        vi = (unsigned)key;
+        vi = pair_of_inst(key);
         pass = block_bit(key, w);
       }
       const unsigned m = __ballot_sync(0xffffffffu, pass);
@@ -675,15 +687,16 @@ __global__ void __launch_bounds__(256) k_blend_fwd(RasterArgs a, const u64* __re
 // Sum over the 32 lanes of N values with a transposed butterfly: each step
 // halves the number of values a lane carries, so N = 10 costs 12 shuffles
 // instead of 50.  Afterwards lane l holds the total of component *comp; *has
-// is true for exactly one lane per component.
-template <int N>
+// is true for exactly one lane per component.  FIRST = 8 sums within each
+// half-warp separately (lanes 0-15 and 16-31, 11 shuffles for N = 10).
+template <int N, int FIRST = 16>
 __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int* comp, bool* has) {
   const unsigned lane = threadIdx.x & 31u;
   int base = 0, cnt = N;
   int n = N;
   unsigned shared_bits = 0;  // lane bits over which the final value is replicated
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
+  for (int o = FIRST; o >= 1; o >>= 1) {
     const bool bit = (lane & (unsigned)o) != 0u;
     if (n > 1) {
       const int half = (n + 1) / 2;
@@ -794,7 +807,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
         unsigned vi = 0;
         if (rel >= sbeg) {
           const u64 key = inst[rg.x + rel];
-          vi = (unsigned)key;
+          vi = pair_of_inst(key);
           pass = block_bit(key, w);
         }
         const unsigned m = __ballot_sync(0xffffffffu, pass);
@@ -877,7 +890,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
         const bool n1 = g1.x != 0.f || g1.y != 0.f || g1.z != 0.f || g1.w != 0.f;
         const bool n2 = q[8] != 0.f || q[9] != 0.f;
         if (n0 || n1 || n2) {
-          float4* gp = a.grad2d + 3ull * (unsigned)inst[rg.x + sbeg + j];
+          float4* gp = a.grad2d + 3ull * pair_of_inst(inst[rg.x + sbeg + j]);
           if (n0) atomicAdd(gp + 0, g0);
           if (n1) atomicAdd(gp + 1, g1);
           if (n2) atomicAdd(reinterpret_cast<float2*>(gp + 2), make_float2(q[8], q[9]));
@@ -948,7 +961,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd_q(RasterArgs a, const u64* __
       unsigned vi = 0;
       if (idx < rg.y) {
         const u64 key = inst[idx];
-        vi = (unsigned)key;
+        vi = pair_of_inst(key);
         pass = block_bit(key, wb);
       }
       const unsigned m = __ballot_sync(0xffffffffu, pass);
@@ -1086,7 +1099,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
       unsigned vi = 0;
       if (rel >= 0) {
         const u64 key = inst[rg.x + rel];
-        vi = (unsigned)key;
+        vi = pair_of_inst(key);
         pass = block_bit(key, wb);
       }
       const unsigned m = __ballot_sync(0xffffffffu, pass);
@@ -1157,6 +1170,334 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
           bool has;
           const float tot = warp_sum_transpose<10>(acc, &comp, &has);
           if (has && tot != 0.f) atomicAdd(g2 + 12ull * s_vi[w][j] + comp, tot);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// ============================================================================
+// Half-warp blends.  As the warp-per-block kernels, but the two halves of a
+// warp own the two 4 x WY halves of its 8 x WY block (lane l: half l / 16,
+// column l % 4, row (l / 4) % 4) and walk separate lists: an instance enters
+// the list of each half whose pixels its support ellipse may reach (two bits
+// of the instance mask).  A small Gaussian that reaches one half therefore
+// occupies 16 lanes instead of 32, and the other half takes the next
+// Gaussian of its own list in the same step.  A half whose pixels are all
+// done (forward) or behind all of its pixels' last contributors (backward)
+// takes no more instances.  The backward reduces each half's Gaussian over
+// its 16 lanes (one transposed butterfly serves both halves).  Per-pixel
+// arithmetic and order are those of the other kernels, so images are
+// identical.
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __restrict__ inst,
+                                                     float* __restrict__ rgb, float* __restrict__ dout) {
+  using L = TileLayout<TW, TH>;
+  constexpr int PPT = L::PPT;
+  // per warp and half: the compacted list of this batch
+  __shared__ float2 s_xy[8][2][32];
+  __shared__ float4 s_con[8][2][32];
+  __shared__ float4 s_col[8][2][32];
+  __shared__ unsigned s_rel[8][2][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4;
+  const unsigned lt = lanemask_lt();
+  const unsigned n_items = 8u * (unsigned)a.n_tiles;
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(&a.counters->tile_queue, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    const unsigned gt = item >> 3, wb = item & 7u;
+    const int bx0 = (int)(wb % L::WPR) * 8, by0 = (int)(wb / L::WPR) * L::WY;
+    const int lx = bx0 + 4 * h + (lane & 3);
+    const int ly = by0 + ((lane >> 2) & 3);
+    const int v = view_of_tile(a.cams, a.V, gt);
+    const DevCam& c = a.cams[v];
+    const int W = c.W, H = c.H;
+    const int local = (int)gt - c.tile_base;
+    const int ty = local / c.ntx, tx = local - ty * c.ntx;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const float x0f = (float)x0, y0f = (float)y0;
+    float T[PPT], Tf[PPT], Cr[PPT], Cg[PPT], Cb[PPT], Dz[PPT];
+    uint32_t last[PPT];
+    unsigned ev = 0, nb = 0;
+    const int px = x0 + lx;
+    int alive = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int py = y0 + ly + 4 * k;
+      T[k] = (px < W && py < H) ? 1.f : 0.f;
+      Tf[k] = T[k];
+      Cr[k] = Cg[k] = Cb[k] = Dz[k] = 0.f;
+      last[k] = 0;
+      alive |= T[k] > 0.f;
+    }
+    const uint2 rg = a.ranges[gt];
+    for (unsigned b0 = rg.x; b0 < rg.y; b0 += 32) {
+      const unsigned am = __ballot_sync(0xffffffffu, alive);
+      if (am == 0u) break;
+      const unsigned idx = b0 + lane;
+      unsigned hb = 0, vi = 0;
+      if (idx < rg.y) {
+        const u64 key = inst[idx];
+        vi = pair_of_inst(key);
+        hb = half_bits(key, wb);
+        if ((am & 0xffffu) == 0u) hb &= 2u;
+        if ((am >> 16) == 0u) hb &= 1u;
+      }
+      const unsigned mL = __ballot_sync(0xffffffffu, hb & 1u), mR = __ballot_sync(0xffffffffu, hb & 2u);
+      if (hb) {
+        const float4 r0 = a.rec[3ull * vi + 0];
+        const float2 xy = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+        const float4 cn = a.rec[3ull * vi + 1], cl = a.rec[3ull * vi + 2];
+        const unsigned rel = idx - rg.x;
+        if (hb & 1u) {
+          const int sl = __popc(mL & lt);
+          s_xy[w][0][sl] = xy;
+          s_con[w][0][sl] = cn;
+          s_col[w][0][sl] = cl;
+          s_rel[w][0][sl] = rel;
+        }
+        if (hb & 2u) {
+          const int sl = __popc(mR & lt);
+          s_xy[w][1][sl] = xy;
+          s_con[w][1][sl] = cn;
+          s_col[w][1][sl] = cl;
+          s_rel[w][1][sl] = rel;
+        }
+      }
+      // the shorter list is padded to the longer one with transparent
+      // entries (opacity 0: alpha 0 < 1/255), so both halves step together
+      // without a branch
+      const int cL = __popc(mL), cR = __popc(mR), cmax = max(cL, cR);
+      const int cmine = h ? cR : cL;
+      if (lane >= cL && lane < cmax) {
+        s_xy[w][0][lane] = make_float2(0.f, 0.f);
+        s_con[w][0][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      if (lane >= cR && lane < cmax) {
+        s_xy[w][1][lane] = make_float2(0.f, 0.f);
+        s_con[w][1][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncwarp();
+      for (int j = 0; j < cmax; ++j) {
+        const unsigned real = j < cmine ? 1u : 0u;
+        const float2 xy = s_xy[w][h][j];
+        const float4 cq = s_con[w][h][j];
+        const float dx = __fsub_rn((float)lx, xy.x);
+        const float sx = __fmul_rn(dx, __fmul_rn(cq.x, dx));
+        const float bx = __fmul_rn(cq.y, dx);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (T[k] > 0.f) {
+            ev += real;
+            const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
+            const float p = blend_power(sx, bx, cq.z, dy);
+            if (p >= kPMin) {
+              const float al = fminf(kAlphaMax, __fmul_rn(cq.w, ex2_approx(p)));
+              if (al >= kAlphaMin) {
+                const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, al));
+                if (Tn < kTMin) {
+                  Tf[k] = T[k];
+                  T[k] = 0.f;
+                } else {
+                  const float4 cl = s_col[w][h][j];
+                  const float wgt = al * T[k];
+                  Cr[k] += wgt * cl.x;
+                  Cg[k] += wgt * cl.y;
+                  Cb[k] += wgt * cl.z;
+                  Dz[k] += wgt * cl.w;
+                  T[k] = Tn;
+                  last[k] = s_rel[w][h][j] + 1;
+                  ++nb;
+                }
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+      alive = 0;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) alive |= T[k] > 0.f;
+    }
+    {
+      const unsigned wev = __reduce_add_sync(0xffffffffu, ev), wnb = __reduce_add_sync(0xffffffffu, nb);
+      if (lane == 0 && wev) atomicAdd(&a.counters->n_eval, (unsigned long long)wev);
+      if (lane == 0 && wnb) atomicAdd(&a.counters->n_blend, (unsigned long long)wnb);
+    }
+    const long long P = (long long)W * H;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int py = y0 + ly + 4 * k;
+      if (px < W && py < H) {
+        const long long pix = (long long)py * W + px;
+        rgb[3 * c.pix_off + pix] = Cr[k];
+        rgb[3 * c.pix_off + P + pix] = Cg[k];
+        rgb[3 * c.pix_off + 2 * P + pix] = Cb[k];
+        dout[c.pix_off + pix] = Dz[k];
+        a.T_final[c.pix_off + pix] = T[k] > 0.f ? T[k] : Tf[k];
+        a.n_contrib[c.pix_off + pix] = last[k];
+      }
+    }
+  }
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_blend_bwd_h(RasterArgs a, const u64* __restrict__ inst,
+                                                     const float* __restrict__ dL_drgb,
+                                                     const float* __restrict__ dL_ddepth) {
+  using L = TileLayout<TW, TH>;
+  constexpr int PPT = L::PPT;
+  __shared__ float2 s_xy[8][2][32];
+  __shared__ float4 s_con[8][2][32];
+  __shared__ float4 s_col[8][2][32];
+  __shared__ unsigned s_rel[8][2][32];
+  __shared__ unsigned s_vi[8][2][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4;
+  const unsigned lt = lanemask_lt();
+  const unsigned n_items = 8u * (unsigned)a.n_tiles;
+  float* const g2 = reinterpret_cast<float*>(a.grad2d);
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(&a.counters->tile_queue_bwd, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    const unsigned gt = item >> 3, wb = item & 7u;
+    const int bx0 = (int)(wb % L::WPR) * 8, by0 = (int)(wb / L::WPR) * L::WY;
+    const int lx = bx0 + 4 * h + (lane & 3);
+    const int ly = by0 + ((lane >> 2) & 3);
+    const int v = view_of_tile(a.cams, a.V, gt);
+    const DevCam& c = a.cams[v];
+    const int W = c.W, H = c.H;
+    const int local = (int)gt - c.tile_base;
+    const int ty = local / c.ntx, tx = local - ty * c.ntx;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const float x0f = (float)x0, y0f = (float)y0;
+    const long long P = (long long)W * H;
+    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Sr[PPT], Sg[PPT], Sb[PPT], Sd[PPT];
+    uint32_t last[PPT];
+    const int px = x0 + lx;
+    uint32_t mylast = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int py = y0 + ly + 4 * k;
+      last[k] = 0;
+      T[k] = 0.f;
+      gr[k] = gg[k] = gb[k] = gd[k] = 0.f;
+      if (px < W && py < H) {
+        const long long pix = (long long)py * W + px;
+        T[k] = a.T_final[c.pix_off + pix];
+        last[k] = a.n_contrib[c.pix_off + pix];
+        gr[k] = dL_drgb[3 * c.pix_off + pix];
+        gg[k] = dL_drgb[3 * c.pix_off + P + pix];
+        gb[k] = dL_drgb[3 * c.pix_off + 2 * P + pix];
+        gd[k] = dL_ddepth[c.pix_off + pix];
+      }
+      Sr[k] = Sg[k] = Sb[k] = Sd[k] = 0.f;
+      mylast = max(mylast, last[k]);
+    }
+    // per half: the largest contributor count of its pixels
+    const unsigned lastL = __reduce_max_sync(0xffffffffu, h ? 0u : mylast);
+    const unsigned lastR = __reduce_max_sync(0xffffffffu, h ? mylast : 0u);
+    const int warplast = (int)max(lastL, lastR);
+    const uint2 rg = a.ranges[gt];
+    for (int hi = warplast; hi > 0; hi -= 32) {
+      const int rel = hi - 1 - lane;  // lane 0 takes the largest index: compaction keeps reverse order
+      unsigned hb = 0, vi = 0;
+      if (rel >= 0) {
+        const u64 key = inst[rg.x + rel];
+        vi = pair_of_inst(key);
+        hb = half_bits(key, wb);
+        if ((unsigned)rel >= lastL) hb &= 2u;
+        if ((unsigned)rel >= lastR) hb &= 1u;
+      }
+      const unsigned mL = __ballot_sync(0xffffffffu, hb & 1u), mR = __ballot_sync(0xffffffffu, hb & 2u);
+      if (hb) {
+        const float4 r0 = a.rec[3ull * vi + 0];
+        const float2 xy = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+        const float4 cn = a.rec[3ull * vi + 1], cl = a.rec[3ull * vi + 2];
+        if (hb & 1u) {
+          const int sl = __popc(mL & lt);
+          s_xy[w][0][sl] = xy;
+          s_con[w][0][sl] = cn;
+          s_col[w][0][sl] = cl;
+          s_rel[w][0][sl] = (unsigned)rel;
+          s_vi[w][0][sl] = vi;
+        }
+        if (hb & 2u) {
+          const int sl = __popc(mR & lt);
+          s_xy[w][1][sl] = xy;
+          s_con[w][1][sl] = cn;
+          s_col[w][1][sl] = cl;
+          s_rel[w][1][sl] = (unsigned)rel;
+          s_vi[w][1][sl] = vi;
+        }
+      }
+      // the shorter list is padded with entries behind every pixel's last
+      // contributor (skipped by the per-pixel test), so both halves step
+      // together without a branch
+      const int cL = __popc(mL), cR = __popc(mR), cmax = max(cL, cR);
+      if (lane >= cL && lane < cmax) s_rel[w][0][lane] = 0x7fffffffu;
+      if (lane >= cR && lane < cmax) s_rel[w][1][lane] = 0x7fffffffu;
+      __syncwarp();
+      for (int j = 0; j < cmax; ++j) {
+        float acc[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) acc[q] = 0.f;
+        bool any = false;
+        {
+          const int r = (int)s_rel[w][h][j];
+          const float2 xy = s_xy[w][h][j];
+          const float4 cq = s_con[w][h][j];
+          const float dx = __fsub_rn((float)lx, xy.x);
+          const float sx = __fmul_rn(dx, __fmul_rn(cq.x, dx));
+          const float bx = __fmul_rn(cq.y, dx);
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            if (r < (int)last[k]) {
+              const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
+              const float p = blend_power(sx, bx, cq.z, dy);
+              if (p >= kPMin) {
+                const float G = ex2_approx(p);
+                const float araw = __fmul_rn(cq.w, G);
+                const float al = fminf(kAlphaMax, araw);
+                if (al >= kAlphaMin) {
+                  any = true;
+                  const float4 cl = s_col[w][h][j];
+                  T[k] = __fdividef(T[k], 1.f - al);
+                  const float wgt = al * T[k];
+                  acc[6] += wgt * gr[k];
+                  acc[7] += wgt * gg[k];
+                  acc[8] += wgt * gb[k];
+                  acc[9] += wgt * gd[k];
+                  const float dal = T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] +
+                                            (cl.z - Sb[k]) * gb[k] + (cl.w - Sd[k]) * gd[k]);
+                  Sr[k] = al * cl.x + (1.f - al) * Sr[k];
+                  Sg[k] = al * cl.y + (1.f - al) * Sg[k];
+                  Sb[k] = al * cl.z + (1.f - al) * Sb[k];
+                  Sd[k] = al * cl.w + (1.f - al) * Sd[k];
+                  if (araw < kAlphaMax) {
+                    const float gG = dal * G;
+                    const float gx = gG * dx, gy = gG * dy;
+                    acc[5] += gG;
+                    acc[0] += gx;
+                    acc[1] += gy;
+                    acc[2] += gx * dx;
+                    acc[3] += gx * dy;
+                    acc[4] += gy * dy;
+                  }
+                }
+              }
+            }
+          }
+        }
+        if (__any_sync(0xffffffffu, any)) {
+          int comp;
+          bool has;
+          const float tot = warp_sum_transpose<10, 8>(acc, &comp, &has);
+          if (has && tot != 0.f) atomicAdd(g2 + 12ull * s_vi[w][h][j] + comp, tot);
         }
       }
       __syncwarp();
@@ -1245,7 +1586,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_slots(RasterArgs a, const u64
         unsigned vi = 0;
         if (rel >= sbeg) {
           const u64 key = inst[rg.x + rel];
-          vi = (unsigned)key;
+          vi = pair_of_inst(key);
           pass = block_bit(key, w);
         }
         const unsigned m = __ballot_sync(0xffffffffu, pass);
@@ -1340,7 +1681,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_slots(RasterArgs a, const u64
         const bool n1 = g1.x != 0.f || g1.y != 0.f || g1.z != 0.f || g1.w != 0.f;
         const bool n2 = q[8] != 0.f || q[9] != 0.f;
         if (n0 || n1 || n2) {
-          float4* gp = a.grad2d + 3ull * (unsigned)inst[rg.x + sbeg + j];
+          float4* gp = a.grad2d + 3ull * pair_of_inst(inst[rg.x + sbeg + j]);
           if (n0) atomicAdd(gp + 0, g0);
           if (n1) atomicAdd(gp + 1, g1);
           if (n2) atomicAdd(reinterpret_cast<float2*>(gp + 2), make_float2(q[8], q[9]));
@@ -1636,6 +1977,29 @@ static void blend_q_launch(bool fwd, RasterArgs& a, const u64* inst, float* rgb,
     k_blend_bwd_q<TW, TH><<<grid, 256, 0, st>>>(a, inst, dr, dd);
 }
 
+template <int TW, int TH>
+static void blend_h_launch(bool fwd, RasterArgs& a, const u64* inst, float* rgb, float* dout, const float* dr,
+                           const float* dd, cudaStream_t st) {
+  static int occ_f = -1, occ_b = -1;
+  if (occ_f < 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_blend_fwd_h<TW, TH>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_blend_bwd_h<TW, TH>, 256, 0);
+  }
+  const int occ = fwd ? occ_f : occ_b;
+  const int grid = max(1, min(a.n_tiles, a.num_sms * max(occ, 1)));
+  if (fwd)
+    k_blend_fwd_h<TW, TH><<<grid, 256, 0, st>>>(a, inst, rgb, dout);
+  else
+    k_blend_bwd_h<TW, TH><<<grid, 256, 0, st>>>(a, inst, dr, dd);
+}
+
+static void blend_h_dispatch(bool fwd, RasterArgs& a, const u64* inst, float* rgb, float* dout, const float* dr,
+                             const float* dd, cudaStream_t st) {
+  if (a.tile_w == 32 && a.tile_h == 32) blend_h_launch<32, 32>(fwd, a, inst, rgb, dout, dr, dd, st);
+  else if (a.tile_w == 32 && a.tile_h == 16) blend_h_launch<32, 16>(fwd, a, inst, rgb, dout, dr, dd, st);
+  else blend_h_launch<16, 16>(fwd, a, inst, rgb, dout, dr, dd, st);
+}
+
 static void blend_q_dispatch(bool fwd, RasterArgs& a, const u64* inst, float* rgb, float* dout, const float* dr,
                              const float* dd, cudaStream_t st) {
   if (a.tile_w == 32 && a.tile_h == 32) blend_q_launch<32, 32>(fwd, a, inst, rgb, dout, dr, dd, st);
@@ -1696,7 +2060,7 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   k_clamp_inst<<<1, 1, 0, st>>>(a.counters, (u64)a.cap_inst, a.errword);
   int tb = 1;
   while ((1ll << tb) < (long long)a.n_tiles) ++tb;
-  u64* is = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, 32, 32 + tb, a.hist, a.P, st);
+  u64* is = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, kTileShift, kTileShift + tb, a.hist, a.P, st);
   cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)max(a.n_tiles, 1), st);
   k_ranges<<<a.num_sms * 8, 256, 0, st>>>(is, &a.counters->n_inst_c, a.ranges);
   count_launch(7 + 3 * ((lbits + 7) / 8) + 3 * ((tb + 7) / 8) + 2);
@@ -1704,6 +2068,8 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   a.prof(PH_BLEND_FWD, true, st);
   if (a.stage == 32) {
     blend_q_dispatch(true, a, is, rgb, dout, nullptr, nullptr, st);
+  } else if (a.stage == 16) {
+    blend_h_dispatch(true, a, is, rgb, dout, nullptr, nullptr, st);
   } else {
 #define FWD_CALL(TW, TH, SG) blend_fwd_launch<TW, TH, SG>(a, is, rgb, dout, st)
     DCG_TILES(FWD_CALL)
@@ -1722,6 +2088,8 @@ void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb
   a.prof(PH_BLEND_BWD, true, st);
   if (a.stage == 32) {
     blend_q_dispatch(false, a, inst_sorted, nullptr, nullptr, dL_drgb, dL_ddepth, st);
+  } else if (a.stage == 16) {
+    blend_h_dispatch(false, a, inst_sorted, nullptr, nullptr, dL_drgb, dL_ddepth, st);
   } else if (a.bwd_slots) {
     if (a.tile_w == 32 && a.tile_h == 32) blend_bwd_slots_launch<32, 32>(a, inst_sorted, dL_drgb, dL_ddepth, st);
     else if (a.tile_w == 32 && a.tile_h == 16) blend_bwd_slots_launch<32, 16>(a, inst_sorted, dL_drgb, dL_ddepth, st);

@@ -380,12 +380,12 @@ def dcg_state_stats(ctx, state=None, stream=None):
 
 
 def dcg_state_read(ctx, state, n_views, n, n_pix, stream=None):
-    """Returns dict(ranges [T,2] u32, ids [K] u32, masks [K] u8, depth [V*n] f32, rect [V*n,4] i32, T [P],
+    """Returns dict(ranges [T,2] u32, ids [K] u32, masks [K] u16, depth [V*n] f32, rect [V*n,4] i32, T [P],
     n_contrib [P])."""
     nv, K, T = dcg_state_stats(ctx, state, stream)
     ranges = np.zeros((T, 2), np.uint32)
     ids = np.zeros(max(K, 1), np.uint32)
-    masks = np.zeros(max(K, 1), np.uint8)
+    masks = np.zeros(max(K, 1), np.uint16)
     depth = np.zeros(max(n_views * n, 1), np.float32)
     rect = np.zeros((max(n_views * n, 1), 4), np.int32)
     Tf = np.zeros(max(n_pix, 1), np.float32)
@@ -421,19 +421,20 @@ def dcg_state_evals(ctx, state=None, stream=None):
 
 
 TUNE_TILES = [(16, 16), (32, 16), (32, 32)]
-TUNE_STAGES = [64, 96, 128, 192, 256, 32]  # 32: warp-per-block kernels
+TUNE_STAGES = [64, 96, 128, 192, 256, 32, 16]  # 32: warp-per-block kernels, 16: half-warp kernels
 
 
 def dcg_autotune(ctx, g: dcg_gaussians, n: int, cams, rgb, depth, dL_drgb, dL_ddepth, grads: dcg_gaussians, reps=3,
                  stream=None):
     arr = make_cameras(cams)
     tw, th, sg = _I32(), _I32(), _I32()
-    ms = np.zeros(18, np.float32)
+    ns = len(TUNE_STAGES)
+    ms = np.zeros(len(TUNE_TILES) * ns, np.float32)
     check(ctx, lib().dcg_autotune(ctx, ctypes.byref(g), n, arr, len(cams), ptr(rgb), ptr(depth), ptr(dL_drgb),
                                   ptr(dL_ddepth), ctypes.byref(grads), reps, ctypes.byref(tw), ctypes.byref(th),
                                   ctypes.byref(sg), ptr(ms), stream_ptr(stream)))
-    table = {f"{TUNE_TILES[i // 6][0]}x{TUNE_TILES[i // 6][1]}/{TUNE_STAGES[i % 6]}": round(float(ms[i]), 4)
-             for i in range(18)}
+    table = {f"{TUNE_TILES[i // ns][0]}x{TUNE_TILES[i // ns][1]}/{TUNE_STAGES[i % ns]}": round(float(ms[i]), 4)
+             for i in range(len(ms))}
     return {"tile": [tw.value, th.value], "stage": sg.value, "ms": table}
 
 

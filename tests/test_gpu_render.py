@@ -50,7 +50,8 @@ def ctx0():
     dcg.dcg_destroy(c)
 
 
-BWD_VARIANTS = {"warp": dict(flags=0), "slots": dict(flags=1), "warp_per_block": dict(flags=0, stage=32)}
+BWD_VARIANTS = {"warp": dict(flags=0), "slots": dict(flags=1), "warp_per_block": dict(flags=0, stage=32),
+                "half_warp": dict(flags=0, stage=16)}
 
 
 @pytest.fixture(scope="module", params=list(BWD_VARIANTS))
@@ -95,15 +96,15 @@ def test_sort_keys_bit_exact_and_tile_lists_valid(ctx0, orc):
     assert np.array_equal(st["depth"].view(np.uint32), z32.view(np.uint32))
     # per tile: the Gaussians whose rectangle covers it, in (depth bits, index) order, less those
     # whose support ellipse misses the tile.  What is left out must miss it: q > 9 at every pixel of
-    # the tile by the oracle's FP64 conic.  Block masks likewise: a cleared bit means q > 9 at every
-    # pixel of that 8 x 4 block.
+    # the tile by the oracle's FP64 conic.  Half-block masks likewise: a cleared bit 2 b + h means
+    # q > 9 at every pixel of the 4 x 4 half h of the 8 x 4 block b.
     pr = orc.project(P, 0, cam)
     rect = st["rect"]
     vis = rect[:, 2] >= rect[:, 0]
     ntx = (cam.W + 15) // 16
     ranges, ids, masks = st["ranges"], st["ids"], st["masks"]
     zb = st["depth"].view(np.uint32)
-    by, bx = np.mgrid[0:4, 0:8]
+    by, bx = np.mgrid[0:4, 0:4]
 
     def q_at(g, xs, ys):
         dx, dy = xs - pr["u"][g], ys - pr["v"][g]
@@ -122,11 +123,13 @@ def test_sort_keys_bit_exact_and_tile_lists_valid(ctx0, orc):
             assert q_at(g, xs, ys).min() > 9.0, (t, g)
             dropped += 1
         for g, m in zip(lst, msk):
-            for b in range(8):
-                if not (m >> b) & 1:
-                    xs = 16 * tx + 8 * (b % 2) + bx
+            assert m != 0, (t, g)
+            for hb in range(16):
+                if not (int(m) >> hb) & 1:
+                    b, h = divmod(hb, 2)
+                    xs = 16 * tx + 8 * (b % 2) + 4 * h + bx
                     ys = 16 * ty + 4 * (b // 2) + by
-                    assert q_at(g, xs, ys).min() > 9.0, (t, g, b)
+                    assert q_at(g, xs, ys).min() > 9.0, (t, g, hb)
             kept += 1
     assert kept > 0 and dropped > 0
     # rectangles agree with the oracle's FP64 extents except within rounding of a pixel boundary
@@ -226,7 +229,7 @@ def test_batched_views_equal_single_views(ctx):
 
 @pytest.mark.parametrize("tile,stage", [((16, 16), 64), ((32, 16), 128), ((32, 32), 256), ((16, 16), 192),
                                         ((32, 32), 96), ((16, 16), 32), ((32, 16), 32),
-                                        ((32, 32), 32)])
+                                        ((32, 32), 32), ((16, 16), 16), ((32, 16), 16), ((32, 32), 16)])
 def test_launch_shapes_agree(ctx, tile, stage):
     P, cams = _room_views(n=60_000, n_views=1, seed=4)
     dcg.dcg_set_launch(ctx, 16, 16, 128)
