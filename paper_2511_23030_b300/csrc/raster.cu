@@ -1180,16 +1180,32 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
 // ============================================================================
 // Half-warp blends.  As the warp-per-block kernels, but the two halves of a
 // warp own the two 4 x WY halves of its 8 x WY block (lane l: half l / 16,
-// column l % 4, row (l / 4) % 4) and walk separate lists: an instance enters
-// the list of each half whose pixels its support ellipse may reach (two bits
-// of the instance mask).  A small Gaussian that reaches one half therefore
-// occupies 16 lanes instead of 32, and the other half takes the next
-// Gaussian of its own list in the same step.  A half whose pixels are all
-// done (forward) or behind all of its pixels' last contributors (backward)
-// takes no more instances.  The backward reduces each half's Gaussian over
-// its 16 lanes (one transposed butterfly serves both halves).  Per-pixel
-// arithmetic and order are those of the other kernels, so images are
-// identical.
+// column l % 4, row (l / 4) % 4) and each half walks its own list: an
+// instance enters the list of each half whose pixels its support ellipse may
+// reach (two bits of the instance mask).  A small Gaussian that reaches one
+// half occupies 16 lanes instead of 32, and the other half takes the next
+// Gaussian of its own list in the same step.  The forward compacts each
+// batch of 32 tile instances into two lists and pads the shorter one with
+// transparent entries.  The backward keeps a ring buffer of R entries per
+// half in shared memory, refilled 32 tile instances at a time while a half
+// holds fewer than 32, so that a half can run ahead of the other across scan
+// batches; a half with nothing to do steps through a neutral entry (slot R).
+// A half whose pixels are all done (forward) or whose instances lie behind
+// all of its pixels' last contributors (backward) takes no more instances.
+// The backward reduces each half's Gaussian over its 16 lanes (one
+// transposed butterfly serves both halves).  Per-pixel arithmetic and order
+// are those of the other kernels, so images are identical.
+constexpr int kRingB = 60;  // ring entries per half (static shared memory under 48 KB)
+
+// Steps the halves run before the next refill: together while both hold
+// entries; otherwise the one that holds entries runs until a refill fits
+// (nothing is left to scan, or its count is down to R - 32).
+__device__ __forceinline__ int ring_steps(int pL, int pR, bool more, int R) {
+  if (pL > 0 && pR > 0) return min(pL, pR);
+  const int p = max(pL, pR);
+  return more ? p - (R - 32) : p;
+}
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __restrict__ inst,
                                                      float* __restrict__ rgb, float* __restrict__ dout) {
@@ -1350,15 +1366,17 @@ __global__ void __launch_bounds__(256) k_blend_bwd_h(RasterArgs a, const u64* __
                                                      const float* __restrict__ dL_ddepth) {
   using L = TileLayout<TW, TH>;
   constexpr int PPT = L::PPT;
-  __shared__ float2 s_xy[8][2][32];
-  __shared__ float4 s_con[8][2][32];
-  __shared__ float4 s_col[8][2][32];
-  __shared__ unsigned s_rel[8][2][32];
-  __shared__ unsigned s_vi[8][2][32];
+  constexpr int R = kRingB;
+  __shared__ float2 s_xy[8][2][R + 1];
+  __shared__ float4 s_con[8][2][R + 1];
+  __shared__ float4 s_col[8][2][R + 1];
+  __shared__ unsigned s_rel[8][2][R + 1];
+  __shared__ unsigned s_vi[8][2][R + 1];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4;
   const unsigned lt = lanemask_lt();
   const unsigned n_items = 8u * (unsigned)a.n_tiles;
   float* const g2 = reinterpret_cast<float*>(a.grad2d);
+  if (lane < 2) s_rel[w][lane][R] = 0x7fffffffu;  // the neutral entry: behind every pixel's last contributor
   for (;;) {
     unsigned item = 0;
     if (lane == 0) item = atomicAdd(&a.counters->tile_queue_bwd, 1u);
@@ -1401,93 +1419,102 @@ __global__ void __launch_bounds__(256) k_blend_bwd_h(RasterArgs a, const u64* __
     // per half: the largest contributor count of its pixels
     const unsigned lastL = __reduce_max_sync(0xffffffffu, h ? 0u : mylast);
     const unsigned lastR = __reduce_max_sync(0xffffffffu, h ? mylast : 0u);
-    const int warplast = (int)max(lastL, lastR);
     const uint2 rg = a.ranges[gt];
-    for (int hi = warplast; hi > 0; hi -= 32) {
-      const int rel = hi - 1 - lane;  // lane 0 takes the largest index: compaction keeps reverse order
-      unsigned hb = 0, vi = 0;
-      if (rel >= 0) {
-        const u64 key = inst[rg.x + rel];
-        vi = pair_of_inst(key);
-        hb = half_bits(key, wb);
-        if ((unsigned)rel >= lastL) hb &= 2u;
-        if ((unsigned)rel >= lastR) hb &= 1u;
-      }
-      const unsigned mL = __ballot_sync(0xffffffffu, hb & 1u), mR = __ballot_sync(0xffffffffu, hb & 2u);
-      if (hb) {
-        const float4 r0 = a.rec[3ull * vi + 0];
-        const float2 xy = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
-        const float4 cn = a.rec[3ull * vi + 1], cl = a.rec[3ull * vi + 2];
-        if (hb & 1u) {
-          const int sl = __popc(mL & lt);
-          s_xy[w][0][sl] = xy;
-          s_con[w][0][sl] = cn;
-          s_col[w][0][sl] = cl;
-          s_rel[w][0][sl] = (unsigned)rel;
-          s_vi[w][0][sl] = vi;
+    int hi = (int)max(lastL, lastR);  // instances [0, hi) are still to scan, from the end
+    int hL = 0, hR = 0, pL = 0, pR = 0;
+    __syncwarp();
+    for (;;) {
+      while (hi > 0 && (pL < 32 || pR < 32) && pL <= R - 32 && pR <= R - 32) {
+        const int rel = hi - 1 - lane;  // lane 0 takes the largest index: rings keep reverse order
+        unsigned hb = 0, vi = 0;
+        if (rel >= 0) {
+          const u64 key = inst[rg.x + rel];
+          vi = pair_of_inst(key);
+          hb = half_bits(key, wb);
+          if ((unsigned)rel >= lastL) hb &= 2u;
+          if ((unsigned)rel >= lastR) hb &= 1u;
         }
-        if (hb & 2u) {
-          const int sl = __popc(mR & lt);
-          s_xy[w][1][sl] = xy;
-          s_con[w][1][sl] = cn;
-          s_col[w][1][sl] = cl;
-          s_rel[w][1][sl] = (unsigned)rel;
-          s_vi[w][1][sl] = vi;
+        const unsigned mL = __ballot_sync(0xffffffffu, hb & 1u), mR = __ballot_sync(0xffffffffu, hb & 2u);
+        if (hb) {
+          const float4 r0 = a.rec[3ull * vi + 0];
+          const float2 xy = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+          const float4 cn = a.rec[3ull * vi + 1], cl = a.rec[3ull * vi + 2];
+          if (hb & 1u) {
+            int sl = hL + pL + __popc(mL & lt);
+            sl -= sl >= R ? R : 0;
+            sl -= sl >= R ? R : 0;
+            s_xy[w][0][sl] = xy;
+            s_con[w][0][sl] = cn;
+            s_col[w][0][sl] = cl;
+            s_rel[w][0][sl] = (unsigned)rel;
+            s_vi[w][0][sl] = vi;
+          }
+          if (hb & 2u) {
+            int sl = hR + pR + __popc(mR & lt);
+            sl -= sl >= R ? R : 0;
+            sl -= sl >= R ? R : 0;
+            s_xy[w][1][sl] = xy;
+            s_con[w][1][sl] = cn;
+            s_col[w][1][sl] = cl;
+            s_rel[w][1][sl] = (unsigned)rel;
+            s_vi[w][1][sl] = vi;
+          }
         }
+        pL += __popc(mL);
+        pR += __popc(mR);
+        hi -= 32;
       }
-      // the shorter list is padded with entries behind every pixel's last
-      // contributor (skipped by the per-pixel test), so both halves step
-      // together without a branch
-      const int cL = __popc(mL), cR = __popc(mR), cmax = max(cL, cR);
-      if (lane >= cL && lane < cmax) s_rel[w][0][lane] = 0x7fffffffu;
-      if (lane >= cR && lane < cmax) s_rel[w][1][lane] = 0x7fffffffu;
       __syncwarp();
-      for (int j = 0; j < cmax; ++j) {
+      if (pL == 0 && pR == 0) break;
+      const int n = ring_steps(pL, pR, hi > 0, R);
+      const int pm = h ? pR : pL, hm = h ? hR : hL;
+      for (int s = 0; s < n; ++s) {
+        int e = hm + s;
+        e -= e >= R ? R : 0;
+        e = s < pm ? e : R;
         float acc[10];
 #pragma unroll
         for (int q = 0; q < 10; ++q) acc[q] = 0.f;
         bool any = false;
-        {
-          const int r = (int)s_rel[w][h][j];
-          const float2 xy = s_xy[w][h][j];
-          const float4 cq = s_con[w][h][j];
-          const float dx = __fsub_rn((float)lx, xy.x);
-          const float sx = __fmul_rn(dx, __fmul_rn(cq.x, dx));
-          const float bx = __fmul_rn(cq.y, dx);
+        const int r = (int)s_rel[w][h][e];
+        const float2 xy = s_xy[w][h][e];
+        const float4 cq = s_con[w][h][e];
+        const float dx = __fsub_rn((float)lx, xy.x);
+        const float sx = __fmul_rn(dx, __fmul_rn(cq.x, dx));
+        const float bx = __fmul_rn(cq.y, dx);
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) {
-            if (r < (int)last[k]) {
-              const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
-              const float p = blend_power(sx, bx, cq.z, dy);
-              if (p >= kPMin) {
-                const float G = ex2_approx(p);
-                const float araw = __fmul_rn(cq.w, G);
-                const float al = fminf(kAlphaMax, araw);
-                if (al >= kAlphaMin) {
-                  any = true;
-                  const float4 cl = s_col[w][h][j];
-                  T[k] = __fdividef(T[k], 1.f - al);
-                  const float wgt = al * T[k];
-                  acc[6] += wgt * gr[k];
-                  acc[7] += wgt * gg[k];
-                  acc[8] += wgt * gb[k];
-                  acc[9] += wgt * gd[k];
-                  const float dal = T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] +
-                                            (cl.z - Sb[k]) * gb[k] + (cl.w - Sd[k]) * gd[k]);
-                  Sr[k] = al * cl.x + (1.f - al) * Sr[k];
-                  Sg[k] = al * cl.y + (1.f - al) * Sg[k];
-                  Sb[k] = al * cl.z + (1.f - al) * Sb[k];
-                  Sd[k] = al * cl.w + (1.f - al) * Sd[k];
-                  if (araw < kAlphaMax) {
-                    const float gG = dal * G;
-                    const float gx = gG * dx, gy = gG * dy;
-                    acc[5] += gG;
-                    acc[0] += gx;
-                    acc[1] += gy;
-                    acc[2] += gx * dx;
-                    acc[3] += gx * dy;
-                    acc[4] += gy * dy;
-                  }
+        for (int k = 0; k < PPT; ++k) {
+          if (r < (int)last[k]) {
+            const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
+            const float p = blend_power(sx, bx, cq.z, dy);
+            if (p >= kPMin) {
+              const float G = ex2_approx(p);
+              const float araw = __fmul_rn(cq.w, G);
+              const float al = fminf(kAlphaMax, araw);
+              if (al >= kAlphaMin) {
+                any = true;
+                const float4 cl = s_col[w][h][e];
+                T[k] = __fdividef(T[k], 1.f - al);
+                const float wgt = al * T[k];
+                acc[6] += wgt * gr[k];
+                acc[7] += wgt * gg[k];
+                acc[8] += wgt * gb[k];
+                acc[9] += wgt * gd[k];
+                const float dal = T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] +
+                                          (cl.w - Sd[k]) * gd[k]);
+                Sr[k] = al * cl.x + (1.f - al) * Sr[k];
+                Sg[k] = al * cl.y + (1.f - al) * Sg[k];
+                Sb[k] = al * cl.z + (1.f - al) * Sb[k];
+                Sd[k] = al * cl.w + (1.f - al) * Sd[k];
+                if (araw < kAlphaMax) {
+                  const float gG = dal * G;
+                  const float gx = gG * dx, gy = gG * dy;
+                  acc[5] += gG;
+                  acc[0] += gx;
+                  acc[1] += gy;
+                  acc[2] += gx * dx;
+                  acc[3] += gx * dy;
+                  acc[4] += gy * dy;
                 }
               }
             }
@@ -1497,9 +1524,16 @@ __global__ void __launch_bounds__(256) k_blend_bwd_h(RasterArgs a, const u64* __
           int comp;
           bool has;
           const float tot = warp_sum_transpose<10, 8>(acc, &comp, &has);
-          if (has && tot != 0.f) atomicAdd(g2 + 12ull * s_vi[w][h][j] + comp, tot);
+          if (has && tot != 0.f) atomicAdd(g2 + 12ull * s_vi[w][h][e] + comp, tot);
         }
       }
+      const int nL = min(n, pL), nR = min(n, pR);
+      hL += nL;
+      hL -= hL >= R ? R : 0;
+      hR += nR;
+      hR -= hR >= R ? R : 0;
+      pL -= nL;
+      pR -= nR;
       __syncwarp();
     }
   }
