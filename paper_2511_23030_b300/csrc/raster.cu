@@ -334,9 +334,15 @@ template <int DEG>
 __global__ void __launch_bounds__(256, 3) k_preprocess_fwd(RasterArgs a) {
   const long long n = a.n;
   constexpr int D = (DEG + 1) * (DEG + 1);
+  // this thread's SH coefficients, loaded once at its first visible view:
+  // element k at shc[k * blockDim.x] (3 D x blockDim.x floats of dynamic shared memory)
+  extern __shared__ float s_dyn[];
+  float* const shc = s_dyn + threadIdx.x;
+  const int bd = blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float* g = a.g;
     const long long S = a.stride;
+    bool have_sh = false;
     const float mx = g[0 * S + i], my = g[1 * S + i], mz = g[2 * S + i];
     // 3D covariance Sigma = M M^T, M = R(q) diag(exp(log s))
     const float s0 = __expf(g[3 * S + i]), s1 = __expf(g[4 * S + i]), s2 = __expf(g[5 * S + i]);
@@ -414,12 +420,17 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_fwd(RasterArgs a) {
       dx *= il; dy *= il; dz *= il;
       float Y[16];
       sh_basis(DEG, dx, dy, dz, Y);
+      if (!have_sh) {
+#pragma unroll
+        for (int k = 0; k < 3 * D; ++k) shc[k * bd] = g[(11 + k) * S + i];
+        have_sh = true;
+      }
       float col[3];
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.f;
 #pragma unroll
-        for (int k = 0; k < D; ++k) acc += g[(11 + 3 * k + ch) * S + i] * Y[k];
+        for (int k = 0; k < D; ++k) acc += shc[(3 * k + ch) * bd] * Y[k];
         col[ch] = fmaxf(acc + 0.5f, 0.f);
       }
       a.rec[3 * vi + 0] = r0;
@@ -1738,17 +1749,24 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
                                                                    long long ostride, float* __restrict__ dpose) {
   const long long n = a.n;
   constexpr int D = (DEG + 1) * (DEG + 1);
-  __shared__ float s_gsh[3 * D][kPreBwdThreads];
-  float* gsh_col = &s_gsh[0][threadIdx.x];  // element k at gsh_col[k * kPreBwdThreads]
+  constexpr int T = kPreBwdThreads;
+  // dynamic shared memory, one column per thread: its SH coefficients
+  // (loaded once, at its first contributing view; element k at shc[k T]) and
+  // the colour gradient of each contributing view (channel ch of view v at
+  // gcv[(3 v + ch) T]), from which the SH gradients are summed after the
+  // view loop
+  extern __shared__ float s_dyn[];
+  float* const shc = s_dyn + threadIdx.x;
+  float* const gcv = s_dyn + 3 * D * T + threadIdx.x;
   const long long S = a.stride;
   // one pass over all threads of the grid; lanes past n still join the warp reductions
   const long long n_round = ((n + 31) / 32) * 32;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_round; i += (long long)gridDim.x * blockDim.x) {
     const bool live = i < n;
     const float* g = a.g;
+    bool have_sh = false;
+    unsigned vact = 0;  // views with a colour gradient
     float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3 * D; ++k) gsh_col[k * kPreBwdThreads] = 0.f;
     float mx = 0, my = 0, mz = 0, sc[3] = {1, 1, 1}, qn[4] = {1, 0, 0, 0}, qlen = 1.f, R[9], M[9], opac = 0.5f;
     float S00 = 0, S01 = 0, S02 = 0, S11 = 0, S12 = 0, S22 = 0;
     if (live) {
@@ -1877,21 +1895,25 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
         float wsum[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
+        if (!have_sh) {
+#pragma unroll
+          for (int k = 0; k < 3 * D; ++k) shc[k * T] = g[(11 + k) * S + i];
+          have_sh = true;
+        }
+        vact |= 1u << v;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-          float shc[D];
+          float sh[D];
           float acc = 0.f;
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            shc[k] = g[(11 + 3 * k + ch) * S + i];
-            acc += shc[k] * Y[k];
+            sh[k] = shc[(3 * k + ch) * T];
+            acc += sh[k] * Y[k];
           }
           const float gc = (acc + 0.5f < 0.f) ? 0.f : dcol[ch];  // no gradient through a clamped channel
+          gcv[(3 * v + ch) * T] = gc;
 #pragma unroll
-          for (int k = 0; k < D; ++k) {
-            gsh_col[(3 * k + ch) * kPreBwdThreads] += gc * Y[k];
-            wsum[k] += gc * shc[k];
-          }
+          for (int k = 0; k < D; ++k) wsum[k] += gc * sh[k];
         }
         float gdir[3] = {0, 0, 0};
         sh_grad_acc(DEG, dx, dy, dz, wsum, gdir);
@@ -1961,8 +1983,27 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
     out[8 * ostride + i] = gq[2];
     out[9 * ostride + i] = gq[3];
     out[10 * ostride + i] = go;
+    // SH gradients: sum over the contributing views (ascending) of gc Y(dir)
+    float gsh[3 * D];
 #pragma unroll
-    for (int k = 0; k < 3 * D; ++k) out[(11 + k) * ostride + i] = gsh_col[k * kPreBwdThreads];
+    for (int k = 0; k < 3 * D; ++k) gsh[k] = 0.f;
+    for (unsigned m = vact; m != 0u; m &= m - 1u) {
+      const int v = __ffs(m) - 1;
+      const DevCam& c = a.cams[v];
+      float dx = mx - c.C[0], dy = my - c.C[1], dz = mz - c.C[2];
+      const float il = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
+      dx *= il; dy *= il; dz *= il;
+      float Y[16];
+      sh_basis(DEG, dx, dy, dz, Y);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float gc = gcv[(3 * v + ch) * T];
+#pragma unroll
+        for (int k = 0; k < D; ++k) gsh[3 * k + ch] += gc * Y[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3 * D; ++k) out[(11 + k) * ostride + i] = gsh[k];
   }
 }
 
@@ -2054,6 +2095,26 @@ static void blend_q_dispatch(bool fwd, RasterArgs& a, const u64* inst, float* rg
   else if (a.tile_w == 32 && a.tile_h == 16) { DCG_STAGES(32, 16, CALL) } \
   else { DCG_STAGES(16, 16, CALL) }
 
+// Dynamic shared memory of the preprocess kernels: the SH coefficients of
+// every thread of the block (3 (deg + 1)^2 floats each).
+static size_t sh_smem(int deg, int threads) { return sizeof(float) * 3 * (deg + 1) * (deg + 1) * threads; }
+// ... and, in the backward, the colour gradient of every view (3 floats each)
+static size_t sh_smem_bwd(int deg, int V) { return sh_smem(deg, kPreBwdThreads) + sizeof(float) * 3 * V * kPreBwdThreads; }
+
+static void preprocess_smem_init() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  cudaFuncSetAttribute(k_preprocess_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem(0, 256));
+  cudaFuncSetAttribute(k_preprocess_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem(1, 256));
+  cudaFuncSetAttribute(k_preprocess_fwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem(2, 256));
+  cudaFuncSetAttribute(k_preprocess_fwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem(3, 256));
+  cudaFuncSetAttribute(k_preprocess_bwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem_bwd(0, kMaxViewsApi));
+  cudaFuncSetAttribute(k_preprocess_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem_bwd(1, kMaxViewsApi));
+  cudaFuncSetAttribute(k_preprocess_bwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem_bwd(2, kMaxViewsApi));
+  cudaFuncSetAttribute(k_preprocess_bwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem_bwd(3, kMaxViewsApi));
+}
+
 static int grid_for(long long n, int num_sms) {
   long long b = (n + 255) / 256;
   long long cap = (long long)num_sms * 8;
@@ -2061,16 +2122,17 @@ static int grid_for(long long n, int num_sms) {
 }
 
 void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u64** inst_sorted, cudaStream_t st) {
+  preprocess_smem_init();
   cudaMemsetAsync(a.counters, 0, sizeof(DevCounters), st);
   const long long pairs = (long long)a.V * a.n;
   a.prof(PH_PRE_FWD, true, st);
   if (a.n > 0) {
     const int gr = grid_for(a.n, a.num_sms);
     switch (a.deg) {
-      case 0: k_preprocess_fwd<0><<<gr, 256, 0, st>>>(a); break;
-      case 1: k_preprocess_fwd<1><<<gr, 256, 0, st>>>(a); break;
-      case 2: k_preprocess_fwd<2><<<gr, 256, 0, st>>>(a); break;
-      default: k_preprocess_fwd<3><<<gr, 256, 0, st>>>(a); break;
+      case 0: k_preprocess_fwd<0><<<gr, 256, sh_smem(0, 256), st>>>(a); break;
+      case 1: k_preprocess_fwd<1><<<gr, 256, sh_smem(1, 256), st>>>(a); break;
+      case 2: k_preprocess_fwd<2><<<gr, 256, sh_smem(2, 256), st>>>(a); break;
+      default: k_preprocess_fwd<3><<<gr, 256, sh_smem(3, 256), st>>>(a); break;
     }
     count_launch();
   }
@@ -2117,6 +2179,7 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
 
 void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb, const float* dL_ddepth, float* grads,
                      long long g_stride, float* dL_dpose, cudaStream_t st) {
+  preprocess_smem_init();
   cudaMemsetAsync(&a.counters->tile_queue_bwd, 0, sizeof(unsigned), st);
   if (dL_dpose) cudaMemsetAsync(dL_dpose, 0, sizeof(float) * 6 * a.V, st);
   a.prof(PH_BLEND_BWD, true, st);
@@ -2139,10 +2202,10 @@ void raster_backward(RasterArgs& a, const u64* inst_sorted, const float* dL_drgb
   if (a.n > 0) {
     const int gr = (int)std::min<long long>((a.n + kPreBwdThreads - 1) / kPreBwdThreads, (long long)a.num_sms * 16);
     switch (a.deg) {
-      case 0: k_preprocess_bwd<0><<<gr, kPreBwdThreads, 0, st>>>(a, grads, g_stride, dL_dpose); break;
-      case 1: k_preprocess_bwd<1><<<gr, kPreBwdThreads, 0, st>>>(a, grads, g_stride, dL_dpose); break;
-      case 2: k_preprocess_bwd<2><<<gr, kPreBwdThreads, 0, st>>>(a, grads, g_stride, dL_dpose); break;
-      default: k_preprocess_bwd<3><<<gr, kPreBwdThreads, 0, st>>>(a, grads, g_stride, dL_dpose); break;
+      case 0: k_preprocess_bwd<0><<<gr, kPreBwdThreads, sh_smem_bwd(0, a.V), st>>>(a, grads, g_stride, dL_dpose); break;
+      case 1: k_preprocess_bwd<1><<<gr, kPreBwdThreads, sh_smem_bwd(1, a.V), st>>>(a, grads, g_stride, dL_dpose); break;
+      case 2: k_preprocess_bwd<2><<<gr, kPreBwdThreads, sh_smem_bwd(2, a.V), st>>>(a, grads, g_stride, dL_dpose); break;
+      default: k_preprocess_bwd<3><<<gr, kPreBwdThreads, sh_smem_bwd(3, a.V), st>>>(a, grads, g_stride, dL_dpose); break;
     }
     count_launch();
   }
