@@ -83,3 +83,22 @@ def rel_l2(a, b):
 
 GROUPS = {"mean": slice(0, 3), "log_scale": slice(3, 6), "quat": slice(6, 10), "opacity": slice(10, 11),
           "sh": slice(11, None)}
+
+
+RGB_TOL = 1e-5  # RGB and T absolute, depth relative (to max(1, |depth|)), at unflagged pixels
+T_TOL = 1e-5
+GRAD_TOL = 1e-4  # relative L2 per parameter group and for the pose twist
+
+
+def check_image(orc_out, rgb, depth, T, tag, max_flag=0.005):
+    """GPU pixels against the oracle's, skipping the pixels the oracle flags
+    (a discrete decision within rounding of its threshold)."""
+    ok = orc_out["flags"] == 0
+    assert ok.mean() >= 1 - max_flag, f"{tag}: flagged {1 - ok.mean():.4%}"
+    e_rgb = np.abs(rgb[ok] - orc_out["rgb"][ok]).max()
+    dz = np.abs(depth[ok] - orc_out["depth"][ok]) / np.maximum(1.0, np.abs(orc_out["depth"][ok]))
+    e_T = np.abs(T[ok] - orc_out["T"][ok]).max()
+    assert e_rgb <= RGB_TOL, f"{tag}: rgb err {e_rgb}"
+    assert dz.max() <= RGB_TOL, f"{tag}: depth err {dz.max()}"
+    assert e_T <= T_TOL, f"{tag}: T err {e_T}"
+    return e_rgb

@@ -15,25 +15,11 @@ import pytest
 
 from paper_2511_23030_b300 import dcg, synth
 
-from gpu_util import GROUPS, backward, make_ctx, out_buffers, planar, rel_l2, render, split_views
+from gpu_util import (GRAD_TOL, GROUPS, RGB_TOL, backward, check_image, make_ctx, out_buffers, planar, rel_l2, render,
+                      split_views)
 
 pytestmark = pytest.mark.gpu
 
-RGB_TOL = 1e-5
-T_TOL = 1e-5
-GRAD_TOL = 1e-4
-
-
-def check_image(orc_out, rgb, depth, T, tag, max_flag=0.005):
-    ok = orc_out["flags"] == 0
-    assert ok.mean() >= 1 - max_flag, f"{tag}: flagged {1 - ok.mean():.4%}"
-    e_rgb = np.abs(rgb[ok] - orc_out["rgb"][ok]).max()
-    dz = np.abs(depth[ok] - orc_out["depth"][ok]) / np.maximum(1.0, np.abs(orc_out["depth"][ok]))
-    e_T = np.abs(T[ok] - orc_out["T"][ok]).max()
-    assert e_rgb <= RGB_TOL, f"{tag}: rgb err {e_rgb}"
-    assert dz.max() <= RGB_TOL, f"{tag}: depth err {dz.max()}"
-    assert e_T <= T_TOL, f"{tag}: T err {e_T}"
-    return e_rgb
 
 
 @pytest.fixture(scope="module")
