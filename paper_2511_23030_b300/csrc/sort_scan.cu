@@ -38,20 +38,23 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d, int nbits, bool vali
 }
 
 // Per-block digit histogram of the block's partition.  Each thread loads
-// kHistUnroll keys (strided by the block size) before ranking them, so that
-// several loads are in flight per thread.
+// kHistUnroll keys (strided by the block size) before counting them, so that
+// several loads are in flight per thread; counts go to one shared-memory
+// histogram per warp (native shared atomics; the order of equal digits does
+// not matter for a count), summed at the end.
 constexpr int kHistUnroll = 4;
 
 __global__ void __launch_bounds__(256) k_radix_hist(const u64* keys, const u64* n_ptr, int shift, int nbits,
                                                     uint32_t* hist) {
-  __shared__ uint32_t h[256];
+  __shared__ uint32_t h[8][256];  // one histogram per warp, summed at the end
   const u64 n = *n_ptr;
   u64 beg, end;
   partition_of(n, &beg, &end);
-  h[threadIdx.x] = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) h[w][threadIdx.x] = 0;
   __syncthreads();
   const u64 mask = (1ull << nbits) - 1;
-  const unsigned lane = lane_id();
+  uint32_t* const hw = h[threadIdx.x >> 5];
   for (u64 c0 = beg; c0 < end; c0 += (u64)kHistUnroll * blockDim.x) {
     u64 k[kHistUnroll];
 #pragma unroll
@@ -62,14 +65,14 @@ __global__ void __launch_bounds__(256) k_radix_hist(const u64* keys, const u64* 
 #pragma unroll
     for (int r = 0; r < kHistUnroll; ++r) {
       const u64 i = c0 + (u64)r * blockDim.x + threadIdx.x;
-      const bool valid = i < end;
-      const unsigned d = valid ? (unsigned)((k[r] >> shift) & mask) : 0u;
-      const unsigned peers = digit_peers(d, nbits, valid);
-      if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+      if (i < end) atomicAdd(&hw[(unsigned)((k[r] >> shift) & mask)], 1u);
     }
   }
   __syncthreads();
-  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+  uint32_t t = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) t += h[w][threadIdx.x];
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = t;
 }
 
 // One block per digit: exclusive scan of hist[d][0..P) in place; the digit's
