@@ -476,6 +476,9 @@ def roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, launch
     }
     dom = max((k for k in algo_bytes), key=lambda k: phases.get(k, 0.0))
     t = phases[dom] / 1e3
+    # every phase against the HBM peak (algorithmic bytes over its live time)
+    by_phase = {k: {"gbs": round(b / (phases[k] / 1e3) / 1e9, 1), "frac": round(b / (phases[k] / 1e3) / 1e9 / hbm, 4)}
+                for k, b in algo_bytes.items() if phases.get(k, 0.0) > 0.01}
     if dom in ("blend_fwd", "blend_bwd"):
         # FP32 issue bound: 148 SMs x 128 lanes x 2 FLOP per clock.  The algorithmic work is the
         # composited (pixel, Gaussian) pairs, independent of how the kernel culls: 22 FLOP per pair
@@ -486,14 +489,16 @@ def roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, launch
         return {"kernel": dom, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round(ach / peak, 4), "traffic": measured_traffic(dom, launch, n_inst),
                 "hbm_gbs": round(algo_bytes[dom] / t / 1e9, 1),
-                "hbm_frac": round(algo_bytes[dom] / t / 1e9 / hbm, 4), "peak_source": f"derived (sm_max {sm_max} MHz)"}
+                "hbm_frac": round(algo_bytes[dom] / t / 1e9 / hbm, 4), "peak_source": f"derived (sm_max {sm_max} MHz)",
+                "hbm_by_phase": by_phase}
     ach = algo_bytes[dom] / t / 1e9
     return {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(ach / hbm, 4), "traffic": measured_traffic(dom, launch, n_inst), "peak_source": src}
+            "frac": round(ach / hbm, 4), "traffic": measured_traffic(dom, launch, n_inst), "peak_source": src,
+            "hbm_by_phase": by_phase}
 
 
 # ----------------------------------------------------------------------------- CPU baseline (oracle)
-def cpu_baseline(pix_per_view: int, views=None, n_gaussians=2_000_000, seed=0, scene=None):
+def cpu_baseline(pix_per_view: int, views=None, n_gaussians=2_000_000, seed=0, scene=None, single_thread_pixels=0):
     """FP64 oracle fwd+bwd on a bounded pixel sample of the window (the whole
     scene is projected for every sampled view)."""
     import oracle
@@ -517,9 +522,23 @@ def cpu_baseline(pix_per_view: int, views=None, n_gaussians=2_000_000, seed=0, s
         oracle.render_bwd(P, sc["deg"], c, gr, gd, pix=pix, n_threads=cores)
         m += len(pix)
     dt = time.perf_counter() - t0
-    return {"value": round(m / dt / 1e6, 8), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{m} pixels ({pix_per_view} per view, views {list(views)}) of the window, fwd+bwd, "
-                      f"{n_gaussians} Gaussians projected per view", "seconds": round(dt, 2)}
+    out = {"value": round(m / dt / 1e6, 8), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{m} pixels ({pix_per_view} per view, views {list(views)}) of the window, fwd+bwd, "
+                     f"{n_gaussians} Gaussians projected per view", "seconds": round(dt, 2)}
+    if single_thread_pixels:
+        # the same on one host thread, on a smaller sample of the last view
+        c = cams[list(views)[-1]]
+        pix = synth.pixel_sample(rng, c.W, c.H, single_thread_pixels)
+        t0 = time.perf_counter()
+        o = oracle.render(P, sc["deg"], c, pix=pix, n_threads=1)
+        gr = np.sign(o["rgb"] - 0.5) / (3.0 * c.W * c.H)
+        gd = 0.1 * np.sign(o["depth"] - 10.0) / (c.W * c.H)
+        oracle.render_bwd(P, sc["deg"], c, gr, gd, pix=pix, n_threads=1)
+        dt1 = time.perf_counter() - t0
+        out["single_thread"] = {"value": round(len(pix) / dt1 / 1e6, 9), "unit": UNIT, "cores": 1,
+                                "sample": f"{len(pix)} pixels of view {list(views)[-1]}, fwd+bwd",
+                                "seconds": round(dt1, 2)}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -659,7 +678,8 @@ def main():
     else:
         out = run_ours(args, rank, world)
         if rank == 0 and not args.no_cpu_baseline and not args.quick:
-            out["cpu_baseline"] = cpu_baseline(args.cpu_pixels, views=[0, 5], n_gaussians=args.gaussians)
+            out["cpu_baseline"] = cpu_baseline(args.cpu_pixels, views=[0, 5], n_gaussians=args.gaussians,
+                                               single_thread_pixels=4)
     if rank == 0 and out is not None:
         print(json.dumps(out))
     if world > 1:
