@@ -285,6 +285,9 @@ dcg_status state_alloc(dcg_ctx* ctx, dcg_render_state* st) {
   CK(dmalloc(&st->touched, (size_t)st->cap_pairs));
   CK(dmalloc(&st->rect, (size_t)st->cap_pairs));
   CK(dmalloc(&st->grad2d, 3 * (size_t)st->cap_pairs));
+  // the 2D gradient slots are zero between backward passes: the blends add
+  // into them and the preprocess backward zeroes each slot it consumes
+  CK(cudaMemset(st->grad2d, 0, sizeof(float4) * 3 * (size_t)st->cap_pairs));
   CK(dmalloc(&st->list_a, (size_t)st->cap_pairs));
   CK(dmalloc(&st->list_b, (size_t)st->cap_pairs));
   CK(dmalloc(&st->inst_a, (size_t)st->cap_inst));

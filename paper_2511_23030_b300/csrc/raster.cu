@@ -11,19 +11,22 @@
 //   3. depth sort         stable LSD radix sort on the depth bits (the view
 //                         bits ride along; the tile sort separates views)
 //   4. instance emission  ordered scan of tiles-touched in depth order; each
-//                         instance is (warp-block mask, global tile id, pair)
+//                         instance is (half-block mask, global tile id, pair)
 //   5. tile sort          stable LSD radix sort on the tile id only: the depth
 //                         order inside a tile survives from step 3
 //   6. ranges             [start, end) per tile
-//   7. k_blend_fwd        persistent blocks take tiles from a device queue,
-//                         stage records in shared memory, blend front to back
+//   7. k_blend_fwd_h      persistent warps take (tile, warp block) items from a
+//                         device queue, compact each half-block's instances in
+//                         shared memory, blend front to back
 // Backward:
-//   8. k_blend_bwd        reverse traversal from each pixel's last contributor,
+//   8. k_blend_bwd_h      reverse traversal from each pixel's last contributor,
 //                         transmittance recomputed by division, per-Gaussian
-//                         2D gradients reduced per warp (transposed butterfly),
-//                         per block in shared memory, then vector atomics
+//                         2D gradients reduced per half-warp (transposed
+//                         butterfly), then atomics into the pair's 2D slot
 //   9. k_preprocess_bwd   one thread per Gaussian, all views: chain rule to the
-//                         parameters (written once) and the pose twist of each view
+//                         parameters (written once) and the pose twist of each
+//                         view; it zeroes the 2D slots it consumes, so they are
+//                         zero whenever a backward starts
 #include <algorithm>
 #include <cstdio>
 
@@ -436,9 +439,6 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_fwd(RasterArgs a) {
       a.rec[3 * vi + 0] = r0;
       a.rec[3 * vi + 1] = cn;
       a.rec[3 * vi + 2] = make_float4(col[0], col[1], col[2], z);
-      a.grad2d[3 * vi + 0] = make_float4(0.f, 0.f, 0.f, 0.f);
-      a.grad2d[3 * vi + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-      a.grad2d[3 * vi + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
 }
@@ -1801,6 +1801,12 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
         g2 = a.grad2d[3 * vi + 2];
         act = (g0.x != 0.f) | (g0.y != 0.f) | (g0.z != 0.f) | (g0.w != 0.f) | (g1.x != 0.f) | (g1.y != 0.f) |
               (g1.z != 0.f) | (g1.w != 0.f) | (g2.x != 0.f) | (g2.y != 0.f);
+        if (act) {  // consumed: the slot is zero again for the next backward
+          const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          a.grad2d[3 * vi + 0] = z4;
+          a.grad2d[3 * vi + 1] = z4;
+          a.grad2d[3 * vi + 2] = z4;
+        }
       }
       if (act) {
         const DevCam& c = a.cams[v];
