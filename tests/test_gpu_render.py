@@ -280,3 +280,22 @@ def test_loss_l1_matches_definition(ctx0, orc):
         assert np.allclose(dr[sl3].cpu().numpy(), gr, rtol=1e-6, atol=0)
         assert np.allclose(dd[sl].cpu().numpy(), gd, rtol=1e-6, atol=0)
     assert math.isclose(loss.item(), L, rel_tol=1e-5)
+
+
+def test_second_backward_of_one_forward_gives_the_same_gradients(ctx0b):
+    """The per-pair 2D gradient slots are consumed (and zeroed) by each
+    backward, so a second backward of the same forward does not accumulate
+    on top of the first."""
+    import torch
+
+    sc = synth.room_small(0)
+    P, cam = sc["params"], sc["cams"][0]
+    n = P.shape[0]
+    g_t, _, rgb, depth = render(ctx0b, P, 0, [cam])
+    rng = np.random.default_rng(7)
+    dr = torch.from_numpy(rng.normal(size=rgb.numel()).astype(np.float32)).cuda()
+    dd = torch.from_numpy((0.1 * rng.normal(size=depth.numel())).astype(np.float32)).cuda()
+    g1, p1 = backward(ctx0b, g_t, 0, n, dr, dd, 1)
+    g2, p2 = backward(ctx0b, g_t, 0, n, dr, dd, 1)
+    assert np.abs(g1).max() > 0
+    assert rel_l2(g2, g1) <= 1e-6 and rel_l2(p2, p1) <= 1e-6
