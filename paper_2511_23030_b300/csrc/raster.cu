@@ -780,7 +780,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
     const int x0 = tx * TW, y0 = ty * TH;
     const float x0f = (float)x0, y0f = (float)y0;
     const long long P = (long long)W * H;
-    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Sr[PPT], Sg[PPT], Sb[PPT], Sd[PPT];
+    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Dg[PPT];
     uint32_t last[PPT];
     const int px = x0 + lx;
     uint32_t mylast = 0;
@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
         gb[k] = dL_drgb[3 * c.pix_off + 2 * P + pix];
         gd[k] = dL_ddepth[c.pix_off + pix];
       }
-      Sr[k] = Sg[k] = Sb[k] = Sd[k] = 0.f;
+      Dg[k] = 0.f;
       mylast = max(mylast, last[k]);
     }
     const int warplast = (int)__reduce_max_sync(0xffffffffu, mylast);
@@ -861,12 +861,12 @@ __global__ void __launch_bounds__(256) k_blend_bwd(RasterArgs a, const u64* __re
                   acc[7] += wgt * gg[k];
                   acc[8] += wgt * gb[k];
                   acc[9] += wgt * gd[k];
-                  const float dal = T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] +
-                                            (cl.w - Sd[k]) * gd[k]);
-                  Sr[k] = al * cl.x + (1.f - al) * Sr[k];
-                  Sg[k] = al * cl.y + (1.f - al) * Sg[k];
-                  Sb[k] = al * cl.z + (1.f - al) * Sb[k];
-                  Sd[k] = al * cl.w + (1.f - al) * Sd[k];
+                  // dL/dalpha = T (c . g - D) with D = sum over channels of g times the
+                  // colour (and depth) composited behind this Gaussian; D follows the
+                  // same over-recursion as the colours themselves
+                  const float cg = cl.x * gr[k] + cl.y * gg[k] + cl.z * gb[k] + cl.w * gd[k];
+                  const float dal = T[k] * (cg - Dg[k]);
+                  Dg[k] = al * cg + (1.f - al) * Dg[k];
                   if (araw < kAlphaMax) {
                     // moments of dL/dalpha * G; the conic and opacity factors are applied per
                     // Gaussian in k_preprocess_bwd
@@ -1080,7 +1080,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
     const int x0 = tx * TW, y0 = ty * TH;
     const float x0f = (float)x0, y0f = (float)y0;
     const long long P = (long long)W * H;
-    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Sr[PPT], Sg[PPT], Sb[PPT], Sd[PPT];
+    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Dg[PPT];
     uint32_t last[PPT];
     const int px = x0 + lx;
     uint32_t mylast = 0;
@@ -1099,7 +1099,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
         gb[k] = dL_drgb[3 * c.pix_off + 2 * P + pix];
         gd[k] = dL_ddepth[c.pix_off + pix];
       }
-      Sr[k] = Sg[k] = Sb[k] = Sd[k] = 0.f;
+      Dg[k] = 0.f;
       mylast = max(mylast, last[k]);
     }
     const int warplast = (int)__reduce_max_sync(0xffffffffu, mylast);
@@ -1154,12 +1154,12 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
                 acc[7] += wgt * gg[k];
                 acc[8] += wgt * gb[k];
                 acc[9] += wgt * gd[k];
-                const float dal = T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] +
-                                          (cl.w - Sd[k]) * gd[k]);
-                Sr[k] = al * cl.x + (1.f - al) * Sr[k];
-                Sg[k] = al * cl.y + (1.f - al) * Sg[k];
-                Sb[k] = al * cl.z + (1.f - al) * Sb[k];
-                Sd[k] = al * cl.w + (1.f - al) * Sd[k];
+                // dL/dalpha = T (c . g - D) with D = sum over channels of g times the
+                // colour (and depth) composited behind this Gaussian; D follows the
+                // same over-recursion as the colours themselves
+                const float cg = cl.x * gr[k] + cl.y * gg[k] + cl.z * gb[k] + cl.w * gd[k];
+                const float dal = T[k] * (cg - Dg[k]);
+                Dg[k] = al * cg + (1.f - al) * Dg[k];
                 if (araw < kAlphaMax) {
                   // moments of dL/dalpha * G; the conic and opacity factors are applied per
                   // Gaussian in k_preprocess_bwd
@@ -1405,7 +1405,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_h(RasterArgs a, const u64* __
     const int x0 = tx * TW, y0 = ty * TH;
     const float x0f = (float)x0, y0f = (float)y0;
     const long long P = (long long)W * H;
-    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Sr[PPT], Sg[PPT], Sb[PPT], Sd[PPT];
+    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Dg[PPT];
     uint32_t last[PPT];
     const int px = x0 + lx;
     uint32_t mylast = 0;
@@ -1424,7 +1424,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_h(RasterArgs a, const u64* __
         gb[k] = dL_drgb[3 * c.pix_off + 2 * P + pix];
         gd[k] = dL_ddepth[c.pix_off + pix];
       }
-      Sr[k] = Sg[k] = Sb[k] = Sd[k] = 0.f;
+      Dg[k] = 0.f;
       mylast = max(mylast, last[k]);
     }
     // per half: the largest contributor count of its pixels
@@ -1511,12 +1511,12 @@ __global__ void __launch_bounds__(256) k_blend_bwd_h(RasterArgs a, const u64* __
                 acc[7] += wgt * gg[k];
                 acc[8] += wgt * gb[k];
                 acc[9] += wgt * gd[k];
-                const float dal = T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] +
-                                          (cl.w - Sd[k]) * gd[k]);
-                Sr[k] = al * cl.x + (1.f - al) * Sr[k];
-                Sg[k] = al * cl.y + (1.f - al) * Sg[k];
-                Sb[k] = al * cl.z + (1.f - al) * Sb[k];
-                Sd[k] = al * cl.w + (1.f - al) * Sd[k];
+                // dL/dalpha = T (c . g - D) with D = sum over channels of g times the
+                // colour (and depth) composited behind this Gaussian; D follows the
+                // same over-recursion as the colours themselves
+                const float cg = cl.x * gr[k] + cl.y * gg[k] + cl.z * gb[k] + cl.w * gd[k];
+                const float dal = T[k] * (cg - Dg[k]);
+                Dg[k] = al * cg + (1.f - al) * Dg[k];
                 if (araw < kAlphaMax) {
                   const float gG = dal * G;
                   const float gx = gG * dx, gy = gG * dy;
@@ -1596,7 +1596,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_slots(RasterArgs a, const u64
     const int x0 = tx * TW, y0 = ty * TH;
     const float x0f = (float)x0, y0f = (float)y0;
     const long long P = (long long)W * H;
-    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Sr[PPT], Sg[PPT], Sb[PPT], Sd[PPT];
+    float T[PPT], gr[PPT], gg[PPT], gb[PPT], gd[PPT], Dg[PPT];
     uint32_t last[PPT];
     const int px = x0 + lx;
     uint32_t mylast = 0;
@@ -1615,7 +1615,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_slots(RasterArgs a, const u64
         gb[k] = dL_drgb[3 * c.pix_off + 2 * P + pix];
         gd[k] = dL_ddepth[c.pix_off + pix];
       }
-      Sr[k] = Sg[k] = Sb[k] = Sd[k] = 0.f;
+      Dg[k] = 0.f;
       mylast = max(mylast, last[k]);
     }
     const int warplast = (int)__reduce_max_sync(0xffffffffu, mylast);
@@ -1674,12 +1674,12 @@ __global__ void __launch_bounds__(256) k_blend_bwd_slots(RasterArgs a, const u64
                   acc[7] += wgt * gg[k];
                   acc[8] += wgt * gb[k];
                   acc[9] += wgt * gd[k];
-                  const float dal = T[k] * ((cl.x - Sr[k]) * gr[k] + (cl.y - Sg[k]) * gg[k] + (cl.z - Sb[k]) * gb[k] +
-                                            (cl.w - Sd[k]) * gd[k]);
-                  Sr[k] = al * cl.x + (1.f - al) * Sr[k];
-                  Sg[k] = al * cl.y + (1.f - al) * Sg[k];
-                  Sb[k] = al * cl.z + (1.f - al) * Sb[k];
-                  Sd[k] = al * cl.w + (1.f - al) * Sd[k];
+                  // dL/dalpha = T (c . g - D) with D = sum over channels of g times the
+                  // colour (and depth) composited behind this Gaussian; D follows the
+                  // same over-recursion as the colours themselves
+                  const float cg = cl.x * gr[k] + cl.y * gg[k] + cl.z * gb[k] + cl.w * gd[k];
+                  const float dal = T[k] * (cg - Dg[k]);
+                  Dg[k] = al * cg + (1.f - al) * Dg[k];
                   if (araw < kAlphaMax) {
                     // moments of dL/dalpha * G; the conic and opacity factors are applied per
                     // Gaussian in k_preprocess_bwd
