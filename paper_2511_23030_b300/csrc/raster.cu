@@ -1317,30 +1317,29 @@ __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __
         const float bx = __fmul_rn(cq.y, dx);
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-          if (T[k] > 0.f) {
-            ev += real;
-            const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
-            const float p = blend_power(sx, bx, cq.z, dy);
-            if (p >= kPMin) {
-              const float al = fminf(kAlphaMax, __fmul_rn(cq.w, ex2_approx(p)));
-              if (al >= kAlphaMin) {
-                const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, al));
-                if (Tn < kTMin) {
-                  Tf[k] = T[k];
-                  T[k] = 0.f;
-                } else {
-                  const float4 cl = s_col[w][h][j];
-                  const float wgt = al * T[k];
-                  Cr[k] += wgt * cl.x;
-                  Cg[k] += wgt * cl.y;
-                  Cb[k] += wgt * cl.z;
-                  Dz[k] += wgt * cl.w;
-                  T[k] = Tn;
-                  last[k] = s_rel[w][h][j] + 1;
-                  ++nb;
-                }
-              }
-            }
+          // the support, alpha and termination tests as predicates (one
+          // branch, for the compositing itself)
+          const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
+          const float p = blend_power(sx, bx, cq.z, dy);
+          const float al = fminf(kAlphaMax, __fmul_rn(cq.w, ex2_approx(p)));
+          const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, al));
+          const bool live = T[k] > 0.f;
+          const bool hit = live && p >= kPMin && al >= kAlphaMin;
+          const bool stop = hit && Tn < kTMin;
+          ev += live ? real : 0u;
+          if (stop) {
+            Tf[k] = T[k];
+            T[k] = 0.f;
+          } else if (hit) {
+            const float4 cl = s_col[w][h][j];
+            const float wgt = al * T[k];
+            Cr[k] += wgt * cl.x;
+            Cg[k] += wgt * cl.y;
+            Cb[k] += wgt * cl.z;
+            Dz[k] += wgt * cl.w;
+            T[k] = Tn;
+            last[k] = s_rel[w][h][j] + 1;
+            ++nb;
           }
         }
       }
@@ -1495,39 +1494,39 @@ __global__ void __launch_bounds__(256) k_blend_bwd_h(RasterArgs a, const u64* __
         const float bx = __fmul_rn(cq.y, dx);
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-          if (r < (int)last[k]) {
-            const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
-            const float p = blend_power(sx, bx, cq.z, dy);
-            if (p >= kPMin) {
-              const float G = ex2_approx(p);
-              const float araw = __fmul_rn(cq.w, G);
-              const float al = fminf(kAlphaMax, araw);
-              if (al >= kAlphaMin) {
-                any = true;
-                const float4 cl = s_col[w][h][e];
-                T[k] = __fdividef(T[k], 1.f - al);
-                const float wgt = al * T[k];
-                acc[6] += wgt * gr[k];
-                acc[7] += wgt * gg[k];
-                acc[8] += wgt * gb[k];
-                acc[9] += wgt * gd[k];
-                // dL/dalpha = T (c . g - D) with D = sum over channels of g times the
-                // colour (and depth) composited behind this Gaussian; D follows the
-                // same over-recursion as the colours themselves
-                const float cg = cl.x * gr[k] + cl.y * gg[k] + cl.z * gb[k] + cl.w * gd[k];
-                const float dal = T[k] * (cg - Dg[k]);
-                Dg[k] = al * cg + (1.f - al) * Dg[k];
-                if (araw < kAlphaMax) {
-                  const float gG = dal * G;
-                  const float gx = gG * dx, gy = gG * dy;
-                  acc[5] += gG;
-                  acc[0] += gx;
-                  acc[1] += gy;
-                  acc[2] += gx * dx;
-                  acc[3] += gx * dy;
-                  acc[4] += gy * dy;
-                }
-              }
+          // the support and alpha tests as predicates (one branch)
+          const float dy = __fsub_rn((float)(ly + 4 * k), xy.y);
+          const float p = blend_power(sx, bx, cq.z, dy);
+          const float G = ex2_approx(p);
+          const float araw = __fmul_rn(cq.w, G);
+          const float al = fminf(kAlphaMax, araw);
+          if (r < (int)last[k] && p >= kPMin && al >= kAlphaMin) {
+            any = true;
+            const float4 cl = s_col[w][h][e];
+            T[k] = __fdividef(T[k], 1.f - al);
+            const float wgt = al * T[k];
+            acc[6] += wgt * gr[k];
+            acc[7] += wgt * gg[k];
+            acc[8] += wgt * gb[k];
+            acc[9] += wgt * gd[k];
+            // dL/dalpha = T (c . g - D) with D = sum over channels of g times the
+            // colour (and depth) composited behind this Gaussian; D follows the
+            // same over-recursion as the colours themselves
+            const float cg = cl.x * gr[k] + cl.y * gg[k] + cl.z * gb[k] + cl.w * gd[k];
+            const float dal = T[k] * (cg - Dg[k]);
+            Dg[k] = al * cg + (1.f - al) * Dg[k];
+            // moments of dL/dalpha G (none through a clamped alpha); the
+            // conic and opacity factors are applied per Gaussian in
+            // k_preprocess_bwd
+            if (araw < kAlphaMax) {
+              const float gG = dal * G;
+              const float gx = gG * dx, gy = gG * dy;
+              acc[5] += gG;
+              acc[0] += gx;
+              acc[1] += gy;
+              acc[2] += gx * dx;
+              acc[3] += gx * dy;
+              acc[4] += gy * dy;
             }
           }
         }
