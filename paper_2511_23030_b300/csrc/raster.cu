@@ -1308,8 +1308,12 @@ __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __
         s_con[w][1][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncwarp();
+      // evaluations counted per batch: a pixel live at its start is evaluated
+      // by every real step until it terminates
+      unsigned nev[PPT];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) nev[k] = T[k] > 0.f ? (unsigned)cmine : 0u;
       for (int j = 0; j < cmax; ++j) {
-        const unsigned real = j < cmine ? 1u : 0u;
         const float2 xy = s_xy[w][h][j];
         const float4 cq = s_con[w][h][j];
         const float dx = __fsub_rn((float)lx, xy.x);
@@ -1326,10 +1330,10 @@ __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __
           const bool live = T[k] > 0.f;
           const bool hit = live && p >= kPMin && al >= kAlphaMin;
           const bool stop = hit && Tn < kTMin;
-          ev += live ? real : 0u;
           if (stop) {
             Tf[k] = T[k];
             T[k] = 0.f;
+            nev[k] = (unsigned)j + 1u;
           } else if (hit) {
             const float4 cl = s_col[w][h][j];
             const float wgt = al * T[k];
@@ -1346,7 +1350,10 @@ __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __
       __syncwarp();
       alive = 0;
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) alive |= T[k] > 0.f;
+      for (int k = 0; k < PPT; ++k) {
+        alive |= T[k] > 0.f;
+        ev += nev[k];
+      }
     }
     {
       const unsigned wev = __reduce_add_sync(0xffffffffu, ev), wnb = __reduce_add_sync(0xffffffffu, nb);
