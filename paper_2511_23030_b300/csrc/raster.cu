@@ -1261,13 +1261,15 @@ __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __
       alive |= T[k] > 0.f;
     }
     const uint2 rg = a.ranges[gt];
+    u64 key_next = rg.x + lane < rg.y ? inst[rg.x + lane] : 0ull;  // the next batch's keys, loaded ahead
     for (unsigned b0 = rg.x; b0 < rg.y; b0 += 32) {
       const unsigned am = __ballot_sync(0xffffffffu, alive);
       if (am == 0u) break;
       const unsigned idx = b0 + lane;
+      const u64 key = key_next;
+      key_next = idx + 32 < rg.y ? inst[idx + 32] : 0ull;
       unsigned hb = 0, vi = 0;
       if (idx < rg.y) {
-        const u64 key = inst[idx];
         vi = pair_of_inst(key);
         hb = half_bits(key, wb);
         if ((am & 0xffffu) == 0u) hb &= 2u;
