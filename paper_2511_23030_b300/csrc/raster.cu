@@ -1261,25 +1261,43 @@ __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __
       alive |= T[k] > 0.f;
     }
     const uint2 rg = a.ranges[gt];
-    u64 key_next = rg.x + lane < rg.y ? inst[rg.x + lane] : 0ull;  // the next batch's keys, loaded ahead
+    // software pipeline over the batches: keys two batches ahead, records
+    // of the instances that reach this warp block one batch ahead
+    u64 key2 = rg.x + 32 + lane < rg.y ? inst[rg.x + 32 + lane] : 0ull;
+    unsigned hbn = 0, vin = 0;
+    float4 r0n = make_float4(0.f, 0.f, 0.f, 0.f), cnn = r0n, cln = r0n;
+    if (rg.x + lane < rg.y) {
+      const u64 k0 = inst[rg.x + lane];
+      vin = pair_of_inst(k0);
+      hbn = half_bits(k0, wb);
+      if (hbn) {
+        r0n = a.rec[3ull * vin + 0];
+        cnn = a.rec[3ull * vin + 1];
+        cln = a.rec[3ull * vin + 2];
+      }
+    }
     for (unsigned b0 = rg.x; b0 < rg.y; b0 += 32) {
       const unsigned am = __ballot_sync(0xffffffffu, alive);
       if (am == 0u) break;
       const unsigned idx = b0 + lane;
-      const u64 key = key_next;
-      key_next = idx + 32 < rg.y ? inst[idx + 32] : 0ull;
-      unsigned hb = 0, vi = 0;
-      if (idx < rg.y) {
-        vi = pair_of_inst(key);
-        hb = half_bits(key, wb);
-        if ((am & 0xffffu) == 0u) hb &= 2u;
-        if ((am >> 16) == 0u) hb &= 1u;
+      unsigned hb = hbn;
+      const float4 r0 = r0n, cn = cnn, cl = cln;
+      {  // the next batch's records, the batch after next's keys
+        const u64 k1 = key2;
+        key2 = idx + 64 < rg.y ? inst[idx + 64] : 0ull;
+        hbn = idx + 32 < rg.y ? half_bits(k1, wb) : 0u;
+        vin = pair_of_inst(k1);
+        if (hbn) {
+          r0n = a.rec[3ull * vin + 0];
+          cnn = a.rec[3ull * vin + 1];
+          cln = a.rec[3ull * vin + 2];
+        }
       }
+      if ((am & 0xffffu) == 0u) hb &= 2u;
+      if ((am >> 16) == 0u) hb &= 1u;
       const unsigned mL = __ballot_sync(0xffffffffu, hb & 1u), mR = __ballot_sync(0xffffffffu, hb & 2u);
       if (hb) {
-        const float4 r0 = a.rec[3ull * vi + 0];
         const float2 xy = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
-        const float4 cn = a.rec[3ull * vi + 1], cl = a.rec[3ull * vi + 2];
         const unsigned rel = idx - rg.x;
         if (hb & 1u) {
           const int sl = __popc(mL & lt);
