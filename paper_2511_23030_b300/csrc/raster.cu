@@ -334,7 +334,7 @@ __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, flo
 // 1. preprocess
 // ============================================================================
 template <int DEG>
-__global__ void __launch_bounds__(256, 3) k_preprocess_fwd(RasterArgs a) {
+__global__ void __launch_bounds__(256, 4) k_preprocess_fwd(RasterArgs a) {
   const long long n = a.n;
   constexpr int D = (DEG + 1) * (DEG + 1);
   // this thread's SH coefficients, loaded once at its first visible view:
