@@ -1816,10 +1816,15 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
     S12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
     S22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
     float dSig[6] = {0, 0, 0, 0, 0, 0};  // dS + dS^T accumulated over views: entries 00 01 02 11 12 22
+    // the views this Gaussian reaches, all loads in flight together
+    unsigned tmask = 0;
+#pragma unroll
+    for (int v = 0; v < kMaxViewsApi; ++v)
+      if (live && v < a.V && a.touched[(long long)v * n + i] != 0u) tmask |= 1u << v;
     for (int v = 0; v < a.V; ++v) {
       float pose[6] = {0, 0, 0, 0, 0, 0};
       const long long vi = (long long)v * n + i;
-      bool act = live && a.touched[vi] != 0u;
+      bool act = (tmask >> v) & 1u;
       float4 g0 = make_float4(0, 0, 0, 0), g1 = g0, g2 = g0;
       if (act) {
         g0 = a.grad2d[3 * vi + 0];
