@@ -1821,15 +1821,30 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
 #pragma unroll
     for (int v = 0; v < kMaxViewsApi; ++v)
       if (live && v < a.V && a.touched[(long long)v * n + i] != 0u) tmask |= 1u << v;
+    // the 2D gradients of the next reached view are loaded one view ahead
+    float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, n2 = n0;
+    if (tmask) {
+      const long long vi0 = (long long)(__ffs(tmask) - 1) * n + i;
+      n0 = a.grad2d[3 * vi0 + 0];
+      n1 = a.grad2d[3 * vi0 + 1];
+      n2 = a.grad2d[3 * vi0 + 2];
+    }
     for (int v = 0; v < a.V; ++v) {
       float pose[6] = {0, 0, 0, 0, 0, 0};
       const long long vi = (long long)v * n + i;
       bool act = (tmask >> v) & 1u;
       float4 g0 = make_float4(0, 0, 0, 0), g1 = g0, g2 = g0;
       if (act) {
-        g0 = a.grad2d[3 * vi + 0];
-        g1 = a.grad2d[3 * vi + 1];
-        g2 = a.grad2d[3 * vi + 2];
+        g0 = n0;
+        g1 = n1;
+        g2 = n2;
+        const unsigned rest = tmask & ~((2u << v) - 1u);
+        if (rest) {
+          const long long vn = (long long)(__ffs(rest) - 1) * n + i;
+          n0 = a.grad2d[3 * vn + 0];
+          n1 = a.grad2d[3 * vn + 1];
+          n2 = a.grad2d[3 * vn + 2];
+        }
         act = (g0.x != 0.f) | (g0.y != 0.f) | (g0.z != 0.f) | (g0.w != 0.f) | (g1.x != 0.f) | (g1.y != 0.f) |
               (g1.z != 0.f) | (g1.w != 0.f) | (g2.x != 0.f) | (g2.y != 0.f);
         if (act) {  // consumed: the slot is zero again for the next backward
