@@ -94,7 +94,8 @@ typedef struct {
                               0 (default): parameters only */
 } dcg_config;
 
-/* Fill *cfg with defaults (s = 4 m, degree 3, budget 6 M, 8 views ...). */
+/* Fill *cfg with defaults (s = 4 m, degree 3, budget 6 M, 8 views, 16x16
+ * tiles with the half-warp blends (stage 16) ...). */
 void dcg_config_default(dcg_config* cfg);
 
 /* Create a context on the current CUDA device; allocates the chunk table,
