@@ -441,10 +441,10 @@ TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profile
 RASTER_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2511_23030_b300", "csrc", "raster.cu")
 
 
-def measured_traffic(phase: str, launch: str, n_inst: int):
-    """DRAM bytes per launch of the phase's kernel from the committed ncu capture, scaled from the
-    captured workload to this one by instances; None unless the capture is of this launch shape and
-    of the rasteriser source as it is now."""
+def measured_traffic(phase: str, launch: str, n_inst: int, field: str = "dram_bytes_per_launch"):
+    """A per-launch figure of the phase's kernel from the committed ncu capture (DRAM bytes, or warp
+    instructions), scaled from the captured workload to this one by instances; None unless the
+    capture is of this launch shape and of the rasteriser source as it is now."""
     import hashlib
 
     try:
@@ -453,9 +453,9 @@ def measured_traffic(phase: str, launch: str, n_inst: int):
     except (OSError, ValueError):
         return None
     k = rec.get("kernels", {}).get(phase)
-    if not k or rec.get("raster_cu_sha256") != sha or rec.get("launch") != launch:
+    if not k or field not in k or rec.get("raster_cu_sha256") != sha or rec.get("launch") != launch:
         return None
-    return int(k["dram_bytes_per_launch"] * n_inst / rec["instances"])
+    return int(k[field] * n_inst / rec["instances"])
 
 
 def roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, launch=""):
@@ -486,11 +486,19 @@ def roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, launch
         flop_per_pair = 22 if dom == "blend_fwd" else 55
         peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12
         ach = n_blend * flop_per_pair / t / 1e12
-        return {"kernel": dom, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(ach / peak, 4), "traffic": measured_traffic(dom, launch, n_inst),
-                "hbm_gbs": round(algo_bytes[dom] / t / 1e9, 1),
-                "hbm_frac": round(algo_bytes[dom] / t / 1e9 / hbm, 4), "peak_source": f"derived (sm_max {sm_max} MHz)",
-                "hbm_by_phase": by_phase}
+        out = {"kernel": dom, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+               "frac": round(ach / peak, 4), "traffic": measured_traffic(dom, launch, n_inst),
+               "hbm_gbs": round(algo_bytes[dom] / t / 1e9, 1),
+               "hbm_frac": round(algo_bytes[dom] / t / 1e9 / hbm, 4), "peak_source": f"derived (sm_max {sm_max} MHz)",
+               "hbm_by_phase": by_phase}
+        # what bounds it: the warp-instruction issue rate (148 SMs x 4 schedulers x 1 per clock) against
+        # the instructions ncu counted per launch (scaled by instances)
+        inst = measured_traffic(dom, launch, n_inst, "warp_instructions_per_launch")
+        if inst is not None:
+            ipeak = 148 * 4 * sm_max * 1e6
+            out["issue"] = {"warp_instructions": inst, "achieved_ginst_s": round(inst / t / 1e9, 1),
+                            "peak_ginst_s": round(ipeak / 1e9, 1), "frac": round(inst / t / ipeak, 4)}
+        return out
     ach = algo_bytes[dom] / t / 1e9
     return {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(ach / hbm, 4), "traffic": measured_traffic(dom, launch, n_inst), "peak_source": src,
