@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--bwd", default="warp", choices=["warp", "slots"], help="backward gradient accumulation")
     ap.add_argument("--length", type=float, default=5000.0, help="corridor: metres of road (1 m per frame)")
     ap.add_argument("--per-m", type=int, default=8000, help="corridor: Gaussians per metre (40M per 5 km)")
+    ap.add_argument("--propose-every", type=int, default=4, help="corridor: frames between prefetch proposals")
     ap.add_argument("--cpu-pixels", type=int, default=48, help="oracle sample: pixels per sampled view")
     return ap.parse_args()
 
@@ -625,7 +626,8 @@ def run_corridor(args):
     t_gen = time.perf_counter() - t0
     out = {"workload": "corridor", "metric": "out-of-core mapping Mpix/s, stall and hidden chunk-load share",
            "unit": UNIT, "config": {"length_m": args.length, "gaussians": N, "view": f"{W}x{H}", "chunk_m": s,
-                                    "budget_gaussians": budget, "frames": len(cams)},
+                                    "budget_gaussians": budget, "frames": len(cams),
+                                    "propose_every": args.propose_every},
            "train": {"samples": n, "positive_frac": round(pos, 4), "loss_per_epoch": [round(v, 4) for v in losses],
                      "seconds": round(t_train, 2)}, "setup_seconds": round(t_gen, 1), "modes": {}}
     for mode in ("none", "cv", "mlp"):
@@ -652,7 +654,7 @@ def run_corridor(args):
             dcg.dcg_render_bwd(ctx, dr, dd, grads, None)
 
         out["config"]["chunks"] = dcg.dcg_chunk_count(ctx)
-        r = prefetch.run_corridor(ctx, cams, mode, s, 1.5 * zfar, pm=pm, render=render)
+        r = prefetch.run_corridor(ctx, cams, mode, s, 1.5 * zfar, pm=pm, render=render, every=args.propose_every)
         dcg.dcg_sync(ctx)
         r["ms_per_step"] = round(r["ms"] / r["steps"], 4)
         r["value"] = round(W * H * r["steps"] / (r["ms"] / 1e3) / 1e6, 2)

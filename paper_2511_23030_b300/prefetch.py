@@ -194,11 +194,13 @@ def constant_velocity_cams(cams, t, ahead=(5, 10, 15, 20)):
 
 
 def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = None, threshold=0.3, render=None,
-                 warm=1):
+                 warm=1, every=1):
     """Map along `cams` one keyframe per step: cull, gather (synchronous loads
     of missing chunks), `render(g, n, cam)`, scatter, then propose prefetches
-    ('none' | 'cv' | 'mlp').  The first `warm` steps (the cold start, which no
-    predictor can see coming) are run but not counted.  Returns statistics."""
+    ('none' | 'cv' | 'mlp') every `every` steps (a proposal covers the next
+    20 frames, so it need not be renewed each frame).  The first `warm` steps
+    (the cold start, which no predictor can see coming) are run but not
+    counted.  Returns statistics."""
     import torch
 
     info = dcg.dcg_chunk_info(ctx)
@@ -233,10 +235,11 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
         # this frame renders (they depend only on poses and residency)
         prop = []
         pending_scores = None
-        if mode == "mlp":
+        propose = t % every == 0
+        if mode == "mlp" and propose:
             cand = dcg.dcg_chunks_near(ctx, cam_centre(cam), radius, only_nonresident=True)
             pending_scores = pm.score_async(pose_history(cams, t), cand, chunk_size, side)
-        elif mode == "cv":
+        elif mode == "cv" and propose:
             fut = set()
             for fc in constant_velocity_cams(cams, t):
                 fut.update(int(c) for c in dcg.dcg_cull_chunks(ctx, [fc], stream=side))
