@@ -317,7 +317,8 @@ def run_ours(args, rank, world):
     mpix_e = npix * K * world / (ms_e / 1e3) / 1e6
     phases = {k: round(v[0] / K, 4) for k, v in prof.items()}
     n_act = n_all
-    roof = roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, f"{tile[0]}x{tile[1]}/{stage}")
+    roof = roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, f"{tile[0]}x{tile[1]}/{stage}",
+                    n_views=len(cams))
     out = {
         "metric": METRIC, "value": round(mpix_b, 2), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(ms_b / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -459,19 +460,21 @@ def measured_traffic(phase: str, launch: str, n_inst: int, field: str = "dram_by
     return int(k[field] * n_inst / rec["instances"])
 
 
-def roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, launch=""):
+def roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, launch="", n_views=8):
     """Dominant phase with its algorithmic bytes (or FLOPs) per launch over its live duration."""
     hbm, sm_max, src = peaks()
     rec = 48
     algo_bytes = {
-        # parameters once per call; per visible pair: record + depth + rect + zeroed 2D gradient; flags all pairs
-        "preprocess_fwd": 4 * F * n_act + n_vis * (rec + 4 + 8 + 48) + 4 * 8 * n_act,
+        # parameters once per call; per visible pair the record; per pair depth, tiles touched, rectangle
+        "preprocess_fwd": 4 * F * n_act + n_vis * rec + 16 * n_views * n_act,
         # key write/read per visible pair and per instance (4 + 2 radix passes, 3 touches each), emission,
         # ranges and masks (instance read and write)
         "binning": 8 * 3 * n_vis * 4 + 8 * 3 * n_inst * 2 + 8 * n_inst + 12 * n_vis + 16 * n_inst,
         "blend_fwd": n_inst * (8 + rec) + npix * (4 * 4 + 8),
         "blend_bwd": n_inst * (8 + rec + 40) + npix * (4 * 4 + 8),
-        "preprocess_bwd": 4 * F * n_act + n_vis * 48 + 4 * F * n_act,
+        # parameters read and gradients written once; per visible pair the 2D gradient slot read and
+        # zeroed; per pair the tiles-touched flag
+        "preprocess_bwd": 4 * F * n_act + n_vis * 2 * 48 + 4 * F * n_act + 4 * n_views * n_act,
         "gather": 2 * 4 * F * n_act,
         "scatter": 2 * 4 * F * n_act,
     }
