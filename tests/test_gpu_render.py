@@ -299,3 +299,36 @@ def test_second_backward_of_one_forward_gives_the_same_gradients(ctx0b):
     g2, p2 = backward(ctx0b, g_t, 0, n, dr, dd, 1)
     assert np.abs(g1).max() > 0
     assert rel_l2(g2, g1) <= 1e-6 and rel_l2(p2, p1) <= 1e-6
+
+
+def test_capacity_errors_leave_the_context_usable():
+    """More instances than configured: the forward clamps its lists (no
+    access past the capacity) and the next dcg_sync reports
+    DCG_ERR_CAPACITY; the context then renders a scene that fits.  More
+    pixels than configured is a capacity error and more views an argument
+    error, both returned at once."""
+    sc = synth.room_small(0)
+    P, cam = sc["params"], sc["cams"][0]
+    n = P.shape[0]
+    ctx = make_ctx(deg=0, n_max=n, views=1, pixels=cam.W * cam.H, inst=2000)
+    try:
+        g_t = planar(P)
+        g = dcg.gaussians(g_t, 0)
+        rgb, depth = out_buffers([cam])
+        dcg.dcg_render_fwd(ctx, g, n, [cam], rgb, depth)
+        with pytest.raises(dcg.DcgError) as e:
+            dcg.dcg_sync(ctx)
+        assert e.value.status == 6
+        small = P[:50].copy()
+        _, _, rgb_s, _ = render(ctx, small, 0, [cam])  # syncs: no error left over
+        assert float(rgb_s.abs().sum()) > 0
+        big = synth.Camera(cam.fx, cam.fy, cam.cx, cam.cy, 2 * cam.W, cam.H, cam.Tcw, cam.znear, cam.zfar)
+        rgb2, depth2 = out_buffers([big])
+        with pytest.raises(dcg.DcgError) as e:
+            dcg.dcg_render_fwd(ctx, g, n, [big], rgb2, depth2)
+        assert e.value.status == 6
+        with pytest.raises(dcg.DcgError) as e:
+            dcg.dcg_render_fwd(ctx, g, n, [cam, cam], rgb2, depth2)
+        assert e.value.status == 1
+    finally:
+        dcg.dcg_destroy(ctx)
