@@ -26,10 +26,12 @@ __global__ void k_part_scan(u64* part, int P, u64* total_out) {
 
 // Peer mask of a lane's digit within the warp, from one ballot per digit bit
 // (stable ranking without match_any); lanes with !valid never match a valid lane.
-__device__ __forceinline__ unsigned digit_peers(unsigned d, int nbits, bool valid) {
+template <int NB>
+__device__ __forceinline__ unsigned digit_peers(unsigned d, bool valid) {
   const unsigned vb = __ballot_sync(0xffffffffu, valid);
   unsigned peers = valid ? vb : ~vb;
-  for (int b = 0; b < nbits; ++b) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
     const bool bit = (d >> b) & 1u;
     const unsigned bb = __ballot_sync(0xffffffffu, bit);
     peers &= bit ? bb : ~bb;
@@ -102,8 +104,10 @@ constexpr int kSortWarps = 8;
 constexpr int kSortRounds = 8;
 constexpr int kSortChunk = kSortWarps * 32 * kSortRounds;
 
+template <int NB>
 __global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, const u64* n_ptr, int shift,
-                                                       int nbits, const uint32_t* hist, const uint32_t* totals) {
+                                                       const uint32_t* hist, const uint32_t* totals) {
+  constexpr int nbits = NB;
   __shared__ uint32_t wcnt[kSortWarps][256];
   __shared__ uint32_t run[256];
   __shared__ uint32_t cstart[256];
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const u64* in, u64* out, 
       const bool valid = i < end;
       const unsigned d = valid ? (unsigned)((key[r] >> shift) & mask) : 0u;
       dig[r] = valid ? d : 256u;
-      const unsigned peers = digit_peers(d, nbits, valid);
+      const unsigned peers = digit_peers<NB>(d, valid);
       const unsigned rank = __popc(peers & lt);
       const unsigned base = valid ? wcnt[w][d] : 0u;
       __syncwarp();
@@ -186,7 +190,16 @@ u64* radix_sort(u64* a, u64* b, const u64* n_ptr, int lo, int hi, uint32_t* hist
     const int nb = min(8, hi - sh);
     k_radix_hist<<<P, 256, 0, s>>>(src, n_ptr, sh, nb, hist);
     k_radix_scan<<<256, 256, 0, s>>>(hist, P, totals);
-    k_radix_scatter<<<P, 256, 0, s>>>(src, dst, n_ptr, sh, nb, hist, totals);
+    switch (nb) {  // the digit width as a compile-time constant (unrolled ranking)
+      case 1: k_radix_scatter<1><<<P, 256, 0, s>>>(src, dst, n_ptr, sh, hist, totals); break;
+      case 2: k_radix_scatter<2><<<P, 256, 0, s>>>(src, dst, n_ptr, sh, hist, totals); break;
+      case 3: k_radix_scatter<3><<<P, 256, 0, s>>>(src, dst, n_ptr, sh, hist, totals); break;
+      case 4: k_radix_scatter<4><<<P, 256, 0, s>>>(src, dst, n_ptr, sh, hist, totals); break;
+      case 5: k_radix_scatter<5><<<P, 256, 0, s>>>(src, dst, n_ptr, sh, hist, totals); break;
+      case 6: k_radix_scatter<6><<<P, 256, 0, s>>>(src, dst, n_ptr, sh, hist, totals); break;
+      case 7: k_radix_scatter<7><<<P, 256, 0, s>>>(src, dst, n_ptr, sh, hist, totals); break;
+      default: k_radix_scatter<8><<<P, 256, 0, s>>>(src, dst, n_ptr, sh, hist, totals); break;
+    }
     u64* t = src;
     src = dst;
     dst = t;
