@@ -133,13 +133,10 @@ __global__ void k_part_emit(const u64* n_ptr, u64 n_host, CountF f, EmitF e, con
 }
 
 // ----------------------------------------------------------------------------
-// LSD radix sort pass over u64 keys on digit [shift, shift+nbits), nbits <= 8.
-// hist layout: [256][P] digit-major (per-block counts, then per-digit
-// exclusive prefixes over blocks), followed by the 256 digit totals.
-__global__ void k_radix_hist(const u64* keys, const u64* n_ptr, int shift, int nbits, uint32_t* hist);
-__global__ void k_radix_scan(uint32_t* hist, int P, uint32_t* totals);
-__global__ void k_radix_scatter(const u64* in, u64* out, const u64* n_ptr, int shift, int nbits,
-                                const uint32_t* hist, const uint32_t* totals);
+// LSD radix sort passes over u64 keys on digits [shift, shift+nbits),
+// nbits <= 8 (kernels in sort_scan.cu).  hist layout: [256][P] digit-major
+// (per-block counts, then per-digit exclusive prefixes over blocks),
+// followed by the 256 digit totals.
 
 // Host driver: stable sort of keys[0..*n_ptr) on bits [lo, hi), ping-pong
 // between a and b; returns the buffer holding the result.  `hist` holds
