@@ -475,7 +475,7 @@ struct InstCount {
 // One thread per visible pair (in depth order) writes its instances: the
 // tiles of its rectangle that the support ellipse reaches (row spans, the
 // same as the count in k_preprocess_fwd), each with the mask of the tile's
-// warp blocks the ellipse reaches (band extents once per tile row).
+// half blocks the ellipse reaches (band extents once per tile row).
 struct InstEmit {
   const u64* list;
   const short4* rect;
@@ -564,7 +564,7 @@ struct TileLayout {
 // Forward blend.  One block per tile (taken from a device queue); each of
 // its 8 warps owns an 8 x WY pixel block and walks the tile's depth-sorted
 // list on its own: 32 instances per step, one per lane, are tested against
-// the warp block, survivors are compacted in order into a per-warp shared
+// the warp block (either half bit), survivors are compacted in order into a per-warp shared
 // buffer and blended by all lanes.  A warp stops when its pixels are done;
 // there is no block barrier inside a tile.
 template <int TW, int TH, int STAGE>
