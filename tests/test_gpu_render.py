@@ -332,3 +332,38 @@ def test_capacity_errors_leave_the_context_usable():
         assert e.value.status == 1
     finally:
         dcg.dcg_destroy(ctx)
+
+
+@pytest.mark.parametrize("deg", [1, 2])
+def test_sixteen_views_batched_equal_single_and_oracle(deg, orc):
+    """The largest batch the ABI takes (16 views of uneven sizes) in the
+    default half-warp launch: every view equals its single-view render bit for
+    bit, and sampled pixels of the last view match the oracle (SH degrees 1
+    and 2, which the other tests do not render)."""
+    P3, cams = _room_views(n=20_000, n_views=16, seed=3)
+    F = 11 + 3 * (deg + 1) ** 2
+    P = np.ascontiguousarray(P3[:, :F])
+    rng = np.random.default_rng(deg)
+    for c in cams:
+        W = int(rng.integers(40, 200))
+        H = int(rng.integers(30, 150))
+        c.W, c.H, c.cx, c.cy = W, H, W / 2, H / 2
+        c.fx = c.fy = 0.8 * W
+    ctx = make_ctx(deg=deg, n_max=P.shape[0], views=16, pixels=sum(c.W * c.H for c in cams), stage=16)
+    try:
+        _, _, rgb_b, depth_b = render(ctx, P, deg, cams)
+        batched = split_views(rgb_b, depth_b, cams)
+        for v, c in enumerate(cams):
+            _, _, rgb_s, depth_s = render(ctx, P, deg, [c])
+            (rs, ds), = split_views(rgb_s, depth_s, [c])
+            assert np.array_equal(rs, batched[v][0]) and np.array_equal(ds, batched[v][1]), v
+        c = cams[-1]
+        pix = synth.pixel_sample(rng, c.W, c.H, 200)
+        o = orc.render(P, deg, c, pix=pix)
+        rv, dv = batched[-1]
+        st = dcg.dcg_state_read(ctx, None, 1, P.shape[0], c.W * c.H)
+        T = st["T"].reshape(c.H, c.W)
+        check_image(o, rv[:, pix[:, 1], pix[:, 0]].T.astype(np.float64), dv[pix[:, 1], pix[:, 0]].astype(np.float64),
+                    T[pix[:, 1], pix[:, 0]].astype(np.float64), f"16 views deg {deg}")
+    finally:
+        dcg.dcg_destroy(ctx)
