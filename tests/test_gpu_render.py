@@ -338,8 +338,9 @@ def test_capacity_errors_leave_the_context_usable():
 def test_sixteen_views_batched_equal_single_and_oracle(deg, orc):
     """The largest batch the ABI takes (16 views of uneven sizes) in the
     default half-warp launch: every view equals its single-view render bit for
-    bit, and sampled pixels of the last view match the oracle (SH degrees 1
-    and 2, which the other tests do not render)."""
+    bit, and sampled pixels of the last view and the gradients of a loss
+    seeded on them match the oracle (SH degrees 1 and 2, which the other
+    tests do not render)."""
     P3, cams = _room_views(n=20_000, n_views=16, seed=3)
     F = 11 + 3 * (deg + 1) ** 2
     P = np.ascontiguousarray(P3[:, :F])
@@ -365,5 +366,24 @@ def test_sixteen_views_batched_equal_single_and_oracle(deg, orc):
         T = st["T"].reshape(c.H, c.W)
         check_image(o, rv[:, pix[:, 1], pix[:, 0]].T.astype(np.float64), dv[pix[:, 1], pix[:, 0]].astype(np.float64),
                     T[pix[:, 1], pix[:, 0]].astype(np.float64), f"16 views deg {deg}")
+        # gradients at this degree, seeded on the sampled pixels of the last view
+        import torch
+
+        g_t, _, _, _ = render(ctx, P, deg, [c])
+        gr = rng.normal(size=(len(pix), 3))
+        gd = rng.normal(size=len(pix)) * 0.1
+        gr[o["flags"] != 0] = 0
+        gd[o["flags"] != 0] = 0
+        full_r = np.zeros((3, c.H, c.W), np.float32)
+        full_d = np.zeros((c.H, c.W), np.float32)
+        full_r[:, pix[:, 1], pix[:, 0]] = gr.T
+        full_d[pix[:, 1], pix[:, 0]] = gd
+        grad, pose = backward(ctx, g_t, deg, P.shape[0], torch.from_numpy(full_r.reshape(-1)).cuda(),
+                              torch.from_numpy(full_d.reshape(-1)).cuda(), 1)
+        og, opose = orc.render_bwd(P, deg, c, gr.astype(np.float32).astype(np.float64),
+                                   gd.astype(np.float32).astype(np.float64), pix=pix)
+        for name, sl in GROUPS.items():
+            assert rel_l2(grad[:, sl], og[:, sl]) <= GRAD_TOL, (name, deg)
+        assert rel_l2(pose[0], opose) <= GRAD_TOL
     finally:
         dcg.dcg_destroy(ctx)
