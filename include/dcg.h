@@ -337,7 +337,9 @@ dcg_status dcg_render_fwd(dcg_ctx* ctx, const dcg_gaussians* g, int64_t n, const
  * the forward, overwritten) and dL_dpose (dev, [n_views, 6], overwritten; may
  * be NULL) out.  The pose gradient is w.r.t. the left perturbation
  * Tcw <- exp(xi^) Tcw, xi = (v, w): a camera-frame point moves by v + w x t.
- * Transmittance is recomputed front-from-back from the stored final value. */
+ * Transmittance is recomputed front-from-back from the stored final value.
+ * A forward may be followed by several backward calls (other loss seeds):
+ * each computes its gradient afresh. */
 dcg_status dcg_render_bwd(dcg_ctx* ctx, dcg_render_state* state, const float* dL_drgb, const float* dL_ddepth,
                           dcg_gaussians* grads, float* dL_dpose, void* stream);
 
