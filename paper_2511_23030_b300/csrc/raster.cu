@@ -450,27 +450,48 @@ struct VisCount {
   const uint32_t* touched;
   __device__ u64 operator()(u64 k) const { return touched[k] ? 1ull : 0ull; }
 };
+// Depth keys: [count | view | depth bits | index].  The bits above the view
+// carry min(tiles touched, cmax) when the key has room (cmax > 0), so that
+// the instance-offset scan reads the key alone; cmax itself means "look the
+// count up".  Only the depth bits are sorted; the rest rides along.
+struct DepthKey {
+  int ib;       // index bits
+  int vb;       // view bits
+  int cs;       // shift of the count field
+  unsigned cmax;
+  __device__ u64 pair(u64 key, long long n) const {
+    const u64 v = (key >> (31 + ib)) & ((1ull << vb) - 1ull);
+    const u64 i = key & ((1ull << ib) - 1);
+    return v * (u64)n + i;
+  }
+  __device__ int view(u64 key) const { return (int)((key >> (31 + ib)) & ((1ull << vb) - 1ull)); }
+};
 struct VisEmit {
   const float* depth;
+  const uint32_t* touched;
   u64* list;
   long long n;
-  int ib;
+  DepthKey dk;
   __device__ void operator()(u64 k, u64 off, u64) const {
     const u64 v = k / (u64)n, i = k - v * (u64)n;
-    list[off] = (v << (31 + ib)) | ((u64)__float_as_uint(depth[k]) << ib) | i;
+    u64 key = (v << (31 + dk.ib)) | ((u64)__float_as_uint(depth[k]) << dk.ib) | i;
+    if (dk.cmax) key |= (u64)min(touched[k], dk.cmax) << dk.cs;
+    list[off] = key;
   }
 };
-__device__ __forceinline__ u64 pair_of_key(u64 key, int ib, long long n) {
-  const u64 v = key >> (31 + ib);
-  const u64 i = key & ((1ull << ib) - 1);
-  return v * (u64)n + i;
-}
 struct InstCount {
   const u64* list;
   const uint32_t* touched;
   long long n;
-  int ib;
-  __device__ u64 operator()(u64 s) const { return touched[pair_of_key(list[s], ib, n)]; }
+  DepthKey dk;
+  __device__ u64 operator()(u64 s) const {
+    const u64 key = list[s];
+    if (dk.cmax) {
+      const unsigned c = (unsigned)(key >> dk.cs);
+      if (c < dk.cmax) return c;
+    }
+    return touched[dk.pair(key, n)];
+  }
 };
 // One thread per visible pair (in depth order) writes its instances: the
 // tiles of its rectangle that the support ellipse reaches (row spans, the
@@ -482,14 +503,14 @@ struct InstEmit {
   const float4* rec;
   const DevCam* cams;
   long long n;
-  int ib;
+  DepthKey dk;
   int tw, th;
   u64* inst;
   u64 cap;
   __device__ void operator()(u64 s, u64 off, u64) const {
     const u64 key = list[s];
-    const u64 vi = pair_of_key(key, ib, n);
-    const int v = (int)(key >> (31 + ib));
+    const u64 vi = dk.pair(key, n);
+    const int v = dk.view(key);
     const short4 r = rect[vi];
     const float4 r0 = rec[3 * vi + 0], cn = rec[3 * vi + 1];
     const bool whole = (r.z - r.x + 1) * (r.w - r.y + 1) > kTightMax;
@@ -2191,7 +2212,14 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   a.prof(PH_PRE_FWD, false, st);
   a.prof(PH_BINNING, true, st);
   // compaction into depth keys
-  part_scan_emit(nullptr, (u64)pairs, VisCount{a.touched}, VisEmit{a.depth, a.list_a, a.n, a.idx_bits}, a.part, a.P,
+  DepthKey dk;
+  dk.ib = a.idx_bits;
+  dk.vb = 0;
+  while ((1 << dk.vb) < a.V) ++dk.vb;
+  dk.cs = 31 + dk.ib + dk.vb;
+  const int cbits = 64 - dk.cs;
+  dk.cmax = cbits >= 4 ? (1u << (cbits < 20 ? cbits : 20)) - 1u : 0u;
+  part_scan_emit(nullptr, (u64)pairs, VisCount{a.touched}, VisEmit{a.depth, a.touched, a.list_a, a.n, dk}, a.part, a.P,
                  &a.counters->n_vis, st);
   // Only the 31 depth bits are sorted: the view bits above them ride along,
   // since the stable tile sort below separates the views anyway.
@@ -2200,11 +2228,11 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   // instance offsets by an ordered scan (the free list buffer holds them),
   // then the emission itself, one thread per visible pair with no barriers
   u64* offs = ls == a.list_a ? a.list_b : a.list_a;
-  part_scan_emit(&a.counters->n_vis, 0, InstCount{ls, a.touched, a.n, a.idx_bits}, InstOffset{offs}, a.part, a.P,
+  part_scan_emit(&a.counters->n_vis, 0, InstCount{ls, a.touched, a.n, dk}, InstOffset{offs}, a.part, a.P,
                  &a.counters->n_inst, st);
   k_emit_at<<<a.num_sms * 8, 256, 0, st>>>(
       &a.counters->n_vis, offs,
-      InstEmit{ls, a.rect, a.rec, a.cams, a.n, a.idx_bits, a.tile_w, a.tile_h, a.inst_a, (u64)a.cap_inst});
+      InstEmit{ls, a.rect, a.rec, a.cams, a.n, dk, a.tile_w, a.tile_h, a.inst_a, (u64)a.cap_inst});
   k_clamp_inst<<<1, 1, 0, st>>>(a.counters, (u64)a.cap_inst, a.errword);
   int tb = 1;
   while ((1ll << tb) < (long long)a.n_tiles) ++tb;
