@@ -34,13 +34,14 @@ def _direct(ctx, g, n, cams, b, trgb, tdep, lam, deg, lam_s):
     dcg.dcg_sync(ctx)
 
 
+@pytest.mark.parametrize("stage", [128, 16])
 @pytest.mark.parametrize("lam_s", [0.0, 0.2])
-def test_window_graph_equals_direct_calls(lam_s):
+def test_window_graph_equals_direct_calls(lam_s, stage):
     import torch
 
     P, cams, sc = _scene()
     n, F = P.shape
-    ctx = make_ctx(deg=3, n_max=n, views=8, pixels=sum(c.W * c.H for c in cams))
+    ctx = make_ctx(deg=3, n_max=n, views=8, pixels=sum(c.W * c.H for c in cams), stage=stage)
     try:
         g_t = planar(P)
         g = dcg.gaussians(g_t, 3)
