@@ -24,7 +24,7 @@ def planar(params_aos: np.ndarray, stride: int | None = None):
 
 
 def make_ctx(deg=3, n_max=600_000, views=8, pixels=None, inst=1 << 24, chunk=4.0, budget=None, host=None,
-             tile=(16, 16), stage=128, dfar=100.0, page=2048, max_chunks=8192, flags=0, moments=0):
+             tile=(16, 16), stage=16, dfar=100.0, page=2048, max_chunks=8192, flags=0, moments=0):
     pixels = 8 * 1241 * 376 if pixels is None else pixels
     budget = n_max if budget is None else budget
     host = n_max if host is None else host

@@ -36,8 +36,8 @@ def ctx0():
     dcg.dcg_destroy(c)
 
 
-BWD_VARIANTS = {"warp": dict(flags=0), "slots": dict(flags=1), "warp_per_block": dict(flags=0, stage=32),
-                "half_warp": dict(flags=0, stage=16)}
+BWD_VARIANTS = {"warp": dict(flags=0, stage=128), "slots": dict(flags=1, stage=128),
+                "warp_per_block": dict(flags=0, stage=32), "half_warp": dict(flags=0, stage=16)}
 
 
 @pytest.fixture(scope="module", params=list(BWD_VARIANTS))
