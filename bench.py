@@ -316,7 +316,7 @@ def run_ours(args, rank, world):
     mpix_b = npix * K * world / (ms_b / 1e3) / 1e6
     mpix_p = npix * K_p * world / (ms_p / 1e3) / 1e6 if ms_p else None
     mpix_e = npix * K * world / (ms_e / 1e3) / 1e6 if ms_e else None
-    phases = {k: round(v[0] / K, 4) for k, v in prof.items()}
+    phases = {k: round(v[0] / K, 4) for k, v in prof.items() if k not in ("log_sample", "loop_closure")}
     n_act = n_all
     roof = roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, f"{tile[0]}x{tile[1]}/{stage}",
                     n_views=len(cams))
@@ -346,6 +346,8 @@ def run_ours(args, rank, world):
     if not args.quick:
         out["train_step"] = train_leg(args, sc, cfg, tile, stage, trgb, tdep, rgb, depth, dr, dd, loss, grads, grads_t,
                                       dpose, npix, K, W)
+        out["log_sample"] = sampling_leg(sc, npix, trgb, rgb, depth, K, W)
+        out["loop_closure"] = loop_closure_leg(sc, max(4, K // 4))
     return out
 
 
@@ -436,6 +438,149 @@ def train_leg(args, sc, cfg, tile, stage, trgb, tdep, rgb, depth, dr, dd, loss, 
                                                                  "unit": "GB/s", "frac": round(gbs / hbm, 4),
                                                                  "bytes_per_launch": int(28 * F * n),
                                                                  "peak_source": src}}
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
+SAMPLE_FRACTION = 0.05  # sampling leg: kappa of Eq. 1 is set so that about this share of pixels is sampled
+
+
+def sampling_leg(sc, npix, trgb, rgb, depth, K, W):
+    """LoG penalty sampling of Eq. 1 over the window's 8 views (the targets against the images the
+    window rendered) and back-projection of the sampled pixels at the rendered depth.  The paper
+    gives no kappa; it is set to SAMPLE_FRACTION / mean(P_s) over the window (from one pass that
+    writes P_s and samples nothing), so about that share of pixels is sampled.  Device time
+    from the library's phase timers; algorithmic bytes per pixel: both images (24 B), the uniform
+    (4 B), the flag written and read twice by the ordered compaction (12 B); per sample the index
+    written and read (8 B), its depth and colour (16 B) and the new Gaussian (4 F B)."""
+    import torch
+
+    from paper_2511_23030_b300 import dcg
+
+    cams, deg = sc["cams"], sc["deg"]
+    F = sc["params"].shape[1]
+    offs = np.cumsum([0] + [c.W * c.H for c in cams])
+    pmax = max(c.W * c.H for c in cams)
+    cfg = dcg.config(sh_degree=deg, max_active=1024, max_views=1, max_pixels=pmax, max_instances=1 << 20,
+                     chunk_size=sc["chunk_size"], device_budget=1024, host_capacity=1024, dfar=60.0)
+    ctx = dcg.dcg_create(cfg)
+    try:
+        u = torch.rand(npix, generator=torch.Generator(device="cuda").manual_seed(7), device="cuda")
+        idx = torch.zeros(pmax, dtype=torch.int32, device="cuda")
+        out = torch.zeros((F, pmax), device="cuda")
+        hbm, _, src = peaks()
+        ps = torch.zeros(npix, device="cuda")
+        for v, c in enumerate(cams):
+            o, Pv = int(offs[v]), c.W * c.H
+            dcg.dcg_log_sample(ctx, trgb[3 * o: 3 * (o + Pv)], rgb[3 * o: 3 * (o + Pv)], c.W, c.H, 0.0, u[o: o + Pv],
+                               idx, ps_out=ps[o: o + Pv])
+        mean_ps = float(ps.mean())
+        kappa = SAMPLE_FRACTION / mean_ps if mean_ps > 0 else 0.0
+        del ps
+
+        def window():
+            ns = 0
+            for v, c in enumerate(cams):
+                o, Pv = int(offs[v]), c.W * c.H
+                k = dcg.dcg_log_sample(ctx, trgb[3 * o: 3 * (o + Pv)], rgb[3 * o: 3 * (o + Pv)], c.W, c.H, kappa,
+                                       u[o: o + Pv], idx)
+                dcg.dcg_backproject(ctx, idx, k, depth[o: o + Pv], trgb[3 * o: 3 * (o + Pv)], c, -2.0, out)
+                ns += k
+            return ns
+
+        for _ in range(W):
+            window()
+        torch.cuda.synchronize()
+        dcg.dcg_profile(ctx, True)
+        dcg.dcg_profile_read(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ns = 0
+        for _ in range(K):
+            ns = window()
+        e1.record()
+        torch.cuda.synchronize()
+        prof = dcg.dcg_profile_read(ctx)
+        dcg.dcg_profile(ctx, False)
+        dev_ms = prof["log_sample"][0] / K
+        api_ms = e0.elapsed_time(e1) / K
+        algo = 40 * npix + ns * (8 + 16 + 4 * F)
+        gbs = algo / (dev_ms / 1e3) / 1e9
+        return {"what": "Eq. 1 LoG penalty sampling of the 8 window views (targets vs rendered) + back-projection",
+                "pixels": npix, "kappa": round(kappa, 4), "mean_penalty": round(mean_ps, 5),
+                "samples_per_window": int(ns), "sampled_fraction": round(ns / npix, 4),
+                "device_ms_per_window": round(dev_ms, 4), "api_ms_per_window": round(api_ms, 4),
+                "value": round(npix / (dev_ms / 1e3) / 1e6, 1), "unit": "Mpix/s",
+                "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(gbs / hbm, 4), "bytes_per_window": int(algo), "peak_source": src},
+                "launches_per_window": 5 * len(cams)}
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
+def _rigid(deg_z, t):
+    a = np.deg2rad(deg_z)
+    C = np.eye(4, dtype=np.float32)
+    C[:2, :2] = [[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]]
+    C[:3, 3] = t
+    return C
+
+
+def loop_closure_leg(sc, K):
+    """Loop-closure correction (Sec. III-F) of the window map: two keyframes' Gaussians move with
+    their pose corrections and are redistributed over the chunks; corrections alternate with their
+    inverses so the map stays near its start.  Wall time per call (host re-bucketing included) and
+    the device phases; algorithmic device bytes per gathered Gaussian: the transform (10 floats read,
+    7 written), the keys (12 B read, 8 B written), the row permutation and the page writes (each
+    4 F B read and written)."""
+    import time
+
+    import torch
+
+    from paper_2511_23030_b300 import dcg
+
+    P, cams, deg = sc["params"], sc["cams"], sc["deg"]
+    n_all, F = P.shape
+    cfg = dcg.config(sh_degree=deg, max_active=n_all + 1024, max_views=8, max_pixels=max(c.W * c.H for c in cams),
+                     max_instances=1 << 20, chunk_size=sc["chunk_size"], device_budget=n_all + (n_all >> 1),
+                     host_capacity=2 * n_all, dfar=60.0)
+    ctx = dcg.dcg_create(cfg)
+    try:
+        g_t = torch.from_numpy(np.ascontiguousarray(P.T)).cuda()
+        dcg.dcg_chunk_table_update(ctx, g_t, n_all)
+        del g_t
+        kfs = [cams[0], cams[3]]
+        fwd = [_rigid(0.5, (0.2, -0.1, 0.05)), _rigid(-0.4, (-0.15, 0.1, 0.02))]
+        inv = [np.linalg.inv(C).astype(np.float32) for C in fwd]
+        hbm, _, src = peaks()
+        dcg.dcg_loop_closure(ctx, kfs, fwd)  # warm-up (allocations, host tier pages)
+        dcg.dcg_loop_closure(ctx, kfs, inv)
+        dcg.dcg_sync(ctx)
+        dcg.dcg_profile(ctx, True)
+        dcg.dcg_profile_read(ctx)
+        wall, nts, nms, ngs = [], [], [], []
+        for r in range(K):
+            counts = dcg.dcg_chunk_info(ctx)["counts"]
+            ngs.append(int(counts[dcg.dcg_cull_chunks(ctx, kfs)].sum()))  # the union the call gathers
+            dcg.dcg_sync(ctx)
+            t0 = time.perf_counter()
+            nt, nm = dcg.dcg_loop_closure(ctx, kfs, fwd if r % 2 == 0 else inv)
+            wall.append((time.perf_counter() - t0) * 1e3)
+            nts.append(nt)
+            nms.append(nm)
+        prof = dcg.dcg_profile_read(ctx)
+        dcg.dcg_profile(ctx, False)
+        dev_ms = prof["loop_closure"][0] / K
+        gather_ms = (prof["gather"][0] + prof["stall"][0]) / K
+        n_g = float(np.mean(ngs))
+        algo = int(n_g * (40 + 28 + 20 + 16 * F))
+        gbs = algo / (dev_ms / 1e3) / 1e9
+        return {"what": "loop-closure correction + chunk redistribution of the 2-keyframe union (synchronous call)",
+                "gaussians": n_all, "gathered": int(n_g), "transformed": int(np.mean(nts)), "moved": int(np.mean(nms)),
+                "wall_ms": round(float(np.median(wall)), 3), "device_ms": round(dev_ms, 4),
+                "gather_ms": round(gather_ms, 4),
+                "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(gbs / hbm, 4), "bytes_per_call": int(algo), "peak_source": src}}
     finally:
         dcg.dcg_destroy(ctx)
 

@@ -513,7 +513,10 @@ enum {
   DCG_PH_PRE_BWD = 7,   /* chain rule to the parameters and the pose */
   DCG_PH_SCATTER = 8,
   DCG_PH_STALL = 9,     /* compute stream idle in dcg_gather_active, waiting for chunk copies */
-  DCG_PH_COUNT = 10
+  DCG_PH_SAMPLE = 10,   /* dcg_log_sample (LoG penalty, flags, ordered compaction) and dcg_backproject */
+  DCG_PH_LOOP = 11,     /* device work of dcg_loop_closure: cull, transform and keys, row permutation
+                           and page writes (its gather is timed as DCG_PH_GATHER / DCG_PH_STALL) */
+  DCG_PH_COUNT = 12
 };
 dcg_status dcg_profile(dcg_ctx* ctx, int32_t enable);
 dcg_status dcg_profile_read(dcg_ctx* ctx, float* ms, int32_t* counts);

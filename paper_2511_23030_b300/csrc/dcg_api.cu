@@ -163,6 +163,10 @@ struct dcg_ctx {
 
 namespace {
 
+static_assert((int)PH_COUNT == (int)DCG_PH_COUNT && (int)PH_SAMPLE == (int)DCG_PH_SAMPLE &&
+                  (int)PH_LOOP == (int)DCG_PH_LOOP && (int)PH_STALL == (int)DCG_PH_STALL,
+              "phase numbering of the ABI and the library differ");
+
 void prof_mark(void* h, int phase, bool begin, cudaStream_t s) {
   dcg_ctx* ctx = (dcg_ctx*)h;
   if (!ctx->prof_on || ctx->ev_next >= ctx->ev_pool.size()) return;
@@ -1074,8 +1078,10 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   // 1. frustum cull of every affected keyframe (pose before the correction)
   std::memcpy(ctx->h_cullcams, kf, sizeof(dcg_camera) * K);
   CK(cudaMemcpyAsync(ctx->d_cullcams, ctx->h_cullcams, sizeof(dcg_camera) * K, cudaMemcpyHostToDevice, s));
+  hook(ctx)(PH_LOOP, true, s);
   launch_cull(ctx->d_coords, C, ctx->d_cullcams, K, ctx->cfg.chunk_size, ctx->cfg.dfar, ctx->d_lcmask, ctx->d_vis,
               ctx->d_list, ctx->d_nlist, s);
+  hook(ctx)(PH_LOOP, false, s);
   CK(cudaGetLastError());
   int32_t nl = 0;
   CK(cudaMemcpyAsync(&nl, ctx->d_nlist, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1129,9 +1135,11 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   uint32_t* d_flags = st->touched;  // render scratch, at least max_active entries
   u64* d_keys = st->list_a;
   const int64_t S = ctx->cfg.max_active;
+  hook(ctx)(PH_LOOP, true, s);
   launch_loop_transform(ctx->d_active, S, n, ctx->d_lcseg, ctx->d_lcsegc, nl, ctx->d_lcmask, C, ctx->d_lcview, K,
                         d_flags, ctx->num_sms, s);
   launch_chunk_keys(ctx->d_active, 1, S, n, ctx->cfg.chunk_size, d_keys, ctx->d_errword, ctx->num_sms, s);
+  hook(ctx)(PH_LOOP, false, s);
   CK(cudaGetLastError());
   std::vector<uint32_t> flags((size_t)n);
   std::vector<uint64_t> keys((size_t)n);
@@ -1214,7 +1222,9 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   CK(cudaMallocAsync((void**)&d_tmp, sizeof(float) * (size_t)Fs * (size_t)n, s));
   CK(cudaMallocAsync((void**)&d_perm, sizeof(long long) * (size_t)n, s));
   CK(cudaMemcpyAsync(d_perm, perm.data(), sizeof(long long) * (size_t)n, cudaMemcpyHostToDevice, s));
+  hook(ctx)(PH_LOOP, true, s);
   launch_permute_rows(ctx->d_active, S, d_tmp, n, d_perm, n, Fs, ctx->num_sms, s);
+  hook(ctx)(PH_LOOP, false, s);
   // gathered chunks: new counts and pages, content written from the permuted rows
   CK(cudaEventSynchronize(ctx->ev_desc));
   int nd = 0;
@@ -1253,7 +1263,9 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   }
   if (nd > 0) CK(cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(long long) * 3 * nd, cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(ctx->ev_desc, s));
+  hook(ctx)(PH_LOOP, true, s);
   launch_page_copy(false, ctx->d_pool, ctx->page_g, Fs, 0, Fs, ctx->d_desc, nd, d_tmp, n, s);
+  hook(ctx)(PH_LOOP, false, s);
   CK(cudaGetLastError());
   // Gaussians leaving for chunks that were not gathered: appended in the host tier
   const int64_t n_out = n - n_kept;
@@ -1343,8 +1355,10 @@ dcg_status dcg_log_sample(dcg_ctx* ctx, const float* image, const float* rendere
     return fail(ctx, DCG_ERR_CAPACITY, "image larger than max_pixels");
   cudaStream_t s = (cudaStream_t)stream;
   dcg_render_state* st = ctx->st0;
+  hook(ctx)(PH_SAMPLE, true, s);
   launch_log_sample(image, rendered, W, H, kappa, u, ps_out, ctx->d_lsflags, idx_out, max_out, st->part, st->P,
                     ctx->d_lscount, s);
+  hook(ctx)(PH_SAMPLE, false, s);
   CK(cudaGetLastError());
   u64 cnt = 0;
   CK(cudaMemcpyAsync(&cnt, ctx->d_lscount, sizeof(u64), cudaMemcpyDeviceToHost, s));
@@ -1360,8 +1374,10 @@ dcg_status dcg_backproject(dcg_ctx* ctx, const int32_t* idx, int32_t n, const fl
   if (!ctx || n < 0 || (n > 0 && (!idx || !depth || !image || !params_out)) || !cam || stride < n)
     return fail(ctx, DCG_ERR_ARG, "bad arguments");
   if (cam->W <= 0 || cam->H <= 0 || !(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(ctx, DCG_ERR_ARG, "bad camera");
+  hook(ctx)(PH_SAMPLE, true, (cudaStream_t)stream);
   launch_backproject(idx, n, depth, image, cam->W, cam->H, view_of(*cam), opacity_logit, ctx->F, params_out, stride,
                      ctx->num_sms, (cudaStream_t)stream);
+  hook(ctx)(PH_SAMPLE, false, (cudaStream_t)stream);
   CK(cudaGetLastError());
   return DCG_OK;
 }

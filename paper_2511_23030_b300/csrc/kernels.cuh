@@ -15,7 +15,7 @@ constexpr int kMaxViewsApi = 16;  // views per render call
 
 // Phases timed by the optional profiler (dcg_profile); same order as in dcg.h.
 enum Phase { PH_CULL = 0, PH_GATHER, PH_PRE_FWD, PH_BINNING, PH_BLEND_FWD, PH_LOSS, PH_BLEND_BWD, PH_PRE_BWD,
-             PH_SCATTER, PH_STALL, PH_COUNT };
+             PH_SCATTER, PH_STALL, PH_SAMPLE, PH_LOOP, PH_COUNT };
 
 // Kernel launches issued by the library in this process (for launch accounting).
 extern unsigned long long g_launches;

@@ -121,7 +121,7 @@ _SIGS = {
 }
 
 PHASES = ["cull", "gather", "preprocess_fwd", "binning", "blend_fwd", "loss", "blend_bwd", "preprocess_bwd", "scatter",
-          "stall"]
+          "stall", "log_sample", "loop_closure"]
 
 
 def lib():

@@ -74,7 +74,13 @@ def test_loop_closure_matches_reference():
         kfs = [sc["cams"][0], sc["cams"][3]]
         corrs = [_corr("z", 2.0, (0.8, -0.4, 0.3)), _corr("x", 1.5, (-0.6, 0.5, 0.2))]
         before = _read_all(ctx, F)
+        dcg.dcg_profile(ctx, True)
         nt, nm = dcg.dcg_loop_closure(ctx, kfs, corrs)
+        prof = dcg.dcg_profile_read(ctx)
+        dcg.dcg_profile(ctx, False)
+        # device intervals: cull, transform + keys, permutation, page writes (the batch load is timed
+        # as a gather, here none: the active buffer already holds the union's chunks)
+        assert prof["loop_closure"][1] == 4 and prof["loop_closure"][0] > 0
         dcg.dcg_flush(ctx)
         after = _read_all(ctx, F)
         want, wt, wm = lc.loop_closure(before, sc["chunk_size"], 60.0, kfs, corrs)

@@ -31,7 +31,12 @@ def test_penalty_and_samples_match_reference(W, H):
         ti, tr, tu = (torch.from_numpy(a.reshape(-1)).cuda() for a in (img, ren, u))
         ps = torch.zeros(W * H, device="cuda")
         idx = torch.zeros(W * H, dtype=torch.int32, device="cuda")
+        dcg.dcg_profile(ctx, True)
         n = dcg.dcg_log_sample(ctx, ti, tr, W, H, 3.0, tu, idx, ps_out=ps)
+        prof = dcg.dcg_profile_read(ctx)
+        dcg.dcg_profile(ctx, False)
+        assert prof["log_sample"][1] == 1 and prof["log_sample"][0] > 0  # one timed interval
+        assert all(v[1] == 0 for k, v in prof.items() if k != "log_sample")
         want = ls.penalty(img, ren).reshape(-1)
         got = ps.cpu().numpy().astype(np.float64)
         assert np.abs(got - want).max() <= 1e-5 * want.max() + 1e-6
