@@ -446,47 +446,38 @@ SAMPLE_FRACTION = 0.05  # sampling leg: kappa of Eq. 1 is set so that about this
 
 
 def sampling_leg(sc, npix, trgb, rgb, depth, K, W):
-    """LoG penalty sampling of Eq. 1 over the window's 8 views (the targets against the images the
-    window rendered) and back-projection of the sampled pixels at the rendered depth.  The paper
-    gives no kappa; it is set to SAMPLE_FRACTION / mean(P_s) over the window (from one pass that
-    writes P_s and samples nothing), so about that share of pixels is sampled.  Device time
-    from the library's phase timers; algorithmic bytes per pixel: both images (24 B), the uniform
-    (4 B), the flag written and read twice by the ordered compaction (12 B); per sample the index
-    written and read (8 B), its depth and colour (16 B) and the new Gaussian (4 F B)."""
+    """LoG penalty sampling of Eq. 1 over the window's 8 views in one call (the targets against the
+    images the window rendered) and back-projection of the sampled pixels at the rendered depth in
+    another.  The paper gives no kappa; it is set to SAMPLE_FRACTION / mean(P_s) over the window
+    (from one pass that writes P_s and samples nothing), so about that share of pixels is sampled.
+    Device time from the library's phase timers; algorithmic bytes per pixel: both images (24 B),
+    the uniform (4 B), the flag written and read twice by the ordered compaction (12 B); per sample
+    the index written and read (8 B), its depth and colour (16 B) and the new Gaussian (4 F B)."""
     import torch
 
     from paper_2511_23030_b300 import dcg
 
     cams, deg = sc["cams"], sc["deg"]
     F = sc["params"].shape[1]
-    offs = np.cumsum([0] + [c.W * c.H for c in cams])
-    pmax = max(c.W * c.H for c in cams)
-    cfg = dcg.config(sh_degree=deg, max_active=1024, max_views=1, max_pixels=pmax, max_instances=1 << 20,
+    cap = npix // 4
+    cfg = dcg.config(sh_degree=deg, max_active=1024, max_views=1, max_pixels=npix, max_instances=1 << 20,
                      chunk_size=sc["chunk_size"], device_budget=1024, host_capacity=1024, dfar=60.0)
     ctx = dcg.dcg_create(cfg)
     try:
         u = torch.rand(npix, generator=torch.Generator(device="cuda").manual_seed(7), device="cuda")
-        idx = torch.zeros(pmax, dtype=torch.int32, device="cuda")
-        out = torch.zeros((F, pmax), device="cuda")
+        idx = torch.zeros(cap, dtype=torch.int32, device="cuda")
+        out = torch.zeros((F, cap), device="cuda")
         hbm, _, src = peaks()
         ps = torch.zeros(npix, device="cuda")
-        for v, c in enumerate(cams):
-            o, Pv = int(offs[v]), c.W * c.H
-            dcg.dcg_log_sample(ctx, trgb[3 * o: 3 * (o + Pv)], rgb[3 * o: 3 * (o + Pv)], c.W, c.H, 0.0, u[o: o + Pv],
-                               idx, ps_out=ps[o: o + Pv])
+        dcg.dcg_log_sample_views(ctx, cams, trgb, rgb, 0.0, u, idx, ps_out=ps)
         mean_ps = float(ps.mean())
         kappa = SAMPLE_FRACTION / mean_ps if mean_ps > 0 else 0.0
         del ps
 
         def window():
-            ns = 0
-            for v, c in enumerate(cams):
-                o, Pv = int(offs[v]), c.W * c.H
-                k = dcg.dcg_log_sample(ctx, trgb[3 * o: 3 * (o + Pv)], rgb[3 * o: 3 * (o + Pv)], c.W, c.H, kappa,
-                                       u[o: o + Pv], idx)
-                dcg.dcg_backproject(ctx, idx, k, depth[o: o + Pv], trgb[3 * o: 3 * (o + Pv)], c, -2.0, out)
-                ns += k
-            return ns
+            n, _ = dcg.dcg_log_sample_views(ctx, cams, trgb, rgb, kappa, u, idx)
+            dcg.dcg_backproject_views(ctx, idx, n, depth, trgb, cams, -2.0, out)
+            return n
 
         for _ in range(W):
             window()
@@ -506,14 +497,15 @@ def sampling_leg(sc, npix, trgb, rgb, depth, K, W):
         api_ms = e0.elapsed_time(e1) / K
         algo = 40 * npix + ns * (8 + 16 + 4 * F)
         gbs = algo / (dev_ms / 1e3) / 1e9
-        return {"what": "Eq. 1 LoG penalty sampling of the 8 window views (targets vs rendered) + back-projection",
+        return {"what": "Eq. 1 LoG penalty sampling of the 8 window views in one call (targets vs rendered) "
+                        "+ back-projection",
                 "pixels": npix, "kappa": round(kappa, 4), "mean_penalty": round(mean_ps, 5),
                 "samples_per_window": int(ns), "sampled_fraction": round(ns / npix, 4),
                 "device_ms_per_window": round(dev_ms, 4), "api_ms_per_window": round(api_ms, 4),
                 "value": round(npix / (dev_ms / 1e3) / 1e6, 1), "unit": "Mpix/s",
                 "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                              "frac": round(gbs / hbm, 4), "bytes_per_window": int(algo), "peak_source": src},
-                "launches_per_window": 5 * len(cams)}
+                "launches_per_window": 6}
     finally:
         dcg.dcg_destroy(ctx)
 

@@ -304,6 +304,31 @@ dcg_status dcg_backproject(dcg_ctx* ctx, const int32_t* idx, int32_t n, const fl
                            const dcg_camera* cam, float opacity_logit, float* params_out, int64_t stride,
                            void* stream);
 
+/* dcg_log_sample over the n_views (1..16) views of a keyframe window in one
+ * call.  The views sit back to back as in dcg_render_fwd's outputs: with
+ * off_v = sum_{w<v} W_w H_w, image and rendered (dev) hold view v's
+ * [3][H_v][W_v] block at 3 off_v floats, u and ps_out (dev, ps_out may be
+ * NULL) its [H_v W_v] pixels at off_v.  Only W and H of cams (host
+ * [n_views]) are read.  idx_out (dev, max_out entries) receives the sampled
+ * pixels as window indices off_v + y W_v + x, ascending (views in order);
+ * counts (host [n_views], may be NULL) the samples per view; *n_out (host)
+ * their total (DCG_ERR_CAPACITY if more than max_out: the first max_out are
+ * written and counted per view).  The same penalty and
+ * sampling rule as the one-view call, view by view; sum of W_v H_v <=
+ * max_pixels (DCG_ERR_CAPACITY) and < 2^31 (DCG_ERR_ARG).  Synchronous. */
+dcg_status dcg_log_sample_views(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views, const float* image,
+                                const float* rendered, float kappa, const float* u, float* ps_out, int32_t* idx_out,
+                                int64_t max_out, int64_t* counts, int64_t* n_out, void* stream);
+
+/* dcg_backproject for window indices idx (dev [n], as written by
+ * dcg_log_sample_views) of the n_views views cams (host): a sample's view is
+ * the last one whose first window pixel off_v is <= its index; depth (dev,
+ * [off_V] pixels) and image (dev, view blocks of [3][H_v][W_v]) are laid out
+ * as in dcg_log_sample_views.  Output as in dcg_backproject. */
+dcg_status dcg_backproject_views(dcg_ctx* ctx, const int32_t* idx, int64_t n, const float* depth, const float* image,
+                                 const dcg_camera* cams, int32_t n_views, float opacity_logit, float* params_out,
+                                 int64_t stride, void* stream);
+
 /* ---------------------------------------------------------------- rendering
  * Differentiable rasterisation of RGB and depth (Sec. III-E: the selected
  * Gaussians are rasterised into RGB and depth images; Eq. 4 needs the depth)
@@ -513,7 +538,8 @@ enum {
   DCG_PH_PRE_BWD = 7,   /* chain rule to the parameters and the pose */
   DCG_PH_SCATTER = 8,
   DCG_PH_STALL = 9,     /* compute stream idle in dcg_gather_active, waiting for chunk copies */
-  DCG_PH_SAMPLE = 10,   /* dcg_log_sample (LoG penalty, flags, ordered compaction) and dcg_backproject */
+  DCG_PH_SAMPLE = 10,   /* dcg_log_sample(_views) (LoG penalty, flags, ordered compaction, per-view counts)
+                           and dcg_backproject(_views) */
   DCG_PH_LOOP = 11,     /* device work of dcg_loop_closure: cull, transform and keys, row permutation
                            and page writes (its gather is timed as DCG_PH_GATHER / DCG_PH_STALL) */
   DCG_PH_COUNT = 12

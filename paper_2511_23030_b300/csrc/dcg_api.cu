@@ -138,6 +138,7 @@ struct dcg_ctx {
   // LoG sampling: per-pixel flags, sample count
   uint32_t* d_lsflags = nullptr;
   u64* d_lscount = nullptr;
+  u64* d_lsvcount = nullptr;  // samples per view of the last sampling call
   cudaEvent_t ev_loss = nullptr;
   int fault = 0;
   // captured window graph
@@ -411,7 +412,8 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
       dmalloc(&ctx->d_losscams, kMaxViewsApi) != cudaSuccess ||
       cudaHostAlloc((void**)&ctx->h_losscams, sizeof(DevCam) * kMaxViewsApi, 0) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
-  if (dmalloc(&ctx->d_lsflags, (size_t)c.max_pixels) != cudaSuccess || dmalloc(&ctx->d_lscount, 1) != cudaSuccess)
+  if (dmalloc(&ctx->d_lsflags, (size_t)c.max_pixels) != cudaSuccess || dmalloc(&ctx->d_lscount, 1) != cudaSuccess ||
+      dmalloc(&ctx->d_lsvcount, kLsMaxViews) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
   if (log_init() != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
   ctx->cap_ssim_tiles = c.max_pixels / 16 + 64 * (int64_t)c.max_views + 64;
@@ -495,6 +497,7 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   if (ctx->h_losscams) cudaFreeHost(ctx->h_losscams);
   cudaFree(ctx->d_lsflags);
   cudaFree(ctx->d_lscount);
+  cudaFree(ctx->d_lsvcount);
   cudaFree(ctx->d_lcmask);
   cudaFree(ctx->d_lcseg);
   cudaFree(ctx->d_lcsegc);
@@ -1345,6 +1348,61 @@ static LcView view_of(const dcg_camera& c) {
   return v;
 }
 
+static_assert(kLsMaxViews == kMaxViewsApi, "one view limit for the sampling calls and the rest of the ABI");
+
+// Table of the views of one sampling / back-projection call: window offsets
+// and penalty tiles.  False if a view is empty or the window is too large.
+static bool ls_table(const dcg_camera* cams, int V, bool with_pose, LsViews* t) {
+  *t = LsViews{};
+  t->V = V;
+  long long off = 0;
+  int tiles = 0;
+  for (int v = 0; v < V; ++v) {
+    const dcg_camera& c = cams[v];
+    if (c.W <= 0 || c.H <= 0) return false;
+    if (with_pose && (!(c.fx > 0.f) || !(c.fy > 0.f))) return false;
+    LsView& w = t->v[v];
+    if (with_pose) {
+      w.cam = view_of(c);
+    } else {
+      w.cam.W = c.W;
+      w.cam.H = c.H;
+    }
+    w.off = off;
+    w.tile0 = tiles;
+    w.ntx = (c.W + kLsTile - 1) / kLsTile;
+    const long long nt = (long long)w.ntx * ((c.H + kLsTile - 1) / kLsTile);
+    off += (long long)c.W * c.H;
+    if (off >= (1ll << 31) || tiles + nt >= (1ll << 31)) return false;
+    tiles += (int)nt;
+  }
+  t->n_tiles = tiles;
+  t->n_pix = off;
+  return true;
+}
+
+static dcg_status log_sample_run(dcg_ctx* ctx, const LsViews& t, const float* image, const float* rendered, float kappa,
+                                 const float* u, float* ps_out, int32_t* idx_out, int64_t max_out, int64_t* counts,
+                                 int64_t* n_out, cudaStream_t s) {
+  if (t.n_pix > ctx->cfg.max_pixels) return fail(ctx, DCG_ERR_CAPACITY, "more pixels than max_pixels");
+  dcg_render_state* st = ctx->st0;
+  hook(ctx)(PH_SAMPLE, true, s);
+  launch_log_sample(image, rendered, t, kappa, u, ps_out, ctx->d_lsflags, idx_out, max_out, st->part, st->P,
+                    ctx->d_lscount, ctx->d_lsvcount, s);
+  hook(ctx)(PH_SAMPLE, false, s);
+  CK(cudaGetLastError());
+  u64 cnt = 0;
+  u64 vc[kLsMaxViews] = {};
+  CK(cudaMemcpyAsync(&cnt, ctx->d_lscount, sizeof(u64), cudaMemcpyDeviceToHost, s));
+  if (counts) CK(cudaMemcpyAsync(vc, ctx->d_lsvcount, sizeof(u64) * t.V, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *n_out = (int64_t)std::min<u64>(cnt, (u64)max_out);
+  if (counts)
+    for (int v = 0; v < t.V; ++v) counts[v] = (int64_t)vc[v];
+  if (cnt > (u64)max_out) return fail(ctx, DCG_ERR_CAPACITY, "more samples than max_out");
+  return DCG_OK;
+}
+
 dcg_status dcg_log_sample(dcg_ctx* ctx, const float* image, const float* rendered, int32_t W, int32_t H, float kappa,
                           const float* u, float* ps_out, int32_t* idx_out, int32_t max_out, int32_t* n_out,
                           void* stream) {
@@ -1353,18 +1411,37 @@ dcg_status dcg_log_sample(dcg_ctx* ctx, const float* image, const float* rendere
     return fail(ctx, DCG_ERR_ARG, "bad arguments");
   if ((int64_t)W * H > ctx->cfg.max_pixels || (int64_t)W * H >= (1ll << 31))
     return fail(ctx, DCG_ERR_CAPACITY, "image larger than max_pixels");
-  cudaStream_t s = (cudaStream_t)stream;
-  dcg_render_state* st = ctx->st0;
+  dcg_camera c{};
+  c.W = W;
+  c.H = H;
+  LsViews t;
+  ls_table(&c, 1, false, &t);
+  int64_t n = 0;
+  const dcg_status r = log_sample_run(ctx, t, image, rendered, kappa, u, ps_out, idx_out, max_out, nullptr, &n,
+                                      (cudaStream_t)stream);
+  *n_out = (int32_t)n;
+  return r;
+}
+
+dcg_status dcg_log_sample_views(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views, const float* image,
+                                const float* rendered, float kappa, const float* u, float* ps_out, int32_t* idx_out,
+                                int64_t max_out, int64_t* counts, int64_t* n_out, void* stream) {
+  if (!ctx || !cams || n_views <= 0 || n_views > kLsMaxViews || !image || !rendered || !u || !idx_out || !n_out ||
+      max_out < 0 || !(kappa >= 0.f) || !std::isfinite(kappa))
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  LsViews t;
+  if (!ls_table(cams, n_views, false, &t)) return fail(ctx, DCG_ERR_ARG, "empty view or window of 2^31 pixels or more");
+  return log_sample_run(ctx, t, image, rendered, kappa, u, ps_out, idx_out, max_out, counts, n_out,
+                        (cudaStream_t)stream);
+}
+
+static dcg_status backproject_run(dcg_ctx* ctx, const LsViews& t, const int32_t* idx, int64_t n, const float* depth,
+                                  const float* image, float opacity_logit, float* params_out, int64_t stride,
+                                  cudaStream_t s) {
   hook(ctx)(PH_SAMPLE, true, s);
-  launch_log_sample(image, rendered, W, H, kappa, u, ps_out, ctx->d_lsflags, idx_out, max_out, st->part, st->P,
-                    ctx->d_lscount, s);
+  launch_backproject(idx, n, depth, image, t, opacity_logit, ctx->F, params_out, stride, ctx->num_sms, s);
   hook(ctx)(PH_SAMPLE, false, s);
   CK(cudaGetLastError());
-  u64 cnt = 0;
-  CK(cudaMemcpyAsync(&cnt, ctx->d_lscount, sizeof(u64), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  *n_out = (int32_t)std::min<u64>(cnt, (u64)max_out);
-  if (cnt > (u64)max_out) return fail(ctx, DCG_ERR_CAPACITY, "more samples than max_out");
   return DCG_OK;
 }
 
@@ -1373,13 +1450,20 @@ dcg_status dcg_backproject(dcg_ctx* ctx, const int32_t* idx, int32_t n, const fl
                            void* stream) {
   if (!ctx || n < 0 || (n > 0 && (!idx || !depth || !image || !params_out)) || !cam || stride < n)
     return fail(ctx, DCG_ERR_ARG, "bad arguments");
-  if (cam->W <= 0 || cam->H <= 0 || !(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(ctx, DCG_ERR_ARG, "bad camera");
-  hook(ctx)(PH_SAMPLE, true, (cudaStream_t)stream);
-  launch_backproject(idx, n, depth, image, cam->W, cam->H, view_of(*cam), opacity_logit, ctx->F, params_out, stride,
-                     ctx->num_sms, (cudaStream_t)stream);
-  hook(ctx)(PH_SAMPLE, false, (cudaStream_t)stream);
-  CK(cudaGetLastError());
-  return DCG_OK;
+  LsViews t;
+  if (!ls_table(cam, 1, true, &t)) return fail(ctx, DCG_ERR_ARG, "bad camera");
+  return backproject_run(ctx, t, idx, n, depth, image, opacity_logit, params_out, stride, (cudaStream_t)stream);
+}
+
+dcg_status dcg_backproject_views(dcg_ctx* ctx, const int32_t* idx, int64_t n, const float* depth, const float* image,
+                                 const dcg_camera* cams, int32_t n_views, float opacity_logit, float* params_out,
+                                 int64_t stride, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!idx || !depth || !image || !params_out)) || !cams || n_views <= 0 ||
+      n_views > kLsMaxViews || stride < n)
+    return fail(ctx, DCG_ERR_ARG, "bad arguments");
+  LsViews t;
+  if (!ls_table(cams, n_views, true, &t)) return fail(ctx, DCG_ERR_ARG, "bad camera or window of 2^31 pixels or more");
+  return backproject_run(ctx, t, idx, n, depth, image, opacity_logit, params_out, stride, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------- rendering

@@ -61,13 +61,31 @@ void launch_permute_rows(const float* src, long long sstride, float* dst, long l
 void launch_cap_rows(float* row, long long n, float cap, int num_sms, cudaStream_t st);
 
 // ---------------------------------------------------------------- sampling.cu
+// The views of one batched sampling or back-projection call, passed by value
+// (kernel parameter space): view v's pixels are the window pixels
+// [off, off + W H) of the concatenated buffers, its 32 x 32 penalty tiles
+// the grid blocks [tile0, tile0 + ntx nty).
+constexpr int kLsMaxViews = 16;
+constexpr int kLsTile = 32;
+struct LsView {
+  LcView cam;  // W, H always; pose and intrinsics for the back-projection
+  long long off;
+  int tile0, ntx;
+};
+struct LsViews {
+  LsView v[kLsMaxViews];
+  int V;
+  int n_tiles;
+  long long n_pix;
+};
 cudaError_t log_init();
-void launch_log_sample(const float* img, const float* ren, int W, int H, float kappa, const float* u, float* ps_out,
-                       uint32_t* flags, int32_t* idx_out, long long cap, u64* part, int Pb, u64* count,
-                       cudaStream_t st);
-void launch_backproject(const int32_t* idx, long long n, const float* depth, const float* img, int W, int H,
-                        const LcView& cam, float logit, int F, float* out, long long stride, int num_sms,
-                        cudaStream_t st);
+// Eq. 1 over all views: flags, ordered compaction of window indices into
+// idx_out (at most cap), total in *count, per-view counts in vcount (device, V).
+void launch_log_sample(const float* img, const float* ren, const LsViews& views, float kappa, const float* u,
+                       float* ps_out, uint32_t* flags, int32_t* idx_out, long long cap, u64* part, int Pb, u64* count,
+                       u64* vcount, cudaStream_t st);
+void launch_backproject(const int32_t* idx, long long n, const float* depth, const float* img, const LsViews& views,
+                        float logit, int F, float* out, long long stride, int num_sms, cudaStream_t st);
 
 // ---------------------------------------------------------------- optim.cu
 constexpr int kAdamMaxF = 64;

@@ -116,6 +116,10 @@ _SIGS = {
                                       _P]),
     "dcg_backproject": (ctypes.c_int, [_P, _P, _I32, _P, _P, ctypes.POINTER(dcg_camera), ctypes.c_float, _P, _I64,
                                        _P]),
+    "dcg_log_sample_views": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _I32, _P, _P, ctypes.c_float, _P, _P, _P,
+                                            _I64, _P, ctypes.POINTER(_I64), _P]),
+    "dcg_backproject_views": (ctypes.c_int, [_P, _P, _I64, _P, _P, ctypes.POINTER(dcg_camera), _I32, ctypes.c_float,
+                                             _P, _I64, _P]),
     "dcg_cull_chunks_noalloc": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(dcg_camera),
                                                _I32, _P, _P, _P, _P]),
 }
@@ -323,6 +327,25 @@ def dcg_log_sample(ctx, image, rendered, W: int, H: int, kappa: float, u, idx_ou
     check(ctx, lib().dcg_log_sample(ctx, ptr(image), ptr(rendered), W, H, float(kappa), ptr(u), ptr(ps_out),
                                     ptr(idx_out), idx_out.numel(), ctypes.byref(n), stream_ptr(stream)))
     return int(n.value)
+
+
+def dcg_log_sample_views(ctx, cams, image, rendered, kappa: float, u, idx_out, ps_out=None, stream=None):
+    """Eq. 1 penalty sampling of a window of views at once; returns (total, per-view counts) with the
+    sampled window indices written to idx_out."""
+    arr = make_cameras(cams)
+    n = _I64()
+    counts = np.zeros(len(cams), np.int64)
+    check(ctx, lib().dcg_log_sample_views(ctx, arr, len(cams), ptr(image), ptr(rendered), float(kappa), ptr(u),
+                                          ptr(ps_out), ptr(idx_out), idx_out.numel(), ptr(counts), ctypes.byref(n),
+                                          stream_ptr(stream)))
+    return int(n.value), counts
+
+
+def dcg_backproject_views(ctx, idx, n: int, depth, image, cams, opacity_logit: float, params_out, stream=None):
+    arr = make_cameras(cams)
+    check(ctx, lib().dcg_backproject_views(ctx, ptr(idx), n, ptr(depth), ptr(image), arr, len(cams),
+                                           float(opacity_logit), ptr(params_out), params_out.stride(0),
+                                           stream_ptr(stream)))
 
 
 def dcg_backproject(ctx, idx, n: int, depth, image, cam, opacity_logit: float, params_out, stream=None):

@@ -87,3 +87,72 @@ def test_backprojection_and_insertion_into_chunks():
         assert int(info["counts"].sum()) == P.shape[0] + n
     finally:
         dcg.dcg_destroy(ctx)
+
+
+def _posed_cam(W, H, f, yaw, t):
+    c, s = np.cos(yaw), np.sin(yaw)
+    T = np.eye(4, dtype=np.float32)
+    T[:3, :3] = [[c, 0, s], [0, 1, 0], [-s, 0, c]]
+    T[:3, 3] = t
+    return synth.Camera(f, f * 1.05, W / 2.0 + 0.3, H / 2.0 - 0.2, W, H, T, 0.2, 100.0)
+
+
+def test_window_of_views_in_one_call_matches_reference_and_single_calls():
+    """Three views of uneven sizes through dcg_log_sample_views / dcg_backproject_views: per view the
+    same P_s and samples as the one-view call (bit-identical) and as the reference; window indices
+    ascending; per-view counts; back-projection with each view's own pose."""
+    import torch
+
+    sizes = [(100, 70), (37, 23), (16, 16)]
+    cams = [_posed_cam(W, H, 80.0 + 10 * k, 0.1 * k, (0.2 * k, -0.1, 0.05 * k)) for k, (W, H) in enumerate(sizes)]
+    offs = np.cumsum([0] + [W * H for W, H in sizes])
+    N = int(offs[-1])
+    imgs, rens = zip(*[_images(W, H, 7 + k) for k, (W, H) in enumerate(sizes)])
+    u = np.random.default_rng(3).uniform(0, 1, N).astype(np.float32)
+    kappa = 3.0
+    ctx = make_ctx(deg=0, n_max=1000, views=1, pixels=N)
+    try:
+        ti = torch.from_numpy(np.concatenate([a.reshape(-1) for a in imgs])).cuda()
+        tr = torch.from_numpy(np.concatenate([a.reshape(-1) for a in rens])).cuda()
+        tu = torch.from_numpy(u).cuda()
+        ps = torch.zeros(N, device="cuda")
+        idx = torch.zeros(N, dtype=torch.int32, device="cuda")
+        n, counts = dcg.dcg_log_sample_views(ctx, cams, ti, tr, kappa, tu, idx, ps_out=ps)
+        got = idx[:n].cpu().numpy().astype(np.int64)
+        assert (np.diff(got) > 0).all() and n == counts.sum()
+        ps_h = ps.cpu().numpy()
+        for v, (W, H) in enumerate(sizes):
+            o, P = int(offs[v]), W * H
+            mine = got[(got >= o) & (got < o + P)] - o
+            assert len(mine) == counts[v]
+            # the one-view call: identical penalty and samples
+            ps1 = torch.zeros(P, device="cuda")
+            idx1 = torch.zeros(P, dtype=torch.int32, device="cuda")
+            n1 = dcg.dcg_log_sample(ctx, ti[3 * o: 3 * (o + P)], tr[3 * o: 3 * (o + P)], W, H, kappa, tu[o: o + P],
+                                    idx1, ps_out=ps1)
+            assert np.array_equal(idx1[:n1].cpu().numpy(), mine)
+            assert np.array_equal(ps1.cpu().numpy(), ps_h[o: o + P])
+            # the reference
+            want = ls.penalty(imgs[v], rens[v]).reshape(-1)
+            assert np.abs(ps_h[o: o + P] - want).max() <= 1e-5 * want.max() + 1e-6
+            amb = set(np.nonzero(np.abs(u[o: o + P] - np.minimum(1.0, kappa * want)) <= 1e-5)[0].tolist())
+            assert set(mine.tolist()) ^ set(ls.sample(want, u[o: o + P], kappa).tolist()) <= amb
+        # capacity: the counts still describe every sample
+        small = torch.zeros(max(1, n // 2), dtype=torch.int32, device="cuda")
+        with pytest.raises(dcg.DcgError) as e:
+            dcg.dcg_log_sample_views(ctx, cams, ti, tr, kappa, tu, small)
+        assert e.value.status == 6
+        # back-projection of the whole window's samples with each view's pose
+        depth = np.random.default_rng(5).uniform(0.5, 4.0, N).astype(np.float32)
+        F = 14
+        out = torch.zeros((F, n), device="cuda")
+        dcg.dcg_backproject_views(ctx, idx, n, torch.from_numpy(depth).cuda(), ti, cams, -1.5, out)
+        dcg.dcg_sync(ctx)
+        gotp = out.T.cpu().numpy().astype(np.float64)
+        for v, (W, H) in enumerate(sizes):
+            o, P = int(offs[v]), W * H
+            sel = (got >= o) & (got < o + P)
+            want = ls.backproject(got[sel] - o, depth[o: o + P], imgs[v], cams[v], -1.5, F)
+            assert np.allclose(gotp[sel], want, rtol=2e-6, atol=2e-6), v
+    finally:
+        dcg.dcg_destroy(ctx)
