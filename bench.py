@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--stage", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="batched timing only (no plain/e2e/CPU legs), for profilers")
-    ap.add_argument("--workload", default="window", choices=["window", "corridor"])
+    ap.add_argument("--workload", default="window", choices=["window", "corridor", "sampling"])
     ap.add_argument("--bwd", default="warp", choices=["warp", "slots"], help="backward gradient accumulation")
     ap.add_argument("--length", type=float, default=5000.0, help="corridor: metres of road (1 m per frame)")
     ap.add_argument("--per-m", type=int, default=8000, help="corridor: Gaussians per metre (40M per 5 km)")
@@ -810,10 +810,47 @@ def run_corridor(args):
     return out
 
 
+def run_sampling(args):
+    """The LoG sampling leg alone: the window is rendered once (forward) to give the rendered
+    images and depth, then Eq. 1 sampling and back-projection of all 8 views are timed."""
+    import torch
+
+    from paper_2511_23030_b300 import build, dcg, synth
+
+    build.build()
+    sc = synth.window_scene(0, n=args.gaussians)
+    P, cams = sc["params"], sc["cams"]
+    n_all = P.shape[0]
+    npix = sum(c.W * c.H for c in cams)
+    cfg = dcg.config(sh_degree=sc["deg"], max_active=n_all + 1024, max_views=8, max_pixels=npix,
+                     max_instances=160 << 20, chunk_size=sc["chunk_size"], device_budget=6_000_000,
+                     host_capacity=n_all + 1024, dfar=60.0)
+    ctx = dcg.dcg_create(cfg)
+    try:
+        g_t = torch.from_numpy(np.ascontiguousarray(P.T)).cuda()
+        dcg.dcg_chunk_table_update(ctx, g_t, n_all)
+        del g_t
+        g, n = dcg.dcg_gather_active(ctx, dcg.dcg_cull_chunks(ctx, cams))
+        rgb, depth = torch.zeros(3 * npix, device="cuda"), torch.zeros(npix, device="cuda")
+        dcg.dcg_render_fwd(ctx, g, n, cams, rgb, depth)
+        dcg.dcg_sync(ctx)
+    finally:
+        dcg.dcg_destroy(ctx)
+    trgb = torch.from_numpy(np.concatenate([t.reshape(-1) for t in sc["target_rgb"]])).cuda()
+    out = sampling_leg(sc, npix, trgb, rgb, depth, args.steps, args.warmup)
+    out.update({"workload": "sampling", "metric": "LoG penalty sampling (Eq. 1) Mpix/s per keyframe window",
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+                "data": "synthetic window scene (8 views, 4,032,000 px)"})
+    return out
+
+
 def main():
     args = parse()
     if args.workload == "corridor":
         print(json.dumps(run_corridor(args)))
+        return
+    if args.workload == "sampling":
+        print(json.dumps(run_sampling(args)))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
