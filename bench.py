@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--stage", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="batched timing only (no plain/e2e/CPU legs), for profilers")
-    ap.add_argument("--workload", default="window", choices=["window", "corridor", "sampling"])
+    ap.add_argument("--workload", default="window", choices=["window", "corridor", "sampling", "loopclosure"])
     ap.add_argument("--bwd", default="warp", choices=["warp", "slots"], help="backward gradient accumulation")
     ap.add_argument("--length", type=float, default=5000.0, help="corridor: metres of road (1 m per frame)")
     ap.add_argument("--per-m", type=int, default=8000, help="corridor: Gaussians per metre (40M per 5 km)")
@@ -851,6 +851,16 @@ def main():
         return
     if args.workload == "sampling":
         print(json.dumps(run_sampling(args)))
+        return
+    if args.workload == "loopclosure":
+        from paper_2511_23030_b300 import build, synth
+
+        build.build()
+        out = loop_closure_leg(synth.window_scene(0, n=args.gaussians), args.steps)
+        out.update({"workload": "loopclosure", "metric": "loop-closure correction ms per call (2M-Gaussian map)",
+                    "steps": args.steps, "higher_is_better": False, "dtype": "f32",
+                    "data": "synthetic window scene (2 keyframes corrected)"})
+        print(json.dumps(out))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -139,6 +139,11 @@ struct dcg_ctx {
   uint32_t* d_lsflags = nullptr;
   u64* d_lscount = nullptr;
   u64* d_lsvcount = nullptr;  // samples per view of the last sampling call
+  char* h_lcstage = nullptr;  // loop closure: pinned keys, permutation and flags of the gathered rows
+  int64_t lc_cap = 0;
+  float* d_lctmp = nullptr;  // loop closure: permuted rows [Fs][n] and the permutation
+  long long* d_lcperm = nullptr;
+  int64_t lc_dev_cap = 0;
   cudaEvent_t ev_loss = nullptr;
   int fault = 0;
   // captured window graph
@@ -490,6 +495,9 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   if (ctx->win_exec) cudaGraphExecDestroy(ctx->win_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->h_wcams) cudaFreeHost(ctx->h_wcams);
+  if (ctx->h_lcstage) cudaFreeHost(ctx->h_lcstage);
+  cudaFree(ctx->d_lctmp);
+  cudaFree(ctx->d_lcperm);
   if (ctx->ev_win) cudaEventDestroy(ctx->ev_win);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
   cudaFree(ctx->d_losscams);
@@ -1144,11 +1152,20 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   launch_chunk_keys(ctx->d_active, 1, S, n, ctx->cfg.chunk_size, d_keys, ctx->d_errword, ctx->num_sms, s);
   hook(ctx)(PH_LOOP, false, s);
   CK(cudaGetLastError());
-  std::vector<uint32_t> flags((size_t)n);
-  std::vector<uint64_t> keys((size_t)n);
+  // per-row flags and keys come back, and the permutation goes out, through pinned staging
+  if (n > ctx->lc_cap) {
+    if (ctx->h_lcstage) cudaFreeHost(ctx->h_lcstage);
+    ctx->h_lcstage = nullptr;
+    ctx->lc_cap = 0;
+    CK(cudaHostAlloc((void**)&ctx->h_lcstage, (size_t)n * (4 + 8 + 8), 0));
+    ctx->lc_cap = n;
+  }
+  uint64_t* const keys = reinterpret_cast<uint64_t*>(ctx->h_lcstage);
+  long long* const perm = reinterpret_cast<long long*>(ctx->h_lcstage + (size_t)n * 8);
+  uint32_t* const flags = reinterpret_cast<uint32_t*>(ctx->h_lcstage + (size_t)n * 16);
   if (n) {
-    CK(cudaMemcpyAsync(flags.data(), d_flags, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(keys.data(), d_keys, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(flags, d_flags, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(keys, d_keys, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
   }
   dcg_status es = dcg_sync(ctx, stream);  // a corrected position outside the key range stops here, table unchanged
   if (es != DCG_OK) {
@@ -1156,44 +1173,62 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
     return es;
   }
   // 4. redistribution: a chunk keeps its remaining Gaussians in stored order
-  // and receives incoming ones after them, in gather order
-  int64_t nt = 0, nm = 0;
-  std::vector<std::vector<int64_t>> stay((size_t)nl);
-  std::map<uint64_t, std::vector<int64_t>> incoming;
-  for (int k = 0, i = 0; k < nl; ++k) {
-    const int64_t end = k + 1 < nl ? seg[(size_t)k + 1] : n;
-    for (; i < end; ++i) {
-      nt += flags[(size_t)i] != 0u;
-      if (keys[(size_t)i] == segkey[(size_t)k]) {
-        stay[(size_t)k].push_back(i);
-      } else {
-        incoming[keys[(size_t)i]].push_back(i);
-        ++nm;
-      }
+  // and receives incoming ones after them, in gather order; only the moved
+  // rows are collected (a rigid correction moves few across chunk borders)
+  int64_t nt = 0;
+  std::vector<std::pair<uint64_t, int64_t>> moved;  // (target key, row) in gather order
+  std::vector<int64_t> stays((size_t)nl);
+  for (int k = 0; k < nl; ++k) {
+    const int64_t a = seg[(size_t)k], end = k + 1 < nl ? seg[(size_t)k + 1] : n;
+    const uint64_t sk = segkey[(size_t)k];
+    int64_t st = 0;
+    for (int64_t i = a; i < end; ++i) {
+      nt += flags[i] != 0u;
+      if (keys[i] == sk)
+        ++st;
+      else
+        moved.emplace_back(keys[i], i);
     }
+    stays[(size_t)k] = st;
   }
+  const int64_t nm = (int64_t)moved.size();
   if (n_transformed) *n_transformed = nt;
   if (n_moved) *n_moved = nm;
   if (nm == 0) return dcg_scatter_back(ctx, &g, n, stream);
-  std::vector<long long> perm;
-  perm.reserve((size_t)n);
+  // by target chunk, gather order kept within each
+  std::stable_sort(moved.begin(), moved.end(),
+                   [](const std::pair<uint64_t, int64_t>& x, const std::pair<uint64_t, int64_t>& y) {
+                     return x.first < y.first;
+                   });
+  std::vector<char> placed((size_t)nm, 0);
   std::vector<int64_t> newcount((size_t)nl);
+  int64_t j = 0;
   for (int k = 0; k < nl; ++k) {
-    perm.insert(perm.end(), stay[(size_t)k].begin(), stay[(size_t)k].end());
-    auto it = incoming.find(segkey[(size_t)k]);
-    if (it != incoming.end()) {
-      perm.insert(perm.end(), it->second.begin(), it->second.end());
-      newcount[(size_t)k] = (int64_t)(stay[(size_t)k].size() + it->second.size());
-      incoming.erase(it);
+    const int64_t a = seg[(size_t)k], end = k + 1 < nl ? seg[(size_t)k + 1] : n;
+    const uint64_t sk = segkey[(size_t)k];
+    if (stays[(size_t)k] == end - a) {
+      for (int64_t i = a; i < end; ++i) perm[j++] = i;
     } else {
-      newcount[(size_t)k] = (int64_t)stay[(size_t)k].size();
+      for (int64_t i = a; i < end; ++i)
+        if (keys[i] == sk) perm[j++] = i;
     }
+    auto lo = std::lower_bound(moved.begin(), moved.end(), sk,
+                               [](const std::pair<uint64_t, int64_t>& x, uint64_t key) { return x.first < key; });
+    int64_t in = 0;
+    for (auto it = lo; it != moved.end() && it->first == sk; ++it, ++in) {
+      perm[j++] = it->second;
+      placed[(size_t)(it - moved.begin())] = 1;
+    }
+    newcount[(size_t)k] = stays[(size_t)k] + in;
   }
-  const int64_t n_kept = (int64_t)perm.size();  // Gaussians staying on the device (gathered chunks)
-  std::vector<std::pair<uint64_t, int64_t>> outside;  // (key, count) of targets that were not gathered
-  for (auto& kv : incoming) {
-    perm.insert(perm.end(), kv.second.begin(), kv.second.end());
-    outside.emplace_back(kv.first, (int64_t)kv.second.size());
+  const int64_t n_kept = j;  // Gaussians staying on the device (gathered chunks)
+  std::vector<std::pair<uint64_t, int64_t>> outside;  // (key, count) of targets that were not gathered, ascending
+  for (int64_t m = 0; m < nm; ++m) {
+    if (placed[(size_t)m]) continue;
+    perm[j++] = moved[(size_t)m].second;
+    if (outside.empty() || outside.back().first != moved[(size_t)m].first)
+      outside.emplace_back(moved[(size_t)m].first, 0);
+    ++outside.back().second;
   }
   // capacity checks before anything changes
   int64_t dev_need = 0, dev_have = 0, host_need = 0, host_have = 0, new_chunks = 0;
@@ -1222,9 +1257,20 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   const int Fs = ctx->Fs;
   float* d_tmp = nullptr;
   long long* d_perm = nullptr;
-  CK(cudaMallocAsync((void**)&d_tmp, sizeof(float) * (size_t)Fs * (size_t)n, s));
-  CK(cudaMallocAsync((void**)&d_perm, sizeof(long long) * (size_t)n, s));
-  CK(cudaMemcpyAsync(d_perm, perm.data(), sizeof(long long) * (size_t)n, cudaMemcpyHostToDevice, s));
+  if (n > ctx->lc_dev_cap) {  // device scratch kept between loop closures, grown on demand
+    CK(cudaStreamSynchronize(s));
+    cudaFree(ctx->d_lctmp);
+    cudaFree(ctx->d_lcperm);
+    ctx->d_lctmp = nullptr;
+    ctx->d_lcperm = nullptr;
+    ctx->lc_dev_cap = 0;
+    CK(cudaMalloc((void**)&ctx->d_lctmp, sizeof(float) * (size_t)Fs * (size_t)n));
+    CK(cudaMalloc((void**)&ctx->d_lcperm, sizeof(long long) * (size_t)n));
+    ctx->lc_dev_cap = n;
+  }
+  d_tmp = ctx->d_lctmp;
+  d_perm = ctx->d_lcperm;
+  CK(cudaMemcpyAsync(d_perm, perm, sizeof(long long) * (size_t)n, cudaMemcpyHostToDevice, s));
   hook(ctx)(PH_LOOP, true, s);
   launch_permute_rows(ctx->d_active, S, d_tmp, n, d_perm, n, Fs, ctx->num_sms, s);
   hook(ctx)(PH_LOOP, false, s);
@@ -1283,8 +1329,6 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
     CK(cudaMemcpy2DAsync(ctx->h_stage, (size_t)n_out * 4, d_tmp + n_kept, (size_t)n * 4, (size_t)n_out * 4, (size_t)Fs,
                          cudaMemcpyDeviceToHost, s));
   }
-  CK(cudaFreeAsync(d_perm, s));
-  CK(cudaFreeAsync(d_tmp, s));
   CK(cudaStreamSynchronize(s));
   if (n_out > 0) {
     bool added = false;
