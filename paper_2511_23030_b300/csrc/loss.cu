@@ -13,11 +13,15 @@
 //   g_xx = -c S / B2,   g_xy = 2 c S / A2
 // (the window is symmetric, so the adjoint correlation is the same one).
 //
-// One block per (16 x 16 output tile, channel): it loads x and y on the tile
-// plus a 10-pixel halo (36 x 36), runs the separable window over it for the
-// five statistics on the tile plus a 5-pixel halo (26 x 26), forms S and the
-// three g maps there (zero outside the image), runs the window over the g
-// maps for the tile, and adds the result to dL/dI.  No global scratch; the
+// One block per (32 x 32 output tile, channel): it stages x and y on the
+// tile plus a 10-pixel halo (52 x 52), runs the horizontal window for the
+// five statistics (x, y, x^2, y^2, x y) over it, then each thread runs the
+// vertical window for 7 pixels of one column of the tile plus a 5-pixel halo
+// (42 x 42) for all five statistics in registers and forms S and the three g
+// maps there (zero outside the image; written over the staged images), runs
+// the horizontal window over the g maps, and each thread finishes 4 pixels
+// of one column of the tile (vertical window of all three maps, x and y read
+// again from global memory) and adds them to dL/dI.  No global scratch; the
 // loss partial of each block is reduced in a fixed order.
 #include <cmath>
 
@@ -28,9 +32,9 @@ namespace dcg {
 namespace {
 
 constexpr int kR = 5;                  // window radius
-constexpr int kT = 16;                 // output tile
-constexpr int kG = kT + 2 * kR;        // 26: region of S and g
-constexpr int kA = kT + 4 * kR;        // 36: region of x and y
+constexpr int kT = 32;                 // output tile
+constexpr int kG = kT + 2 * kR;        // 42: region of S and g
+constexpr int kA = kT + 4 * kR;        // 52: region of x and y
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
@@ -49,23 +53,29 @@ __device__ __forceinline__ void win_run(const float (&in)[RUN + 2 * kR], float (
   }
 }
 
-constexpr int kRunH = 13;  // outputs per thread in the forward horizontal pass (26 = 2 x 13)
-constexpr int kRunV = 13;  // outputs per thread in the forward vertical pass
-constexpr int kRunBH = 8;  // outputs per thread in the backward horizontal pass (half a row)
-constexpr int kRunBV = 4;  // outputs per thread in the backward vertical pass (a quarter column)
+constexpr int kRunH = 14;  // forward horizontal: outputs per item (42 = 3 x 14)
+constexpr int kRunV = 7;   // forward vertical + S: pixels per item (42 = 6 x 7; 42 x 6 = 252 items)
+constexpr int kRunBH = 8;  // backward horizontal: outputs per item (32 = 4 x 8)
+constexpr int kRunBV = 4;  // backward vertical: pixels per item (32 = 8 x 4; 32 x 8 = 256 items)
+// shared memory: the staged images (later the g maps) and the horizontal
+// results (later the backward horizontal results)
+constexpr int kXP = kA + 1, kHP = kG + 1, kGP = kG + 1, kBP = kT + 1;
+constexpr int kSmX = 2 * kA * kXP;  // sx, sy
+constexpr int kSmH = 5 * kA * kHP;  // h[5]
+static_assert(3 * kG * kGP <= kSmX, "g maps fit over the staged images");
+static_assert(3 * kG * kBP <= kSmH, "backward horizontal results fit over h");
+constexpr size_t kSsimSmem = sizeof(float) * (size_t)(kSmX + kSmH);
 
 __global__ void __launch_bounds__(256) k_ssim(const float* __restrict__ rgb, const float* __restrict__ trgb,
                                               const DevCam* __restrict__ cams, int V, float lam_s,
                                               float* __restrict__ dr, float* __restrict__ part) {
-  __shared__ float sx[kA][kA + 1], sy[kA][kA + 1];
-  __shared__ float h[5][kA][kG + 1];
-  // vertical-pass statistics st[0..4]; after the S pass st[0..2] hold the g
-  // maps and the backward horizontal pass writes hb over st[3..4]
-  __shared__ float st_raw[5 * kG * (kG + 1)];
+  extern __shared__ float sm[];
+  float* const sx = sm;               // [kA][kXP]
+  float* const sy = sm + kA * kXP;    // [kA][kXP]
+  float* const g = sm;                // [3][kG][kGP], after the forward horizontal pass
+  float* const h = sm + kSmX;         // [5][kA][kHP]
+  float* const hb = sm + kSmX;        // [3][kG][kBP], after the forward vertical pass
   __shared__ float red[8];
-  float(*st)[kG][kG + 1] = reinterpret_cast<float(*)[kG][kG + 1]>(st_raw);
-  float(*hb)[kG][kT + 1] = reinterpret_cast<float(*)[kG][kT + 1]>(st_raw + 3 * kG * (kG + 1));
-  static_assert(3 * kG * (kT + 1) <= 2 * kG * (kG + 1), "hb fits over st[3..4]");
   const int tid = threadIdx.x;
   const int gt = blockIdx.x, ch = blockIdx.y;
   int v = 0;
@@ -75,7 +85,7 @@ __global__ void __launch_bounds__(256) k_ssim(const float* __restrict__ rgb, con
   const long long P = (long long)W * H;
   const int local = gt - c.tile_base;
   const int ty = local / c.ntx, tx = local - ty * c.ntx;
-  const int ax = tx * kT - 2 * kR, ay = ty * kT - 2 * kR;  // origin of the 36 x 36 region
+  const int ax = tx * kT - 2 * kR, ay = ty * kT - 2 * kR;  // origin of the 52 x 52 region
   const float* X = rgb + 3 * c.pix_off + ch * P;
   const float* Y = trgb + 3 * c.pix_off + ch * P;
   float* D = dr + 3 * c.pix_off + ch * P;
@@ -84,108 +94,117 @@ __global__ void __launch_bounds__(256) k_ssim(const float* __restrict__ rgb, con
     const int gx = ax + q, gy = ay + r;
     const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
     const long long k = (long long)gy * W + gx;
-    sx[r][q] = in ? X[k] : 0.f;
-    sy[r][q] = in ? Y[k] : 0.f;
+    sx[r * kXP + q] = in ? X[k] : 0.f;
+    sy[r * kXP + q] = in ? Y[k] : 0.f;
   }
   __syncthreads();
-  // horizontal pass: item = (row, half of the 26 columns, group); groups:
-  // 0 -> (x, x^2), 1 -> (y, y^2), 2 -> x y
-  for (int it = tid; it < kA * 2 * 3; it += 256) {
-    const int grp = it / (kA * 2), rem = it - grp * (kA * 2), r = rem >> 1, q0 = (rem & 1) * kRunH;
+  // forward horizontal pass: item = (group, row, run of 14 columns); groups:
+  // 0 -> (x, x^2) into h[0], h[2]; 1 -> (y, y^2) into h[1], h[3]; 2 -> x y into h[4]
+  for (int it = tid; it < 3 * kA * 3; it += 256) {
+    const int grp = it / (kA * 3), rem = it - grp * (kA * 3), r = rem / 3, q0 = (rem - r * 3) * kRunH;
     float a[kRunH + 2 * kR], o1[kRunH], o2[kRunH];
+    const float* rx = sx + r * kXP + q0;
+    const float* ry = sy + r * kXP + q0;
     if (grp == 0) {
 #pragma unroll
-      for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = sx[r][q0 + k];
+      for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = rx[k];
     } else if (grp == 1) {
 #pragma unroll
-      for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = sy[r][q0 + k];
+      for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = ry[k];
     } else {
 #pragma unroll
-      for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = sx[r][q0 + k] * sy[r][q0 + k];
+      for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = rx[k] * ry[k];
     }
     win_run<kRunH>(a, o1);
+    float* d1 = h + ((grp == 2 ? 4 : grp) * kA + r) * kHP + q0;
+#pragma unroll
+    for (int o = 0; o < kRunH; ++o) d1[o] = o1[o];
     if (grp < 2) {
 #pragma unroll
       for (int k = 0; k < kRunH + 2 * kR; ++k) a[k] = a[k] * a[k];
       win_run<kRunH>(a, o2);
-    }
-    float* d1 = grp == 0 ? &h[0][r][q0] : (grp == 1 ? &h[1][r][q0] : &h[4][r][q0]);
-    float* d2 = grp == 0 ? &h[2][r][q0] : &h[3][r][q0];
-#pragma unroll
-    for (int o = 0; o < kRunH; ++o) d1[o] = o1[o];
-    if (grp < 2) {
+      float* d2 = h + ((2 + grp) * kA + r) * kHP + q0;
 #pragma unroll
       for (int o = 0; o < kRunH; ++o) d2[o] = o2[o];
     }
   }
   __syncthreads();
-  // vertical pass: item = (statistic, column, half of the 26 rows)
-  for (int it = tid; it < 5 * kG * 2; it += 256) {
-    const int sidx = it / (kG * 2), rem = it - sidx * (kG * 2), q = rem >> 1, r0 = (rem & 1) * kRunV;
-    float a[kRunV + 2 * kR], o[kRunV];
-#pragma unroll
-    for (int k = 0; k < kRunV + 2 * kR; ++k) a[k] = h[sidx][r0 + k][q];
-    win_run<kRunV>(a, o);
-#pragma unroll
-    for (int k = 0; k < kRunV; ++k) st[sidx][r0 + k][q] = o[k];
-  }
-  __syncthreads();
-  // S and the g maps on the 26 x 26 region (g written over the statistics)
+  // forward vertical pass of all five statistics for 7 pixels of one column
+  // of the 42 x 42 region, then S and the g maps (written over the staged images)
   const float coef = -lam_s / (3.f * (float)P);
   float acc = 0.f;
-  for (int i = tid; i < kG * kG; i += 256) {
-    const int r = i / kG, q = i - r * kG;
-    const float mx = st[0][r][q], my = st[1][r][q], xx = st[2][r][q], yy = st[3][r][q], xy = st[4][r][q];
-    const int px = ax + kR + q, py = ay + kR + r;
-    const bool in = px >= 0 && px < W && py >= 0 && py < H;
-    float gmu = 0.f, gxx = 0.f, gxy = 0.f;
-    if (in) {
-      const float A1 = 2.f * mx * my + kC1, A2 = 2.f * (xy - mx * my) + kC2;
-      const float B1 = mx * mx + my * my + kC1, B2 = (xx - mx * mx) + (yy - my * my) + kC2;
-      const float iA1 = 1.f / A1, iA2 = 1.f / A2, iB1 = 1.f / B1, iB2 = 1.f / B2;
-      const float S = A1 * A2 * iB1 * iB2;
-      const float cs = coef * S;
-      gmu = cs * (2.f * my * (iA1 - iA2) + 2.f * mx * (iB2 - iB1));
-      gxx = -cs * iB2;
-      gxy = 2.f * cs * iA2;
-      if (r >= kR && r < kR + kT && q >= kR && q < kR + kT) acc += S;
+  if (tid < kG * (kG / kRunV)) {
+    const int q = tid % kG, r0 = (tid / kG) * kRunV;
+    float stv[5][kRunV];
+#pragma unroll
+    for (int sidx = 0; sidx < 5; ++sidx) {
+      float a[kRunV + 2 * kR];
+      const float* col = h + (sidx * kA + r0) * kHP + q;
+#pragma unroll
+      for (int k = 0; k < kRunV + 2 * kR; ++k) a[k] = col[k * kHP];
+      win_run<kRunV>(a, stv[sidx]);
     }
-    st[0][r][q] = gmu;  // each thread rewrites only its own position
-    st[1][r][q] = gxx;
-    st[2][r][q] = gxy;
+    const int px = ax + kR + q;
+#pragma unroll
+    for (int o = 0; o < kRunV; ++o) {
+      const int r = r0 + o, py = ay + kR + r;
+      const bool in = px >= 0 && px < W && py >= 0 && py < H;
+      float gmu = 0.f, gxx = 0.f, gxy = 0.f;
+      if (in) {
+        const float mx = stv[0][o], my = stv[1][o], xx = stv[2][o], yy = stv[3][o], xy = stv[4][o];
+        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * (xy - mx * my) + kC2;
+        const float B1 = mx * mx + my * my + kC1, B2 = (xx - mx * mx) + (yy - my * my) + kC2;
+        const float iA1 = 1.f / A1, iA2 = 1.f / A2, iB1 = 1.f / B1, iB2 = 1.f / B2;
+        const float S = A1 * A2 * iB1 * iB2;
+        const float cs = coef * S;
+        gmu = cs * (2.f * my * (iA1 - iA2) + 2.f * mx * (iB2 - iB1));
+        gxx = -cs * iB2;
+        gxy = 2.f * cs * iA2;
+        if (r >= kR && r < kR + kT && q >= kR && q < kR + kT) acc += S;
+      }
+      g[(0 * kG + r) * kGP + q] = gmu;
+      g[(1 * kG + r) * kGP + q] = gxx;
+      g[(2 * kG + r) * kGP + q] = gxy;
+    }
   }
   __syncthreads();
-  // backward horizontal pass: item = (g map, row, half of the 16 output columns)
-  constexpr int kSegH = kT / kRunBH;
-  for (int it = tid; it < 3 * kG * kSegH; it += 256) {
-    const int m = it / (kG * kSegH), rem = it - m * (kG * kSegH), r = rem / kSegH, q0 = (rem - r * kSegH) * kRunBH;
+  // backward horizontal pass: item = (g map, row, run of 8 output columns)
+  for (int it = tid; it < 3 * kG * (kT / kRunBH); it += 256) {
+    const int m = it / (kG * (kT / kRunBH)), rem = it - m * (kG * (kT / kRunBH));
+    const int r = rem / (kT / kRunBH), q0 = (rem - r * (kT / kRunBH)) * kRunBH;
     float a[kRunBH + 2 * kR], o[kRunBH];
+    const float* row = g + (m * kG + r) * kGP + q0;
 #pragma unroll
-    for (int k = 0; k < kRunBH + 2 * kR; ++k) a[k] = st[m][r][q0 + k];
+    for (int k = 0; k < kRunBH + 2 * kR; ++k) a[k] = row[k];
     win_run<kRunBH>(a, o);
+    float* d = hb + (m * kG + r) * kBP + q0;
 #pragma unroll
-    for (int k = 0; k < kRunBH; ++k) hb[m][r][q0 + k] = o[k];
+    for (int k = 0; k < kRunBH; ++k) d[k] = o[k];
   }
   __syncthreads();
-  // backward vertical pass: item = (g map, column, quarter of the 16 output rows);
-  // the window sums on the tile go to h[m] rows 0..15
-  constexpr int kSegV = kT / kRunBV;
-  for (int it = tid; it < 3 * kT * kSegV; it += 256) {
-    const int m = it / (kT * kSegV), rem = it - m * (kT * kSegV), q = rem / kSegV, r0 = (rem - q * kSegV) * kRunBV;
-    float a[kRunBV + 2 * kR], o[kRunBV];
-#pragma unroll
-    for (int k = 0; k < kRunBV + 2 * kR; ++k) a[k] = hb[m][r0 + k][q];
-    win_run<kRunBV>(a, o);
-#pragma unroll
-    for (int k = 0; k < kRunBV; ++k) h[m][r0 + k][q] = o[k];
-  }
-  __syncthreads();
+  // backward vertical pass of the three maps for 4 pixels of one column of
+  // the tile, and dL/dI there
   {
-    const int r = tid / kT, q = tid - r * kT;  // 256 threads = one output pixel each
-    const int px = tx * kT + q, py = ty * kT + r;
-    if (px < W && py < H) {
-      const float x = sx[r + 2 * kR][q + 2 * kR], y = sy[r + 2 * kR][q + 2 * kR];
-      D[(long long)py * W + px] += h[0][r][q] + 2.f * x * h[1][r][q] + y * h[2][r][q];
+    const int q = tid % kT, r0 = (tid / kT) * kRunBV;
+    float wm[3][kRunBV];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      float a[kRunBV + 2 * kR];
+      const float* col = hb + (m * kG + r0) * kBP + q;
+#pragma unroll
+      for (int k = 0; k < kRunBV + 2 * kR; ++k) a[k] = col[k * kBP];
+      win_run<kRunBV>(a, wm[m]);
+    }
+    const int px = tx * kT + q;
+    if (px < W) {
+#pragma unroll
+      for (int o = 0; o < kRunBV; ++o) {
+        const int py = ty * kT + r0 + o;
+        if (py < H) {
+          const long long p = (long long)py * W + px;
+          D[p] += wm[0][o] + 2.f * X[p] * wm[1][o] + Y[p] * wm[2][o];
+        }
+      }
     }
   }
   // loss partial of this block: -lambda_s / (3 P) * sum S (fixed-order reduction)
@@ -226,13 +245,15 @@ cudaError_t ssim_init() {
   for (int k = -kR; k <= kR; ++k) s += (w[k + kR] = std::exp(-(double)(k * k) / (2.0 * 1.5 * 1.5)));
   float wf[2 * kR + 1];
   for (int k = 0; k <= 2 * kR; ++k) wf[k] = (float)(w[k] / s);
-  return cudaMemcpyToSymbol(c_win, wf, sizeof(wf));
+  cudaError_t e = cudaMemcpyToSymbol(c_win, wf, sizeof(wf));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ssim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsimSmem);
+  return e;
 }
 
 void launch_ssim(const float* rgb, const float* trgb, const DevCam* cams, int V, int n_tiles, float lam_s, float* dr,
                  float* loss, float* part, cudaStream_t st) {
   if (n_tiles <= 0) return;
-  k_ssim<<<dim3((unsigned)n_tiles, 3), 256, 0, st>>>(rgb, trgb, cams, V, lam_s, dr, part);
+  k_ssim<<<dim3((unsigned)n_tiles, 3), 256, kSsimSmem, st>>>(rgb, trgb, cams, V, lam_s, dr, part);
   k_sum_partials<<<1, 256, 0, st>>>(part, 3ll * n_tiles, lam_s * (float)V, loss);
   count_launch(2);
 }
