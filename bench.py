@@ -521,10 +521,11 @@ def _rigid(deg_z, t):
 def loop_closure_leg(sc, K):
     """Loop-closure correction (Sec. III-F) of the window map: two keyframes' Gaussians move with
     their pose corrections and are redistributed over the chunks; corrections alternate with their
-    inverses so the map stays near its start.  Wall time per call (host re-bucketing included) and
-    the device phases; algorithmic device bytes per gathered Gaussian: the transform (10 floats read,
-    7 written), the keys (12 B read, 8 B written), the row permutation and the page writes (each
-    4 F B read and written)."""
+    inverses so the map stays near its start.  Wall time per call (host planning of the moved rows
+    included) and the device phases; algorithmic device bytes per gathered Gaussian: the transform
+    (10 floats read, 7 written), the keys (12 B read, 8 B written), the moved flags (flag and key read,
+    flag written), their ordered compaction (flag read twice), the destinations (flag read, index
+    written), the row permutation and the page writes (each 4 F B read and written)."""
     import time
 
     import torch
@@ -565,7 +566,7 @@ def loop_closure_leg(sc, K):
         dev_ms = prof["loop_closure"][0] / K
         gather_ms = (prof["gather"][0] + prof["stall"][0]) / K
         n_g = float(np.mean(ngs))
-        algo = int(n_g * (40 + 28 + 20 + 16 * F))
+        algo = int(n_g * (40 + 28 + 20 + 36 + 16 * F))
         gbs = algo / (dev_ms / 1e3) / 1e9
         return {"what": "loop-closure correction + chunk redistribution of the 2-keyframe union (synchronous call)",
                 "gaussians": n_all, "gathered": int(n_g), "transformed": int(np.mean(nts)), "moved": int(np.mean(nms)),

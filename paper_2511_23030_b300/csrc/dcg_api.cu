@@ -139,11 +139,14 @@ struct dcg_ctx {
   uint32_t* d_lsflags = nullptr;
   u64* d_lscount = nullptr;
   u64* d_lsvcount = nullptr;  // samples per view of the last sampling call
-  char* h_lcstage = nullptr;  // loop closure: pinned keys, permutation and flags of the gathered rows
-  int64_t lc_cap = 0;
-  float* d_lctmp = nullptr;  // loop closure: permuted rows [Fs][n] and the permutation
-  long long* d_lcperm = nullptr;
+  float* d_lctmp = nullptr;  // loop closure: permuted rows [Fs][n], the permutation,
+  long long* d_lcperm = nullptr;  // the moved rows and their keys (later their destinations)
+  long long* d_lcmidx = nullptr;
+  u64* d_lcmkey = nullptr;
   int64_t lc_dev_cap = 0;
+  u64* d_lcsegkey = nullptr;      // per gathered chunk: id, destination base (max_chunks each)
+  long long* d_lcsegbase = nullptr;
+  u64* d_lccnt = nullptr;         // transformed and moved row counts
   cudaEvent_t ev_loss = nullptr;
   int fault = 0;
   // captured window graph
@@ -429,7 +432,9 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
   if (ssim_init() != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
   if (dmalloc(&ctx->d_lcmask, (size_t)kMaxViewsApi * c.max_chunks) != cudaSuccess ||
       dmalloc(&ctx->d_lcseg, (size_t)c.max_chunks) != cudaSuccess ||
-      dmalloc(&ctx->d_lcsegc, (size_t)c.max_chunks) != cudaSuccess || dmalloc(&ctx->d_lcview, kMaxViewsApi) != cudaSuccess)
+      dmalloc(&ctx->d_lcsegc, (size_t)c.max_chunks) != cudaSuccess || dmalloc(&ctx->d_lcview, kMaxViewsApi) != cudaSuccess ||
+      dmalloc(&ctx->d_lcsegkey, (size_t)c.max_chunks) != cudaSuccess ||
+      dmalloc(&ctx->d_lcsegbase, (size_t)c.max_chunks) != cudaSuccess || dmalloc(&ctx->d_lccnt, 2) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
   if (dmalloc(&ctx->d_errword, 1) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
   cudaMemset(ctx->d_errword, 0, sizeof(unsigned));
@@ -495,9 +500,13 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   if (ctx->win_exec) cudaGraphExecDestroy(ctx->win_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->h_wcams) cudaFreeHost(ctx->h_wcams);
-  if (ctx->h_lcstage) cudaFreeHost(ctx->h_lcstage);
   cudaFree(ctx->d_lctmp);
   cudaFree(ctx->d_lcperm);
+  cudaFree(ctx->d_lcmidx);
+  cudaFree(ctx->d_lcmkey);
+  cudaFree(ctx->d_lcsegkey);
+  cudaFree(ctx->d_lcsegbase);
+  cudaFree(ctx->d_lccnt);
   if (ctx->ev_win) cudaEventDestroy(ctx->ev_win);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
   cudaFree(ctx->d_losscams);
@@ -1152,84 +1161,105 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   launch_chunk_keys(ctx->d_active, 1, S, n, ctx->cfg.chunk_size, d_keys, ctx->d_errword, ctx->num_sms, s);
   hook(ctx)(PH_LOOP, false, s);
   CK(cudaGetLastError());
-  // per-row flags and keys come back, and the permutation goes out, through pinned staging
-  if (n > ctx->lc_cap) {
-    if (ctx->h_lcstage) cudaFreeHost(ctx->h_lcstage);
-    ctx->h_lcstage = nullptr;
-    ctx->lc_cap = 0;
-    CK(cudaHostAlloc((void**)&ctx->h_lcstage, (size_t)n * (4 + 8 + 8), 0));
-    ctx->lc_cap = n;
+  // 4. redistribution: a chunk keeps its remaining Gaussians in stored order
+  // and receives incoming ones after them, in gather order.  The device marks
+  // and compacts the moved rows (a rigid correction moves few across chunk
+  // borders), the host plans only those and the per-chunk offsets, and the
+  // device writes the permutation.
+  const int Fs = ctx->Fs;
+  if (n > ctx->lc_dev_cap) {  // device scratch kept between loop closures, grown on demand
+    CK(cudaStreamSynchronize(s));
+    cudaFree(ctx->d_lctmp);
+    cudaFree(ctx->d_lcperm);
+    cudaFree(ctx->d_lcmidx);
+    cudaFree(ctx->d_lcmkey);
+    ctx->d_lctmp = nullptr;
+    ctx->d_lcperm = ctx->d_lcmidx = nullptr;
+    ctx->d_lcmkey = nullptr;
+    ctx->lc_dev_cap = 0;
+    CK(cudaMalloc((void**)&ctx->d_lctmp, sizeof(float) * (size_t)Fs * (size_t)n));
+    CK(cudaMalloc((void**)&ctx->d_lcperm, sizeof(long long) * (size_t)n));
+    CK(cudaMalloc((void**)&ctx->d_lcmidx, sizeof(long long) * (size_t)n));
+    CK(cudaMalloc((void**)&ctx->d_lcmkey, sizeof(u64) * (size_t)n));
+    ctx->lc_dev_cap = n;
   }
-  uint64_t* const keys = reinterpret_cast<uint64_t*>(ctx->h_lcstage);
-  long long* const perm = reinterpret_cast<long long*>(ctx->h_lcstage + (size_t)n * 8);
-  uint32_t* const flags = reinterpret_cast<uint32_t*>(ctx->h_lcstage + (size_t)n * 16);
-  if (n) {
-    CK(cudaMemcpyAsync(flags, d_flags, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(keys, d_keys, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
-  }
+  CK(cudaMemcpyAsync(ctx->d_lcsegkey, segkey.data(), sizeof(u64) * (size_t)nl, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ctx->d_lccnt, 0, 2 * sizeof(u64), s));
+  hook(ctx)(PH_LOOP, true, s);
+  launch_lc_moved(d_flags, d_keys, n, ctx->d_lcseg, ctx->d_lcsegkey, nl, (unsigned long long*)ctx->d_lccnt,
+                  ctx->d_lcmidx, ctx->d_lcmkey, st->part, st->P, ctx->d_lccnt + 1, ctx->num_sms, s);
+  hook(ctx)(PH_LOOP, false, s);
+  CK(cudaGetLastError());
+  u64 cnt[2] = {0, 0};
+  CK(cudaMemcpyAsync(cnt, ctx->d_lccnt, sizeof(cnt), cudaMemcpyDeviceToHost, s));
   dcg_status es = dcg_sync(ctx, stream);  // a corrected position outside the key range stops here, table unchanged
   if (es != DCG_OK) {
     ctx->active_valid = false;
     return es;
   }
-  // 4. redistribution: a chunk keeps its remaining Gaussians in stored order
-  // and receives incoming ones after them, in gather order; only the moved
-  // rows are collected (a rigid correction moves few across chunk borders)
-  int64_t nt = 0;
-  std::vector<std::pair<uint64_t, int64_t>> moved;  // (target key, row) in gather order
-  std::vector<int64_t> stays((size_t)nl);
-  for (int k = 0; k < nl; ++k) {
-    const int64_t a = seg[(size_t)k], end = k + 1 < nl ? seg[(size_t)k + 1] : n;
-    const uint64_t sk = segkey[(size_t)k];
-    int64_t st = 0;
-    for (int64_t i = a; i < end; ++i) {
-      nt += flags[i] != 0u;
-      if (keys[i] == sk)
-        ++st;
-      else
-        moved.emplace_back(keys[i], i);
-    }
-    stays[(size_t)k] = st;
-  }
-  const int64_t nm = (int64_t)moved.size();
+  const int64_t nt = (int64_t)cnt[0], nm = (int64_t)cnt[1];
   if (n_transformed) *n_transformed = nt;
   if (n_moved) *n_moved = nm;
   if (nm == 0) return dcg_scatter_back(ctx, &g, n, stream);
-  // by target chunk, gather order kept within each
-  std::stable_sort(moved.begin(), moved.end(),
-                   [](const std::pair<uint64_t, int64_t>& x, const std::pair<uint64_t, int64_t>& y) {
-                     return x.first < y.first;
-                   });
-  std::vector<char> placed((size_t)nm, 0);
-  std::vector<int64_t> newcount((size_t)nl);
-  int64_t j = 0;
+  std::vector<long long> midx((size_t)nm);
+  std::vector<uint64_t> mkey((size_t)nm);
+  CK(cudaMemcpyAsync(midx.data(), ctx->d_lcmidx, sizeof(long long) * (size_t)nm, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(mkey.data(), ctx->d_lcmkey, sizeof(u64) * (size_t)nm, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // per segment: rows moving out and moved rows before its first row
+  std::vector<int64_t> out_k((size_t)nl, 0), mb_k((size_t)nl, 0), size_k((size_t)nl);
+  {
+    int64_t m = 0;
+    for (int k = 0; k < nl; ++k) {
+      const int64_t end = k + 1 < nl ? seg[(size_t)k + 1] : n;
+      size_k[(size_t)k] = end - seg[(size_t)k];
+      mb_k[(size_t)k] = m;
+      while (m < nm && midx[(size_t)m] < end) {
+        ++out_k[(size_t)k];
+        ++m;
+      }
+    }
+  }
+  // moved rows by target chunk, gather order kept within each
+  std::vector<int64_t> order((size_t)nm);
+  for (int64_t t = 0; t < nm; ++t) order[(size_t)t] = t;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return mkey[(size_t)x] < mkey[(size_t)y]; });
+  std::vector<std::pair<uint64_t, int>> keyk((size_t)nl);
+  for (int k = 0; k < nl; ++k) keyk[(size_t)k] = {segkey[(size_t)k], k};
+  std::sort(keyk.begin(), keyk.end());
+  auto gathered = [&](uint64_t key) {  // list position of the gathered chunk with this id, or -1
+    auto it = std::lower_bound(keyk.begin(), keyk.end(), std::make_pair(key, -1));
+    return it != keyk.end() && it->first == key ? it->second : -1;
+  };
+  std::vector<int64_t> in_k((size_t)nl, 0);
+  for (int64_t t = 0; t < nm; ++t) {
+    const int k = gathered(mkey[(size_t)order[(size_t)t]]);
+    if (k >= 0) ++in_k[(size_t)k];
+  }
+  std::vector<int64_t> newcount((size_t)nl), newoff((size_t)nl);
+  int64_t n_kept = 0;  // Gaussians staying on the device (gathered chunks)
   for (int k = 0; k < nl; ++k) {
-    const int64_t a = seg[(size_t)k], end = k + 1 < nl ? seg[(size_t)k + 1] : n;
-    const uint64_t sk = segkey[(size_t)k];
-    if (stays[(size_t)k] == end - a) {
-      for (int64_t i = a; i < end; ++i) perm[j++] = i;
-    } else {
-      for (int64_t i = a; i < end; ++i)
-        if (keys[i] == sk) perm[j++] = i;
-    }
-    auto lo = std::lower_bound(moved.begin(), moved.end(), sk,
-                               [](const std::pair<uint64_t, int64_t>& x, uint64_t key) { return x.first < key; });
-    int64_t in = 0;
-    for (auto it = lo; it != moved.end() && it->first == sk; ++it, ++in) {
-      perm[j++] = it->second;
-      placed[(size_t)(it - moved.begin())] = 1;
-    }
-    newcount[(size_t)k] = stays[(size_t)k] + in;
+    newcount[(size_t)k] = size_k[(size_t)k] - out_k[(size_t)k] + in_k[(size_t)k];
+    newoff[(size_t)k] = n_kept;
+    n_kept += newcount[(size_t)k];
   }
-  const int64_t n_kept = j;  // Gaussians staying on the device (gathered chunks)
+  std::vector<long long> mdest((size_t)nm), base((size_t)nl);
+  std::vector<int64_t> fill((size_t)nl, 0);
   std::vector<std::pair<uint64_t, int64_t>> outside;  // (key, count) of targets that were not gathered, ascending
-  for (int64_t m = 0; m < nm; ++m) {
-    if (placed[(size_t)m]) continue;
-    perm[j++] = moved[(size_t)m].second;
-    if (outside.empty() || outside.back().first != moved[(size_t)m].first)
-      outside.emplace_back(moved[(size_t)m].first, 0);
-    ++outside.back().second;
+  int64_t od = n_kept;
+  for (int64_t t = 0; t < nm; ++t) {
+    const int64_t pos = order[(size_t)t];
+    const uint64_t key = mkey[(size_t)pos];
+    const int k = gathered(key);
+    if (k >= 0) {
+      mdest[(size_t)pos] = newoff[(size_t)k] + size_k[(size_t)k] - out_k[(size_t)k] + fill[(size_t)k]++;
+    } else {
+      mdest[(size_t)pos] = od++;
+      if (outside.empty() || outside.back().first != key) outside.emplace_back(key, 0);
+      ++outside.back().second;
+    }
   }
+  for (int k = 0; k < nl; ++k) base[(size_t)k] = newoff[(size_t)k] - seg[(size_t)k] + mb_k[(size_t)k];
   // capacity checks before anything changes
   int64_t dev_need = 0, dev_have = 0, host_need = 0, host_have = 0, new_chunks = 0;
   for (int k = 0; k < nl; ++k) {
@@ -1253,24 +1283,16 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   if (host_need - host_have > (int64_t)ctx->host_free.size()) return fail(ctx, DCG_ERR_CAPACITY, "host tier full");
   if ((int64_t)ctx->chunks.size() + new_chunks > ctx->cfg.max_chunks)
     return fail(ctx, DCG_ERR_CAPACITY, "chunk table full");
-  // permuted copy of the active rows (parameters and moments)
-  const int Fs = ctx->Fs;
-  float* d_tmp = nullptr;
-  long long* d_perm = nullptr;
-  if (n > ctx->lc_dev_cap) {  // device scratch kept between loop closures, grown on demand
-    CK(cudaStreamSynchronize(s));
-    cudaFree(ctx->d_lctmp);
-    cudaFree(ctx->d_lcperm);
-    ctx->d_lctmp = nullptr;
-    ctx->d_lcperm = nullptr;
-    ctx->lc_dev_cap = 0;
-    CK(cudaMalloc((void**)&ctx->d_lctmp, sizeof(float) * (size_t)Fs * (size_t)n));
-    CK(cudaMalloc((void**)&ctx->d_lcperm, sizeof(long long) * (size_t)n));
-    ctx->lc_dev_cap = n;
-  }
-  d_tmp = ctx->d_lctmp;
-  d_perm = ctx->d_lcperm;
-  CK(cudaMemcpyAsync(d_perm, perm, sizeof(long long) * (size_t)n, cudaMemcpyHostToDevice, s));
+  // the permutation from the planned destinations, then the permuted copy of
+  // the active rows (parameters and moments)
+  float* const d_tmp = ctx->d_lctmp;
+  long long* const d_perm = ctx->d_lcperm;
+  CK(cudaMemcpyAsync(ctx->d_lcmkey, mdest.data(), sizeof(long long) * (size_t)nm, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->d_lcsegbase, base.data(), sizeof(long long) * (size_t)nl, cudaMemcpyHostToDevice, s));
+  hook(ctx)(PH_LOOP, true, s);
+  launch_lc_dest(d_flags, n, ctx->d_lcseg, ctx->d_lcsegbase, nl, ctx->d_lcmidx,
+                 reinterpret_cast<const long long*>(ctx->d_lcmkey), nm, d_perm, ctx->num_sms, s);
+  hook(ctx)(PH_LOOP, false, s);
   hook(ctx)(PH_LOOP, true, s);
   launch_permute_rows(ctx->d_active, S, d_tmp, n, d_perm, n, Fs, ctx->num_sms, s);
   hook(ctx)(PH_LOOP, false, s);

@@ -56,6 +56,16 @@ struct LcView {
 void launch_loop_transform(float* act, long long stride, long long n, const long long* seg_off, const int* seg_chunk,
                            int nseg, const uint8_t* mask, int C, const LcView* kf, int K, uint32_t* flags, int num_sms,
                            cudaStream_t st);
+// Loop-closure redistribution: moved flags (in place of the transformed
+// flags, whose count goes to *n_transformed), the moved rows ascending with
+// their keys in midx / mkey and their number in *n_moved; then the
+// permutation perm (gather form) from the planned destinations.
+void launch_lc_moved(uint32_t* flags, const u64* keys, long long n, const long long* seg_off, const u64* seg_key,
+                     int nseg, unsigned long long* n_transformed, long long* midx, u64* mkey, u64* part, int P,
+                     u64* n_moved, int num_sms, cudaStream_t st);
+void launch_lc_dest(const uint32_t* moved, long long n, const long long* seg_off, const long long* seg_base, int nseg,
+                    const long long* midx, const long long* mdest, long long nm, long long* perm, int num_sms,
+                    cudaStream_t st);
 void launch_permute_rows(const float* src, long long sstride, float* dst, long long dstride, const long long* perm,
                          long long n, int rows, int num_sms, cudaStream_t st);
 void launch_cap_rows(float* row, long long n, float cap, int num_sms, cudaStream_t st);

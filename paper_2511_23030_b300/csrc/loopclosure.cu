@@ -11,6 +11,7 @@
 // and the chunk ids recomputed from the result (Eq. 5/6) are reproducible.
 #include <algorithm>
 
+#include "device_scan.cuh"
 #include "kernels.cuh"
 
 namespace dcg {
@@ -72,6 +73,86 @@ __global__ void k_permute_rows(const float* __restrict__ src, long long sstride,
 __global__ void k_cap_rows(float* __restrict__ row, long long n, float cap) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
     row[j] = fminf(row[j], cap);
+}
+
+// Redistribution on the device.  The gathered rows form nseg segments (chunk
+// k owns rows [seg_off[k], seg_off[k + 1])); a row moves if its recomputed
+// chunk id differs from its segment's.  k_lc_moved turns the transformed
+// flag of each row into its moved flag and counts the transformed rows;
+// the moved rows (ascending) are then compacted by the ordered scan.
+__device__ __forceinline__ int lc_seg_of(const long long* __restrict__ seg_off, int nseg, long long i) {
+  int lo = 0, hi = nseg - 1;  // last k with seg_off[k] <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg_off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_lc_moved(uint32_t* __restrict__ flags, const u64* __restrict__ keys, long long n,
+                           const long long* __restrict__ seg_off, const u64* __restrict__ seg_key, int nseg,
+                           unsigned long long* n_transformed) {
+  unsigned long long cnt = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    cnt += flags[i] != 0u;
+    flags[i] = keys[i] != seg_key[lc_seg_of(seg_off, nseg, i)] ? 1u : 0u;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(n_transformed, cnt);
+}
+
+struct LcMovedCount {
+  const uint32_t* f;
+  __device__ u64 operator()(u64 i) const { return f[i]; }
+};
+struct LcMovedEmit {
+  long long* idx;
+  u64* key_out;
+  const u64* keys;
+  __device__ void operator()(u64 i, u64 off, u64) const {
+    idx[off] = (long long)i;
+    key_out[off] = keys[i];
+  }
+};
+
+// Destination of every row in the redistributed order: a moved row is the
+// j-th moved row, j = the number of moved rows before it, and goes to
+// mdest[j]; a staying row of segment k keeps its rank among the segment's
+// stays: dest = i - (moved rows before i) + seg_base[k].  perm[dest] = i.
+__global__ void k_lc_dest(const uint32_t* __restrict__ moved, long long n, const long long* __restrict__ seg_off,
+                          const long long* __restrict__ seg_base, int nseg, const long long* __restrict__ midx,
+                          const long long* __restrict__ mdest, long long nm, long long* __restrict__ perm) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    long long lo = 0, hi = nm;  // moved rows with index < i
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if (midx[mid] < i) lo = mid + 1; else hi = mid;
+    }
+    const long long d = moved[i] ? mdest[lo] : i - lo + seg_base[lc_seg_of(seg_off, nseg, i)];
+    perm[d] = i;
+  }
+}
+
+void launch_lc_moved(uint32_t* flags, const u64* keys, long long n, const long long* seg_off, const u64* seg_key,
+                     int nseg, unsigned long long* n_transformed, long long* midx, u64* mkey, u64* part, int P,
+                     u64* n_moved, int num_sms, cudaStream_t st) {
+  if (n <= 0) return;
+  const long long blocks = (n + 255) / 256;
+  k_lc_moved<<<(int)std::min<long long>(blocks, (long long)num_sms * 8), 256, 0, st>>>(flags, keys, n, seg_off,
+                                                                                     seg_key, nseg, n_transformed);
+  part_scan_emit(nullptr, (u64)n, LcMovedCount{flags}, LcMovedEmit{midx, mkey, keys}, part, P, n_moved, st);
+  count_launch(4);
+}
+
+void launch_lc_dest(const uint32_t* moved, long long n, const long long* seg_off, const long long* seg_base, int nseg,
+                    const long long* midx, const long long* mdest, long long nm, long long* perm, int num_sms,
+                    cudaStream_t st) {
+  if (n <= 0) return;
+  const long long blocks = (n + 255) / 256;
+  k_lc_dest<<<(int)std::min<long long>(blocks, (long long)num_sms * 8), 256, 0, st>>>(moved, n, seg_off, seg_base,
+                                                                                    nseg, midx, mdest, nm, perm);
+  count_launch();
 }
 
 void launch_loop_transform(float* act, long long stride, long long n, const long long* seg_off, const int* seg_chunk,

@@ -78,9 +78,9 @@ def test_loop_closure_matches_reference():
         nt, nm = dcg.dcg_loop_closure(ctx, kfs, corrs)
         prof = dcg.dcg_profile_read(ctx)
         dcg.dcg_profile(ctx, False)
-        # device intervals: cull, transform + keys, permutation, page writes (the batch load is timed
-        # as a gather, here none: the active buffer already holds the union's chunks)
-        assert prof["loop_closure"][1] == 4 and prof["loop_closure"][0] > 0
+        # device intervals: cull, transform + keys, moved rows, destinations, permutation, page writes
+        # (the batch load is timed as a gather, here none: the active buffer already holds the union)
+        assert prof["loop_closure"][1] == 6 and prof["loop_closure"][0] > 0
         dcg.dcg_flush(ctx)
         after = _read_all(ctx, F)
         want, wt, wm = lc.loop_closure(before, sc["chunk_size"], 60.0, kfs, corrs)
