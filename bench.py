@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--stage", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="batched timing only (no plain/e2e/CPU legs), for profilers")
-    ap.add_argument("--workload", default="window", choices=["window", "corridor", "sampling", "loopclosure"])
+    ap.add_argument("--workload", default="window", choices=["window", "corridor", "sampling", "loopclosure", "loss"])
     ap.add_argument("--bwd", default="warp", choices=["warp", "slots"], help="backward gradient accumulation")
     ap.add_argument("--length", type=float, default=5000.0, help="corridor: metres of road (1 m per frame)")
     ap.add_argument("--per-m", type=int, default=8000, help="corridor: Gaussians per metre (40M per 5 km)")
@@ -845,8 +845,71 @@ def run_sampling(args):
     return out
 
 
+def run_loss(args):
+    """The image loss of Eq. 2-4 alone (L1 colour and depth plus the SSIM term, lambda_s = 0.2) and
+    its gradient over the window's 8 views: the window is rendered once, then dcg_loss is timed with
+    the library's phase timers.  SSIM bound: FP32 issue; its work is ~290 FMA per pixel and channel
+    (the window passes of the 32 x 32-tile kernel), its bytes 24 per pixel and channel plus the L1
+    parts (40 per pixel)."""
+    import torch
+
+    from paper_2511_23030_b300 import build, dcg, synth
+
+    build.build()
+    sc = synth.window_scene(0, n=args.gaussians)
+    P, cams = sc["params"], sc["cams"]
+    n_all = P.shape[0]
+    npix = sum(c.W * c.H for c in cams)
+    cfg = dcg.config(sh_degree=sc["deg"], max_active=n_all + 1024, max_views=8, max_pixels=npix,
+                     max_instances=160 << 20, chunk_size=sc["chunk_size"], device_budget=6_000_000,
+                     host_capacity=n_all + 1024, dfar=60.0)
+    ctx = dcg.dcg_create(cfg)
+    try:
+        g_t = torch.from_numpy(np.ascontiguousarray(P.T)).cuda()
+        dcg.dcg_chunk_table_update(ctx, g_t, n_all)
+        del g_t
+        g, n = dcg.dcg_gather_active(ctx, dcg.dcg_cull_chunks(ctx, cams))
+        rgb, depth = torch.zeros(3 * npix, device="cuda"), torch.zeros(npix, device="cuda")
+        dcg.dcg_render_fwd(ctx, g, n, cams, rgb, depth)
+        trgb = torch.from_numpy(np.concatenate([t.reshape(-1) for t in sc["target_rgb"]])).cuda()
+        tdep = torch.from_numpy(np.concatenate([t.reshape(-1) for t in sc["target_depth"]])).cuda()
+        dr, dd, loss = torch.zeros_like(rgb), torch.zeros_like(depth), torch.zeros(1, device="cuda")
+
+        def step():
+            loss.zero_()
+            dcg.dcg_loss(ctx, rgb, depth, trgb, tdep, cams, LAMBDA_S, sc["lambda_depth"], dr, dd, loss)
+
+        for _ in range(args.warmup):
+            step()
+        dcg.dcg_sync(ctx)
+        dcg.dcg_profile(ctx, True)
+        dcg.dcg_profile_read(ctx)
+        for _ in range(args.steps):
+            step()
+        prof = dcg.dcg_profile_read(ctx)
+        dcg.dcg_profile(ctx, False)
+        ms = prof["loss"][0] / args.steps
+        hbm, sm_max, src = peaks()
+        flops = 2 * 290 * 3 * npix
+        peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12
+        return {"workload": "loss", "metric": "image loss (L1 + SSIM, Eq. 2-4) and gradient, Mpix/s per keyframe window",
+                "value": round(npix / (ms / 1e3) / 1e6, 1), "unit": "Mpix/s", "ms_per_window": round(ms, 4),
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+                "lambda_s": LAMBDA_S, "loss": float(loss),
+                "roofline": {"bound": "alu", "achieved": round(flops / (ms / 1e3) / 1e12, 2), "peak": round(peak, 1),
+                             "unit": "TFLOP/s", "frac": round(flops / (ms / 1e3) / 1e12 / peak, 4),
+                             "hbm_gbs": round((24 * 3 + 40) * npix / (ms / 1e3) / 1e9, 1), "hbm_peak": hbm,
+                             "peak_source": f"derived (sm_max {sm_max} MHz); HBM {src}"},
+                "data": "synthetic window scene (8 views, 4,032,000 px)"}
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
 def main():
     args = parse()
+    if args.workload == "loss":
+        print(json.dumps(run_loss(args)))
+        return
     if args.workload == "corridor":
         print(json.dumps(run_corridor(args)))
         return
