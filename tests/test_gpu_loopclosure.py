@@ -68,18 +68,29 @@ def _same(after, want):
         assert (err <= 2e-6 * np.abs(qw).max(1) + 1e-30).all(), k
 
 
-def test_loop_closure_matches_reference():
+# (keyframes, corrections): two keyframes whose frusta gather every chunk (moved rows go to gathered
+# chunks and to new ones); one keyframe gathering 48 of the 64 chunks, shifted 4 m (moved rows also go
+# to 13 existing chunks outside the union, which are written back and appended to)
+SCENARIOS = {
+    "two_keyframes": ([0, 3], [("z", 2.0, (0.8, -0.4, 0.3)), ("x", 1.5, (-0.6, 0.5, 0.2))]),
+    "partial_union": ([3], [("z", 3.0, (0.0, 0.0, 4.0))]),
+}
+
+
+@pytest.mark.parametrize("scenario", list(SCENARIOS))
+def test_loop_closure_matches_reference(scenario):
     ctx, sc, F = _setup()
     try:
-        kfs = [sc["cams"][0], sc["cams"][3]]
-        corrs = [_corr("z", 2.0, (0.8, -0.4, 0.3)), _corr("x", 1.5, (-0.6, 0.5, 0.2))]
+        kf_ids, cs = SCENARIOS[scenario]
+        kfs = [sc["cams"][k] for k in kf_ids]
+        corrs = [_corr(*c) for c in cs]
         before = _read_all(ctx, F)
         dcg.dcg_profile(ctx, True)
         nt, nm = dcg.dcg_loop_closure(ctx, kfs, corrs)
         prof = dcg.dcg_profile_read(ctx)
         dcg.dcg_profile(ctx, False)
         # device intervals: cull, transform + keys, moved rows, destinations, permutation, page writes
-        # (the batch load is timed as a gather, here none: the active buffer already holds the union)
+        # (the batch load of the union is timed as a gather)
         assert prof["loop_closure"][1] == 6 and prof["loop_closure"][0] > 0
         dcg.dcg_flush(ctx)
         after = _read_all(ctx, F)
