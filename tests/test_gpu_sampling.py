@@ -97,13 +97,22 @@ def _posed_cam(W, H, f, yaw, t):
     return synth.Camera(f, f * 1.05, W / 2.0 + 0.3, H / 2.0 - 0.2, W, H, T, 0.2, 100.0)
 
 
-def test_window_of_views_in_one_call_matches_reference_and_single_calls():
-    """Three views of uneven sizes through dcg_log_sample_views / dcg_backproject_views: per view the
-    same P_s and samples as the one-view call (bit-identical) and as the reference; window indices
-    ascending; per-view counts; back-projection with each view's own pose."""
+WINDOWS = {
+    "three_views": [(100, 70), (37, 23), (16, 16)],
+    # the most views a call takes, uneven and mostly below one 32 x 32 tile
+    "sixteen_views": [(1, 1), (5, 3), (33, 31), (64, 8), (2, 40), (17, 17), (31, 33), (3, 1),
+                      (40, 40), (7, 9), (1, 64), (32, 32), (9, 2), (65, 33), (4, 4), (12, 30)],
+}
+
+
+@pytest.mark.parametrize("window", list(WINDOWS))
+def test_window_of_views_in_one_call_matches_reference_and_single_calls(window):
+    """A window of views of uneven sizes through dcg_log_sample_views / dcg_backproject_views: per
+    view the same P_s and samples as the one-view call (bit-identical) and as the reference; window
+    indices ascending; per-view counts; back-projection with each view's own pose."""
     import torch
 
-    sizes = [(100, 70), (37, 23), (16, 16)]
+    sizes = WINDOWS[window]
     cams = [_posed_cam(W, H, 80.0 + 10 * k, 0.1 * k, (0.2 * k, -0.1, 0.05 * k)) for k, (W, H) in enumerate(sizes)]
     offs = np.cumsum([0] + [W * H for W, H in sizes])
     N = int(offs[-1])
