@@ -13,11 +13,13 @@
 // A call covers every view of a keyframe window at once: one penalty grid
 // over all views' 32 x 32 tiles (a block finds its view in the table passed
 // by value), one ordered compaction over the concatenated pixels (window
-// indices: views in order, each ascending), one back-projection.
+// indices: views in order, each ascending), the samples per view by a search
+// of the sorted indices, one back-projection.
 //
 // One block of 256 threads per 32 x 32 output tile takes the six image x
-// channel planes one at a time (16 KB of shared memory, so 8 blocks fit an
-// SM): it stages the plane on the tile plus a 3-pixel halo (38 x 38), runs
+// channel planes one at a time (16 KB of shared memory; its 64 registers
+// leave four blocks per SM): it stages the plane on the tile plus a 3-pixel
+// halo (38 x 38), runs
 // the two horizontal passes (g, g2) as a sliding window (a task is 4
 // adjacent outputs of one row from three float4 loads, written as two
 // float4), then each thread runs the vertical pass for 4 rows of one column
