@@ -762,7 +762,9 @@ def run_corridor(args):
     for c in cams:
         c.zfar = zfar
     N, F = P.shape
-    budget = min(6_000_000, int(0.15 * N))  # device active set: 6 M Gaussians on the 5 km drive
+    # device active set: 6 M Gaussians on the 5 km drive; at least 1.2 M, which holds the chunks one
+    # frame sees (about 0.5-0.7 M Gaussians at 8000 per metre), so that short drives run too
+    budget = min(6_000_000, max(int(0.15 * N), 1_200_000))
     Pt = torch.from_numpy(np.ascontiguousarray(P.T))
     del P
     t_gen = time.perf_counter() - t0
