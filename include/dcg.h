@@ -180,6 +180,15 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* chunk_list, int32_t n_
  * A caller buffer is copied at once (the moments from the active buffer). */
 dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n, void* stream);
 
+/* For every row j of the last gathered active set (n_active rows): the
+ * chunk it belongs to (its index in the table now, as in dcg_chunk_info) in
+ * chunk_out[j] and its row in that chunk's stored order in row_out[j] (dev
+ * [n_active] each, either may be NULL).  Rows follow the gather: listed
+ * chunks in ascending id, each with the count it had when gathered.
+ * DCG_ERR_STATE without a valid gathered set (none yet, or after a loop
+ * closure).  Asynchronous on `stream`. */
+dcg_status dcg_active_map(dcg_ctx* ctx, int32_t* chunk_out, int32_t* row_out, void* stream);
+
 /* Complete a deferred write-back of the active buffer, copy every resident
  * dirty chunk back to the host tier and wait. */
 dcg_status dcg_flush(dcg_ctx* ctx, void* stream);

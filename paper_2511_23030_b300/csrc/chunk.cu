@@ -192,6 +192,30 @@ __global__ void k_scatter_pages(float* __restrict__ pool, long long page_g, int 
   }
 }
 
+// Chunk index and row within the chunk of every active row: the last
+// gathered chunk whose first active row is at or before it (off ascending).
+__global__ void k_active_map(const long long* __restrict__ off, const int32_t* __restrict__ chunk, int nl, long long n,
+                             int32_t* __restrict__ chunk_out, int32_t* __restrict__ row_out) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    if (chunk_out) chunk_out[j] = chunk[lo];
+    if (row_out) row_out[j] = (int32_t)(j - off[lo]);
+  }
+}
+
+void launch_active_map(const long long* off, const int32_t* chunk, int nl, long long n, int32_t* chunk_out,
+                       int32_t* row_out, int num_sms, cudaStream_t st) {
+  if (n <= 0 || nl <= 0) return;
+  const long long blocks = (n + 255) / 256;
+  k_active_map<<<(int)(blocks < num_sms * 8ll ? blocks : num_sms * 8ll), 256, 0, st>>>(off, chunk, nl, n, chunk_out,
+                                                                                     row_out);
+  count_launch();
+}
+
 void launch_page_copy(bool gather, float* pool, long long page_g, int Fp, int c0, int nc, const long long* desc, int nd,
                       float* active, long long stride, cudaStream_t st) {
   if (nd <= 0 || nc <= 0) return;

@@ -101,6 +101,7 @@ struct dcg_ctx {
   float* d_active = nullptr;
   int64_t n_active = 0;
   std::vector<uint64_t> active_keys;
+  std::vector<int64_t> active_counts;  // the gathered chunks' counts at the gather
   bool active_valid = false;
   // The active buffer as a write-back copy of the listed chunks: active_fresh
   // means a scatter_back of the buffer itself made it the chunks' stored value
@@ -147,6 +148,8 @@ struct dcg_ctx {
   u64* d_lcsegkey = nullptr;      // per gathered chunk: id, destination base (max_chunks each)
   long long* d_lcsegbase = nullptr;
   u64* d_lccnt = nullptr;         // transformed and moved row counts
+  long long* d_amoff = nullptr;   // active map: first active row and table index per gathered chunk
+  int32_t* d_amchunk = nullptr;
   cudaEvent_t ev_loss = nullptr;
   int fault = 0;
   // captured window graph
@@ -434,7 +437,9 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
       dmalloc(&ctx->d_lcseg, (size_t)c.max_chunks) != cudaSuccess ||
       dmalloc(&ctx->d_lcsegc, (size_t)c.max_chunks) != cudaSuccess || dmalloc(&ctx->d_lcview, kMaxViewsApi) != cudaSuccess ||
       dmalloc(&ctx->d_lcsegkey, (size_t)c.max_chunks) != cudaSuccess ||
-      dmalloc(&ctx->d_lcsegbase, (size_t)c.max_chunks) != cudaSuccess || dmalloc(&ctx->d_lccnt, 2) != cudaSuccess)
+      dmalloc(&ctx->d_lcsegbase, (size_t)c.max_chunks) != cudaSuccess || dmalloc(&ctx->d_lccnt, 2) != cudaSuccess ||
+      dmalloc(&ctx->d_amoff, (size_t)c.max_chunks) != cudaSuccess ||
+      dmalloc(&ctx->d_amchunk, (size_t)c.max_chunks) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
   if (dmalloc(&ctx->d_errword, 1) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
   cudaMemset(ctx->d_errword, 0, sizeof(unsigned));
@@ -507,6 +512,8 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   cudaFree(ctx->d_lcsegkey);
   cudaFree(ctx->d_lcsegbase);
   cudaFree(ctx->d_lccnt);
+  cudaFree(ctx->d_amoff);
+  cudaFree(ctx->d_amchunk);
   if (ctx->ev_win) cudaEventDestroy(ctx->ev_win);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
   cudaFree(ctx->d_losscams);
@@ -785,9 +792,11 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
   int nd = 0;
   int64_t off = 0;
   ctx->active_keys.clear();
+  ctx->active_counts.clear();
   for (int k = 0; k < n_list; ++k) {
     const Chunk& ch = ctx->chunks[list[k]];
     ctx->active_keys.push_back(ch.key);
+    ctx->active_counts.push_back(ch.count);
     for (size_t p = 0; p < ch.dev_pages.size(); ++p) {
       const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - (int64_t)p * ctx->page_g);
       ctx->h_desc[3 * nd + 0] = ch.dev_pages[p];
@@ -922,6 +931,29 @@ dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev_compute, s));
   for (uint64_t k : ctx->active_keys) ctx->chunks[ctx->index[k]].dirty = true;
+  return DCG_OK;
+}
+
+dcg_status dcg_active_map(dcg_ctx* ctx, int32_t* chunk_out, int32_t* row_out, void* stream) {
+  if (!ctx) return DCG_ERR_ARG;
+  if (!ctx->active_valid) return fail(ctx, DCG_ERR_STATE, "no gathered active set");
+  const int nl = (int)ctx->active_keys.size();
+  if (nl == 0 || ctx->n_active == 0 || (!chunk_out && !row_out)) return DCG_OK;
+  std::vector<long long> off((size_t)nl);
+  std::vector<int32_t> ci((size_t)nl);
+  long long o = 0;
+  for (int k = 0; k < nl; ++k) {
+    auto it = ctx->index.find(ctx->active_keys[(size_t)k]);
+    if (it == ctx->index.end()) return fail(ctx, DCG_ERR_STATE, "a gathered chunk left the table");
+    ci[(size_t)k] = it->second;
+    off[(size_t)k] = o;
+    o += ctx->active_counts[(size_t)k];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(ctx->d_amoff, off.data(), sizeof(long long) * (size_t)nl, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->d_amchunk, ci.data(), sizeof(int32_t) * (size_t)nl, cudaMemcpyHostToDevice, s));
+  launch_active_map(ctx->d_amoff, ctx->d_amchunk, nl, ctx->n_active, chunk_out, row_out, ctx->num_sms, s);
+  CK(cudaGetLastError());
   return DCG_OK;
 }
 

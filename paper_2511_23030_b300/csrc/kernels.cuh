@@ -39,6 +39,8 @@ void launch_chunk_keys(const float* means, long long row, long long col, long lo
                        unsigned* errword, int num_sms, cudaStream_t st);
 void launch_cull(const int32_t* coords, int C, const dcg_camera* cams, int V, float s, float dfar, uint8_t* mask,
                  uint8_t* vis, int32_t* list, int32_t* n, cudaStream_t st);
+void launch_active_map(const long long* off, const int32_t* chunk, int nl, long long n, int32_t* chunk_out,
+                       int32_t* row_out, int num_sms, cudaStream_t st);
 void launch_page_copy(bool gather, float* pool, long long page_g, int Fp, int c0, int nc, const long long* desc, int nd,
                       float* active, long long stride, cudaStream_t st);
 

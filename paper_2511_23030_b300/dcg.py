@@ -116,6 +116,7 @@ _SIGS = {
                                       _P]),
     "dcg_backproject": (ctypes.c_int, [_P, _P, _I32, _P, _P, ctypes.POINTER(dcg_camera), ctypes.c_float, _P, _I64,
                                        _P]),
+    "dcg_active_map": (ctypes.c_int, [_P, _P, _P, _P]),
     "dcg_log_sample_views": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _I32, _P, _P, ctypes.c_float, _P, _P, _P,
                                             _I64, _P, ctypes.POINTER(_I64), _P]),
     "dcg_backproject_views": (ctypes.c_int, [_P, _P, _I64, _P, _P, ctypes.POINTER(dcg_camera), _I32, ctypes.c_float,
@@ -327,6 +328,11 @@ def dcg_log_sample(ctx, image, rendered, W: int, H: int, kappa: float, u, idx_ou
     check(ctx, lib().dcg_log_sample(ctx, ptr(image), ptr(rendered), W, H, float(kappa), ptr(u), ptr(ps_out),
                                     ptr(idx_out), idx_out.numel(), ctypes.byref(n), stream_ptr(stream)))
     return int(n.value)
+
+
+def dcg_active_map(ctx, chunk_out=None, row_out=None, stream=None):
+    """Chunk index and row within the chunk of every row of the last gathered active set."""
+    check(ctx, lib().dcg_active_map(ctx, ptr(chunk_out), ptr(row_out), stream_ptr(stream)))
 
 
 def dcg_log_sample_views(ctx, cams, image, rendered, kappa: float, u, idx_out, ps_out=None, stream=None):

@@ -134,6 +134,41 @@ def test_gather_order_and_scatter_round_trip(orc):
         dcg.dcg_destroy(ctx)
 
 
+def test_active_map_names_each_active_row():
+    """dcg_active_map: every active row's chunk and row within the chunk, checked against the chunk
+    contents (bit-exact) and the gather order (listed chunks ascending, stored order within)."""
+    import torch
+
+    ctx, sc = _window_table()
+    try:
+        with pytest.raises(dcg.DcgError) as e:  # nothing gathered yet
+            dcg.dcg_active_map(ctx, torch.zeros(1, dtype=torch.int32, device="cuda"))
+        assert e.value.status == 9
+        F = sc["params"].shape[1]
+        info = dcg.dcg_chunk_info(ctx)
+        lst = dcg.dcg_cull_chunks(ctx, sc["cams"][2:5])
+        g, n = dcg.dcg_gather_active(ctx, lst)
+        chunk = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        row = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        dcg.dcg_active_map(ctx, chunk, row)
+        dcg.dcg_sync(ctx)
+        chunk, row = chunk.cpu().numpy(), row.cpu().numpy()
+        want_chunk = np.concatenate([np.full(int(info["counts"][c]), c) for c in lst])
+        want_row = np.concatenate([np.arange(int(info["counts"][c])) for c in lst])
+        assert np.array_equal(chunk, want_chunk) and np.array_equal(row, want_row)
+        act = _read_active(g, n, F)
+        for c in lst[:: max(1, len(lst) // 6)]:
+            stored = dcg.dcg_chunk_read(ctx, int(c), int(info["counts"][c]), F).T
+            sel = chunk == c
+            assert np.array_equal(act[sel], stored[row[sel]])
+        only_rows = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        dcg.dcg_active_map(ctx, None, only_rows)  # either output may be omitted
+        dcg.dcg_sync(ctx)
+        assert np.array_equal(only_rows.cpu().numpy(), want_row)
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
 def _read_active(g, n, F):
     """Copy of the library-owned active buffer (planar, stride g.stride) as numpy [n, F]."""
     return dcg.active_tensor(g, n, F).T.cpu().numpy()
