@@ -155,6 +155,15 @@ def project(params: np.ndarray, deg: int, cam) -> dict:
     return {k: out[:, i] for i, k in enumerate(PROJ_FIELDS)}
 
 
+def clamp_flags(params: np.ndarray, deg: int, cam) -> np.ndarray:
+    """Per Gaussian: bit 0 if x/z, bit 1 if y/z is clamped in the perspective
+    Jacobian (the image extended by 15 % per side)."""
+    P = np.ascontiguousarray(params, np.float64)
+    out = np.zeros(P.shape[0], np.int32)
+    lib().orc_clamp_flags(_p(P), ctypes.c_int64(P.shape[0]), ctypes.c_int(deg), ctypes.byref(_cam(cam)), _p(out))
+    return out
+
+
 def depth_f32(means: np.ndarray, cam) -> np.ndarray:
     means = np.ascontiguousarray(means, np.float32)
     T = np.ascontiguousarray(np.asarray(cam.Tcw, np.float32).reshape(16))
@@ -163,7 +172,10 @@ def depth_f32(means: np.ndarray, cam) -> np.ndarray:
     return z
 
 
-DEFAULT_EPS = (1e-4, 1e-4, 1e-4, 0.0)  # relative bands of q = 9, alpha = 1/255, T = 1e-4
+# Flag bands around the discrete thresholds q = 9, alpha = 1/255, T = 1e-4:
+# constant relative floors (none) and the factor on the first-order FP32 error
+# bounds the oracle derives per pixel and Gaussian (see orc_collect).
+DEFAULT_EPS = (0.0, 0.0, 0.0, 4.0)
 
 
 def all_pixels(W: int, H: int) -> np.ndarray:

@@ -465,6 +465,18 @@ int orc_project_all(const double* params, int64_t n, int deg, const OrcCam* cam,
   return 0;
 }
 
+// Which Gaussians take the clamped branch of the perspective Jacobian:
+// out[i] = clamp_x | clamp_y << 1 (0 for Gaussians culled by the near plane).
+int orc_clamp_flags(const double* params, int64_t n, int deg, const OrcCam* cam, int32_t* out) {
+  const int F = 11 + 3 * orc_nsh(deg);
+  for (int64_t i = 0; i < n; ++i) {
+    OrcProj g;
+    orc_project(&params[F * i], deg, cam, &g);
+    out[i] = g.vis ? (g.clamp_x | (g.clamp_y << 1)) : 0;
+  }
+  return 0;
+}
+
 // FP32 camera depth, the sort key of the kernels: ((W20*mx + W21*my) + W22*mz) + t2,
 // one rounding per operation.
 int orc_depth_f32(const float* means, int64_t n, const float* Tcw, float* z) {
@@ -488,15 +500,29 @@ int orc_depth_f32(const float* means, int64_t n, const float* Tcw, float* z) {
 //   front to back: stop before any Gaussian with T (1-alpha) < 1e-4;
 //   otherwise C += T alpha c, D += T alpha z, T *= (1 - alpha).  Background 0.
 // Order: ascending (FP32 depth key, index), see orc_project.
-// flags (for comparing with an FP32 implementation): bit0 a Gaussian at
-// |q-9| <= eps_q*9 that would pass the alpha test, bit1 alpha within
-// eps_a*(1/255) of the cut-off, bit2 T(1-alpha) within eps_t*1e-4 of the
-// cut-off.
+// flags (for comparing with an FP32 implementation): bit0 a Gaussian whose q
+// lies within the band of 9 that would pass the alpha test, bit1 alpha within
+// its band of the 1/255 cut-off, bit2 T(1-alpha) within its band of the 1e-4
+// cut-off.  Each band is a constant relative floor (eps_q, eps_a, eps_t) plus
+// k times a first-order bound of the error with which an FP32 evaluation
+// (unit roundoff u = 2^-24) reaches the same quantity:
+//   q:     e_q = u (6 S + 3 q kappa_det + 2 (|g_x| (|dx| + 32) + |g_y| (|dy| + 32)))
+//          S = |A| dx^2 + 2 |B dx dy| + |C| dy^2 (the terms of q before they
+//          cancel), kappa_det = (|a c| + b^2) / (a c - b^2) (the relative error
+//          of the covariance's determinant, which scales every conic
+//          coefficient), g = conic d (an offset d held with an absolute error of
+//          u (|d| + 32) px moves q by 2 g . delta);
+//   alpha: relative e_a = e_q / 2 + 16 u (alpha = o exp(-q/2); 16 u covers the
+//          opacity, the exponential and the product);
+//   T:     relative e_T after n Gaussians = sum_j (alpha_j / (1 - alpha_j)) e_a,j
+//          + 2 u per factor (each (1 - alpha) inherits alpha's error scaled by
+//          alpha / (1 - alpha), and the product rounds once per factor).
 // ---------------------------------------------------------------------------
 struct OrcCand {
   float z;
   int64_t i;
   double alpha, G, q;
+  double ea;  // relative FP32 error bound of alpha (flags only)
 };
 
 struct OrcScene {
@@ -518,8 +544,19 @@ static void orc_scene(const double* params, int64_t n, int deg, const OrcCam* ca
 }
 
 struct OrcEps {
-  double q, a, t;
+  double q, a, t, k;  // constant relative floors of the three bands, factor on the derived bounds
 };
+
+static const double kOrcU32 = 1.0 / 16777216.0;  // 2^-24, FP32 unit roundoff
+
+// First-order bound of the FP32 error of q at offset (dx, dy), see above.
+static double orc_q_error(const OrcProj& g, double dx, double dy, double q) {
+  const double S = std::fabs(g.A) * dx * dx + 2.0 * std::fabs(g.B * dx * dy) + std::fabs(g.Cc) * dy * dy;
+  const double kdet = (std::fabs(g.a * g.c) + g.b * g.b) / g.det;
+  const double gx = g.A * dx + g.B * dy, gy = g.B * dx + g.Cc * dy;
+  const double cen = 2.0 * (std::fabs(gx) * (std::fabs(dx) + 32.0) + std::fabs(gy) * (std::fabs(dy) + 32.0));
+  return kOrcU32 * (6.0 * S + 3.0 * std::fabs(q) * kdet + cen);
+}
 
 static int orc_collect(const OrcScene& sc, const OrcCam* cam, double x, double y,
                        std::vector<OrcCand>& cand, const OrcEps* eps, int* flags) {
@@ -530,16 +567,19 @@ static int orc_collect(const OrcScene& sc, const OrcCam* cam, double x, double y
     const OrcProj& g = sc.proj[(size_t)i];
     double dx = x - g.u, dy = y - g.v;
     double q = g.A * dx * dx + 2.0 * g.B * dx * dy + g.Cc * dy * dy;
+    double ea = 0.0;
     if (eps) {
-      if (std::fabs(q - 9.0) <= eps->q * 9.0 && g.o * std::exp(-4.5) >= a_cut * (1.0 - eps->a)) fl |= 1;
+      const double eq = eps->k * orc_q_error(g, dx, dy, q);
+      ea = eq / 2.0 + eps->k * 16.0 * kOrcU32;
+      if (std::fabs(q - 9.0) <= eps->q * 9.0 + eq && g.o * std::exp(-4.5) >= a_cut * (1.0 - eps->a - ea)) fl |= 1;
     }
     if (q > 9.0) continue;
     double G = std::exp(-0.5 * q);
     double araw = g.o * G;
-    if (eps && std::fabs(araw - a_cut) <= eps->a * a_cut) fl |= 2;
+    if (eps && std::fabs(araw - a_cut) <= (eps->a + ea) * a_cut) fl |= 2;
     double alpha = araw < 0.99 ? araw : 0.99;
     if (alpha < a_cut) continue;
-    cand.push_back({g.z32, i, alpha, G, q});
+    cand.push_back({g.z32, i, alpha, G, q, ea});
   }
   std::sort(cand.begin(), cand.end(), [](const OrcCand& l, const OrcCand& r) {
     return l.z < r.z || (l.z == r.z && l.i < r.i);
@@ -551,12 +591,16 @@ static int orc_collect(const OrcScene& sc, const OrcCam* cam, double x, double y
 // Number of Gaussians blended (the prefix before the termination point).
 static size_t orc_blend_prefix(const std::vector<OrcCand>& cand, const OrcEps* eps, int* flags,
                                double* T_out) {
-  double T = 1.0;
+  double T = 1.0, eT = 0.0;
   size_t n = 0;
   int fl = flags ? *flags : 0;
   for (; n < cand.size(); ++n) {
-    double Tn = T * (1.0 - cand[n].alpha);
-    if (eps && std::fabs(Tn - 1e-4) <= eps->t * 1e-4) fl |= 4;
+    const double a = cand[n].alpha;
+    double Tn = T * (1.0 - a);
+    if (eps) {
+      eT += a / (1.0 - a) * cand[n].ea + eps->k * 2.0 * kOrcU32;
+      if (std::fabs(Tn - 1e-4) <= eps->t * 1e-4 + eT * Tn) fl |= 4;
+    }
     if (Tn < 1e-4) break;
     T = Tn;
   }
@@ -580,7 +624,7 @@ int orc_render(const double* params, int64_t n, int deg, const OrcCam* cam, cons
                double* T_final, int32_t* n_contrib, int32_t* flags) {
   OrcScene sc;
   orc_scene(params, n, deg, cam, &sc);
-  OrcEps eps = {eps4[0], eps4[1], eps4[2]};
+  OrcEps eps = {eps4[0], eps4[1], eps4[2], eps4[3]};
   const int nt = orc_threads(n_threads);
 #pragma omp parallel num_threads(nt)
   {

@@ -171,6 +171,31 @@ def room_indoor(seed: int = 0, n: int = 500_000, W: int = 640, H: int = 480, n_s
 # ----------------------------------------------------------------------------
 # batched keyframe window: 2M Gaussians, 64 chunks of 4 m, 8 mixed views
 # ----------------------------------------------------------------------------
+def clamp_scene(seed: int = 21, deg: int = 3):
+    """A 48x40 view (f = 30, identity pose) and 13 Gaussians: ten whose centres
+    project beyond the image extended by 15 % of its size on each side (right,
+    left, below, above and two corners; x/z or y/z or both outside the limits
+    of the perspective Jacobian) with scales large enough that their 3-sigma
+    ellipses reach into the image, and three inside it."""
+    W, H = 48, 40
+    cam = Camera(30.0, 30.0, 23.5, 19.5, W, H, np.eye(4, dtype=np.float32), 0.2, 50.0)
+    # (x/z, y/z, z, scale)
+    spec = [(1.30, 0.05, 3.0, 0.80), (1.22, -0.30, 3.6, 0.90), (-1.25, 0.10, 3.2, 0.85), (-1.18, 0.40, 2.8, 0.75),
+            (0.10, 1.05, 3.1, 0.80), (-0.20, 0.98, 3.5, 0.75), (0.20, -1.02, 3.3, 0.80), (-0.10, -0.97, 2.9, 0.70),
+            (1.20, 1.00, 3.4, 1.00), (-1.15, -0.95, 3.0, 1.00),
+            (0.10, 0.05, 4.0, 0.10), (-0.40, 0.20, 3.7, 0.12), (0.35, -0.30, 3.9, 0.08)]
+    rng = np.random.default_rng(seed)
+    n = len(spec)
+    P = np.zeros((n, n_fields(deg)))
+    for i, (rx, ry, z, s) in enumerate(spec):
+        P[i, 0:3] = (rx * z, ry * z, z)
+        P[i, 3:6] = np.log(s * rng.uniform(0.6, 1.0, 3))
+    P[:, 6:10] = random_quats(rng, n)
+    P[:, 10] = rng.uniform(-0.5, 0.5, n)
+    P[:, 11:] = rng.normal(0, 0.3, (n, P.shape[1] - 11))
+    return P, cam
+
+
 WINDOW_SIZES = [(1200, 680)] * 4 + [(640, 480)] * 2 + [(320, 240)] * 2
 
 

@@ -98,6 +98,9 @@ def check_image(orc_out, rgb, depth, T, tag, max_flag=0.005):
     e_rgb = np.abs(rgb[ok] - orc_out["rgb"][ok]).max()
     dz = np.abs(depth[ok] - orc_out["depth"][ok]) / np.maximum(1.0, np.abs(orc_out["depth"][ok]))
     e_T = np.abs(T[ok] - orc_out["T"][ok]).max()
+    e_zabs = np.abs(depth[ok] - orc_out["depth"][ok]).max()
+    print(f"{tag}: flagged {1 - ok.mean():.4%} rgb {e_rgb:.2e} T {e_T:.2e} depth rel {dz.max():.2e} abs {e_zabs:.2e}"
+          f" (max depth {np.abs(orc_out['depth'][ok]).max():.2f})")
     assert e_rgb <= RGB_TOL, f"{tag}: rgb err {e_rgb}"
     assert dz.max() <= RGB_TOL, f"{tag}: depth err {dz.max()}"
     assert e_T <= T_TOL, f"{tag}: T err {e_T}"

@@ -209,3 +209,43 @@ def test_tiny_views_match_oracle(ctx, orc, w, h):
         for name, sl in GROUPS.items():
             assert rel_l2(grad[:, sl], og[:, sl]) <= GRAD_TOL, name
         assert rel_l2(pose, opose) <= GRAD_TOL
+
+
+def test_clamped_jacobian_gaussians_match_oracle(orc):
+    """Gaussians whose centres project beyond the image extended by 15 % per
+    side, so that the perspective Jacobian takes x/z, y/z or both at the limit
+    (the clamped branch of the forward and of its gradient), but whose ellipses
+    reach into the image: every pixel and every gradient, pose included."""
+    P, cam = synth.clamp_scene()
+    P = P.astype(np.float32)
+    fl = orc.clamp_flags(P, 3, cam)
+    assert (fl & 1).sum() >= 4 and (fl & 2).sum() >= 4 and (fl == 3).sum() >= 2
+    c = make_ctx(deg=3, n_max=64, views=1, pixels=cam.W * cam.H)
+    try:
+        import torch
+
+        n = P.shape[0]
+        g_t, _, rgb, depth = render(c, P, 3, [cam])
+        st = dcg.dcg_state_read(c, None, 1, n, cam.W * cam.H)
+        o = orc.render(P, 3, cam)
+        check_image(o, rgb.view(3, -1).T.cpu().numpy().astype(np.float64), depth.cpu().numpy().astype(np.float64),
+                    st["T"].astype(np.float64), "clamped", max_flag=0.01)
+        rng = np.random.default_rng(5)
+        Pn = cam.W * cam.H
+        gr = rng.normal(size=(Pn, 3))
+        gd = rng.normal(size=Pn) * 0.1
+        gr[o["flags"] != 0] = 0
+        gd[o["flags"] != 0] = 0
+        dr = torch.from_numpy(np.ascontiguousarray(gr.T.reshape(-1)).astype(np.float32)).cuda()
+        dd = torch.from_numpy(gd.astype(np.float32)).cuda()
+        grad, pose = backward(c, g_t, 3, n, dr, dd, 1)
+        og, opose = orc.render_bwd(P, 3, cam, gr.astype(np.float32).astype(np.float64),
+                                   gd.astype(np.float32).astype(np.float64))
+        clamped = np.nonzero(fl)[0]
+        assert np.abs(og[clamped]).max(1).min() > 1e-6  # every clamped Gaussian reaches the image
+        for name, sl in GROUPS.items():
+            assert rel_l2(grad[:, sl], og[:, sl]) <= GRAD_TOL, name
+            assert rel_l2(grad[clamped, sl], og[clamped, sl]) <= GRAD_TOL, name
+        assert rel_l2(pose[0], opose) <= GRAD_TOL, (pose[0], opose)
+    finally:
+        dcg.dcg_destroy(c)

@@ -4,10 +4,12 @@ the chunk path, in the launch shapes the benchmark's autotuner picks from,
 against the oracle on sampled pixels of two views: the images, and the
 parameter and pose gradients of a loss seeded on those pixels only.
 
-A pixel of this scene weighs about a hundred Gaussians, so the chance that
-one of them sits within the oracle's 1e-4 band around a discrete threshold
-(q = 9, alpha = 1/255, T = 1e-4) is far higher than in the sparse test
-scenes: up to 5 % of the sampled pixels may be flagged (and skipped)."""
+A pixel of this scene weighs about a hundred Gaussians, so one of them is
+more often within the oracle's derived FP32 error band of a discrete
+threshold (q = 9, alpha = 1/255, T = 1e-4) than in the sparse test scenes: the
+oracle flags 0 to 1.2 % of the pixels of each of the eight views (0.36 % over
+4800 sampled pixels), so at most 2 % of the sampled pixels may be flagged (and
+skipped)."""
 import numpy as np
 import pytest
 
@@ -65,7 +67,7 @@ def test_full_window_sampled_pixels_and_gradients(window, orc, stage):
             T = st["T"][offs[v]: offs[v + 1]].reshape(c.H, c.W)
             check_image(o, rv[:, pix[:, 1], pix[:, 0]].T.astype(np.float64),
                         dv[pix[:, 1], pix[:, 0]].astype(np.float64), T[pix[:, 1], pix[:, 0]].astype(np.float64),
-                        f"view {v} stage {stage}", max_flag=0.05)
+                        f"view {v} stage {stage}", max_flag=0.02)
             gr = rng.normal(size=(len(pix), 3))
             gd = rng.normal(size=len(pix)) * 0.1
             gr[o["flags"] != 0] = 0

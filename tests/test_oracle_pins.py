@@ -399,6 +399,95 @@ def test_finite_differences_of_oracle(orc):
         assert abs(fd - gpose[k]) <= 1e-6 * max(1.0, abs(gpose[k])), (k, fd, gpose[k])
 
 
+def test_finite_differences_in_the_clamped_jacobian_branch(orc):
+    """The perspective Jacobian evaluated at x/z and y/z clamped to the image
+    extended by 15 % per side (the 3DGS lineage's frustum clamp): central
+    differences of the oracle's forward against its analytic gradient on
+    Gaussians that take that branch, for every parameter kind and the pose."""
+    from scipy.linalg import expm
+
+    P, cam = synth.clamp_scene()
+    fl = orc.clamp_flags(P, 3, cam)
+    pix = orc.all_pixels(cam.W, cam.H)
+    out = orc.render(P, 3, cam, pix=pix)
+    rng = np.random.default_rng(22)
+    gr = rng.normal(size=(len(pix), 3))
+    gd = rng.normal(size=len(pix)) * 0.1
+    grad, gpose = orc.render_bwd(P, 3, cam, gr, gd, pix=pix)
+    reach = np.abs(grad).max(1) > 1e-6  # composited somewhere in the image
+    clamped = np.nonzero((fl != 0) & reach)[0]
+    # every side of the clamp is exercised, by Gaussians that reach the image
+    assert len(clamped) >= 8 and ((fl[clamped] & 1) != 0).sum() >= 4 and ((fl[clamped] & 2) != 0).sum() >= 4
+    assert (fl[clamped] == 3).sum() >= 2
+    assert not fl[10:].any() and (out["n"] > 0).mean() > 0.5
+
+    def loss(Pv):
+        o = orc.render(Pv, 3, cam, pix=pix)
+        return float((o["rgb"] * gr).sum() + (o["depth"] * gd).sum())
+
+    cols = list(range(0, 11)) + [11, 12, 13, 14, 20, 30, 40, 50, 58]
+    for i in clamped:
+        for c in cols:
+            h = 1e-6 * max(1.0, abs(P[i, c]))
+            Pp, Pm = P.copy(), P.copy()
+            Pp[i, c] += h
+            Pm[i, c] -= h
+            fd = (loss(Pp) - loss(Pm)) / (2 * h)
+            assert abs(fd - grad[i, c]) <= 1e-6 * max(1.0, abs(grad[i, c])) + 1e-7, (i, c, fd, grad[i, c])
+    # the pose twist, with the clamped Gaussians carrying most of the image
+    T0 = np.asarray(cam.Tcw, np.float64)
+    for k in range(6):
+        mats = []
+        for sgn in (1, -1):
+            xi = np.zeros(6)
+            xi[k] = sgn * 1e-6
+            Xh = np.zeros((4, 4))
+            w = xi[3:]
+            Xh[:3, :3] = [[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]]
+            Xh[:3, 3] = xi[:3]
+            mats.append(expm(Xh) @ T0)
+        fd = (_loss_T(orc, P, cam, mats[0], pix, gr, gd) - _loss_T(orc, P, cam, mats[1], pix, gr, gd)) / 2e-6
+        assert abs(fd - gpose[k]) <= 1e-6 * max(1.0, abs(gpose[k])), (k, fd, gpose[k])
+    # the clamp matters here: without it the same Gaussians would have other covariances
+    pr = orc.project(P, 3, cam)
+    assert np.isfinite(pr["A"][clamped]).all()
+
+
+def test_clamped_covariance_closed_form(orc):
+    """For an isotropic Gaussian (variance s^2) and an identity pose, the dilated
+    2D covariance is s^2 J J^T + 0.3 I with the perspective Jacobian
+    J = [[f/z, 0, -f x'/z^2], [0, f/z, -f y'/z^2]], where x' / z and y' / z are the
+    centre's x / z and y / z limited to the image extended by 15 % of its size
+    on each side: a = s^2 f^2 (1/z^2 + x'^2/z^4) + 0.3, b = s^2 f^2 x' y' / z^4,
+    c = s^2 f^2 (1/z^2 + y'^2/z^4) + 0.3 (written out in scalars here; the oracle
+    forms J W Sigma W^T J^T as matrix products)."""
+    W, H, f = 48, 40, 30.0
+    cam = synth.Camera(f, f, 23.5, 19.5, W, H, np.eye(4, dtype=np.float32), 0.2, 50.0)
+    xlo, xhi = (-0.15 * W - 23.5) / f, (1.15 * W - 23.5) / f
+    ylo, yhi = (-0.15 * H - 19.5) / f, (1.15 * H - 19.5) / f
+    cases = [(1.30, 0.05), (-1.25, 0.10), (0.10, 1.05), (-0.20, -0.98), (1.20, 1.00), (-1.15, -0.95), (0.3, -0.2)]
+    P = np.zeros((len(cases), synth.n_fields(0)))
+    z, s = 3.0, 0.5
+    for i, (rx, ry) in enumerate(cases):
+        P[i, 0:3] = (rx * z, ry * z, z)
+    P[:, 3:6] = math.log(s)
+    P[:, 6] = 1.0
+    pr = orc.project(P, 0, cam)
+    fl = orc.clamp_flags(P, 0, cam)
+    assert list(fl) == [1, 1, 2, 2, 3, 3, 0]
+    for i, (rx, ry) in enumerate(cases):
+        xc = min(max(rx, xlo), xhi) * z
+        yc = min(max(ry, ylo), yhi) * z
+        a = s * s * f * f * (1 / z ** 2 + xc * xc / z ** 4) + 0.3
+        b = s * s * f * f * xc * yc / z ** 4
+        c = s * s * f * f * (1 / z ** 2 + yc * yc / z ** 4) + 0.3
+        assert math.isclose(pr["a"][i], a, rel_tol=1e-13)
+        assert math.isclose(pr["b2"][i], b, rel_tol=1e-13, abs_tol=1e-15)
+        assert math.isclose(pr["c"][i], c, rel_tol=1e-13)
+        # the centre itself is not clamped
+        assert math.isclose(pr["u"][i], f * rx + 23.5, rel_tol=1e-14)
+
+
 def _loss_T(orc, P, cam, T, pix, gr, gd):
     """Render with a float64 pose (bypasses the float32 camera widening)."""
     import ctypes
