@@ -42,8 +42,11 @@ typedef enum {
   DCG_ERR_BUDGET = 4,    /* the visible chunks alone exceed the device Gaussian budget */
   DCG_ERR_KEY_RANGE = 5, /* a chunk coordinate lies outside [-2^20, 2^20-1] (Eq. 6) */
   DCG_ERR_CAPACITY = 6,  /* a configured capacity (instances, pixels, chunks, host tier) was exceeded */
-  DCG_ERR_TIMEOUT = 7,   /* a bounded device-side wait gave up */
-  DCG_ERR_FAULT = 8,     /* an injected host-side fault (testing) */
+  DCG_ERR_TIMEOUT = 7,   /* reserved for a bounded device-side wait that gives up; no kernel of
+                            this library waits on another block or on a flag (the persistent
+                            kernels' work queues are counters that never block), so none is
+                            returned today */
+  DCG_ERR_FAULT = 8,     /* a chunk load failed verification, or an injected host-side fault */
   DCG_ERR_STATE = 9      /* call order violated (e.g. backward without a forward) */
 } dcg_status;
 
@@ -88,7 +91,14 @@ typedef struct {
   float dfar;              /* distance filter of the chunk cull, metres */
   int32_t page_gaussians;  /* Gaussians per device/host page (power of two) */
   int32_t flags;           /* bit 0: backward blend accumulates per-lane shared slots instead of
-                              reducing each Gaussian across the warp (same result); others 0 */
+                              reducing each Gaussian across the warp (same result); bit 1: the
+                              half-warp backward (stage 16) puts pixels on the lanes, one Gaussian
+                              per half block and step, instead of Gaussians on the lanes with the
+                              half block's pixels in turn (same result); bit 2: verify every chunk
+                              load (a checksum of the host pages against one of the pages that
+                              arrived, compared before dcg_gather_active returns; a chunk that
+                              fails is dropped and the call returns DCG_ERR_FAULT, so a retry
+                              loads it again); others 0 */
   int32_t with_moments;    /* 1: every Gaussian stores its Adam moments m and v beside its
                               parameters (pages, host tier and active buffer hold 3 F components);
                               0 (default): parameters only */
@@ -147,10 +157,23 @@ dcg_status dcg_chunk_info(const dcg_ctx* ctx, int32_t* coords, uint64_t* keys, i
  * distance from the camera centre to the cube is <= dfar.  FP64, fixed
  * evaluation order.  Outputs: mask_out (dev, [n_views, C] u8, may be NULL),
  * list_out (host, capacity C) = ascending chunk indices visible in any view,
- * *n_out (host) = their number.  Synchronises `stream` (the list is needed on
- * the host by dcg_gather_active). */
+ * *n_out (host) = their number.  The list is needed on the host by
+ * dcg_gather_active, so the call waits for the cull: with mask_out it runs on
+ * `stream` and synchronises it; without, it runs on a stream of the context
+ * and waits for that only (work the caller queued keeps running). */
 dcg_status dcg_cull_chunks(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views, uint8_t* mask_out,
                            int32_t* list_out, int32_t* n_out, void* stream);
+
+/* The same cull, left on the device and not waited for: list_out (dev,
+ * capacity = chunk count) ascending indices visible in any view, *n_out (dev)
+ * their number, mask_out as above (dev, may be NULL).  Asynchronous on
+ * `stream`; cams (1 to 16 views, independent of max_views) is copied into
+ * the launch's parameters before return.  For
+ * work that overlaps rendering (prefetch proposals on a side stream).  It has
+ * its own scratch, so it may overlap dcg_cull_chunks, but two calls of it on
+ * one context must not overlap on the GPU. */
+dcg_status dcg_cull_chunks_async(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views, uint8_t* mask_out,
+                                 int32_t* list_out, int32_t* n_out, void* stream);
 
 /* Make the listed chunks (host, ascending chunk indices) resident and gather
  * their Gaussians into the library-owned active buffer (Sec. III-E: load
@@ -186,7 +209,10 @@ dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n
  * [n_active] each, either may be NULL).  Rows follow the gather: listed
  * chunks in ascending id, each with the count it had when gathered.
  * DCG_ERR_STATE without a valid gathered set (none yet, or after a loop
- * closure).  Asynchronous on `stream`. */
+ * closure).  Asynchronous on `stream`; the table goes up from pinned staging
+ * that the next call reuses once this upload has run.  The device copy of the
+ * table is per context, so calls on one context must not overlap on the GPU
+ * (one stream, or the caller orders them). */
 dcg_status dcg_active_map(dcg_ctx* ctx, int32_t* chunk_out, int32_t* row_out, void* stream);
 
 /* Complete a deferred write-back of the active buffer, copy every resident
@@ -515,19 +541,43 @@ dcg_status dcg_mlp_gather_rows(const uint16_t* x, const float* y, const int32_t*
  * below refer to this order) and distance filter dfar: mask_out (dev,
  * [n_views, n_chunks] u8, may be NULL), list_out (dev, capacity n_chunks)
  * ascending indices visible in any view, *n_out (dev, one int32).
- * Asynchronous on `stream`; cams is a host array (copied before return).
- * Its scratch (camera table and per-chunk flags) is a fixed array in device
+ * Asynchronous on `stream`; cams is a host array, copied into the kernel's
+ * launch parameters before return (pageable or pinned, it may be reused at
+ * once).  Its scratch (one flag per chunk) is a fixed 1 MiB array in device
  * memory that every GPU loading the library keeps until the process exits:
  * at most 2^20 chunks and 16 views per call, larger requests return
- * DCG_ERR_CAPACITY without doing anything.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the array and it
- * keeps the previous call's contents (the call clears what it needs), so
- * calls that overlap on the GPU -- on different streams, or from different
- * host threads -- race and must be serialised by the caller. */
+ * DCG_ERR_CAPACITY without doing anything.  The first call on a device, and
+ * the first after a cudaDeviceReset, looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the previous call's contents (the
+ * call clears the flags before use), so calls that overlap on the GPU -- on
+ * different streams, or from different host threads -- race and must be
+ * serialised by the caller.  A failed launch or clear returns DCG_ERR_CUDA. */
 dcg_status dcg_cull_chunks_noalloc(const int32_t* coords, int32_t n_chunks, float chunk_size, float dfar,
                                    const dcg_camera* cams, int32_t n_views, uint8_t* mask_out, int32_t* list_out,
                                    int32_t* n_out, void* stream);
+
+/* ---------------------------------------------------------------- failure injection (testing)
+ * Host-side faults of the chunk tier, for testing how a caller recovers; no
+ * fault touches the GPU beyond ordinary copies.  An armed fault fires once,
+ * on the (skip + 1)-th opportunity, and is then disarmed:
+ *   DCG_FAULT_H2D_FAIL   a chunk load fails before its copies are issued
+ *                        (dcg_gather_active / dcg_prefetch return DCG_ERR_FAULT;
+ *                        the chunk stays in the host tier only);
+ *   DCG_FAULT_SHORT_COPY the last page of a chunk load is copied only half
+ *                        (the rest of the page holds a fill pattern); arming
+ *                        it turns on load verification, which detects it:
+ *                        the next dcg_gather_active drops the chunk and returns
+ *                        DCG_ERR_FAULT before anything is rendered from it;
+ *   DCG_FAULT_BUDGET     dcg_gather_active returns DCG_ERR_BUDGET as if the
+ *                        listed chunks exceeded the device budget.
+ * After any of them the context stays usable and a repeated call succeeds
+ * with the same result as without the fault.  The environment variable
+ * DCG_FAULT=h2d_fail|short_copy|budget[:skip] arms one at dcg_create. */
+enum { DCG_FAULT_NONE = 0, DCG_FAULT_H2D_FAIL = 1, DCG_FAULT_SHORT_COPY = 2, DCG_FAULT_BUDGET = 3 };
+dcg_status dcg_inject_fault(dcg_ctx* ctx, int32_t kind, int32_t skip);
+/* Parses "none|h2d_fail|short_copy|budget[:skip]" (host only, no context). */
+dcg_status dcg_fault_parse(const char* spec, int32_t* kind, int32_t* skip);
 
 /* ---------------------------------------------------------------- profiling
  * Optional per-phase device timers.  When enabled, every call records CUDA

@@ -114,13 +114,14 @@ __device__ bool cull_box(const double pl[6][4], const double C[3], double dfar, 
   return d2 <= __dmul_rn(dfar, dfar);
 }
 
-// grid: (blocks over chunks, n_views); mask [V][C] (may be null), vis [C] OR-union
-__global__ void k_cull(const int32_t* __restrict__ coords, int C, const dcg_camera* __restrict__ cams, float s,
-                       float dfar, uint8_t* __restrict__ mask, uint8_t* __restrict__ vis) {
+// One block row of the cull: view v = blockIdx.y against chunks strided over
+// blockIdx.x; mask [V][C] (may be null), vis [C] OR-union.
+__device__ __forceinline__ void cull_view(const dcg_camera& cam, const int32_t* __restrict__ coords, int C, float s,
+                                          float dfar, uint8_t* __restrict__ mask, uint8_t* __restrict__ vis) {
   __shared__ double pl[6][4];
   __shared__ double Cc[3];
   const int v = blockIdx.y;
-  if (threadIdx.x == 0) cull_planes(cams[v], pl, Cc);
+  if (threadIdx.x == 0) cull_planes(cam, pl, Cc);
   __syncthreads();
   const double sd = (double)s;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < C; k += gridDim.x * blockDim.x) {
@@ -137,6 +138,18 @@ __global__ void k_cull(const int32_t* __restrict__ coords, int C, const dcg_came
   }
 }
 
+// cameras in device memory
+__global__ void k_cull(const int32_t* __restrict__ coords, int C, const dcg_camera* __restrict__ cams, float s,
+                       float dfar, uint8_t* __restrict__ mask, uint8_t* __restrict__ vis) {
+  cull_view(cams[blockIdx.y], coords, C, s, dfar, mask, vis);
+}
+
+// cameras passed by value in the kernel's parameters
+__global__ void k_cull_tab(const int32_t* __restrict__ coords, int C, const CullCams cams, float s, float dfar,
+                           uint8_t* __restrict__ mask, uint8_t* __restrict__ vis) {
+  cull_view(cams.c[blockIdx.y], coords, C, s, dfar, mask, vis);
+}
+
 // Single block: ordered compaction of vis[0..C) into list, count into *n.
 __global__ void k_compact_list(const uint8_t* __restrict__ vis, int C, int32_t* __restrict__ list, int32_t* n) {
   int base = 0;
@@ -151,15 +164,20 @@ __global__ void k_compact_list(const uint8_t* __restrict__ vis, int C, int32_t* 
   if (threadIdx.x == 0) *n = base;
 }
 
-void launch_cull(const int32_t* coords, int C, const dcg_camera* cams, int V, float s, float dfar, uint8_t* mask,
-                 uint8_t* vis, int32_t* list, int32_t* n, cudaStream_t st) {
-  cudaMemsetAsync(vis, 0, (size_t)(C > 0 ? C : 1), st);
+cudaError_t launch_cull(const int32_t* coords, int C, const dcg_camera* cams, const CullCams* tab, int V, float s,
+                        float dfar, uint8_t* mask, uint8_t* vis, int32_t* list, int32_t* n, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(vis, 0, (size_t)(C > 0 ? C : 1), st);
+  if (e != cudaSuccess) return e;
   if (C > 0) {
     dim3 grid((C + 255) / 256, V);
-    k_cull<<<grid, 256, 0, st>>>(coords, C, cams, s, dfar, mask, vis);
+    if (tab)
+      k_cull_tab<<<grid, 256, 0, st>>>(coords, C, *tab, s, dfar, mask, vis);
+    else
+      k_cull<<<grid, 256, 0, st>>>(coords, C, cams, s, dfar, mask, vis);
   }
   k_compact_list<<<1, 1024, 0, st>>>(vis, C, list, n);
   count_launch(C > 0 ? 2 : 1);
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------
@@ -167,16 +185,27 @@ void launch_cull(const int32_t* coords, int C, const dcg_camera* cams, int V, fl
 // components: component c of slot j at page[c * page_g + j].
 // desc[3d .. 3d+2] = (page index, count, offset in the active buffer).
 // Components [c0, c0 + nc) of each page map to rows 0 .. nc-1 of `active`.
+// cnt floats from s to t, coalesced, four loads in flight per thread
+__device__ __forceinline__ void copy_run(const float* __restrict__ s, float* __restrict__ t, long long cnt) {
+  const long long B = blockDim.x;
+  long long j = threadIdx.x;
+  for (; j + 3 * B < cnt; j += 4 * B) {
+    const float a0 = s[j], a1 = s[j + B], a2 = s[j + 2 * B], a3 = s[j + 3 * B];
+    t[j] = a0;
+    t[j + B] = a1;
+    t[j + 2 * B] = a2;
+    t[j + 3 * B] = a3;
+  }
+  for (; j < cnt; j += B) t[j] = s[j];
+}
+
 __global__ void k_gather_pages(const float* __restrict__ pool, long long page_g, int Fp, int c0, int nc,
                                const long long* __restrict__ desc, float* __restrict__ active, long long stride) {
   const long long d = blockIdx.x;
   const long long page = desc[3 * d], cnt = desc[3 * d + 1], off = desc[3 * d + 2];
   const float* src = pool + page * page_g * Fp + (long long)c0 * page_g;
-  for (int c = blockIdx.y; c < nc; c += gridDim.y) {
-    const float* s = src + (long long)c * page_g;
-    float* t = active + (long long)c * stride + off;
-    for (long long j = threadIdx.x; j < cnt; j += blockDim.x) t[j] = s[j];
-  }
+  for (int c = blockIdx.y; c < nc; c += gridDim.y)
+    copy_run(src + (long long)c * page_g, active + (long long)c * stride + off, cnt);
 }
 
 __global__ void k_scatter_pages(float* __restrict__ pool, long long page_g, int Fp, int c0, int nc,
@@ -185,11 +214,36 @@ __global__ void k_scatter_pages(float* __restrict__ pool, long long page_g, int 
   const long long d = blockIdx.x;
   const long long page = desc[3 * d], cnt = desc[3 * d + 1], off = desc[3 * d + 2];
   float* dst = pool + page * page_g * Fp + (long long)c0 * page_g;
-  for (int c = blockIdx.y; c < nc; c += gridDim.y) {
-    float* t = dst + (long long)c * page_g;
-    const float* s = active + (long long)c * stride + off;
-    for (long long j = threadIdx.x; j < cnt; j += blockDim.x) t[j] = s[j];
+  for (int c = blockIdx.y; c < nc; c += gridDim.y)
+    copy_run(active + (long long)c * stride + off, dst + (long long)c * page_g, cnt);
+}
+
+// Load verification: checksum of a chunk's pages, the sum over its used
+// words w of w * (2 i + 1) mod 2^64, i the word's index in the chunk's page
+// sequence ((page * Fp + component) * page_g + row).  One launch per page:
+// `page` is page number p of the chunk, holding `cnt` rows; the sum is added
+// to *out (order-independent, so the result is deterministic).
+__global__ void k_page_checksum(const float* __restrict__ page, long long p, long long page_g, int Fp, long long cnt,
+                                unsigned long long* __restrict__ out) {
+  const unsigned* src = reinterpret_cast<const unsigned*>(page);
+  unsigned long long acc = 0ull;
+  for (int c = blockIdx.y; c < Fp; c += gridDim.y) {
+    const unsigned long long base = ((unsigned long long)p * Fp + c) * (unsigned long long)page_g;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < cnt; j += (long long)gridDim.x * blockDim.x)
+      acc += (unsigned long long)src[(long long)c * page_g + j] * (2ull * (base + (unsigned long long)j) + 1ull);
   }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+void launch_page_checksum(const float* page, long long p, long long page_g, int Fp, long long cnt,
+                          unsigned long long* out, cudaStream_t st) {
+  if (cnt <= 0) return;
+  const long long bx = (cnt + 255) / 256;
+  dim3 grid((unsigned)(bx < 8 ? bx : 8), Fp < 32 ? Fp : 32);
+  k_page_checksum<<<grid, 256, 0, st>>>(page, p, page_g, Fp, cnt, out);
+  count_launch();
 }
 
 // Chunk index and row within the chunk of every active row: the last

@@ -2,6 +2,7 @@
 // for the paper's disk tier), device page pool with LRU eviction, and the
 // render / loss calls (Sec. III-D, III-E).
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -72,7 +73,8 @@ struct dcg_ctx {
   std::string err;
   int tile_w = 16, tile_h = 16, stage = 128;
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_copy = nullptr, ev_compute = nullptr, ev_desc = nullptr;
+  cudaStream_t cull_stream = nullptr;  // dcg_cull_chunks without a mask: waits for nothing the caller queued
+  cudaEvent_t ev_copy = nullptr, ev_compute = nullptr;
   unsigned* d_errword = nullptr;
   unsigned* h_errword = nullptr;
   // chunk table
@@ -109,9 +111,14 @@ struct dcg_ctx {
   // into the device pages is still deferred.
   bool active_fresh = false;
   bool active_dirty = false;
+  // page descriptors (page, count, offset) in two slots used in turn, so that
+  // filling one waits only for the upload of the gather before last; desc_slot
+  // is the slot of the active set's descriptors (used by its write-back)
   long long* d_desc = nullptr;
   long long* h_desc = nullptr;
   int64_t max_desc = 0;
+  int desc_slot = 0;
+  cudaEvent_t ev_descs[2] = {nullptr, nullptr};
   int n_desc = 0;
   // staging for table updates
   uint64_t* d_keys = nullptr;
@@ -150,8 +157,20 @@ struct dcg_ctx {
   u64* d_lccnt = nullptr;         // transformed and moved row counts
   long long* d_amoff = nullptr;   // active map: first active row and table index per gathered chunk
   int32_t* d_amchunk = nullptr;
+  uint8_t* d_vis_async = nullptr;  // union flags of dcg_cull_chunks_async (its own, so it may overlap a synchronous cull)
+  long long* h_amoff = nullptr;   // their pinned staging, reused once ev_am shows the last upload consumed
+  int32_t* h_amchunk = nullptr;
+  cudaEvent_t ev_am = nullptr;
   cudaEvent_t ev_loss = nullptr;
-  int fault = 0;
+  // injected faults (testing): the armed kind fires once, after fault_skip opportunities pass
+  int fault_kind = DCG_FAULT_NONE;
+  int fault_skip = 0;
+  // load verification (config flag bit 2, or a short_copy fault armed): every chunk
+  // load is checked against the checksum of its host pages before the gather returns
+  bool verify_loads = false;
+  unsigned long long* d_loadsum = nullptr;  // checksum of the arrived pages, one per pending check
+  unsigned long long* h_loadsum = nullptr;  // pinned read-back
+  std::vector<std::pair<uint64_t, unsigned long long>> load_checks;  // (chunk id, expected checksum)
   // captured window graph
   cudaStream_t cap_stream = nullptr;  // private stream for capture (the legacy stream cannot be captured)
   cudaGraphExec_t win_exec = nullptr;
@@ -261,18 +280,71 @@ dcg_status evict_chunk(dcg_ctx* ctx, Chunk& ch) {
   return DCG_OK;
 }
 
+// True (and disarmed) if the armed fault is `kind` and its skip count has run out.
+bool fault_fires(dcg_ctx* ctx, int kind) {
+  if (ctx->fault_kind != kind) return false;
+  if (ctx->fault_skip > 0) {
+    --ctx->fault_skip;
+    return false;
+  }
+  ctx->fault_kind = DCG_FAULT_NONE;
+  return true;
+}
+
+// Checksum of a chunk's host pages, the same definition as k_page_checksum:
+// the sum over its used words w of w * (2 i + 1) mod 2^64, i the word's index
+// in the chunk's page sequence ((page * Fs + component) * page_g + row).
+unsigned long long host_checksum(const dcg_ctx* ctx, const Chunk& ch) {
+  unsigned long long acc = 0ull;
+  for (size_t p = 0; p < ch.host_pages.size(); ++p) {
+    const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - (int64_t)p * ctx->page_g);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(ctx->h_tier + (int64_t)ch.host_pages[p] * ctx->page_floats);
+    for (int c = 0; c < ctx->Fs; ++c) {
+      const unsigned long long base = ((unsigned long long)p * ctx->Fs + c) * (unsigned long long)ctx->page_g;
+      for (int64_t j = 0; j < cnt; ++j)
+        acc += (unsigned long long)src[(int64_t)c * ctx->page_g + j] * (2ull * (base + (unsigned long long)j) + 1ull);
+    }
+  }
+  return acc;
+}
+
 dcg_status load_chunk(dcg_ctx* ctx, Chunk& ch) {
   const int64_t np = pages_for(ctx, ch.count);
   if ((int64_t)ctx->dev_free.size() < np) return fail(ctx, DCG_ERR_BUDGET, "device page pool exhausted");
-  if (ctx->fault == 1) return fail(ctx, DCG_ERR_FAULT, "injected host->device copy failure");
+  if (fault_fires(ctx, DCG_FAULT_H2D_FAIL)) return fail(ctx, DCG_ERR_FAULT, "injected host->device copy failure");
+  const bool shorten = fault_fires(ctx, DCG_FAULT_SHORT_COPY);
+  unsigned long long expect = 0ull;
+  if (ctx->verify_loads) {
+    // the host pages must be final: an eviction's device->host copy may still be running
+    CK(cudaStreamSynchronize(ctx->copy_stream));
+    expect = host_checksum(ctx, ch);
+  }
   ch.dev_pages.resize((size_t)np);
   for (int64_t p = 0; p < np; ++p) {
     ch.dev_pages[(size_t)p] = ctx->dev_free.back();
     ctx->dev_free.pop_back();
-    const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - p * ctx->page_g);
-    CK(page_copy(ctx, dev_page(ctx, ch.dev_pages[(size_t)p]), host_page(ctx, ch.host_pages[(size_t)p]), cnt,
-                 cudaMemcpyHostToDevice, ctx->copy_stream));
+    int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - p * ctx->page_g);
+    float* dst = dev_page(ctx, ch.dev_pages[(size_t)p]);
+    if (shorten && p == np - 1) {
+      // injected short copy: the page's old contents are overwritten with a
+      // pattern and only half of its rows are copied
+      CK(cudaMemsetAsync(dst, 0xff, (size_t)ctx->page_floats * 4, ctx->copy_stream));
+      cnt /= 2;
+    }
+    CK(page_copy(ctx, dst, host_page(ctx, ch.host_pages[(size_t)p]), cnt, cudaMemcpyHostToDevice, ctx->copy_stream));
     ctx->bytes_h2d += cnt * ctx->Fs * 4;
+  }
+  if (ctx->verify_loads) {
+    const size_t slot = ctx->load_checks.size();
+    if ((int64_t)slot >= ctx->cfg.max_chunks) return fail(ctx, DCG_ERR_CAPACITY, "too many unchecked loads");
+    CK(cudaMemsetAsync(ctx->d_loadsum + slot, 0, sizeof(unsigned long long), ctx->copy_stream));
+    for (int64_t p = 0; p < np; ++p) {
+      const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - p * ctx->page_g);
+      launch_page_checksum(dev_page(ctx, ch.dev_pages[(size_t)p]), p, ctx->page_g, ctx->Fs, cnt,
+                           ctx->d_loadsum + slot, ctx->copy_stream);
+    }
+    CK(cudaGetLastError());
+    ctx->load_checks.push_back({ch.key, expect});
   }
   if (!ch.ev_load) CK(cudaEventCreateWithFlags(&ch.ev_load, cudaEventDisableTiming));
   CK(cudaEventRecord(ch.ev_load, ctx->copy_stream));
@@ -349,11 +421,32 @@ extern "C" {
 
 // Copies a deferred scatter_back of the active buffer into the device pages
 // (on stream s, before anything reads, evicts or rewrites those pages).
+// Device descriptors of the active set (the slot its gather filled).
+const long long* active_desc(const dcg_ctx* ctx) { return ctx->d_desc + (size_t)ctx->desc_slot * 3 * ctx->max_desc; }
+
+// The host staging of the other descriptor slot, once the upload that last
+// used it has run; desc_upload() then sends nd descriptors and makes it current.
+dcg_status desc_stage(dcg_ctx* ctx, long long** h) {
+  const int slot = ctx->desc_slot ^ 1;
+  CK(cudaEventSynchronize(ctx->ev_descs[slot]));
+  *h = ctx->h_desc + (size_t)slot * 3 * ctx->max_desc;
+  return DCG_OK;
+}
+dcg_status desc_upload(dcg_ctx* ctx, int nd, cudaStream_t s) {
+  const int slot = ctx->desc_slot ^ 1;
+  const size_t o = (size_t)slot * 3 * ctx->max_desc;
+  if (nd > 0) CK(cudaMemcpyAsync(ctx->d_desc + o, ctx->h_desc + o, sizeof(long long) * 3 * nd, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(ctx->ev_descs[slot], s));
+  ctx->desc_slot = slot;
+  ctx->n_desc = nd;
+  return DCG_OK;
+}
+
 dcg_status writeback_active(dcg_ctx* ctx, cudaStream_t s) {
   if (!ctx->active_dirty) return DCG_OK;
   ctx->active_dirty = false;
   if (!ctx->active_valid) return DCG_OK;
-  launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->Fs, ctx->d_desc, ctx->n_desc, ctx->d_active,
+  launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->Fs, active_desc(ctx), ctx->n_desc, ctx->d_active,
                    ctx->cfg.max_active, s);
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev_compute, s));
@@ -411,9 +504,12 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
   if (cudaGetDevice(&ctx->device) != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
   if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
+  if (cudaStreamCreateWithFlags(&ctx->cull_stream, cudaStreamNonBlocking) != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
   cudaEventCreateWithFlags(&ctx->ev_copy, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ctx->ev_compute, cudaEventDisableTiming);
-  cudaEventCreateWithFlags(&ctx->ev_desc, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_descs[0], cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_descs[1], cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_am, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ctx->ev_loss, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ctx->ev_win, cudaEventDisableTiming);
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return cleanup_fail(DCG_ERR_CUDA);
@@ -439,14 +535,26 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
       dmalloc(&ctx->d_lcsegkey, (size_t)c.max_chunks) != cudaSuccess ||
       dmalloc(&ctx->d_lcsegbase, (size_t)c.max_chunks) != cudaSuccess || dmalloc(&ctx->d_lccnt, 2) != cudaSuccess ||
       dmalloc(&ctx->d_amoff, (size_t)c.max_chunks) != cudaSuccess ||
-      dmalloc(&ctx->d_amchunk, (size_t)c.max_chunks) != cudaSuccess)
+      dmalloc(&ctx->d_amchunk, (size_t)c.max_chunks) != cudaSuccess ||
+      cudaHostAlloc((void**)&ctx->h_amoff, sizeof(long long) * (size_t)c.max_chunks, 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&ctx->h_amchunk, sizeof(int32_t) * (size_t)c.max_chunks, 0) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
+  if (dmalloc(&ctx->d_loadsum, (size_t)c.max_chunks) != cudaSuccess ||
+      cudaHostAlloc((void**)&ctx->h_loadsum, sizeof(unsigned long long) * (size_t)c.max_chunks, 0) != cudaSuccess)
+    return cleanup_fail(DCG_ERR_OOM);
+  ctx->verify_loads = (c.flags & 4) != 0;
+  if (const char* spec = std::getenv("DCG_FAULT")) {
+    int32_t kind = 0, skip = 0;
+    if (dcg_fault_parse(spec, &kind, &skip) != DCG_OK) return cleanup_fail(DCG_ERR_ARG);
+    dcg_inject_fault(ctx, kind, skip);
+  }
   if (dmalloc(&ctx->d_errword, 1) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
   cudaMemset(ctx->d_errword, 0, sizeof(unsigned));
   if (cudaHostAlloc((void**)&ctx->h_errword, sizeof(unsigned), 0) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
   // chunk table mirror
   if (dmalloc(&ctx->d_coords, 3 * (size_t)c.max_chunks) != cudaSuccess ||
       dmalloc(&ctx->d_vis, (size_t)c.max_chunks) != cudaSuccess || dmalloc(&ctx->d_list, (size_t)c.max_chunks) != cudaSuccess ||
+      dmalloc(&ctx->d_vis_async, (size_t)c.max_chunks) != cudaSuccess ||
       dmalloc(&ctx->d_nlist, 1) != cudaSuccess || dmalloc(&ctx->d_cullcams, kMaxViewsApi) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
   if (cudaHostAlloc((void**)&ctx->h_list, sizeof(int32_t) * c.max_chunks, 0) != cudaSuccess ||
@@ -464,8 +572,8 @@ dcg_status dcg_create(const dcg_config* cfg, dcg_ctx** out) {
   // active buffer and page descriptors
   if (dmalloc(&ctx->d_active, (size_t)ctx->Fs * c.max_active) != cudaSuccess) return cleanup_fail(DCG_ERR_OOM);
   ctx->max_desc = ctx->dev_pages;
-  if (dmalloc(&ctx->d_desc, 3 * (size_t)ctx->max_desc) != cudaSuccess ||
-      cudaHostAlloc((void**)&ctx->h_desc, sizeof(long long) * 3 * (size_t)ctx->max_desc, 0) != cudaSuccess)
+  if (dmalloc(&ctx->d_desc, 2 * 3 * (size_t)ctx->max_desc) != cudaSuccess ||
+      cudaHostAlloc((void**)&ctx->h_desc, sizeof(long long) * 2 * 3 * (size_t)ctx->max_desc, 0) != cudaSuccess)
     return cleanup_fail(DCG_ERR_OOM);
   ctx->st0 = new dcg_render_state();
   if (state_alloc(ctx, ctx->st0) != DCG_OK) return cleanup_fail(DCG_ERR_OOM);
@@ -486,6 +594,7 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   cudaFree(ctx->d_errword);
   if (ctx->h_errword) cudaFreeHost(ctx->h_errword);
   cudaFree(ctx->d_coords); cudaFree(ctx->d_vis); cudaFree(ctx->d_list); cudaFree(ctx->d_nlist); cudaFree(ctx->d_cullcams);
+  cudaFree(ctx->d_vis_async);
   if (ctx->h_list) cudaFreeHost(ctx->h_list);
   if (ctx->h_nlist) cudaFreeHost(ctx->h_nlist);
   if (ctx->h_cullcams) cudaFreeHost(ctx->h_cullcams);
@@ -498,9 +607,11 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   if (ctx->h_keys) cudaFreeHost(ctx->h_keys);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->cull_stream) cudaStreamDestroy(ctx->cull_stream);
   if (ctx->ev_copy) cudaEventDestroy(ctx->ev_copy);
   if (ctx->ev_compute) cudaEventDestroy(ctx->ev_compute);
-  if (ctx->ev_desc) cudaEventDestroy(ctx->ev_desc);
+  for (cudaEvent_t e : ctx->ev_descs)
+    if (e) cudaEventDestroy(e);
   if (ctx->ev_loss) cudaEventDestroy(ctx->ev_loss);
   if (ctx->win_exec) cudaGraphExecDestroy(ctx->win_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -512,8 +623,13 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   cudaFree(ctx->d_lcsegkey);
   cudaFree(ctx->d_lcsegbase);
   cudaFree(ctx->d_lccnt);
+  cudaFree(ctx->d_loadsum);
+  if (ctx->h_loadsum) cudaFreeHost(ctx->h_loadsum);
   cudaFree(ctx->d_amoff);
   cudaFree(ctx->d_amchunk);
+  if (ctx->h_amoff) cudaFreeHost(ctx->h_amoff);
+  if (ctx->h_amchunk) cudaFreeHost(ctx->h_amchunk);
+  if (ctx->ev_am) cudaEventDestroy(ctx->ev_am);
   if (ctx->ev_win) cudaEventDestroy(ctx->ev_win);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
   cudaFree(ctx->d_losscams);
@@ -531,6 +647,36 @@ dcg_status dcg_destroy(dcg_ctx* ctx) {
   cudaFree(ctx->d_ssimpart);
   if (ctx->h_ssimcams) cudaFreeHost(ctx->h_ssimcams);
   delete ctx;
+  return DCG_OK;
+}
+
+dcg_status dcg_fault_parse(const char* spec, int32_t* kind, int32_t* skip) {
+  if (!spec || !kind || !skip) return DCG_ERR_ARG;
+  const std::string sp(spec);
+  const size_t colon = sp.find(':');
+  const std::string name = sp.substr(0, colon);
+  int32_t k = -1;
+  if (name == "none" || name.empty()) k = DCG_FAULT_NONE;
+  else if (name == "h2d_fail") k = DCG_FAULT_H2D_FAIL;
+  else if (name == "short_copy") k = DCG_FAULT_SHORT_COPY;
+  else if (name == "budget") k = DCG_FAULT_BUDGET;
+  if (k < 0) return DCG_ERR_ARG;
+  long n = 0;
+  if (colon != std::string::npos) {
+    const std::string rest = sp.substr(colon + 1);
+    if (rest.empty() || rest.size() > 9 || rest.find_first_not_of("0123456789") != std::string::npos) return DCG_ERR_ARG;
+    n = std::stol(rest);
+  }
+  *kind = k;
+  *skip = (int32_t)n;
+  return DCG_OK;
+}
+
+dcg_status dcg_inject_fault(dcg_ctx* ctx, int32_t kind, int32_t skip) {
+  if (!ctx || kind < DCG_FAULT_NONE || kind > DCG_FAULT_BUDGET || skip < 0) return DCG_ERR_ARG;
+  ctx->fault_kind = kind;
+  ctx->fault_skip = skip;
+  if (kind == DCG_FAULT_SHORT_COPY) ctx->verify_loads = true;  // the checksum is what detects it
   return DCG_OK;
 }
 
@@ -680,20 +826,72 @@ dcg_status dcg_cull_chunks(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views
   if (!ctx) return DCG_ERR_ARG;
   dcg_status cs = check_cams(ctx, cams, n_views);
   if (cs != DCG_OK) return cs;
-  cudaStream_t s = (cudaStream_t)stream;
+  // The cull reads only the chunk table (uploaded synchronously), so without a
+  // mask to order against the caller's stream it runs on the context's own
+  // stream and the host waits for that alone, not for the caller's queued work.
+  cudaStream_t s = mask_out ? (cudaStream_t)stream : ctx->cull_stream;
   const int C = (int)ctx->chunks.size();
   std::memcpy(ctx->h_cullcams, cams, sizeof(dcg_camera) * n_views);
   CK(cudaMemcpyAsync(ctx->d_cullcams, ctx->h_cullcams, sizeof(dcg_camera) * n_views, cudaMemcpyHostToDevice, s));
   hook(ctx)(PH_CULL, true, s);
-  launch_cull(ctx->d_coords, C, ctx->d_cullcams, n_views, ctx->cfg.chunk_size, ctx->cfg.dfar, mask_out, ctx->d_vis,
-              ctx->d_list, ctx->d_nlist, s);
+  CK(launch_cull(ctx->d_coords, C, ctx->d_cullcams, nullptr, n_views, ctx->cfg.chunk_size, ctx->cfg.dfar, mask_out,
+                 ctx->d_vis, ctx->d_list, ctx->d_nlist, s));
   hook(ctx)(PH_CULL, false, s);
-  CK(cudaGetLastError());
   CK(cudaMemcpyAsync(ctx->h_nlist, ctx->d_nlist, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   if (C > 0) CK(cudaMemcpyAsync(ctx->h_list, ctx->d_list, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (n_out) *n_out = *ctx->h_nlist;
   if (list_out) std::memcpy(list_out, ctx->h_list, sizeof(int32_t) * (size_t)*ctx->h_nlist);
+  return DCG_OK;
+}
+
+// Compares every pending load check (verification mode) with the checksum of
+// the pages that arrived.  A chunk that fails is dropped from the device (its
+// pages freed, not written back), so the next gather loads it again.
+dcg_status check_loads(dcg_ctx* ctx) {
+  if (ctx->load_checks.empty()) return DCG_OK;
+  const size_t n = ctx->load_checks.size();
+  CK(cudaMemcpyAsync(ctx->h_loadsum, ctx->d_loadsum, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost,
+                     ctx->copy_stream));
+  CK(cudaStreamSynchronize(ctx->copy_stream));
+  int bad = 0;
+  for (size_t k = 0; k < n; ++k) {
+    if (ctx->h_loadsum[k] == ctx->load_checks[k].second) continue;
+    auto it = ctx->index.find(ctx->load_checks[k].first);
+    if (it == ctx->index.end()) continue;
+    Chunk& ch = ctx->chunks[(size_t)it->second];
+    if (!ch.resident) continue;
+    for (int32_t p : ch.dev_pages) ctx->dev_free.push_back(p);
+    ch.dev_pages.clear();
+    ch.resident = false;
+    ch.dirty = false;
+    ctx->resident_g -= ch.count;
+    ++bad;
+  }
+  ctx->load_checks.clear();
+  if (bad) return fail(ctx, DCG_ERR_FAULT, std::to_string(bad) + " chunk load(s) failed verification (dropped)");
+  return DCG_OK;
+}
+
+dcg_status dcg_cull_chunks_async(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views, uint8_t* mask_out,
+                                 int32_t* list_out, int32_t* n_out, void* stream) {
+  if (!ctx) return DCG_ERR_ARG;
+  // up to 16 views, whatever the render capacity (max_views) of the context
+  if (!cams || n_views <= 0 || n_views > kMaxViewsApi) return fail(ctx, DCG_ERR_ARG, "bad views");
+  for (int v = 0; v < n_views; ++v) {
+    const dcg_camera& c = cams[v];
+    if (c.W <= 0 || c.H <= 0 || !(c.fx > 0) || !(c.fy > 0) || !(c.znear > 0) || !(c.zfar > c.znear))
+      return fail(ctx, DCG_ERR_ARG, "bad camera");
+  }
+  if (!list_out || !n_out) return fail(ctx, DCG_ERR_ARG, "list_out and n_out are required");
+  CullCams tab;
+  std::memset(&tab, 0, sizeof(tab));
+  std::memcpy(tab.c, cams, sizeof(dcg_camera) * n_views);
+  cudaStream_t s = (cudaStream_t)stream;
+  hook(ctx)(PH_CULL, true, s);
+  CK(launch_cull(ctx->d_coords, (int)ctx->chunks.size(), nullptr, &tab, n_views, ctx->cfg.chunk_size, ctx->cfg.dfar,
+                 mask_out, ctx->d_vis_async, list_out, n_out, s));
+  hook(ctx)(PH_CULL, false, s);
   return DCG_OK;
 }
 
@@ -717,7 +915,7 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
   }
   if (total > ctx->cfg.device_budget || total > ctx->cfg.max_active)
     return fail(ctx, DCG_ERR_BUDGET, "visible chunks exceed the device budget");
-  if (ctx->fault == 2) return fail(ctx, DCG_ERR_BUDGET, "injected budget failure");
+  if (fault_fires(ctx, DCG_FAULT_BUDGET)) return fail(ctx, DCG_ERR_BUDGET, "injected budget failure");
   // the active buffer already holds exactly these chunks: hand it out again
   bool reuse = ctx->active_valid && ctx->active_fresh && (size_t)n_list == ctx->active_keys.size();
   for (int k = 0; reuse && k < n_list; ++k)
@@ -776,6 +974,10 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
     }
     ch.last_access = ctx->step;
   }
+  {
+    dcg_status vs = check_loads(ctx);
+    if (vs != DCG_OK) return vs;
+  }
   // wait only for the copies the listed chunks need: the copy stream is in
   // order, so the listed chunk loaded last stands for all of them (prefetches
   // of chunks not needed yet keep running)
@@ -788,7 +990,11 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
   if (newest) CK(cudaStreamWaitEvent(s, newest->ev_load, 0));
   hook(ctx)(PH_STALL, false, s);
   // page descriptors: (page, count, offset in the active buffer)
-  CK(cudaEventSynchronize(ctx->ev_desc));  // the previous descriptor upload has been consumed
+  long long* hd = nullptr;
+  {
+    dcg_status ds = desc_stage(ctx, &hd);
+    if (ds != DCG_OK) return ds;
+  }
   int nd = 0;
   int64_t off = 0;
   ctx->active_keys.clear();
@@ -799,18 +1005,19 @@ dcg_status dcg_gather_active(dcg_ctx* ctx, const int32_t* list, int32_t n_list, 
     ctx->active_counts.push_back(ch.count);
     for (size_t p = 0; p < ch.dev_pages.size(); ++p) {
       const int64_t cnt = std::min<int64_t>(ctx->page_g, ch.count - (int64_t)p * ctx->page_g);
-      ctx->h_desc[3 * nd + 0] = ch.dev_pages[p];
-      ctx->h_desc[3 * nd + 1] = cnt;
-      ctx->h_desc[3 * nd + 2] = off;
+      hd[3 * nd + 0] = ch.dev_pages[p];
+      hd[3 * nd + 1] = cnt;
+      hd[3 * nd + 2] = off;
       off += cnt;
       ++nd;
     }
   }
-  ctx->n_desc = nd;
-  if (nd > 0) CK(cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(long long) * 3 * nd, cudaMemcpyHostToDevice, s));
-  CK(cudaEventRecord(ctx->ev_desc, s));
+  {
+    dcg_status us = desc_upload(ctx, nd, s);
+    if (us != DCG_OK) return us;
+  }
   hook(ctx)(PH_GATHER, true, s);
-  launch_page_copy(true, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->Fs, ctx->d_desc, nd, ctx->d_active,
+  launch_page_copy(true, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->Fs, active_desc(ctx), nd, ctx->d_active,
                    ctx->cfg.max_active, s);
   hook(ctx)(PH_GATHER, false, s);
   CK(cudaGetLastError());
@@ -921,10 +1128,10 @@ dcg_status dcg_scatter_back(dcg_ctx* ctx, const dcg_gaussians* active, int64_t n
   } else {  // parameters from the caller's buffer, moments from the active buffer
     ctx->active_dirty = false;
     ctx->active_fresh = false;
-    launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->F, ctx->d_desc, ctx->n_desc, active->data,
+    launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, 0, ctx->F, active_desc(ctx), ctx->n_desc, active->data,
                      active->stride, s);
     if (ctx->Fs > ctx->F)
-      launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, ctx->F, ctx->Fs - ctx->F, ctx->d_desc, ctx->n_desc,
+      launch_page_copy(false, ctx->d_pool, ctx->page_g, ctx->Fs, ctx->F, ctx->Fs - ctx->F, active_desc(ctx), ctx->n_desc,
                        ctx->d_active + (size_t)ctx->F * ctx->cfg.max_active, ctx->cfg.max_active, s);
   }
   hook(ctx)(PH_SCATTER, false, s);
@@ -939,19 +1146,20 @@ dcg_status dcg_active_map(dcg_ctx* ctx, int32_t* chunk_out, int32_t* row_out, vo
   if (!ctx->active_valid) return fail(ctx, DCG_ERR_STATE, "no gathered active set");
   const int nl = (int)ctx->active_keys.size();
   if (nl == 0 || ctx->n_active == 0 || (!chunk_out && !row_out)) return DCG_OK;
-  std::vector<long long> off((size_t)nl);
-  std::vector<int32_t> ci((size_t)nl);
+  // the staging buffers are free once the previous call's upload has run
+  CK(cudaEventSynchronize(ctx->ev_am));
   long long o = 0;
   for (int k = 0; k < nl; ++k) {
     auto it = ctx->index.find(ctx->active_keys[(size_t)k]);
     if (it == ctx->index.end()) return fail(ctx, DCG_ERR_STATE, "a gathered chunk left the table");
-    ci[(size_t)k] = it->second;
-    off[(size_t)k] = o;
+    ctx->h_amchunk[k] = it->second;
+    ctx->h_amoff[k] = o;
     o += ctx->active_counts[(size_t)k];
   }
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(ctx->d_amoff, off.data(), sizeof(long long) * (size_t)nl, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(ctx->d_amchunk, ci.data(), sizeof(int32_t) * (size_t)nl, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->d_amoff, ctx->h_amoff, sizeof(long long) * (size_t)nl, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->d_amchunk, ctx->h_amchunk, sizeof(int32_t) * (size_t)nl, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(ctx->ev_am, s));
   launch_active_map(ctx->d_amoff, ctx->d_amchunk, nl, ctx->n_active, chunk_out, row_out, ctx->num_sms, s);
   CK(cudaGetLastError());
   return DCG_OK;
@@ -1112,6 +1320,282 @@ static Chunk make_chunk(uint64_t k) {
   return ch;
 }
 
+// Device scratch of a loop closure over n gathered Gaussians, kept between
+// calls and grown on demand (a loop closure is a rare event, not a render step).
+static dcg_status lc_reserve(dcg_ctx* ctx, int64_t n, cudaStream_t s) {
+  if (n <= ctx->lc_dev_cap) return DCG_OK;
+  const int Fs = ctx->Fs;
+  CK(cudaStreamSynchronize(s));
+  cudaFree(ctx->d_lctmp);
+  cudaFree(ctx->d_lcperm);
+  cudaFree(ctx->d_lcmidx);
+  cudaFree(ctx->d_lcmkey);
+  ctx->d_lctmp = nullptr;
+  ctx->d_lcperm = ctx->d_lcmidx = nullptr;
+  ctx->d_lcmkey = nullptr;
+  ctx->lc_dev_cap = 0;
+  CK(cudaMalloc((void**)&ctx->d_lctmp, sizeof(float) * (size_t)Fs * (size_t)n));
+  CK(cudaMalloc((void**)&ctx->d_lcperm, sizeof(long long) * (size_t)n));
+  CK(cudaMalloc((void**)&ctx->d_lcmidx, sizeof(long long) * (size_t)n));
+  CK(cudaMalloc((void**)&ctx->d_lcmkey, sizeof(u64) * (size_t)n));
+  ctx->lc_dev_cap = n;
+  return DCG_OK;
+}
+
+// Drops the device copy of a chunk that is not dirty (its pages are freed).
+static void drop_resident(dcg_ctx* ctx, Chunk& ch) {
+  if (!ch.resident) return;
+  for (int32_t p : ch.dev_pages) ctx->dev_free.push_back(p);
+  ch.dev_pages.clear();
+  ch.resident = false;
+  ch.dirty = false;
+  ctx->resident_g -= ch.count;
+}
+
+// The keyframe-by-keyframe order of Sec. III-F, for when the union of the
+// affected keyframes' chunks does not fit the device budget: the keyframes
+// are taken one at a time in the given order, each loading only the chunks
+// its own cull keeps.  A Gaussian is tested against keyframe k at its
+// uncorrected position unless an earlier keyframe has moved it: that global
+// transformation mask persists across the loads as one flag per (chunk, row)
+// on the host (rows keep their places until the end).  Every keyframe's
+// corrections and moved rows are recorded on the host and applied to the
+// host tier at the end, in the order the batch load produces (remaining
+// rows in stored order, then the incoming ones by source chunk id and row),
+// so the result equals the batch result; nothing changes before the last
+// keyframe has been processed (a position outside the key range leaves the
+// table as it was).  hmask: [K][C] cull of each keyframe.
+static dcg_status loop_closure_by_keyframe(dcg_ctx* ctx, const uint8_t* hmask, int K, int C, int64_t* n_transformed,
+                                           int64_t* n_moved, cudaStream_t s) {
+  const int64_t cap = std::min<int64_t>(ctx->cfg.device_budget, ctx->cfg.max_active);
+  std::vector<std::vector<int32_t>> lists((size_t)K);
+  for (int k = 0; k < K; ++k) {
+    int64_t total = 0;
+    for (int c = 0; c < C; ++c)
+      if (hmask[(size_t)k * C + c]) {
+        lists[(size_t)k].push_back(c);
+        total += ctx->chunks[(size_t)c].count;
+      }
+    if (total > cap) return fail(ctx, DCG_ERR_BUDGET, "the chunks of one keyframe exceed the device budget");
+  }
+  const int Fs = ctx->Fs;
+  const int64_t S = ctx->cfg.max_active;
+  dcg_render_state* st = ctx->st0;
+  uint32_t* d_flags = st->touched;  // render scratch, at least max_active entries
+  u64* d_keys = st->list_a;
+  std::vector<std::vector<uint8_t>> done((size_t)C);  // the global transformation mask
+  struct TRow {
+    int32_t c;
+    int64_t r;
+    float v[7];  // corrected mean and quaternion
+  };
+  struct MRow {
+    int32_t c;
+    int64_t r;
+    uint64_t key;  // chunk id of the corrected position
+  };
+  std::vector<TRow> trows;
+  std::vector<MRow> mrows;
+  int64_t nt = 0;
+  std::vector<uint32_t> hflags;
+  std::vector<float> hval;
+  std::vector<long long> midx;
+  std::vector<uint64_t> mkey;
+  for (int k = 0; k < K; ++k) {
+    const std::vector<int32_t>& lk = lists[(size_t)k];
+    if (lk.empty()) continue;
+    const int nl = (int)lk.size();
+    dcg_gaussians g{};
+    int64_t n = 0;
+    dcg_status gs = dcg_gather_active(ctx, lk.data(), nl, &g, &n, s);
+    if (gs != DCG_OK) return gs;
+    ctx->active_valid = false;  // worked on in place below and never written back
+    if (n == 0) continue;
+    dcg_status rs = lc_reserve(ctx, n, s);
+    if (rs != DCG_OK) return rs;
+    std::vector<long long> seg((size_t)nl);
+    std::vector<int> segc((size_t)nl);
+    std::vector<uint64_t> segkey((size_t)nl);
+    hflags.assign((size_t)n, 0u);
+    long long off = 0;
+    for (int j = 0; j < nl; ++j) {
+      const Chunk& ch = ctx->chunks[(size_t)lk[(size_t)j]];
+      seg[(size_t)j] = off;
+      segc[(size_t)j] = lk[(size_t)j];
+      segkey[(size_t)j] = ch.key;
+      const std::vector<uint8_t>& dn = done[(size_t)lk[(size_t)j]];
+      for (size_t r = 0; r < dn.size(); ++r) hflags[(size_t)off + r] = dn[r];
+      off += ch.count;
+    }
+    CK(cudaMemcpyAsync(ctx->d_lcseg, seg.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_lcsegc, segc.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_lcsegkey, segkey.data(), sizeof(u64) * nl, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_flags, hflags.data(), sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+    hook(ctx)(PH_LOOP, true, s);
+    launch_loop_transform(ctx->d_active, S, n, ctx->d_lcseg, ctx->d_lcsegc, nl, ctx->d_lcmask + (size_t)k * C, C,
+                          ctx->d_lcview + k, 1, d_flags, 1, ctx->num_sms, s);
+    launch_chunk_keys(ctx->d_active, 1, S, n, ctx->cfg.chunk_size, d_keys, ctx->d_errword, ctx->num_sms, s);
+    hook(ctx)(PH_LOOP, false, s);
+    CK(cudaGetLastError());
+    // the rows this keyframe moved, and the corrected mean and rotation of every row
+    CK(cudaMemcpyAsync(hflags.data(), d_flags, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    hval.resize((size_t)7 * n);
+    CK(cudaMemcpy2DAsync(hval.data(), (size_t)n * 4, ctx->d_active, (size_t)S * 4, (size_t)n * 4, 3,
+                         cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpy2DAsync(hval.data() + 3 * n, (size_t)n * 4, ctx->d_active + 6 * S, (size_t)S * 4, (size_t)n * 4, 4,
+                         cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(ctx->d_lccnt, 0, 2 * sizeof(u64), s));
+    hook(ctx)(PH_LOOP, true, s);
+    launch_lc_moved(d_flags, d_keys, n, ctx->d_lcseg, ctx->d_lcsegkey, nl, (unsigned long long*)ctx->d_lccnt,
+                    ctx->d_lcmidx, ctx->d_lcmkey, st->part, st->P, ctx->d_lccnt + 1, ctx->num_sms, s);
+    hook(ctx)(PH_LOOP, false, s);
+    CK(cudaGetLastError());
+    u64 cnt[2] = {0, 0};
+    CK(cudaMemcpyAsync(cnt, ctx->d_lccnt, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    dcg_status es = dcg_sync(ctx, s);  // a position outside the key range stops here; nothing has changed yet
+    if (es != DCG_OK) return es;
+    const int64_t nm = (int64_t)cnt[1];
+    midx.resize((size_t)nm);
+    mkey.resize((size_t)nm);
+    if (nm > 0) {
+      CK(cudaMemcpyAsync(midx.data(), ctx->d_lcmidx, sizeof(long long) * (size_t)nm, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(mkey.data(), ctx->d_lcmkey, sizeof(u64) * (size_t)nm, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    for (int j = 0; j < nl; ++j) {
+      const int32_t c = lk[(size_t)j];
+      const int64_t cntc = ctx->chunks[(size_t)c].count;
+      std::vector<uint8_t>& dn = done[(size_t)c];
+      for (int64_t r = 0; r < cntc; ++r) {
+        const int64_t i = seg[(size_t)j] + r;
+        if (!hflags[(size_t)i]) continue;
+        if (dn.empty()) dn.assign((size_t)cntc, 0);
+        dn[(size_t)r] = 1;
+        TRow t;
+        t.c = c;
+        t.r = r;
+        for (int q = 0; q < 7; ++q) t.v[q] = hval[(size_t)q * n + i];
+        trows.push_back(t);
+      }
+    }
+    for (int64_t m = 0; m < nm; ++m) {
+      const long long i = midx[(size_t)m];
+      const int j = (int)(std::upper_bound(seg.begin(), seg.end(), i) - seg.begin()) - 1;
+      mrows.push_back({lk[(size_t)j], (int64_t)(i - seg[(size_t)j]), mkey[(size_t)m]});
+    }
+    nt += (int64_t)cnt[0];
+  }
+  // apply, with the host tier as the stored value of every chunk
+  {
+    dcg_status fs = dcg_flush(ctx, s);
+    if (fs != DCG_OK) return fs;
+  }
+  std::sort(mrows.begin(), mrows.end(), [](const MRow& a, const MRow& b) { return a.c < b.c || (a.c == b.c && a.r < b.r); });
+  const int64_t nm = (int64_t)mrows.size();
+  std::vector<int64_t> out_c((size_t)C, 0);
+  std::map<uint64_t, int64_t> in_key;
+  for (const MRow& m : mrows) {
+    ++out_c[(size_t)m.c];
+    ++in_key[m.key];
+  }
+  int64_t host_need = 0, new_chunks = 0;
+  for (int c = 0; c < C; ++c) {
+    const Chunk& ch = ctx->chunks[(size_t)c];
+    auto it = in_key.find(ch.key);
+    const int64_t in = it == in_key.end() ? 0 : it->second;
+    if (out_c[(size_t)c] || in) host_need += pages_for(ctx, ch.count - out_c[(size_t)c] + in) - (int64_t)ch.host_pages.size();
+  }
+  for (auto& kv : in_key)
+    if (!ctx->index.count(kv.first)) {
+      ++new_chunks;
+      host_need += pages_for(ctx, kv.second);
+    }
+  if (host_need > (int64_t)ctx->host_free.size()) return fail(ctx, DCG_ERR_CAPACITY, "host tier full");
+  if ((int64_t)ctx->chunks.size() + new_chunks > ctx->cfg.max_chunks)
+    return fail(ctx, DCG_ERR_CAPACITY, "chunk table full");
+  // device copies of every chunk that changes are dropped (clean after the flush)
+  for (const TRow& t : trows) drop_resident(ctx, ctx->chunks[(size_t)t.c]);
+  for (auto& kv : in_key) {
+    auto it = ctx->index.find(kv.first);
+    if (it != ctx->index.end()) drop_resident(ctx, ctx->chunks[(size_t)it->second]);
+  }
+  // 1. the rigid corrections, in place
+  static const int kComp[7] = {0, 1, 2, 6, 7, 8, 9};
+  for (const TRow& t : trows) {
+    const Chunk& ch = ctx->chunks[(size_t)t.c];
+    const int64_t p = t.r / ctx->page_g, o = t.r - p * ctx->page_g;
+    float* page = host_page(ctx, ch.host_pages[(size_t)p]);
+    for (int q = 0; q < 7; ++q) page[(int64_t)kComp[q] * ctx->page_g + o] = t.v[q];
+  }
+  // 2. the moved rows' contents (planar [Fs][nm], gather order), then the
+  // sources keep their remaining rows in stored order
+  std::vector<float> mdata((size_t)Fs * (size_t)std::max<int64_t>(nm, 1));
+  for (int64_t m = 0; m < nm; ++m) {
+    const Chunk& ch = ctx->chunks[(size_t)mrows[(size_t)m].c];
+    const int64_t r = mrows[(size_t)m].r, p = r / ctx->page_g, o = r - p * ctx->page_g;
+    const float* page = host_page(ctx, ch.host_pages[(size_t)p]);
+    for (int f = 0; f < Fs; ++f) mdata[(size_t)f * nm + m] = page[(int64_t)f * ctx->page_g + o];
+  }
+  {
+    int64_t m = 0;
+    std::vector<float> tmp;
+    while (m < nm) {
+      const int32_t c = mrows[(size_t)m].c;
+      Chunk& ch = ctx->chunks[(size_t)c];
+      tmp.assign((size_t)Fs * ch.count, 0.f);
+      for (int64_t r = 0; r < ch.count; ++r) {
+        const int64_t p = r / ctx->page_g, o = r - p * ctx->page_g;
+        const float* page = host_page(ctx, ch.host_pages[(size_t)p]);
+        for (int f = 0; f < Fs; ++f) tmp[(size_t)f * ch.count + r] = page[(int64_t)f * ctx->page_g + o];
+      }
+      const int64_t old = ch.count;
+      int64_t w = 0;
+      for (int64_t r = 0; r < old; ++r) {
+        if (m < nm && mrows[(size_t)m].c == c && mrows[(size_t)m].r == r) {
+          ++m;
+          continue;
+        }
+        const int64_t p = w / ctx->page_g, o = w - p * ctx->page_g;
+        float* page = host_page(ctx, ch.host_pages[(size_t)p]);
+        for (int f = 0; f < Fs; ++f) page[(int64_t)f * ctx->page_g + o] = tmp[(size_t)f * old + r];
+        ++w;
+      }
+      ch.count = w;
+      ch.dirty = false;
+      while ((int64_t)ch.host_pages.size() > pages_for(ctx, ch.count)) {
+        ctx->host_free.push_back(ch.host_pages.back());
+        ch.host_pages.pop_back();
+      }
+    }
+  }
+  // 3. the destinations receive the incoming rows after their own, in gather order
+  bool added = false;
+  for (int64_t m = 0; m < nm; ++m) {
+    const uint64_t key = mrows[(size_t)m].key;
+    auto it = ctx->index.find(key);
+    if (it == ctx->index.end()) {
+      ctx->chunks.push_back(make_chunk(key));
+      ctx->index[key] = (int32_t)ctx->chunks.size() - 1;
+      it = ctx->index.find(key);
+      added = true;
+    }
+    append_host_row(ctx, ctx->chunks[(size_t)it->second], mdata.data(), nm, m, Fs);
+  }
+  if (added) {
+    std::sort(ctx->chunks.begin(), ctx->chunks.end(), [](const Chunk& a, const Chunk& b) { return a.key < b.key; });
+    ctx->index.clear();
+    for (size_t k = 0; k < ctx->chunks.size(); ++k) ctx->index[ctx->chunks[k].key] = (int32_t)k;
+    dcg_status us = upload_coords(ctx);
+    if (us != DCG_OK) return us;
+  }
+  ctx->active_valid = false;
+  ctx->active_fresh = false;
+  ctx->active_dirty = false;
+  if (n_transformed) *n_transformed = nt;
+  if (n_moved) *n_moved = nm;
+  return DCG_OK;
+}
+
 dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* corr, int32_t K, int64_t* n_transformed,
                             int64_t* n_moved, void* stream) {
   if (!ctx || !kf || !corr || K <= 0 || K > kMaxViewsApi) return fail(ctx, DCG_ERR_ARG, "bad arguments");
@@ -1131,21 +1615,47 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   std::memcpy(ctx->h_cullcams, kf, sizeof(dcg_camera) * K);
   CK(cudaMemcpyAsync(ctx->d_cullcams, ctx->h_cullcams, sizeof(dcg_camera) * K, cudaMemcpyHostToDevice, s));
   hook(ctx)(PH_LOOP, true, s);
-  launch_cull(ctx->d_coords, C, ctx->d_cullcams, K, ctx->cfg.chunk_size, ctx->cfg.dfar, ctx->d_lcmask, ctx->d_vis,
-              ctx->d_list, ctx->d_nlist, s);
+  CK(launch_cull(ctx->d_coords, C, ctx->d_cullcams, nullptr, K, ctx->cfg.chunk_size, ctx->cfg.dfar, ctx->d_lcmask,
+                 ctx->d_vis, ctx->d_list, ctx->d_nlist, s));
   hook(ctx)(PH_LOOP, false, s);
-  CK(cudaGetLastError());
   int32_t nl = 0;
   CK(cudaMemcpyAsync(&nl, ctx->d_nlist, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   std::vector<int32_t> list((size_t)nl);
   if (nl) CK(cudaMemcpy(list.data(), ctx->d_list, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost));
   if (nl == 0) return DCG_OK;
-  // 2. batch-load the union (DCG_ERR_BUDGET if it does not fit); a deferred
-  // write-back goes to the pages first, as the transform below works in place
+  // the keyframes: pose before the correction, intrinsics, correction and its rotation
+  std::vector<LcView> views((size_t)K);
+  for (int k = 0; k < K; ++k) {
+    const dcg_camera& c = kf[k];
+    LcView& v = views[(size_t)k];
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) v.R[3 * r + q] = c.Tcw[4 * r + q];
+      v.t[r] = c.Tcw[4 * r + 3];
+      for (int q = 0; q < 4; ++q) v.C[4 * r + q] = corr[16 * k + 4 * r + q];
+    }
+    v.fx = c.fx; v.fy = c.fy; v.cx = c.cx; v.cy = c.cy; v.znear = c.znear; v.zfar = c.zfar; v.W = c.W; v.H = c.H;
+    double Rd[9], qd[4];
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) Rd[3 * r + q] = corr[16 * k + 4 * r + q];
+    rot_to_quat(Rd, qd);
+    for (int q = 0; q < 4; ++q) v.q[q] = (float)qd[q];
+  }
+  CK(cudaMemcpyAsync(ctx->d_lcview, views.data(), sizeof(LcView) * K, cudaMemcpyHostToDevice, s));
+  // a deferred write-back goes to the pages first, as the transform works in place
   {
     dcg_status wb = writeback_active(ctx, s);
     if (wb != DCG_OK) return wb;
+  }
+  // 2. batch-load the union; when it exceeds the device budget, one keyframe at a time
+  {
+    int64_t total = 0;
+    for (int k = 0; k < nl; ++k) total += ctx->chunks[(size_t)list[(size_t)k]].count;
+    if (total > std::min<int64_t>(ctx->cfg.device_budget, ctx->cfg.max_active)) {
+      std::vector<uint8_t> hmask((size_t)K * C);
+      CK(cudaMemcpy(hmask.data(), ctx->d_lcmask, (size_t)K * C, cudaMemcpyDeviceToHost));
+      return loop_closure_by_keyframe(ctx, hmask.data(), K, C, n_transformed, n_moved, s);
+    }
   }
   dcg_gaussians g{};
   int64_t n = 0;
@@ -1163,25 +1673,8 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
       off += ctx->chunks[list[(size_t)k]].count;
     }
   }
-  std::vector<LcView> views((size_t)K);
-  for (int k = 0; k < K; ++k) {
-    const dcg_camera& c = kf[k];
-    LcView& v = views[(size_t)k];
-    for (int r = 0; r < 3; ++r) {
-      for (int q = 0; q < 3; ++q) v.R[3 * r + q] = c.Tcw[4 * r + q];
-      v.t[r] = c.Tcw[4 * r + 3];
-      for (int q = 0; q < 4; ++q) v.C[4 * r + q] = corr[16 * k + 4 * r + q];
-    }
-    v.fx = c.fx; v.fy = c.fy; v.cx = c.cx; v.cy = c.cy; v.znear = c.znear; v.zfar = c.zfar; v.W = c.W; v.H = c.H;
-    double Rd[9], qd[4];
-    for (int r = 0; r < 3; ++r)
-      for (int q = 0; q < 3; ++q) Rd[3 * r + q] = corr[16 * k + 4 * r + q];
-    rot_to_quat(Rd, qd);
-    for (int q = 0; q < 4; ++q) v.q[q] = (float)qd[q];
-  }
   CK(cudaMemcpyAsync(ctx->d_lcseg, seg.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ctx->d_lcsegc, segc.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(ctx->d_lcview, views.data(), sizeof(LcView) * K, cudaMemcpyHostToDevice, s));
   // 3. rigid correction under the global mask, then chunk ids of the result (Eq. 5/6)
   dcg_render_state* st = ctx->st0;
   uint32_t* d_flags = st->touched;  // render scratch, at least max_active entries
@@ -1189,7 +1682,7 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   const int64_t S = ctx->cfg.max_active;
   hook(ctx)(PH_LOOP, true, s);
   launch_loop_transform(ctx->d_active, S, n, ctx->d_lcseg, ctx->d_lcsegc, nl, ctx->d_lcmask, C, ctx->d_lcview, K,
-                        d_flags, ctx->num_sms, s);
+                        d_flags, 0, ctx->num_sms, s);
   launch_chunk_keys(ctx->d_active, 1, S, n, ctx->cfg.chunk_size, d_keys, ctx->d_errword, ctx->num_sms, s);
   hook(ctx)(PH_LOOP, false, s);
   CK(cudaGetLastError());
@@ -1199,21 +1692,9 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   // borders), the host plans only those and the per-chunk offsets, and the
   // device writes the permutation.
   const int Fs = ctx->Fs;
-  if (n > ctx->lc_dev_cap) {  // device scratch kept between loop closures, grown on demand
-    CK(cudaStreamSynchronize(s));
-    cudaFree(ctx->d_lctmp);
-    cudaFree(ctx->d_lcperm);
-    cudaFree(ctx->d_lcmidx);
-    cudaFree(ctx->d_lcmkey);
-    ctx->d_lctmp = nullptr;
-    ctx->d_lcperm = ctx->d_lcmidx = nullptr;
-    ctx->d_lcmkey = nullptr;
-    ctx->lc_dev_cap = 0;
-    CK(cudaMalloc((void**)&ctx->d_lctmp, sizeof(float) * (size_t)Fs * (size_t)n));
-    CK(cudaMalloc((void**)&ctx->d_lcperm, sizeof(long long) * (size_t)n));
-    CK(cudaMalloc((void**)&ctx->d_lcmidx, sizeof(long long) * (size_t)n));
-    CK(cudaMalloc((void**)&ctx->d_lcmkey, sizeof(u64) * (size_t)n));
-    ctx->lc_dev_cap = n;
+  {
+    dcg_status rs = lc_reserve(ctx, n, s);
+    if (rs != DCG_OK) return rs;
   }
   CK(cudaMemcpyAsync(ctx->d_lcsegkey, segkey.data(), sizeof(u64) * (size_t)nl, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(ctx->d_lccnt, 0, 2 * sizeof(u64), s));
@@ -1329,7 +1810,11 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
   launch_permute_rows(ctx->d_active, S, d_tmp, n, d_perm, n, Fs, ctx->num_sms, s);
   hook(ctx)(PH_LOOP, false, s);
   // gathered chunks: new counts and pages, content written from the permuted rows
-  CK(cudaEventSynchronize(ctx->ev_desc));
+  long long* hd = nullptr;
+  {
+    dcg_status ds = desc_stage(ctx, &hd);
+    if (ds != DCG_OK) return ds;
+  }
   int nd = 0;
   int64_t off = 0;
   for (int k = 0; k < nl; ++k) {
@@ -1357,17 +1842,19 @@ dcg_status dcg_loop_closure(dcg_ctx* ctx, const dcg_camera* kf, const float* cor
     ch.dirty = true;
     for (size_t p = 0; p < np; ++p) {
       const int64_t cnt = std::min<int64_t>(ctx->page_g, nc - (int64_t)p * ctx->page_g);
-      ctx->h_desc[3 * nd + 0] = ch.dev_pages[p];
-      ctx->h_desc[3 * nd + 1] = cnt;
-      ctx->h_desc[3 * nd + 2] = off;
+      hd[3 * nd + 0] = ch.dev_pages[p];
+      hd[3 * nd + 1] = cnt;
+      hd[3 * nd + 2] = off;
       off += cnt;
       ++nd;
     }
   }
-  if (nd > 0) CK(cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(long long) * 3 * nd, cudaMemcpyHostToDevice, s));
-  CK(cudaEventRecord(ctx->ev_desc, s));
+  {
+    dcg_status us = desc_upload(ctx, nd, s);
+    if (us != DCG_OK) return us;
+  }
   hook(ctx)(PH_LOOP, true, s);
-  launch_page_copy(false, ctx->d_pool, ctx->page_g, Fs, 0, Fs, ctx->d_desc, nd, d_tmp, n, s);
+  launch_page_copy(false, ctx->d_pool, ctx->page_g, Fs, 0, Fs, active_desc(ctx), nd, d_tmp, n, s);
   hook(ctx)(PH_LOOP, false, s);
   CK(cudaGetLastError());
   // Gaussians leaving for chunks that were not gathered: appended in the host tier
@@ -1634,6 +2121,7 @@ static void fill_args(dcg_render_state* st, RasterArgs& a) {
   a.num_sms = ctx->num_sms;
   a.prof = hook(ctx);
   a.bwd_slots = (ctx->cfg.flags & 1) ? 1 : 0;
+  a.bwd_pix = (ctx->cfg.flags & 2) ? 1 : 0;
 }
 
 static void fill_devcams(const dcg_camera* cams, int V, int tw, int th, DevCam* out, int64_t* pix_out,

@@ -32,13 +32,23 @@ struct ProfHook {
 // device error word bits
 constexpr unsigned ERRW_KEY_RANGE_BIT = 1u;
 constexpr unsigned ERRW_CAPACITY_BIT = 2u;
-constexpr unsigned ERRW_TIMEOUT_BIT = 4u;
+constexpr unsigned ERRW_TIMEOUT_BIT = 4u;  // reserved: no kernel waits on another block or a flag
 
 // ---------------------------------------------------------------- chunk.cu
 void launch_chunk_keys(const float* means, long long row, long long col, long long n, float s, u64* keys,
                        unsigned* errword, int num_sms, cudaStream_t st);
-void launch_cull(const int32_t* coords, int C, const dcg_camera* cams, int V, float s, float dfar, uint8_t* mask,
-                 uint8_t* vis, int32_t* list, int32_t* n, cudaStream_t st);
+// Cameras of one cull passed by value (kernel parameter space, 1.5 KB).
+struct CullCams {
+  dcg_camera c[kMaxViewsApi];
+};
+// Cull of C chunks against V views: the cameras come from device memory
+// (cams) or, when tab is not null, by value from *tab.  Clears vis first;
+// returns the first error of the clear or the launches.
+cudaError_t launch_cull(const int32_t* coords, int C, const dcg_camera* cams, const CullCams* tab, int V, float s,
+                        float dfar, uint8_t* mask, uint8_t* vis, int32_t* list, int32_t* n, cudaStream_t st);
+// Load verification: adds the checksum of page p of a chunk (cnt rows) to *out.
+void launch_page_checksum(const float* page, long long p, long long page_g, int Fp, long long cnt,
+                          unsigned long long* out, cudaStream_t st);
 void launch_active_map(const long long* off, const int32_t* chunk, int nl, long long n, int32_t* chunk_out,
                        int32_t* row_out, int num_sms, cudaStream_t st);
 void launch_page_copy(bool gather, float* pool, long long page_g, int Fp, int c0, int nc, const long long* desc, int nd,
@@ -55,9 +65,11 @@ struct LcView {
   float C[12];
   float q[4];
 };
+// flags: per row, on return the keyframe (1-based) that moved it, else 0; with
+// skip_done a nonzero flag on entry marks a row already moved (left alone, flag cleared).
 void launch_loop_transform(float* act, long long stride, long long n, const long long* seg_off, const int* seg_chunk,
-                           int nseg, const uint8_t* mask, int C, const LcView* kf, int K, uint32_t* flags, int num_sms,
-                           cudaStream_t st);
+                           int nseg, const uint8_t* mask, int C, const LcView* kf, int K, uint32_t* flags, int skip_done,
+                           int num_sms, cudaStream_t st);
 // Loop-closure redistribution: moved flags (in place of the transformed
 // flags, whose count goes to *n_transformed), the moved rows ascending with
 // their keys in midx / mkey and their number in *n_moved; then the
@@ -170,6 +182,7 @@ struct RasterArgs {
   unsigned* errword;
   int num_sms;
   int bwd_slots;  // 1: backward accumulates per-lane slots instead of warp reductions
+  int bwd_pix;    // 1: the half-warp backward keeps pixels on the lanes (one Gaussian per half per step)
   ProfHook prof;
 };
 

@@ -20,11 +20,18 @@ __device__ __forceinline__ float dot3_rn(const float* r, float x, float y, float
   return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r[0], x), __fmul_rn(r[1], y)), __fmul_rn(r[2], z)), t);
 }
 
+// skip_done: flags[i] != 0 on entry marks a Gaussian that an earlier keyframe
+// has already moved (the global transformation mask carried across loads of
+// the keyframe-by-keyframe order); it is left alone and its flag cleared.
 __global__ void k_loop_transform(float* __restrict__ act, long long stride, long long n,
                                  const long long* __restrict__ seg_off, const int* __restrict__ seg_chunk, int nseg,
                                  const uint8_t* __restrict__ mask, int C, const LcView* __restrict__ kf, int K,
-                                 uint32_t* __restrict__ flags) {
+                                 uint32_t* __restrict__ flags, int skip_done) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (skip_done && flags[i] != 0u) {
+      flags[i] = 0u;
+      continue;
+    }
     // chunk of active Gaussian i: the last segment starting at or before i
     int lo = 0, hi = nseg - 1;
     while (lo < hi) {
@@ -79,7 +86,8 @@ __global__ void k_cap_rows(float* __restrict__ row, long long n, float cap) {
 // k owns rows [seg_off[k], seg_off[k + 1])); a row moves if its recomputed
 // chunk id differs from its segment's.  k_lc_moved turns the transformed
 // flag of each row into its moved flag and counts the transformed rows;
-// the moved rows (ascending) are then compacted by the ordered scan.
+// the moved rows (ascending) are then compacted by the ordered scan.  A row
+// the call did not transform keeps its position and therefore its chunk.
 __device__ __forceinline__ int lc_seg_of(const long long* __restrict__ seg_off, int nseg, long long i) {
   int lo = 0, hi = nseg - 1;  // last k with seg_off[k] <= i
   while (lo < hi) {
@@ -94,8 +102,10 @@ __global__ void k_lc_moved(uint32_t* __restrict__ flags, const u64* __restrict__
                            unsigned long long* n_transformed) {
   unsigned long long cnt = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    cnt += flags[i] != 0u;
-    flags[i] = keys[i] != seg_key[lc_seg_of(seg_off, nseg, i)] ? 1u : 0u;
+    // only a Gaussian transformed by this call can have left its chunk
+    const bool t = flags[i] != 0u;
+    cnt += t;
+    flags[i] = t && keys[i] != seg_key[lc_seg_of(seg_off, nseg, i)] ? 1u : 0u;
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -156,13 +166,12 @@ void launch_lc_dest(const uint32_t* moved, long long n, const long long* seg_off
 }
 
 void launch_loop_transform(float* act, long long stride, long long n, const long long* seg_off, const int* seg_chunk,
-                           int nseg, const uint8_t* mask, int C, const LcView* kf, int K, uint32_t* flags, int num_sms,
-                           cudaStream_t st) {
+                           int nseg, const uint8_t* mask, int C, const LcView* kf, int K, uint32_t* flags, int skip_done,
+                           int num_sms, cudaStream_t st) {
   if (n <= 0) return;
   const long long blocks = (n + 255) / 256;
-  k_loop_transform<<<(int)std::min<long long>(blocks, (long long)num_sms * 8), 256, 0, st>>>(act, stride, n, seg_off,
-                                                                                           seg_chunk, nseg, mask, C,
-                                                                                           kf, K, flags);
+  k_loop_transform<<<(int)std::min<long long>(blocks, (long long)num_sms * 8), 256, 0, st>>>(
+      act, stride, n, seg_off, seg_chunk, nseg, mask, C, kf, K, flags, skip_done);
   count_launch();
 }
 

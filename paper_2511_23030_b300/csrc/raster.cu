@@ -1597,6 +1597,225 @@ __global__ void __launch_bounds__(256) k_blend_bwd_h(RasterArgs a, const u64* __
   }
 }
 
+// Backward blend with Gaussians on the lanes.  One warp per (tile, half
+// block): the half's 4 x WY pixels and the Gaussians of the tile's list that
+// reach the half (its half-block bit), taken 16 at a time from the end, the
+// deepest first.  Both half-warps hold the same 16 Gaussians (lane l and
+// l + 16 hold Gaussian l & 15) and take two pixels of the half block at a
+// time, one each: the lanes evaluate their Gaussians at their half's pixel,
+// and one warp scan in lane order (deep to front) over the affine maps
+//   (T, Q) -> (r T, Q + r alpha (c . g) T),   r = 1 / (1 - alpha)
+// (the reverse traversal of one pixel past one Gaussian; identity where the
+// Gaussian does not composite) gives every lane what the traversal gives one
+// Gaussian at a time: the transmittance in front of it, T_j = T_behind A_j,
+// and the loss-weighted colour composited behind it,
+// Q_j = Q_behind + T_behind B_j - T_j alpha_j (c_j . g), with
+// dL/dalpha_j = T_j (c_j . g) - Q_j / (1 - alpha_j).  The pixel's
+// (T_behind, Q_behind) then move past the chunk.  Every lane accumulates its
+// Gaussian's 2D-gradient moments over its half's pixels, so no reduction
+// over Gaussians is needed: after the pixels the two half-warps' sums are
+// added and each Gaussian's ten sums go to its gradient slot with vector
+// atomics.
+constexpr int kRingG = 64;  // staged Gaussians per warp
+constexpr int kChunkG = 16;  // Gaussians per chunk (lanes of a half-warp)
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+__device__ __forceinline__ void red_add_v2(float* p, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_blend_bwd_g(RasterArgs a, const u64* __restrict__ inst,
+                                                     const float* __restrict__ dL_drgb,
+                                                     const float* __restrict__ dL_ddepth) {
+  using L = TileLayout<TW, TH>;
+  constexpr int WY = L::WY;
+  constexpr int NP = 4 * WY;  // pixels of a half block
+  constexpr int R = kRingG;
+  constexpr int CH = kChunkG;
+  __shared__ float2 s_xy[8][R];
+  __shared__ float4 s_con[8][R];
+  __shared__ float4 s_col[8][R];
+  __shared__ int s_rel[8][R];
+  __shared__ unsigned s_vi[8][R];
+  __shared__ float4 s_g[8][NP];   // dL/d(r, g, b, depth) of each pixel of the half
+  __shared__ float4 s_st[8][NP];  // (T behind, Q behind, last contributor (int bits), unused)
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, hl = lane >> 4, gl = lane & 15;
+  const unsigned lt = lanemask_lt();
+  const unsigned n_items = 16u * (unsigned)a.n_tiles;
+  float* const g2 = reinterpret_cast<float*>(a.grad2d);
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(&a.counters->tile_queue_bwd, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    const unsigned gt = item >> 4, wb = (item >> 1) & 7u, h = item & 1u;
+    const int bx0 = (int)(wb % L::WPR) * 8 + 4 * (int)h, by0 = (int)(wb / L::WPR) * WY;
+    const int v = view_of_tile(a.cams, a.V, gt);
+    const DevCam& c = a.cams[v];
+    const int W = c.W, H = c.H;
+    const int local = (int)gt - c.tile_base;
+    const int ty = local / c.ntx, tx = local - ty * c.ntx;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const float x0f = (float)x0, y0f = (float)y0;
+    const long long P = (long long)W * H;
+    // the half's pixels: loss gradients and the forward's end state
+    unsigned mylast = 0;
+    for (int p = lane; p < NP; p += 32) {
+      const int px = x0 + bx0 + (p & 3), py = y0 + by0 + (p >> 2);
+      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+      float Tf = 0.f;
+      unsigned last = 0;
+      if (px < W && py < H) {
+        const long long pix = (long long)py * W + px;
+        Tf = a.T_final[c.pix_off + pix];
+        last = a.n_contrib[c.pix_off + pix];
+        g = make_float4(dL_drgb[3 * c.pix_off + pix], dL_drgb[3 * c.pix_off + P + pix],
+                        dL_drgb[3 * c.pix_off + 2 * P + pix], dL_ddepth[c.pix_off + pix]);
+      }
+      s_g[w][p] = g;
+      s_st[w][p] = make_float4(Tf, 0.f, __int_as_float((int)last), 0.f);
+      mylast = max(mylast, last);
+    }
+    int hi = (int)__reduce_max_sync(0xffffffffu, mylast);  // instances [0, hi) are still to scan
+    const uint2 rg = a.ranges[gt];
+    int hd = 0, pc = 0;  // ring head and count
+    __syncwarp();
+    for (;;) {
+      while (hi > 0 && pc < CH) {
+        const int rel = hi - 1 - lane;  // lane 0 takes the largest index: the ring keeps reverse order
+        bool take = false;
+        unsigned vi = 0;
+        if (rel >= 0) {
+          const u64 key = inst[rg.x + rel];
+          vi = pair_of_inst(key);
+          take = (half_bits(key, (int)wb) >> h) & 1u;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        if (take) {
+          int sl = hd + pc + __popc(m & lt);
+          sl -= sl >= R ? R : 0;
+          sl -= sl >= R ? R : 0;
+          const float4 r0 = a.rec[3ull * vi + 0];
+          s_xy[w][sl] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+          s_con[w][sl] = a.rec[3ull * vi + 1];
+          s_col[w][sl] = a.rec[3ull * vi + 2];
+          s_rel[w][sl] = rel;
+          s_vi[w][sl] = vi;
+        }
+        pc += __popc(m);
+        hi -= 32;
+      }
+      __syncwarp();
+      if (pc == 0) break;
+      const int cnt = min(pc, CH);
+      int e = hd + gl;
+      e -= e >= R ? R : 0;
+      const bool mine = gl < cnt;
+      const float2 xy = mine ? s_xy[w][e] : make_float2(0.f, 0.f);
+      const float4 cq = mine ? s_con[w][e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 cl = mine ? s_col[w][e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int rl = mine ? s_rel[w][e] : 0x7fffffff;
+      const unsigned vi = mine ? s_vi[w][e] : 0u;
+      const int minrel = __shfl_sync(0xffffffffu, rl, cnt - 1);  // the chunk's front-most instance
+      float acc[10];
+#pragma unroll
+      for (int q = 0; q < 10; ++q) acc[q] = 0.f;
+      // this half-warp's two pixel columns of the half block: hl and hl + 2
+      float dxc[2], sxc[2], bxc[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        dxc[q] = __fsub_rn((float)(bx0 + 2 * q + hl), xy.x);
+        sxc[q] = __fmul_rn(dxc[q], __fmul_rn(cq.x, dxc[q]));
+        bxc[q] = __fmul_rn(cq.y, dxc[q]);
+      }
+      for (int rr = 0; rr < WY; ++rr) {
+        const float dy = __fsub_rn((float)(by0 + rr), xy.y);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int p = 4 * rr + 2 * q + hl;  // this half-warp's pixel
+          const float4 st = s_st[w][p];
+          const int lastp = __float_as_int(st.z);
+          // pixels whose last contributor lies in front of the whole chunk take no part
+          if (!__any_sync(0xffffffffu, minrel < lastp)) continue;
+          // the same decisions, bit for bit, as the forward blend
+          const float pw = blend_power(sxc[q], bxc[q], cq.z, dy);
+          const float G = ex2_approx(pw);
+          const float araw = __fmul_rn(cq.w, G);
+          const float al = fminf(kAlphaMax, araw);
+          const bool valid = rl < lastp && pw >= kPMin && al >= kAlphaMin;
+          if (!__any_sync(0xffffffffu, valid)) continue;  // nothing composites: the states are unchanged
+          const float4 g = s_g[w][p];
+          const float r = valid ? rcp_approx(__fsub_rn(1.f, al)) : 1.f;
+          const float cg = cl.x * g.x + cl.y * g.y + cl.z * g.z + cl.w * g.w;
+          float A = r, B = valid ? r * al * cg : 0.f;
+#pragma unroll
+          for (int o = 1; o < CH; o <<= 1) {
+            const float Au = __shfl_up_sync(0xffffffffu, A, o, CH);
+            const float Bu = __shfl_up_sync(0xffffffffu, B, o, CH);
+            if (gl >= o) {
+              B = fmaf(Au, B, Bu);
+              A = Au * A;
+            }
+          }
+          const float Tj = st.x * A;
+          if (valid) {
+            const float wgt = al * Tj;
+            acc[6] += wgt * g.x;
+            acc[7] += wgt * g.y;
+            acc[8] += wgt * g.z;
+            acc[9] += wgt * g.w;
+            // moments of dL/dalpha G (none through a clamped alpha); the conic
+            // and opacity factors are applied per Gaussian in k_preprocess_bwd
+            if (araw < kAlphaMax) {
+              const float Q = fmaf(st.x, B, st.y) - wgt * cg;
+              const float dal = Tj * cg - Q * r;
+              const float gG = dal * G;
+              const float gx = gG * dxc[q], gy = gG * dy;
+              acc[5] += gG;
+              acc[0] += gx;
+              acc[1] += gy;
+              acc[2] += gx * dxc[q];
+              acc[3] += gx * dy;
+              acc[4] += gy * dy;
+            }
+          }
+          const float At = __shfl_sync(0xffffffffu, A, CH - 1, CH), Bt = __shfl_sync(0xffffffffu, B, CH - 1, CH);
+          if (gl == CH - 1) {
+            s_st[w][p].x = st.x * At;
+            s_st[w][p].y = fmaf(st.x, Bt, st.y);
+          }
+        }
+      }
+      // the two half-warps hold partial sums of the same Gaussians
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < 10; ++q) {
+        acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 16);
+        any |= acc[q] != 0.f;
+      }
+      if (hl == 0 && mine && any) {
+        float* s = g2 + 12ull * vi;
+        red_add_v4(s, acc[0], acc[1], acc[2], acc[3]);
+        red_add_v4(s + 4, acc[4], acc[5], acc[6], acc[7]);
+        red_add_v2(s + 8, acc[8], acc[9]);
+      }
+      hd += cnt;
+      hd -= hd >= R ? R : 0;
+      pc -= cnt;
+      __syncwarp();
+    }
+  }
+}
+
 // Backward variant without per-Gaussian warp reductions: every lane adds its
 // own contribution to a private slot of a block-shared accumulator
 // [segment Gaussian][component][lane] (shared-memory atomics, since warps of
@@ -2132,6 +2351,13 @@ static void blend_h_launch(bool fwd, RasterArgs& a, const u64* inst, float* rgb,
   if (occ_f < 0) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_blend_fwd_h<TW, TH>, 256, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_blend_bwd_h<TW, TH>, 256, 0);
+  }
+  static int occ_g = -1;
+  if (occ_g < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_g, k_blend_bwd_g<TW, TH>, 256, 0);
+  if (!fwd && !a.bwd_pix) {  // Gaussians on the lanes: items are (tile, half block)
+    const int grid = max(1, min(2 * a.n_tiles, a.num_sms * max(occ_g, 1)));
+    k_blend_bwd_g<TW, TH><<<grid, 256, 0, st>>>(a, inst, dr, dd);
+    return;
   }
   const int occ = fwd ? occ_f : occ_b;
   const int grid = max(1, min(a.n_tiles, a.num_sms * max(occ, 1)));

@@ -123,7 +123,13 @@ _SIGS = {
                                              _P, _I64, _P]),
     "dcg_cull_chunks_noalloc": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(dcg_camera),
                                                _I32, _P, _P, _P, _P]),
+    "dcg_inject_fault": (ctypes.c_int, [_P, _I32, _I32]),
+    "dcg_cull_chunks_async": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _I32, _P, _P, _P, _P]),
+    "dcg_fault_parse": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
 }
+
+FAULTS = {"none": 0, "h2d_fail": 1, "short_copy": 2, "budget": 3}
+FLAG_VERIFY_LOADS = 4  # dcg_config.flags bit 2: chunk loads checked by checksum
 
 PHASES = ["cull", "gather", "preprocess_fwd", "binning", "blend_fwd", "loss", "blend_bwd", "preprocess_bwd", "scatter",
           "stall", "log_sample", "loop_closure"]
@@ -569,3 +575,25 @@ def dcg_chunks_near(ctx, p, radius: float, only_nonresident: bool = False) -> np
     pp = np.ascontiguousarray(p, np.float32)
     check(ctx, lib().dcg_chunks_near(ctx, ptr(pp), float(radius), int(only_nonresident), ptr(out), ctypes.byref(k)))
     return out[: k.value].copy()
+
+
+def dcg_inject_fault(ctx, kind, skip: int = 0):
+    """Arm one host-side fault of the chunk tier (kind: name or DCG_FAULT_* value)."""
+    k = FAULTS[kind] if isinstance(kind, str) else int(kind)
+    check(ctx, lib().dcg_inject_fault(ctx, k, int(skip)))
+
+
+def dcg_fault_parse(spec: str):
+    """(kind, skip) of a DCG_FAULT specification; DcgError if it is malformed."""
+    k, n = ctypes.c_int32(), ctypes.c_int32()
+    st = lib().dcg_fault_parse(spec.encode(), ctypes.byref(k), ctypes.byref(n))
+    if st != DCG_OK:
+        raise DcgError(st, f"bad fault specification {spec!r}")
+    return k.value, n.value
+
+
+def dcg_cull_chunks_async(ctx, cams, list_out, n_out, mask_out=None, stream=None):
+    """Cull left on the device (list_out: dev int32 [chunk count], n_out: dev int32 [1])."""
+    arr = make_cameras(cams)
+    check(ctx, lib().dcg_cull_chunks_async(ctx, arr, len(cams), ptr(mask_out), ptr(list_out), ptr(n_out),
+                                           stream_ptr(stream)))

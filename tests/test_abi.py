@@ -64,3 +64,17 @@ def test_build_targets_sm_103a_only():
     from paper_2511_23030_b300 import build
 
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_fault_specification_parses_on_the_host(libpath):
+    """DCG_FAULT=kind[:skip], read at dcg_create, parsed by a host-only call."""
+    from paper_2511_23030_b300 import dcg
+
+    assert dcg.dcg_fault_parse("h2d_fail") == (1, 0)
+    assert dcg.dcg_fault_parse("short_copy:3") == (2, 3)
+    assert dcg.dcg_fault_parse("budget:0") == (3, 0)
+    assert dcg.dcg_fault_parse("none") == (0, 0)
+    for bad in ("h2d", "budget:", "budget:-1", "short_copy:1x", "budget:12345678901"):
+        with pytest.raises(dcg.DcgError) as e:
+            dcg.dcg_fault_parse(bad)
+        assert e.value.status == 1

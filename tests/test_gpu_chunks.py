@@ -169,6 +169,62 @@ def test_active_map_names_each_active_row():
         dcg.dcg_destroy(ctx)
 
 
+def test_active_map_after_table_update_and_on_the_reuse_path():
+    """The map keeps the gather-time rows when a table update afterwards grows a
+    gathered chunk and adds a chunk with a lower id (which renumbers the table):
+    chunk_out names the chunks by their new table index, with the counts they had
+    when gathered.  A repeat gather of the same list after scatter_back (the
+    library's buffer handed out again without a copy) gives the same map."""
+    import torch
+
+    ctx, sc = _window_table()
+    try:
+        P = sc["params"]
+        F = P.shape[1]
+        info0 = dcg.dcg_chunk_info(ctx)
+        lst = dcg.dcg_cull_chunks(ctx, sc["cams"][2:5])
+        g, n = dcg.dcg_gather_active(ctx, lst)
+        keys0 = info0["keys"][lst]
+        counts0 = info0["counts"][lst]
+        # grow the first listed chunk by 100 copies of its own Gaussians, and add 50
+        # Gaussians in a chunk below every existing one (x coordinate -6 chunks)
+        first = dcg.dcg_chunk_read(ctx, int(lst[0]), int(counts0[0]), F).T[:100].copy()
+        low = first[:50].copy()
+        low[:, 0] = -6.0 * sc["chunk_size"]
+        dcg.dcg_chunk_table_update(ctx, planar(np.concatenate([first, low]).astype(np.float32)), 150)
+        info1 = dcg.dcg_chunk_info(ctx)
+        assert len(info1["keys"]) == len(info0["keys"]) + 1 and info1["keys"][0] < info0["keys"][0]
+        new_idx = np.searchsorted(info1["keys"], keys0)
+        assert np.array_equal(info1["keys"][new_idx], keys0) and np.array_equal(new_idx, lst + 1)
+        assert info1["counts"][new_idx[0]] == counts0[0] + 100
+        chunk = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        row = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        dcg.dcg_active_map(ctx, chunk, row)
+        dcg.dcg_sync(ctx)
+        want_chunk = np.concatenate([np.full(int(c), k) for k, c in zip(new_idx, counts0)])
+        want_row = np.concatenate([np.arange(int(c)) for c in counts0])
+        assert np.array_equal(chunk.cpu().numpy(), want_chunk) and np.array_equal(row.cpu().numpy(), want_row)
+    finally:
+        dcg.dcg_destroy(ctx)
+    ctx, sc = _window_table()
+    try:
+        info = dcg.dcg_chunk_info(ctx)
+        lst = dcg.dcg_cull_chunks(ctx, sc["cams"][1:3])
+        g, n = dcg.dcg_gather_active(ctx, lst)
+        dcg.dcg_scatter_back(ctx, g, n)  # the library's own buffer: write-back deferred
+        g2, n2 = dcg.dcg_gather_active(ctx, lst)  # the same list: handed out again without a copy
+        assert n2 == n and g2.data == g.data
+        chunk = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        row = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        dcg.dcg_active_map(ctx, chunk, row)
+        dcg.dcg_sync(ctx)
+        want_chunk = np.concatenate([np.full(int(info["counts"][c]), c) for c in lst])
+        want_row = np.concatenate([np.arange(int(info["counts"][c])) for c in lst])
+        assert np.array_equal(chunk.cpu().numpy(), want_chunk) and np.array_equal(row.cpu().numpy(), want_row)
+    finally:
+        dcg.dcg_destroy(ctx)
+
+
 def _read_active(g, n, F):
     """Copy of the library-owned active buffer (planar, stride g.stride) as numpy [n, F]."""
     return dcg.active_tensor(g, n, F).T.cpu().numpy()

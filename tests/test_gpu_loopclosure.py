@@ -36,8 +36,20 @@ def _setup(budget=None):
     ctx = make_ctx(deg=1, n_max=N, chunk=sc["chunk_size"], budget=budget, host=N, page=512, dfar=60.0, moments=1)
     dcg.dcg_chunk_table_update(ctx, planar(sc["params"]), N)
     F = sc["params"].shape[1]
-    if budget is None:  # give the moments non-zero values
-        g, n = dcg.dcg_gather_active(ctx, np.arange(dcg.dcg_chunk_count(ctx), dtype=np.int32))
+    # give the moments non-zero values: one Adam step with gradient sin(3 p), elementwise, so
+    # gathering the chunks in groups that fit the budget gives every context the same map
+    info = dcg.dcg_chunk_info(ctx)
+    cap = N if budget is None else budget
+    groups, cur, tot = [], [], 0
+    for c, cnt in enumerate(info["counts"]):
+        if tot + cnt > cap:
+            groups.append(cur)
+            cur, tot = [], 0
+        cur.append(c)
+        tot += int(cnt)
+    groups.append(cur)
+    for grp in groups:
+        g, n = dcg.dcg_gather_active(ctx, np.asarray(grp, np.int32))
         grad = torch.sin(3.0 * dcg.active_tensor(g, n, F)).contiguous()
         dcg.dcg_adam_step(ctx, g, dcg.gaussians(grad, 1), n, np.full(F, 1e-3, np.float32), step=1)
         dcg.dcg_scatter_back(ctx, g, n)
@@ -108,6 +120,54 @@ def test_loop_closure_matches_reference(scenario):
         assert n == N and float(rgb.abs().sum()) > 0
     finally:
         dcg.dcg_destroy(ctx)
+
+
+def _zoomed(c, f=3.0):
+    """A 320 x 240 view from pose c with f times its field-of-view scale (sees 22-28 of the 64 chunks)."""
+    s = f * 320.0 / c.W
+    return synth.Camera(c.fx * s, c.fy * s, 160.0, 120.0, 320, 240, c.Tcw, c.znear, c.zfar)
+
+
+def test_keyframe_by_keyframe_when_the_union_exceeds_the_budget():
+    """Sec. III-F: when the affected keyframes' chunks do not fit together, the keyframes are
+    processed one at a time with the global transformation mask carried across the loads.  The
+    result is the batch result, bit for bit (a context whose budget holds the union), and the
+    reference's."""
+    kfs = [_zoomed(c) for c in synth.window_scene(0, n=1000, deg=1)["cams"][:3]]
+    corrs = [_corr("z", 2.0, (0.8, -0.4, 0.3)), _corr("x", 1.5, (-0.6, 0.5, 0.2)), _corr("z", -1.0, (0.3, 0.6, 0.0))]
+    big, sc, F = _setup()
+    small, _, _ = _setup(budget=30_000)
+    try:
+        before = _read_all(small, F)
+        assert all(np.array_equal(before[k], v) for k, v in _read_all(big, F).items())
+        info = dcg.dcg_chunk_info(small)
+        lists = [dcg.dcg_cull_chunks(small, [k]) for k in kfs]
+        own = [int(info["counts"][l].sum()) for l in lists]
+        union = int(info["counts"][np.unique(np.concatenate(lists))].sum())
+        assert max(own) <= 30_000 < union  # only the keyframe order fits
+        nt_b, nm_b = dcg.dcg_loop_closure(big, kfs, corrs)
+        nt_s, nm_s = dcg.dcg_loop_closure(small, kfs, corrs)
+        dcg.dcg_flush(big)
+        dcg.dcg_flush(small)
+        after_b, after_s = _read_all(big, F), _read_all(small, F)
+        assert (nt_s, nm_s) == (nt_b, nm_b) and nt_s > 1000 and nm_s > 100
+        assert sorted(after_s) == sorted(after_b)
+        assert all(np.array_equal(after_s[k], after_b[k]) for k in after_b)
+        want, wt, wm = lc.loop_closure(before, sc["chunk_size"], 60.0, kfs, corrs)
+        assert (nt_s, nm_s) == (wt, wm)
+        _same(after_s, want)
+        # the corrected map still gathers and renders within the budget
+        import torch
+
+        c = kfs[1]
+        g, n = dcg.dcg_gather_active(small, dcg.dcg_cull_chunks(small, [c]))
+        rgb, depth = torch.zeros(3 * c.W * c.H, device="cuda"), torch.zeros(c.W * c.H, device="cuda")
+        dcg.dcg_render_fwd(small, g, n, [c], rgb, depth)
+        dcg.dcg_sync(small)
+        assert 0 < n <= 30_000 and float(rgb.abs().sum()) > 0
+    finally:
+        dcg.dcg_destroy(big)
+        dcg.dcg_destroy(small)
 
 
 def test_identity_correction_changes_nothing_and_budget_error_leaves_the_table():

@@ -36,8 +36,12 @@ def ctx0():
     dcg.dcg_destroy(c)
 
 
+# blend kernels: block per tile (warp reductions or lane slots), warp per block,
+# half-warp per half block with Gaussians on the lanes in the backward (the
+# product launch) or with pixels on the lanes (one Gaussian per half per step)
 BWD_VARIANTS = {"warp": dict(flags=0, stage=128), "slots": dict(flags=1, stage=128),
-                "warp_per_block": dict(flags=0, stage=32), "half_warp": dict(flags=0, stage=16)}
+                "warp_per_block": dict(flags=0, stage=32), "half_warp": dict(flags=0, stage=16),
+                "half_warp_pixel_lanes": dict(flags=2, stage=16)}
 
 
 @pytest.fixture(scope="module", params=list(BWD_VARIANTS))

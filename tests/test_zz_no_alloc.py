@@ -65,3 +65,45 @@ def test_noalloc_cull_rejects_oversized_requests():
     with pytest.raises(dcg.DcgError) as e:
         dcg.dcg_cull_chunks_noalloc(coords[:4], 4.0, 10.0, [c] * 17, None, lst, n)
     assert e.value.status == 6
+
+
+def test_noalloc_cull_cameras_in_pinned_memory_may_be_reused_at_once():
+    """The cameras are taken at the call, also from page-locked memory: the
+    caller overwrites them right after the call, while the stream is still
+    held back by a sleeping kernel, and the cull still sees the originals."""
+    import ctypes
+
+    import torch
+
+    sc = synth.window_scene(0, n=64_000, deg=1)
+    ctx = make_ctx(deg=1, n_max=64_000, chunk=sc["chunk_size"], dfar=60.0, page=512)
+    try:
+        dcg.dcg_chunk_table_update(ctx, planar(sc["params"]), 64_000)
+        info = dcg.dcg_chunk_info(ctx)
+        C = len(info["keys"])
+        coords = torch.from_numpy(np.ascontiguousarray(info["coords"])).cuda()
+        cams = sc["cams"][:4]
+        V = len(cams)
+        mask_ref = torch.zeros(V * C, dtype=torch.uint8, device="cuda")
+        lst_ref = dcg.dcg_cull_chunks(ctx, cams, mask_ref)
+        nbytes = ctypes.sizeof(dcg.dcg_camera) * V
+        pinned = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        ctypes.memmove(pinned.data_ptr(), dcg.make_cameras(cams), nbytes)
+        away = [synth.Camera(c.fx, c.fy, c.cx, c.cy, c.W, c.H, synth.look_at([0, 0, 500.0], [0, 0, 600.0]), 0.2, 1.0)
+                for c in cams]
+        mask = torch.zeros(V * C, dtype=torch.uint8, device="cuda")
+        lst = torch.full((C,), -1, dtype=torch.int32, device="cuda")
+        n = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
+        torch.cuda._sleep(20_000_000)  # about 10 ms of GPU time ahead of the cull on this stream
+        st = dcg.lib().dcg_cull_chunks_noalloc(dcg.ptr(coords), C, float(sc["chunk_size"]), 60.0,
+                                               ctypes.cast(pinned.data_ptr(), ctypes.POINTER(dcg.dcg_camera)), V,
+                                               dcg.ptr(mask), dcg.ptr(lst), dcg.ptr(n), dcg.stream_ptr(stream))
+        assert st == dcg.DCG_OK
+        ctypes.memmove(pinned.data_ptr(), dcg.make_cameras(away), nbytes)  # the caller reuses its array
+        torch.cuda.synchronize()
+        assert torch.equal(mask, mask_ref)
+        k = int(n.item())
+        assert k == len(lst_ref) > 0 and np.array_equal(lst[:k].cpu().numpy(), lst_ref)
+    finally:
+        dcg.dcg_destroy(ctx)
