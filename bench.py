@@ -48,11 +48,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="batched timing only (no plain/e2e/CPU legs), for profilers")
     ap.add_argument("--workload", default="window", choices=["window", "corridor", "sampling", "loopclosure", "loss"])
-    ap.add_argument("--bwd", default="warp", choices=["warp", "slots"], help="backward gradient accumulation")
+    ap.add_argument("--bwd", default="warp", choices=["warp", "slots", "pixel"],
+                    help="backward blend: default, lane slots, or (half-warp launch) pixels on the lanes")
     ap.add_argument("--length", type=float, default=5000.0, help="corridor: metres of road (1 m per frame)")
     ap.add_argument("--per-m", type=int, default=8000, help="corridor: Gaussians per metre (40M per 5 km)")
     ap.add_argument("--propose-every", type=int, default=4, help="corridor: frames between prefetch proposals")
     ap.add_argument("--cpu-pixels", type=int, default=48, help="oracle sample: pixels per sampled view")
+    ap.add_argument("--no-side-workloads", action="store_true",
+                    help="window only: skip the indoor-room and 1 km corridor legs of the default run")
     return ap.parse_args()
 
 
@@ -143,7 +146,7 @@ def run_ours(args, rank, world):
     npix = sum(c.W * c.H for c in cams)
     cfg = dcg.config(sh_degree=deg, max_active=n_all + 1024, max_views=8, max_pixels=npix, max_instances=160 << 20,
                      chunk_size=sc["chunk_size"], device_budget=6_000_000, host_capacity=n_all + 1024, dfar=60.0,
-                     flags=1 if args.bwd == "slots" else 0)
+                     flags={"warp": 0, "slots": 1, "pixel": 2}[args.bwd])
     ctx = dcg.dcg_create(cfg)
     stream = torch.cuda.current_stream()
     g_t = torch.from_numpy(np.ascontiguousarray(P.T)).cuda()
@@ -312,11 +315,22 @@ def run_ours(args, rank, world):
             ms_e = timed_e2e(K, 2)
     clocks = clk.summary()
     dcg.dcg_sync(ctx)
+    # per-phase device times of the plain path (outside the timed legs): the plain
+    # path gathers and writes back per view, so the render phases alone say how
+    # much of the batched/plain ratio comes from batching the render itself
+    prof_p = None
+    if not args.quick:
+        _, _, prof_p = timed(step_plain, K_p, 1, profile=True)
 
     mpix_b = npix * K * world / (ms_b / 1e3) / 1e6
     mpix_p = npix * K_p * world / (ms_p / 1e3) / 1e6 if ms_p else None
     mpix_e = npix * K * world / (ms_e / 1e3) / 1e6 if ms_e else None
     phases = {k: round(v[0] / K, 4) for k, v in prof.items() if k not in ("log_sample", "loop_closure")}
+    render_phases = ("preprocess_fwd", "binning", "blend_fwd", "blend_bwd", "preprocess_bwd")
+    plain_phases = ({k: round(v[0] / K_p, 4) for k, v in prof_p.items() if k not in ("log_sample", "loop_closure")}
+                    if prof_p else None)
+    render_b = sum(phases[k] for k in render_phases)
+    render_p = sum(plain_phases[k] for k in render_phases) if plain_phases else None
     n_act = n_all
     roof = roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, f"{tile[0]}x{tile[1]}/{stage}",
                     n_views=len(cams))
@@ -332,7 +346,11 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "batched_direct_calls_ms_per_step": round(sum(v[0] for v in prof.values()) / K, 4),
         "plain": {"value": round(mpix_p, 2), "unit": UNIT, "ms_per_step": round(ms_p / K_p, 4),
-                  "speedup_batched_over_plain": round(mpix_b / mpix_p, 3)} if ms_p else None,
+                  "speedup_batched_over_plain": round(mpix_b / mpix_p, 3),
+                  "phases_ms_per_step": plain_phases,
+                  "render_only": {"phases": list(render_phases), "batched_ms": round(render_b, 4),
+                                  "plain_ms": round(render_p, 4),
+                                  "speedup_batched_over_plain": round(render_p / render_b, 3)}} if ms_p else None,
         "phases_ms_per_step": phases,
         "counts": {"visible_pairs": n_vis, "instances": n_inst, "tiles": n_tiles, "blend_evaluations": n_eval,
                    "blended_pairs": n_blend},
@@ -348,7 +366,104 @@ def run_ours(args, rank, world):
                                       dpose, npix, K, W)
         out["log_sample"] = sampling_leg(sc, npix, trgb, rgb, depth, K, W)
         out["loop_closure"] = loop_closure_leg(sc, max(4, K // 4))
+        if not args.no_side_workloads:
+            out["indoor"] = indoor_leg(K, W)
+            out["corridor"] = corridor_bench(1000.0, 8000, args.propose_every, train_length=1000.0)
     return out
+
+
+def indoor_leg(K, W, cpu_pixels=24):
+    """The indoor-room workload: 640x480 views and 500k Gaussians on the walls,
+    floor and ceiling of a 10x8x3 m room (5 cm jitter, 4 m chunks, SH degree 3),
+    one keyframe per step along a smooth random-walk trajectory: cull, gather,
+    render fwd, L1 RGB + 0.1 L1 depth against the step's target, bwd, scatter.
+    Mpix/s of the step, its phases and the dominant kernel's roofline; the FP64
+    oracle times fwd + bwd on a pixel sample of one keyframe (all 500k
+    Gaussians projected) on the host cores."""
+    import torch
+
+    import oracle
+    from paper_2511_23030_b300 import dcg, synth
+
+    steps = K + W
+    sc = synth.room_indoor(0, n=500_000, n_steps=steps)
+    P, cams, deg = sc["params"], sc["cams"], sc["deg"]
+    n, F = P.shape
+    Wd, Hd = cams[0].W, cams[0].H
+    npx = Wd * Hd
+    cfg = dcg.config(sh_degree=deg, max_active=n, max_views=1, max_pixels=npx, max_instances=48 << 20,
+                     chunk_size=sc["chunk_size"], device_budget=n, host_capacity=n, dfar=20.0)
+    ctx = dcg.dcg_create(cfg)
+    try:
+        g_t = torch.from_numpy(np.ascontiguousarray(P.T)).cuda()
+        dcg.dcg_chunk_table_update(ctx, g_t, n)
+        del g_t
+        trgb = torch.from_numpy(np.stack([t.reshape(-1) for t in sc["target_rgb"]])).cuda()
+        tdep = torch.from_numpy(np.stack([t.reshape(-1) for t in sc["target_depth"]])).cuda()
+        rgb, depth = torch.zeros(3 * npx, device="cuda"), torch.zeros(npx, device="cuda")
+        dr, dd = torch.zeros_like(rgb), torch.zeros_like(depth)
+        loss = torch.zeros(1, device="cuda")
+        grads_t = torch.zeros((F, n), device="cuda")
+        grads = dcg.gaussians(grads_t, deg)
+        dpose = torch.zeros(6, device="cuda")
+        lam = sc["lambda_depth"]
+        act = []
+
+        def step(t):
+            c = cams[t]
+            g, na = dcg.dcg_gather_active(ctx, dcg.dcg_cull_chunks(ctx, [c]))
+            dcg.dcg_render_fwd(ctx, g, na, [c], rgb, depth)
+            loss.zero_()
+            dcg.dcg_loss_l1(ctx, rgb, depth, trgb[t], tdep[t], [c], lam, dr, dd, loss)
+            dcg.dcg_render_bwd(ctx, dr, dd, grads, dpose)
+            dcg.dcg_scatter_back(ctx, g, na)
+            act.append(na)
+
+        stream = torch.cuda.current_stream()
+        for t in range(W):
+            step(t)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        act.clear()
+        e0.record(stream)
+        for t in range(W, steps):
+            step(t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        n_act = int(np.mean(act))
+        # phases of the same steps (the library's event timers)
+        dcg.dcg_profile(ctx, True)
+        dcg.dcg_profile_read(ctx)
+        vis = inst = blend = 0
+        for t in range(W, steps):
+            step(t)
+            nv, ni, _ = dcg.dcg_state_stats(ctx)
+            _, nb = dcg.dcg_state_evals(ctx)
+            vis, inst, blend = vis + nv, inst + ni, blend + nb
+        prof = dcg.dcg_profile_read(ctx)
+        dcg.dcg_profile(ctx, False)
+        phases = {k: round(v[0] / K, 4) for k, v in prof.items() if k not in ("log_sample", "loop_closure")}
+        roof = roofline(phases, n_act, vis // K, inst // K, blend // K, npx, deg, F, None, "", n_views=1)
+    finally:
+        dcg.dcg_destroy(ctx)
+    # the oracle on a bounded sample of one keyframe
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    c = cams[W]
+    pix = synth.pixel_sample(np.random.default_rng(3), Wd, Hd, cpu_pixels)
+    t0 = time.perf_counter()
+    o = oracle.render(P, deg, c, pix=pix, n_threads=cores)
+    oracle.render_bwd(P, deg, c, np.sign(o["rgb"] - 0.5) / (3.0 * npx), lam * np.sign(o["depth"] - 3.0) / npx,
+                      pix=pix, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"what": "indoor room: one 640x480 keyframe per step (cull, gather, fwd, L1 + 0.1 L1 depth, bwd, "
+                    "scatter) over 500k Gaussians (SH3) in 4 m chunks",
+            "value": round(npx / (ms / 1e3) / 1e6, 2), "unit": UNIT, "ms_per_step": round(ms, 4), "steps": K,
+            "warmup": W, "active_gaussians_mean": n_act, "phases_ms_per_step": phases, "roofline": roof,
+            "cpu_baseline": {"value": round(len(pix) / dt / 1e6, 9), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{len(pix)} pixels of one keyframe, fwd+bwd, 500000 Gaussians projected",
+                             "seconds": round(dt, 2)}}
 
 
 LAMBDA_S = 0.2  # weight of the SSIM term of Eq. 3 in the training leg (the 3DGS value)
@@ -723,12 +838,18 @@ def run_reference(args, rank, world):
 
 
 def run_corridor(args):
+    return corridor_bench(args.length, args.per_m, args.propose_every, train_length=3000.0)
+
+
+def corridor_bench(length, per_m, propose_every, train_length=3000.0):
     """Out-of-core mapping along a driving corridor (1241x376 views, 8 m chunks,
     5 km and 40 M Gaussians by default, device budget 15 % of the map capped
     at 6 M Gaussians, pinned host tier), one keyframe per metre:
     cull, gather, render fwd, L1 loss, bwd, scatter, then a prefetch proposal:
     none, constant-velocity extrapolation, or the learned MLP (trained here on
-    a different drive with samples the mapper generates from its exact cull)."""
+    a different drive, `train_length` metres, with samples the mapper
+    generates from its exact cull).  Both predictors propose on a side stream
+    every `propose_every` frames."""
     import torch
 
     from paper_2511_23030_b300 import build, dcg, prefetch, synth
@@ -738,7 +859,7 @@ def run_corridor(args):
     W, H = 1241, 376
     t0 = time.perf_counter()
     # training drive (seed 1): chunk layout only, sparse Gaussians
-    xy, head = synth.corridor_path(1, 3000.0)
+    xy, head = synth.corridor_path(1, train_length)
     Ptr = synth.corridor_gaussians(np.random.default_rng(6), xy, head, 40, deg=0)
     cams_tr = synth.corridor_cameras(xy, head, W=W, H=H)
     for c in cams_tr:
@@ -756,8 +877,8 @@ def run_corridor(args):
     dcg.dcg_destroy(ctx)
     del X, y
     # evaluation drive (seed 0)
-    xy, head = synth.corridor_path(0, args.length)
-    P = synth.corridor_gaussians(np.random.default_rng(5), xy, head, args.per_m, deg=3)
+    xy, head = synth.corridor_path(0, length)
+    P = synth.corridor_gaussians(np.random.default_rng(5), xy, head, per_m, deg=3)
     cams = synth.corridor_cameras(xy, head, W=W, H=H)
     for c in cams:
         c.zfar = zfar
@@ -769,9 +890,9 @@ def run_corridor(args):
     del P
     t_gen = time.perf_counter() - t0
     out = {"workload": "corridor", "metric": "out-of-core mapping Mpix/s, stall and hidden chunk-load share",
-           "unit": UNIT, "config": {"length_m": args.length, "gaussians": N, "view": f"{W}x{H}", "chunk_m": s,
+           "unit": UNIT, "config": {"length_m": length, "gaussians": N, "view": f"{W}x{H}", "chunk_m": s,
                                     "budget_gaussians": budget, "frames": len(cams),
-                                    "propose_every": args.propose_every},
+                                    "propose_every": propose_every, "train_drive_m": train_length},
            "train": {"samples": n, "positive_frac": round(pos, 4), "loss_per_epoch": [round(v, 4) for v in losses],
                      "seconds": round(t_train, 2)}, "setup_seconds": round(t_gen, 1), "modes": {}}
     for mode in ("none", "cv", "mlp"):
@@ -798,7 +919,7 @@ def run_corridor(args):
             dcg.dcg_render_bwd(ctx, dr, dd, grads, None)
 
         out["config"]["chunks"] = dcg.dcg_chunk_count(ctx)
-        r = prefetch.run_corridor(ctx, cams, mode, s, 1.5 * zfar, pm=pm, render=render, every=args.propose_every)
+        r = prefetch.run_corridor(ctx, cams, mode, s, 1.5 * zfar, pm=pm, render=render, every=propose_every)
         dcg.dcg_sync(ctx)
         r["ms_per_step"] = round(r["ms"] / r["steps"], 4)
         r["value"] = round(W * H * r["steps"] / (r["ms"] / 1e3) / 1e6, 2)

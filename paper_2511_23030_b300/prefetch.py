@@ -193,6 +193,42 @@ def constant_velocity_cams(cams, t, ahead=(5, 10, 15, 20)):
     return out
 
 
+class _PendingList:
+    def __init__(self, ev, buf, n_h):
+        self.ev, self.buf, self.n_h = ev, buf, n_h
+
+    def result(self):
+        self.ev.synchronize()
+        return self.buf[: int(self.n_h[0])].numpy().copy()
+
+
+class ConstantVelocity:
+    """The non-learned predictor: the exact cull of the poses extrapolated from
+    the last step's motion, run like the MLP on a side stream while the frame
+    renders (one asynchronous cull of all extrapolated poses; the list comes
+    back through pinned memory and is waited for after the frame)."""
+
+    def __init__(self, ctx):
+        import torch
+
+        C = max(dcg.dcg_chunk_count(ctx), 1)
+        self.list = torch.zeros(C, dtype=torch.int32, device="cuda")
+        self.n = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.list_h = torch.zeros(C, dtype=torch.int32).pin_memory()
+        self.n_h = torch.zeros(1, dtype=torch.int32).pin_memory()
+
+    def propose_async(self, ctx, cams, t, stream):
+        import torch
+
+        with torch.cuda.stream(stream):
+            dcg.dcg_cull_chunks_async(ctx, constant_velocity_cams(cams, t), self.list, self.n, stream=stream)
+            self.list_h.copy_(self.list, non_blocking=True)
+            self.n_h.copy_(self.n, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return _PendingList(ev, self.list_h, self.n_h)
+
+
 def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = None, threshold=0.3, render=None,
                  warm=1, every=1):
     """Map along `cams` one keyframe per step: cull, gather (synchronous loads
@@ -211,6 +247,8 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
     dcg.dcg_profile(ctx, True)
     dcg.dcg_profile_read(ctx)
     side = torch.cuda.Stream()
+    cvp = ConstantVelocity(ctx) if mode == "cv" else None
+    resident_trace = []  # Gaussians on the device after each step's gather
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for t, cam in enumerate(cams):
@@ -218,6 +256,7 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
             torch.cuda.synchronize()
             dcg.dcg_profile_read(ctx)
             hits = misses = wasted = hit_g = miss_g = 0
+            resident_trace = []
             e0.record()
         lst = dcg.dcg_cull_chunks(ctx, [cam])
         res = dcg.dcg_chunk_info(ctx)["resident"].astype(bool)
@@ -231,20 +270,18 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
                 hit_g += int(counts[c])
                 pending.discard(int(c))
         g, n = dcg.dcg_gather_active(ctx, lst)
+        resident_trace.append(dcg.dcg_tier_stats(ctx)["resident"])
         # proposals for the coming frames are computed on a side stream while
-        # this frame renders (they depend only on poses and residency)
+        # this frame renders (they depend only on poses and residency); both
+        # predictors wait for that stream only after the frame is enqueued
         prop = []
-        pending_scores = None
+        pending_scores = pending_cv = None
         propose = t % every == 0
         if mode == "mlp" and propose:
             cand = dcg.dcg_chunks_near(ctx, cam_centre(cam), radius, only_nonresident=True)
             pending_scores = pm.score_async(pose_history(cams, t), cand, chunk_size, side)
         elif mode == "cv" and propose:
-            fut = set()
-            for fc in constant_velocity_cams(cams, t):
-                fut.update(int(c) for c in dcg.dcg_cull_chunks(ctx, [fc], stream=side))
-            res = dcg.dcg_chunk_info(ctx)["resident"].astype(bool)
-            prop = sorted(c for c in fut if not res[c])
+            pending_cv = cvp.propose_async(ctx, cams, t, side)
         if render is not None:
             render(g, n, cam)
         dcg.dcg_scatter_back(ctx, g, n)
@@ -252,6 +289,10 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
             p = pending_scores.result()
             order = np.argsort(-p, kind="stable")
             prop = [int(cand[i]) for i in order if p[i] > threshold]
+        elif pending_cv is not None:
+            fut = pending_cv.result()
+            res = dcg.dcg_chunk_info(ctx)["resident"].astype(bool)
+            prop = [int(c) for c in fut if not res[c]]
         if prop:
             before = dcg.dcg_chunk_info(ctx)["resident"].astype(bool)
             dcg.dcg_prefetch(ctx, prop)
@@ -267,6 +308,9 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
     prof = dcg.dcg_profile_read(ctx)
     dcg.dcg_profile(ctx, False)
     wasted += len(pending)
+    tr = np.asarray(resident_trace, np.int64)
     return {"mode": mode, "steps": len(cams) - warm, "ms": e0.elapsed_time(e1), "stall_ms": prof["stall"][0],
             "hits": hits, "misses": misses, "wasted_prefetches": wasted,
-            "hidden_load_frac": hit_g / max(hit_g + miss_g, 1), "tier": dcg.dcg_tier_stats(ctx)}
+            "hidden_load_frac": hit_g / max(hit_g + miss_g, 1), "tier": dcg.dcg_tier_stats(ctx),
+            "resident_max": int(tr.max()) if tr.size else 0,
+            "resident_trace": [int(v) for v in tr[:: max(1, len(tr) // 40)]]}

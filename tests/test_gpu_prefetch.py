@@ -64,7 +64,8 @@ def test_prefetch_hides_loads_and_never_changes_images():
             try:
                 results[mode] = prefetch.run_corridor(ctx, cams, mode, 8.0, 1.5 * ZFAR, pm=pm, render=render)
                 images[mode] = shots
-                assert dcg.dcg_tier_stats(ctx)["resident"] <= budget
+                # the device never holds more than the budget, at any step of the drive
+                assert results[mode]["resident_max"] <= budget and dcg.dcg_tier_stats(ctx)["resident"] <= budget
             finally:
                 dcg.dcg_destroy(ctx)
         for mode in ("cv", "mlp"):
@@ -75,6 +76,12 @@ def test_prefetch_hides_loads_and_never_changes_images():
         assert results["none"]["hits"] == 0 and results["none"]["misses"] > 20, summary
         assert results["mlp"]["hidden_load_frac"] >= 0.8, summary
         assert results["mlp"]["stall_ms"] < 0.5 * results["none"]["stall_ms"], summary
+        # the learned predictor against the constant-velocity one, both proposing on the side stream
+        # with the same period: both hide most loads; which hides more is reported, not assumed
+        assert results["cv"]["hidden_load_frac"] >= 0.8, summary
+        print("mlp vs cv: hits %d vs %d, misses %d vs %d, stall %.3f vs %.3f ms" % (
+            results["mlp"]["hits"], results["cv"]["hits"], results["mlp"]["misses"], results["cv"]["misses"],
+            results["mlp"]["stall_ms"], results["cv"]["stall_ms"]))
     finally:
         pm.close()
         if ctx_tr is not None:
