@@ -48,6 +48,7 @@ struct dcg_render_state {
   DevCam* h_cams = nullptr;
   cudaEvent_t ev_cams = nullptr;
   float4* rec = nullptr;
+  float4* bin = nullptr;  // binning record per pair: 32 B (centre, conic, tile rectangle)
   float* depth = nullptr;
   uint32_t* touched = nullptr;
   short4* rect = nullptr;
@@ -372,6 +373,7 @@ dcg_status state_alloc(dcg_ctx* ctx, dcg_render_state* st) {
   CK(dmalloc(&st->depth, (size_t)st->cap_pairs));
   CK(dmalloc(&st->touched, (size_t)st->cap_pairs));
   CK(dmalloc(&st->rect, (size_t)st->cap_pairs));
+  CK(dmalloc(&st->bin, 2 * (size_t)st->cap_pairs));
   CK(dmalloc(&st->grad2d, 3 * (size_t)st->cap_pairs));
   // the 2D gradient slots are zero between backward passes: the blends add
   // into them and the preprocess backward zeroes each slot it consumes
@@ -394,6 +396,7 @@ void state_free(dcg_render_state* st) {
   if (st->h_cams) cudaFreeHost(st->h_cams);
   if (st->ev_cams) cudaEventDestroy(st->ev_cams);
   cudaFree(st->rec); cudaFree(st->depth); cudaFree(st->touched); cudaFree(st->rect); cudaFree(st->grad2d);
+  cudaFree(st->bin);
   cudaFree(st->list_a); cudaFree(st->list_b); cudaFree(st->inst_a); cudaFree(st->inst_b);
   cudaFree(st->ranges); cudaFree(st->T_final); cudaFree(st->n_contrib); cudaFree(st->counters);
   cudaFree(st->part); cudaFree(st->hist);
@@ -693,6 +696,7 @@ dcg_status dcg_sync(dcg_ctx* ctx, void* stream) {
     if (w & ERRW_KEY_RANGE_BIT) return fail(ctx, DCG_ERR_KEY_RANGE, "chunk coordinate outside [-2^20, 2^20-1]");
     if (w & ERRW_CAPACITY_BIT) return fail(ctx, DCG_ERR_CAPACITY, "instance capacity exceeded");
     if (w & ERRW_TIMEOUT_BIT) return fail(ctx, DCG_ERR_TIMEOUT, "bounded device wait gave up");
+    if (w & ERRW_BOUNDS_BIT) return fail(ctx, DCG_ERR_BOUNDS, "index outside its buffer (access skipped)");
   }
   return DCG_OK;
 }
@@ -829,7 +833,9 @@ dcg_status dcg_cull_chunks(dcg_ctx* ctx, const dcg_camera* cams, int32_t n_views
   // The cull reads only the chunk table (uploaded synchronously), so without a
   // mask to order against the caller's stream it runs on the context's own
   // stream and the host waits for that alone, not for the caller's queued work.
-  cudaStream_t s = mask_out ? (cudaStream_t)stream : ctx->cull_stream;
+  // With the phase timers on it stays on the caller's stream, so that its
+  // interval times the cull and not its wait for SMs busy with queued work.
+  cudaStream_t s = (mask_out || ctx->prof_on) ? (cudaStream_t)stream : ctx->cull_stream;
   const int C = (int)ctx->chunks.size();
   std::memcpy(ctx->h_cullcams, cams, sizeof(dcg_camera) * n_views);
   CK(cudaMemcpyAsync(ctx->d_cullcams, ctx->h_cullcams, sizeof(dcg_camera) * n_views, cudaMemcpyHostToDevice, s));
@@ -2103,6 +2109,7 @@ static void fill_args(dcg_render_state* st, RasterArgs& a) {
   a.depth = st->depth;
   a.touched = st->touched;
   a.rect = st->rect;
+  a.bin = st->bin;
   a.grad2d = st->grad2d;
   a.list_a = st->list_a;
   a.list_b = st->list_b;

@@ -33,6 +33,22 @@ struct ProfHook {
 constexpr unsigned ERRW_KEY_RANGE_BIT = 1u;
 constexpr unsigned ERRW_CAPACITY_BIT = 2u;
 constexpr unsigned ERRW_TIMEOUT_BIT = 4u;  // reserved: no kernel waits on another block or a flag
+constexpr unsigned ERRW_BOUNDS_BIT = 8u;   // an index outside its buffer (bounds-check build)
+
+// Bounds-check build (compiled with -DDCG_CHECKS=1): dcg_oob(i, n, ew) is true
+// when index i is outside a buffer of n elements; it then sets
+// ERRW_BOUNDS_BIT in the device error word and the caller skips the access
+// (nothing traps); dcg_sync reports DCG_ERR_BOUNDS.  In the normal build it
+// is constant false and the guarded branches compile away.
+#if defined(DCG_CHECKS) && DCG_CHECKS
+__device__ __forceinline__ bool dcg_oob(unsigned long long i, unsigned long long n, unsigned* ew) {
+  if (i < n) return false;
+  atomicOr(ew, ERRW_BOUNDS_BIT);
+  return true;
+}
+#else
+__device__ __forceinline__ bool dcg_oob(unsigned long long, unsigned long long, unsigned*) { return false; }
+#endif
 
 // ---------------------------------------------------------------- chunk.cu
 void launch_chunk_keys(const float* means, long long row, long long col, long long n, float s, u64* keys,
@@ -165,6 +181,7 @@ struct RasterArgs {
   float* depth;
   uint32_t* touched;
   short4* rect;
+  float4* bin;         // per pair, 2 float4: (u, v, A', B'), (C', rect x0|y0 << 16, rect x1|y1 << 16, 0)
   float4* grad2d;
   // lists
   u64* list_a;

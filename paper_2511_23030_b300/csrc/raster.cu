@@ -362,6 +362,7 @@ __global__ void __launch_bounds__(256, 4) k_preprocess_fwd(RasterArgs a) {
     const float S12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
     const float S22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
     const float opac = 1.f / (1.f + __expf(-g[10 * S + i]));
+    if (dcg_oob((u64)a.V * (u64)n, (u64)a.cap_pairs + 1ull, a.errword)) return;
     for (int v = 0; v < a.V; ++v) {
       const long long vi = (long long)v * n + i;
       const DevCam& c = a.cams[v];
@@ -415,8 +416,16 @@ __global__ void __launch_bounds__(256, 4) k_preprocess_fwd(RasterArgs a) {
       const float A = cc * idet, B = -cb * idet, Cn = ca * idet;
       const float4 r0 = make_float4(ud.hi, vd.hi, ud.lo, vd.lo);
       const float4 cn = make_float4(-0.5f * kLog2e * A, -kLog2e * B, -0.5f * kLog2e * Cn, opac);
-      // tiles of the rectangle that the support ellipse reaches
-      a.touched[vi] = tight_count(r0, cn, rc, a.tile_w, a.tile_h);
+      // tiles of the rectangle that the support ellipse reaches, from the
+      // binning record the emission reads back (the centre's leading parts
+      // only: the support margin of 1e-3 px covers the rest, < 1e-4 px)
+      const float4 b0 = make_float4(ud.hi, vd.hi, cn.x, cn.y);
+      const float4 b1 = make_float4(cn.z, __int_as_float((tx0 & 0xffff) | (ty0 << 16)),
+                                    __int_as_float((tx1 & 0xffff) | (ty1 << 16)), 0.f);
+      a.bin[2 * vi + 0] = b0;
+      a.bin[2 * vi + 1] = b1;
+      a.touched[vi] = tight_count(make_float4(b0.x, b0.y, 0.f, 0.f), make_float4(b0.z, b0.w, b1.x, 0.f), rc,
+                                  a.tile_w, a.tile_h);
       // colour: SH of the direction from the camera centre
       float dx = mx - c.C[0], dy = my - c.C[1], dz = mz - c.C[2];
       const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
@@ -499,20 +508,26 @@ struct InstCount {
 // half blocks the ellipse reaches (band extents once per tile row).
 struct InstEmit {
   const u64* list;
-  const short4* rect;
-  const float4* rec;
+  const float4* bin;
   const DevCam* cams;
   long long n;
   DepthKey dk;
   int tw, th;
   u64* inst;
   u64 cap;
+  u64 cap_pairs;     // bounds-check build: pair and tile indices against their buffers
+  unsigned n_tiles;
+  unsigned* errword;
   __device__ void operator()(u64 s, u64 off, u64) const {
     const u64 key = list[s];
     const u64 vi = dk.pair(key, n);
     const int v = dk.view(key);
-    const short4 r = rect[vi];
-    const float4 r0 = rec[3 * vi + 0], cn = rec[3 * vi + 1];
+    if (dcg_oob(vi, cap_pairs, errword)) return;
+    // one 32-byte binning record: centre (leading parts), conic, tile rectangle
+    const float4 b0 = bin[2 * vi + 0], b1 = bin[2 * vi + 1];
+    const int p0 = __float_as_int(b1.y), p1 = __float_as_int(b1.z);
+    const short4 r = make_short4((short)(p0 & 0xffff), (short)(p0 >> 16), (short)(p1 & 0xffff), (short)(p1 >> 16));
+    const float4 r0 = make_float4(b0.x, b0.y, 0.f, 0.f), cn = make_float4(b0.z, b0.w, b1.x, 0.f);
     const bool whole = (r.z - r.x + 1) * (r.w - r.y + 1) > kTightMax;
     const SupportEllipse e = support_of(cn);
     const u64 base = (u64)cams[v].tile_base;
@@ -528,6 +543,7 @@ struct InstEmit {
       for (int j = j0; j <= j1; ++j, ++o) {
         const float ul = df_sub_round(r0.x, r0.z, (float)((r.x + j) * tw));
         const u64 m = tile_block_mask(bands, bl, br, ul, wpr, nbr);
+        if (dcg_oob(row + (u64)j, n_tiles, errword)) continue;
         if (o < cap) inst[o] = (m << kMaskShift) | ((row + (u64)j) << kTileShift) | vi;
       }
     }
@@ -553,10 +569,12 @@ __global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
 }
 
 // Per-tile ranges [start, end) of the sorted instances.
-__global__ void k_ranges(const u64* __restrict__ inst, const u64* n_ptr, uint2* __restrict__ ranges) {
+__global__ void k_ranges(const u64* __restrict__ inst, const u64* n_ptr, uint2* __restrict__ ranges, unsigned n_tiles,
+                         unsigned* errword) {
   const u64 K = *n_ptr;
   for (u64 k = blockIdx.x * (u64)blockDim.x + threadIdx.x; k < K; k += (u64)gridDim.x * blockDim.x) {
     const unsigned t = (unsigned)(inst[k] >> kTileShift) & kTileMask;
+    if (dcg_oob(t, n_tiles, errword)) continue;
     if (k == 0 || ((unsigned)(inst[k - 1] >> kTileShift) & kTileMask) != t) ranges[t].x = (unsigned)k;
     if (k + 1 == K || ((unsigned)(inst[k + 1] >> kTileShift) & kTileMask) != t) ranges[t].y = (unsigned)(k + 1);
   }
@@ -1056,7 +1074,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd_q(RasterArgs a, const u64* __
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const int py = y0 + ly + 4 * k;
-      if (px < W && py < H) {
+      if (px < W && py < H && !dcg_oob((u64)(c.pix_off + (long long)py * W + px), (u64)a.n_pix, a.errword)) {
         const long long pix = (long long)py * W + px;
         rgb[3 * c.pix_off + pix] = Cr[k];
         rgb[3 * c.pix_off + P + pix] = Cg[k];
@@ -1281,7 +1299,8 @@ __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __
       last[k] = 0;
       alive |= T[k] > 0.f;
     }
-    const uint2 rg = a.ranges[gt];
+    uint2 rg = a.ranges[gt];
+    if (dcg_oob(rg.y, (u64)a.cap_inst + 1ull, a.errword)) rg.y = rg.x;
     // software pipeline over the batches: keys two batches ahead, records
     // of the instances that reach this warp block one batch ahead
     u64 key2 = rg.x + 32 + lane < rg.y ? inst[rg.x + 32 + lane] : 0ull;
@@ -1291,6 +1310,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __
       const u64 k0 = inst[rg.x + lane];
       vin = pair_of_inst(k0);
       hbn = half_bits(k0, wb);
+      if (hbn && dcg_oob(vin, (u64)a.cap_pairs, a.errword)) hbn = 0u;
       if (hbn) {
         r0n = a.rec[3ull * vin + 0];
         cnn = a.rec[3ull * vin + 1];
@@ -1308,6 +1328,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __
         key2 = idx + 64 < rg.y ? inst[idx + 64] : 0ull;
         hbn = idx + 32 < rg.y ? half_bits(k1, wb) : 0u;
         vin = pair_of_inst(k1);
+        if (hbn && dcg_oob(vin, (u64)a.cap_pairs, a.errword)) hbn = 0u;
         if (hbn) {
           r0n = a.rec[3ull * vin + 0];
           cnn = a.rec[3ull * vin + 1];
@@ -1405,7 +1426,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const int py = y0 + ly + 4 * k;
-      if (px < W && py < H) {
+      if (px < W && py < H && !dcg_oob((u64)(c.pix_off + (long long)py * W + px), (u64)a.n_pix, a.errword)) {
         const long long pix = (long long)py * W + px;
         rgb[3 * c.pix_off + pix] = Cr[k];
         rgb[3 * c.pix_off + P + pix] = Cg[k];
@@ -1674,7 +1695,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_g(RasterArgs a, const u64* __
       float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
       float Tf = 0.f;
       unsigned last = 0;
-      if (px < W && py < H) {
+      if (px < W && py < H && !dcg_oob((u64)(c.pix_off + (long long)py * W + px), (u64)a.n_pix, a.errword)) {
         const long long pix = (long long)py * W + px;
         Tf = a.T_final[c.pix_off + pix];
         last = a.n_contrib[c.pix_off + pix];
@@ -1687,6 +1708,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_g(RasterArgs a, const u64* __
     }
     int hi = (int)__reduce_max_sync(0xffffffffu, mylast);  // instances [0, hi) are still to scan
     const uint2 rg = a.ranges[gt];
+    if (dcg_oob((u64)rg.x + (u64)hi, (u64)a.cap_inst + 1ull, a.errword)) hi = 0;
     int hd = 0, pc = 0;  // ring head and count
     __syncwarp();
     for (;;) {
@@ -1698,6 +1720,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_g(RasterArgs a, const u64* __
           const u64 key = inst[rg.x + rel];
           vi = pair_of_inst(key);
           take = (half_bits(key, (int)wb) >> h) & 1u;
+          if (take && dcg_oob(vi, (u64)a.cap_pairs, a.errword)) take = false;
         }
         const unsigned m = __ballot_sync(0xffffffffu, take);
         if (take) {
@@ -2058,9 +2081,10 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
     float dSig[6] = {0, 0, 0, 0, 0, 0};  // dS + dS^T accumulated over views: entries 00 01 02 11 12 22
     // the views this Gaussian reaches, all loads in flight together
     unsigned tmask = 0;
+    const bool in_cap = !dcg_oob((u64)a.V * (u64)n, (u64)a.cap_pairs + 1ull, a.errword);
 #pragma unroll
     for (int v = 0; v < kMaxViewsApi; ++v)
-      if (live && v < a.V && a.touched[(long long)v * n + i] != 0u) tmask |= 1u << v;
+      if (live && in_cap && v < a.V && a.touched[(long long)v * n + i] != 0u) tmask |= 1u << v;
     // the 2D gradients of the next reached view are loaded one view ahead
     float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, n2 = n0;
     if (tmask) {
@@ -2458,13 +2482,14 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
                  &a.counters->n_inst, st);
   k_emit_at<<<a.num_sms * 8, 256, 0, st>>>(
       &a.counters->n_vis, offs,
-      InstEmit{ls, a.rect, a.rec, a.cams, a.n, dk, a.tile_w, a.tile_h, a.inst_a, (u64)a.cap_inst});
+      InstEmit{ls, a.bin, a.cams, a.n, dk, a.tile_w, a.tile_h, a.inst_a, (u64)a.cap_inst, (u64)a.cap_pairs,
+               (unsigned)a.n_tiles, a.errword});
   k_clamp_inst<<<1, 1, 0, st>>>(a.counters, (u64)a.cap_inst, a.errword);
   int tb = 1;
   while ((1ll << tb) < (long long)a.n_tiles) ++tb;
   u64* is = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, kTileShift, kTileShift + tb, a.hist, a.P, st);
   cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)max(a.n_tiles, 1), st);
-  k_ranges<<<a.num_sms * 8, 256, 0, st>>>(is, &a.counters->n_inst_c, a.ranges);
+  k_ranges<<<a.num_sms * 8, 256, 0, st>>>(is, &a.counters->n_inst_c, a.ranges, (unsigned)a.n_tiles, a.errword);
   count_launch(7 + 3 * ((lbits + 7) / 8) + 3 * ((tb + 7) / 8) + 2);
   a.prof(PH_BINNING, false, st);
   a.prof(PH_BLEND_FWD, true, st);
