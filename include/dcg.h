@@ -47,7 +47,10 @@ typedef enum {
                             kernels' work queues are counters that never block), so none is
                             returned today */
   DCG_ERR_FAULT = 8,     /* a chunk load failed verification, or an injected host-side fault */
-  DCG_ERR_STATE = 9      /* call order violated (e.g. backward without a forward) */
+  DCG_ERR_STATE = 9,     /* call order violated (e.g. backward without a forward) */
+  DCG_ERR_BOUNDS = 10    /* bounds-check build only (libdcg_checks.so): a kernel met an index outside
+                            its buffer, skipped the access and recorded it; reported by the next
+                            dcg_sync */
 } dcg_status;
 
 typedef struct dcg_ctx dcg_ctx;

@@ -13,11 +13,13 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdcg.so")
+# DCG_LIB=checks selects the bounds-check build of the same library (libdcg_checks.so)
+LIB_PATH = os.path.join(_HERE, "libdcg_checks.so" if os.environ.get("DCG_LIB") == "checks" else "libdcg.so")
 
 DCG_OK = 0
 STATUS = {0: "DCG_OK", 1: "DCG_ERR_ARG", 2: "DCG_ERR_OOM", 3: "DCG_ERR_CUDA", 4: "DCG_ERR_BUDGET",
-          5: "DCG_ERR_KEY_RANGE", 6: "DCG_ERR_CAPACITY", 7: "DCG_ERR_TIMEOUT", 8: "DCG_ERR_FAULT", 9: "DCG_ERR_STATE"}
+          5: "DCG_ERR_KEY_RANGE", 6: "DCG_ERR_CAPACITY", 7: "DCG_ERR_TIMEOUT", 8: "DCG_ERR_FAULT", 9: "DCG_ERR_STATE",
+          10: "DCG_ERR_BOUNDS"}
 
 
 class DcgError(RuntimeError):

@@ -78,3 +78,18 @@ def test_fault_specification_parses_on_the_host(libpath):
         with pytest.raises(dcg.DcgError) as e:
             dcg.dcg_fault_parse(bad)
         assert e.value.status == 1
+
+
+def test_bounds_check_build_exports_the_same_symbols(libpath):
+    """libdcg_checks.so (-DDCG_CHECKS=1) is the same library with index checks in its kernels."""
+    from paper_2511_23030_b300 import build
+
+    checks = build.build(checks=True)
+    assert checks.endswith("libdcg_checks.so")
+
+    def exported(p):
+        out = subprocess.check_output(["nm", "-D", "--defined-only", p]).decode()
+        return {l.split()[-1] for l in out.splitlines() if " T " in l and l.split()[-1].startswith("dcg_")}
+
+    assert exported(checks) == exported(libpath)
+    assert not [n for n in declared_functions() if n not in exported(checks)]
