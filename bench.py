@@ -144,8 +144,10 @@ def run_ours(args, rank, world):
     n_all = P.shape[0]
     F = P.shape[1]
     npix = sum(c.W * c.H for c in cams)
-    cfg = dcg.config(sh_degree=deg, max_active=n_all + 1024, max_views=8, max_pixels=npix, max_instances=160 << 20,
-                     chunk_size=sc["chunk_size"], device_budget=6_000_000, host_capacity=n_all + 1024, dfar=60.0,
+    # capacities sized to the scene (the window makes about 10 instances per Gaussian)
+    cfg = dcg.config(sh_degree=deg, max_active=n_all + 1024, max_views=8, max_pixels=npix,
+                     max_instances=max(32 << 20, 24 * n_all), chunk_size=sc["chunk_size"],
+                     device_budget=n_all + 1024, host_capacity=n_all + 1024, dfar=60.0,
                      flags={"warp": 0, "slots": 1, "pixel": 2}[args.bwd])
     ctx = dcg.dcg_create(cfg)
     stream = torch.cuda.current_stream()
