@@ -370,6 +370,7 @@ def run_ours(args, rank, world):
         out["loop_closure"] = loop_closure_leg(sc, max(4, K // 4))
         if not args.no_side_workloads:
             out["indoor"] = indoor_leg(K, W)
+            out["mlp"] = mlp_leg()
             out["corridor"] = corridor_bench(1000.0, 8000, args.propose_every, train_length=1000.0)
     return out
 
@@ -466,6 +467,60 @@ def indoor_leg(K, W, cpu_pixels=24):
             "cpu_baseline": {"value": round(len(pix) / dt / 1e6, 9), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{len(pix)} pixels of one keyframe, fwd+bwd, 500000 Gaussians projected",
                              "seconds": round(dt, 2)}}
+
+
+def mlp_leg(reps=50):
+    """The prefetch MLP's GEMMs on the two tensor-core paths (tcgen05 with TMA-staged operands, and
+    mma.sync): forward of a 4096-candidate batch and one training step of a 2048-sample batch,
+    timed with CUDA events over `reps` calls each.  FLOPs per forward: 2 x (128 x 256 + 2 x 256 x
+    256) per row (the three hidden layers); a training step adds the two backward products per
+    layer (about 3 x the forward)."""
+    import torch
+
+    from paper_2511_23030_b300 import dcg, synth
+
+    rng = np.random.default_rng(3)
+    x = torch.from_numpy(rng.normal(0, 1, (4096, 128)).astype(np.float32)).cuda().to(torch.bfloat16).view(torch.int16)
+    y = torch.from_numpy((rng.uniform(size=4096) < 0.4).astype(np.float32)).cuda()
+    prob = torch.zeros(4096, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    flop_row = 2 * (128 * 256 + 2 * 256 * 256)
+    _, _, _ = peaks()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = float(json.load(f)["bf16_tflops"])
+            src = "measured"
+    except Exception:
+        bf16_peak, src = 1800.0, "fallback"
+    out = {"what": "prefetch MLP 128-256-256-256-1, BF16 products, FP32 accumulation", "peak_bf16_tflops": bf16_peak,
+           "peak_source": src}
+    stream = torch.cuda.current_stream()
+    for gemm in ("tcgen05", "mma_sync"):
+        m = dcg.dcg_mlp_create(4096)
+        try:
+            dcg.dcg_mlp_set_gemm(m, gemm)
+            dcg.dcg_mlp_set_params(m, synth.mlp_init_params(0))
+            res = {}
+            for name, fn, rows, mult in (("forward_4096", lambda: dcg.dcg_mlp_forward(m, x, 4096, prob), 4096, 1),
+                                         ("train_step_2048",
+                                          lambda: dcg.dcg_mlp_train_step(m, x[:2048], y[:2048], 2048, 1e-4, loss),
+                                          2048, 3)):
+                for _ in range(5):
+                    fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                us = e0.elapsed_time(e1) * 1e3 / reps
+                tf = mult * flop_row * rows / (us * 1e-6) / 1e12
+                res[name] = {"us": round(us, 2), "tflops": round(tf, 2), "frac": round(tf / bf16_peak, 4)}
+            dcg.dcg_mlp_get_params(m)  # raises if a bounded wait of the tensor-core path gave up
+            out[gemm] = res
+        finally:
+            dcg.dcg_mlp_destroy(m)
+    return out
 
 
 LAMBDA_S = 0.2  # weight of the SSIM term of Eq. 3 in the training leg (the 3DGS value)

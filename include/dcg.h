@@ -42,10 +42,9 @@ typedef enum {
   DCG_ERR_BUDGET = 4,    /* the visible chunks alone exceed the device Gaussian budget */
   DCG_ERR_KEY_RANGE = 5, /* a chunk coordinate lies outside [-2^20, 2^20-1] (Eq. 6) */
   DCG_ERR_CAPACITY = 6,  /* a configured capacity (instances, pixels, chunks, host tier) was exceeded */
-  DCG_ERR_TIMEOUT = 7,   /* reserved for a bounded device-side wait that gives up; no kernel of
-                            this library waits on another block or on a flag (the persistent
-                            kernels' work queues are counters that never block), so none is
-                            returned today */
+  DCG_ERR_TIMEOUT = 7,   /* a bounded device-side wait gave up: the MLP's tcgen05 GEMM waits on
+                            its own mbarriers (TMA arrivals, MMA completion) for at most about two
+                            seconds each; no render kernel waits on another block or on a flag */
   DCG_ERR_FAULT = 8,     /* a chunk load failed verification, or an injected host-side fault */
   DCG_ERR_STATE = 9,     /* call order violated (e.g. backward without a forward) */
   DCG_ERR_BOUNDS = 10    /* bounds-check build only (libdcg_checks.so): a kernel met an index outside
@@ -501,13 +500,20 @@ dcg_status dcg_state_read(dcg_render_state* st, uint32_t* ranges, uint32_t* ids,
  * Network: 128 inputs (99 used) -> 256 -> 256 -> 256 -> 1, GELU (erf form)
  * after each hidden layer, sigmoid output, binary cross-entropy (mean over
  * the batch) and Adam (beta 0.9 / 0.999, eps 1e-8).  Matrix products in BF16
- * on the tensor cores with FP32 accumulation; FP32 master parameters.
+ * on the tensor cores with FP32 accumulation; FP32 master parameters.  On
+ * sm_100 and later the products use tcgen05.mma into tensor memory with
+ * operands staged by TMA; dcg_mlp_set_gemm selects the mma.sync kernels
+ * instead (same products, FP32 sums in another order).  The tcgen05 kernel
+ * bounds its waits; if one gives up, the next dcg_mlp_get_params returns
+ * DCG_ERR_TIMEOUT (and the affected outputs are not written).
  * Parameters, flat FP32 (dcg_mlp_num_params() = 164865 values):
  *   W1[128][256] b1[256] W2[256][256] b2[256] W3[256][256] b3[256] w4[256] b4
  * (W[i][j]: input i -> output j).  Inputs x are BF16 rows of 128 (dev);
  * batch sizes B are multiples of 64 up to max_batch. */
 typedef struct dcg_mlp dcg_mlp;
+enum { DCG_MLP_GEMM_TCGEN05 = 0, DCG_MLP_GEMM_MMA_SYNC = 1 };
 dcg_status dcg_mlp_create(int32_t max_batch, dcg_mlp** out);
+dcg_status dcg_mlp_set_gemm(dcg_mlp* m, int32_t kind);
 dcg_status dcg_mlp_destroy(dcg_mlp* m);
 int32_t dcg_mlp_num_params(void);
 dcg_status dcg_mlp_set_params(dcg_mlp* m, const float* host_params); /* also resets Adam */

@@ -1,10 +1,14 @@
 // Learned chunk-prefetch proposal: a small MLP 128 (99 used) -> 256 -> 256 ->
 // 256 -> 1 with GELU (erf form) and a sigmoid output, trained with binary
 // cross-entropy and Adam.  GEMMs run on the tensor cores in BF16 with FP32
-// accumulation (mma.sync m16n8k16); weights are kept in FP32 (master copy)
-// and converted to BF16 for every step.  Nothing here changes what is
+// accumulation: by default with tcgen05.mma into tensor memory, operands
+// staged by TMA (k_gemm_tc), or with mma.sync m16n8k16 (k_gemm_bf16, the
+// pre-Blackwell path, kept selectable); weights are kept in FP32 (master
+// copy) and converted to BF16 for every step.  Nothing here changes what is
 // rendered: the exact frustum cull decides the active set, the MLP only
 // proposes chunks whose copy can start early.
+#include <cuda.h>
+
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -134,6 +138,298 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
 static void gemm(const GemmArgs& g, cudaStream_t s) {
   dim3 grid(g.N / BN, g.M / BM);
   k_gemm_bf16<<<grid, 128, 0, s>>>(g);
+  count_launch();
+}
+
+// ----------------------------------------------------------------------------
+// The same GEMMs on Blackwell's tensor cores: C[M,N] = A[M,K] B[N,K]^T with
+// both operands K-major (row-major with K contiguous), BF16, FP32
+// accumulation in tensor memory.  One CTA of 8 warps computes a 128 x 64 tile
+// of C: K is walked in steps of 64 through a 4-stage ring of shared memory
+// that TMA fills (128-byte swizzle, one mbarrier per stage counting the bytes
+// that arrive); one thread of warp 1 issues tcgen05.mma (M 128, N 64, K 16;
+// four per stage) into a 64-column TMEM accumulator and commits each stage
+// back to the TMA thread (warp 0) when its MMAs have read it; after the last
+// stage every warp reads 32 TMEM lanes (rows of C) x 32 columns with
+// tcgen05.ld (warps w and w + 4 share the lanes of w's quarter, one column
+// half each) and runs the same epilogues as the mma.sync kernel, with 16-byte
+// stores.  Every mbarrier wait is bounded in time: on expiry the kernel sets
+// the MLP's error word, stops issuing, waits (bounded) for the copies it
+// started, frees its TMEM and returns.
+namespace tc {
+
+constexpr int BM = 128, BN = 64, BK = 64, STAGES = 4, THREADS = 256;
+constexpr int A_BYTES = BM * BK * 2;            // 16 KB
+constexpr int B_BYTES = BN * BK * 2;            // 8 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // 24 KB, a multiple of the 1024-byte swizzle atom
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;  // + alignment slack + barriers
+constexpr long long kWaitCycles = 4000000000ll;  // about 2 s at the maximum SM clock
+
+// instruction descriptor of tcgen05.mma kind::f16: D F32 (bits 4-5 = 1), A and
+// B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
+// 17, M >> 4 at bit 24
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// wait for the phase of parity `parity` to complete, at most kWaitCycles
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* err) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) {
+      atomicOr(err, 1u);
+      return false;
+    }
+  }
+  return true;
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1 (bit 46),
+// swizzle mode 2 (bits 61-63); the start address advances by 32 bytes per
+// K step of 16 inside a swizzle row
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+struct Epilogue {
+  int M, N;            // rows of C (valid), columns of C (row pitch)
+  int epi;
+  float* C;            // EPI_F32
+  int accumulate;
+  const float* bias;   // EPI_BIAS_GELU
+  float* Z;
+  uint16_t* H;
+  const float* Zin;    // EPI_DGELU
+  unsigned* err;       // bounded waits that gave up
+};
+
+__global__ void __launch_bounds__(THREADS) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
+                                                     const __grid_constant__ CUtensorMap tb, int K, Epilogue e) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);  // full[4], empty[4], done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int KT = K / BK;
+  const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES), done = su32(bars + 2 * STAGES);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * s));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * s));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done));
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&ta) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tb) : "memory");
+  }
+  if (warp == 0) {  // the accumulator: BN columns of 128 lanes x 32 bits
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  int issued = 0;  // stages the TMA thread filled
+  if (warp == 0 && lane == 0) {
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % STAGES;
+      if (kt >= STAGES && !mbar_wait(empty0 + 8 * s, (uint32_t)((kt / STAGES - 1) & 1), e.err)) *abort_flag = 1;
+      if (*abort_flag) break;
+      const uint32_t sa = su32(smem + s * STAGE_BYTES), sb = sa + A_BYTES, fb = full0 + 8 * s;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES) : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(sa),
+          "l"(&ta), "r"(kt * BK), "r"(m0), "r"(fb)
+          : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(sb),
+          "l"(&tb), "r"(kt * BK), "r"(n0), "r"(fb)
+          : "memory");
+      issued = kt + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % STAGES;
+      if (!mbar_wait(full0 + 8 * s, (uint32_t)((kt / STAGES) & 1), e.err)) *abort_flag = 1;
+      if (*abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = su32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t da = sdesc(sa + 32 * kk), db = sdesc(sb + 32 * kk);
+        const uint32_t acc = (kt | kk) != 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(kIdesc), "r"(acc)
+            : "memory");
+      }
+      // the stage is free again once these MMAs have read it
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done) : "memory");
+  }
+  __syncwarp();
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile),
+  // columns 32 (w / 4) .. + 31 (warp-uniform: tcgen05.ld is .sync.aligned)
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0u, e.err) && !*abort_flag);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int q = warp & 3, c = 32 * (warp >> 2);
+    const int m = m0 + 32 * q + lane;
+    uint32_t v[32];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (m < e.M) {
+      const int nb = n0 + c;                       // first of this thread's 32 columns
+      const long long o = (long long)m * e.N + nb;  // 32-element aligned: 16-byte vector accesses
+      if (e.epi == EPI_F32) {
+        float4* dst = reinterpret_cast<float4*>(e.C + o);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float4 a = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]), __uint_as_float(v[4 * j + 2]),
+                                 __uint_as_float(v[4 * j + 3]));
+          if (e.accumulate) {
+            const float4 b = dst[j];
+            a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+          }
+          dst[j] = a;
+        }
+      } else {
+        uint32_t hb[16];
+        if (e.epi == EPI_BIAS_GELU) {
+          float4* zd = reinterpret_cast<float4*>(e.Z + o);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float z[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) z[t] = __uint_as_float(v[4 * j + t]) + e.bias[nb + 4 * j + t];
+            zd[j] = make_float4(z[0], z[1], z[2], z[3]);
+            hb[2 * j] = (uint32_t)f2bf(gelu(z[0])) | ((uint32_t)f2bf(gelu(z[1])) << 16);
+            hb[2 * j + 1] = (uint32_t)f2bf(gelu(z[2])) | ((uint32_t)f2bf(gelu(z[3])) << 16);
+          }
+        } else {
+          const float4* zi = reinterpret_cast<const float4*>(e.Zin + o);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 zz = zi[j];
+            const float g0 = __uint_as_float(v[4 * j]) * gelu_grad(zz.x), g1 = __uint_as_float(v[4 * j + 1]) * gelu_grad(zz.y);
+            const float g2 = __uint_as_float(v[4 * j + 2]) * gelu_grad(zz.z), g3 = __uint_as_float(v[4 * j + 3]) * gelu_grad(zz.w);
+            hb[2 * j] = (uint32_t)f2bf(g0) | ((uint32_t)f2bf(g1) << 16);
+            hb[2 * j + 1] = (uint32_t)f2bf(g2) | ((uint32_t)f2bf(g3) << 16);
+          }
+        }
+        uint4* hd = reinterpret_cast<uint4*>(e.H + o);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hd[j] = make_uint4(hb[4 * j], hb[4 * j + 1], hb[4 * j + 2], hb[4 * j + 3]);
+      }
+    }
+  }
+  // copies this CTA started and nobody consumed (only after a wait gave up)
+  if (warp == 0 && lane == 0)
+    for (int kt = issued > STAGES ? issued - STAGES : 0; kt < issued; ++kt)
+      mbar_wait(full0 + 8 * (kt % STAGES), (uint32_t)((kt / STAGES) & 1), e.err);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+}  // namespace tc
+
+// host side of the tensor-core path: 2D tensor maps over K-major BF16
+// matrices (rows x K, row pitch `pitch` elements), boxes of 64 x box_rows
+// with the 128-byte swizzle the MMA descriptors expect; the encoder comes
+// from the driver through the runtime (no link-time driver dependency)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+static bool kmajor_map(CUtensorMap* m, const uint16_t* base, long long rows, long long K, long long pitch,
+                       int box_rows) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15u) || (pitch * 2) % 16 || K % tc::BK) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(pitch * 2)};
+  const cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// C[M,N] = A[M,K] B[N,K]^T on tcgen05, A and B K-major with row pitches lda, ldb
+static cudaError_t gemm_tc(const uint16_t* A, long long lda, const uint16_t* B, long long ldb, int M, int N, int K,
+                           const tc::Epilogue& e, cudaStream_t s) {
+  CUtensorMap ma, mb;
+  if (N % tc::BN || !kmajor_map(&ma, A, M, K, lda, tc::BM) || !kmajor_map(&mb, B, N, K, ldb, tc::BN))
+    return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t r = cudaFuncSetAttribute(tc::k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    if (r != cudaSuccess) return r;
+    attr = true;
+  }
+  dim3 grid((M + tc::BM - 1) / tc::BM, N / tc::BN);
+  tc::k_gemm_tc<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, K, e);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// dst[c * ld_dst + r] = src[r * ld_src + c] for r < R, c < C (BF16), 32 x 32 tiles
+__global__ void k_transpose_bf16(const uint16_t* __restrict__ src, int R, int C, int ld_src, uint16_t* __restrict__ dst,
+                                 int ld_dst) {
+  __shared__ uint16_t t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int r = r0 + y, c = c0 + threadIdx.x;
+    t[y][threadIdx.x] = (r < R && c < C) ? src[(long long)r * ld_src + c] : (uint16_t)0;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int c = c0 + y, r = r0 + threadIdx.x;
+    if (r < R && c < C) dst[(long long)c * ld_dst + r] = t[threadIdx.x][y];
+  }
+}
+
+static void transpose_bf16(const uint16_t* src, int R, int C, int ld_src, uint16_t* dst, int ld_dst, cudaStream_t s) {
+  dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+  k_transpose_bf16<<<grid, block, 0, s>>>(src, R, C, ld_src, dst, ld_dst);
   count_launch();
 }
 
@@ -286,6 +582,13 @@ struct dcg_mlp {
   uint16_t *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *dZ = nullptr, *dZ2 = nullptr;
   float* logit = nullptr;
   long long t = 0;
+  // tensor-core path: K-major operands (transposed weights W^T [256][K],
+  // transposed layer input and dZ [256][batch] for the weight gradients)
+  int gemm = DCG_MLP_GEMM_TCGEN05;
+  uint16_t* WT = nullptr;  // W1^T [256][128], W2^T [256][256], W3^T [256][256]
+  uint16_t *Ta = nullptr, *Tb = nullptr;
+  unsigned* err = nullptr;  // a bounded wait of k_gemm_tc gave up
+  cudaError_t launch_err = cudaSuccess;  // first failure to set up or launch a tensor-core GEMM
 };
 
 namespace {
@@ -295,11 +598,50 @@ cudaError_t mal(T** p, size_t n) {
   return cudaMalloc((void**)p, sizeof(T) * (n > 0 ? n : 1));
 }
 
+constexpr int kOffWT1 = 0, kOffWT2 = kHid * kIn, kOffWT3 = kOffWT2 + kHid * kHid, kNWT = kOffWT3 + kHid * kHid;
+
+void tc_run(dcg_mlp* m, cudaError_t r) {
+  if (r != cudaSuccess && m->launch_err == cudaSuccess) m->launch_err = r;
+}
+
+tc::Epilogue tc_epi(dcg_mlp* m, int M, const GemmArgs& g) {
+  tc::Epilogue e{};
+  e.M = M;
+  e.N = g.N;
+  e.epi = g.epi;
+  e.C = g.C;
+  e.accumulate = g.accumulate;
+  e.bias = g.bias;
+  e.Z = g.Z;
+  e.H = g.H;
+  e.Zin = g.Zin;
+  e.err = m->err;
+  return e;
+}
+
 // forward through the three hidden layers; returns logits in m->logit
 void mlp_forward(dcg_mlp* m, const uint16_t* x, int B, float* prob, cudaStream_t s) {
   k_to_bf16<<<64, 256, 0, s>>>(m->P, m->Pb, kNParams);
   count_launch();
   const uint16_t* Pb = m->Pb;
+  if (m->gemm == DCG_MLP_GEMM_TCGEN05) {
+    // W^T (K-major B operands) of the three hidden layers
+    transpose_bf16(Pb + kOffW1, kIn, kHid, kHid, m->WT + kOffWT1, kIn, s);
+    transpose_bf16(Pb + kOffW2, kHid, kHid, kHid, m->WT + kOffWT2, kHid, s);
+    transpose_bf16(Pb + kOffW3, kHid, kHid, kHid, m->WT + kOffWT3, kHid, s);
+    GemmArgs g{};
+    g.epi = EPI_BIAS_GELU;
+    g.N = kHid;
+    g.bias = m->P + kOffB1; g.Z = m->Z1; g.H = m->H1;
+    tc_run(m, gemm_tc(x, kIn, m->WT + kOffWT1, kIn, B, kHid, kIn, tc_epi(m, B, g), s));
+    g.bias = m->P + kOffB2; g.Z = m->Z2; g.H = m->H2;
+    tc_run(m, gemm_tc(m->H1, kHid, m->WT + kOffWT2, kHid, B, kHid, kHid, tc_epi(m, B, g), s));
+    g.bias = m->P + kOffB3; g.Z = m->Z3; g.H = m->H3;
+    tc_run(m, gemm_tc(m->H2, kHid, m->WT + kOffWT3, kHid, B, kHid, kHid, tc_epi(m, B, g), s));
+    k_head_fwd<<<(B * 32 + 255) / 256, 256, 0, s>>>(m->H3, m->P, B, m->logit, prob);
+    count_launch();
+    return;
+  }
   GemmArgs g{};
   g.epi = EPI_BIAS_GELU;
   g.M = B;
@@ -334,6 +676,7 @@ void mlp_backward(dcg_mlp* m, const uint16_t* x, const float* y, int B, float* l
   } layers[3] = {{x, kIn, kOffW1, kOffB1, nullptr}, {m->H1, kHid, kOffW2, kOffB2, m->Z1}, {m->H2, kHid, kOffW3, kOffB3, m->Z2}};
   uint16_t* dcur = m->dZ;   // dZ of the current layer [B, 256]
   uint16_t* dnext = m->dZ2;
+  const bool tcg = m->gemm == DCG_MLP_GEMM_TCGEN05;
   for (int l = 2; l >= 0; --l) {
     const L& ly = layers[l];
     // dW[K,256] = in^T dZ : M' = K, N' = 256, K' = B
@@ -343,7 +686,13 @@ void mlp_backward(dcg_mlp* m, const uint16_t* x, const float* y, int B, float* l
     gw.A = ly.in; gw.a_m = 1; gw.a_k = ly.K;
     gw.B = dcur; gw.b_n = 1; gw.b_k = kHid;
     gw.C = m->G + ly.offW;
-    gemm(gw, s);
+    if (tcg) {  // both operands K-major along the batch: in^T [K][B], dZ^T [256][B]
+      transpose_bf16(ly.in, B, ly.K, ly.K, m->Ta, B, s);
+      transpose_bf16(dcur, B, kHid, kHid, m->Tb, B, s);
+      tc_run(m, gemm_tc(m->Ta, B, m->Tb, B, ly.K, kHid, B, tc_epi(m, ly.K, gw), s));
+    } else {
+      gemm(gw, s);
+    }
     k_colsum<<<(kHid + 127) / 128, 128, 0, s>>>(dcur, B, kHid, m->G + ly.offB);
     count_launch();
     if (l > 0) {
@@ -355,7 +704,10 @@ void mlp_backward(dcg_mlp* m, const uint16_t* x, const float* y, int B, float* l
       gx.B = Pb + ly.offW; gx.b_n = kHid; gx.b_k = 1;
       gx.Zin = ly.Zprev;
       gx.H = dnext;
-      gemm(gx, s);
+      if (tcg)  // W [K_in][256] is already K-major along the output index
+        tc_run(m, gemm_tc(dcur, kHid, Pb + ly.offW, kHid, B, kHid, kHid, tc_epi(m, B, gx), s));
+      else
+        gemm(gx, s);
       uint16_t* t = dcur;
       dcur = dnext;
       dnext = t;
@@ -377,7 +729,8 @@ dcg_status dcg_mlp_create(int32_t max_batch, dcg_mlp** out) {
             mal(&m->Pb, kNParams) == cudaSuccess && mal(&m->Z1, BH) == cudaSuccess && mal(&m->Z2, BH) == cudaSuccess &&
             mal(&m->Z3, BH) == cudaSuccess && mal(&m->H1, BH) == cudaSuccess && mal(&m->H2, BH) == cudaSuccess &&
             mal(&m->H3, BH) == cudaSuccess && mal(&m->dZ, BH) == cudaSuccess && mal(&m->dZ2, BH) == cudaSuccess &&
-            mal(&m->logit, (size_t)max_batch) == cudaSuccess;
+            mal(&m->logit, (size_t)max_batch) == cudaSuccess && mal(&m->WT, (size_t)kNWT) == cudaSuccess &&
+            mal(&m->Ta, BH) == cudaSuccess && mal(&m->Tb, BH) == cudaSuccess && mal(&m->err, 1) == cudaSuccess;
   if (!ok) {
     dcg_mlp_destroy(m);
     return DCG_ERR_OOM;
@@ -385,7 +738,18 @@ dcg_status dcg_mlp_create(int32_t max_batch, dcg_mlp** out) {
   cudaMemset(m->P, 0, sizeof(float) * kNParams);
   cudaMemset(m->m1, 0, sizeof(float) * kNParams);
   cudaMemset(m->m2, 0, sizeof(float) * kNParams);
+  cudaMemset(m->err, 0, sizeof(unsigned));
+  int dev = 0, major = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  m->gemm = major >= 10 ? DCG_MLP_GEMM_TCGEN05 : DCG_MLP_GEMM_MMA_SYNC;
   *out = m;
+  return DCG_OK;
+}
+
+dcg_status dcg_mlp_set_gemm(dcg_mlp* m, int32_t kind) {
+  if (!m || (kind != DCG_MLP_GEMM_TCGEN05 && kind != DCG_MLP_GEMM_MMA_SYNC)) return DCG_ERR_ARG;
+  m->gemm = kind;
   return DCG_OK;
 }
 
@@ -394,6 +758,7 @@ dcg_status dcg_mlp_destroy(dcg_mlp* m) {
   cudaFree(m->P); cudaFree(m->G); cudaFree(m->m1); cudaFree(m->m2); cudaFree(m->Pb);
   cudaFree(m->Z1); cudaFree(m->Z2); cudaFree(m->Z3); cudaFree(m->H1); cudaFree(m->H2); cudaFree(m->H3);
   cudaFree(m->dZ); cudaFree(m->dZ2); cudaFree(m->logit);
+  cudaFree(m->WT); cudaFree(m->Ta); cudaFree(m->Tb); cudaFree(m->err);
   delete m;
   return DCG_OK;
 }
@@ -411,13 +776,28 @@ dcg_status dcg_mlp_set_params(dcg_mlp* m, const float* host_params) {
 
 dcg_status dcg_mlp_get_params(dcg_mlp* m, float* host_params) {
   if (!m || !host_params) return DCG_ERR_ARG;
-  return cudaMemcpy(host_params, m->P, sizeof(float) * kNParams, cudaMemcpyDeviceToHost) == cudaSuccess ? DCG_OK
-                                                                                                           : DCG_ERR_CUDA;
+  if (cudaMemcpy(host_params, m->P, sizeof(float) * kNParams, cudaMemcpyDeviceToHost) != cudaSuccess) return DCG_ERR_CUDA;
+  unsigned err = 0;
+  if (cudaMemcpy(&err, m->err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return DCG_ERR_CUDA;
+  if (err) {  // reported once
+    cudaMemset(m->err, 0, sizeof(unsigned));
+    return DCG_ERR_TIMEOUT;
+  }
+  return DCG_OK;
+}
+
+// the first tensor-core GEMM that could not be set up or launched since the last call
+static dcg_status take_launch_err(dcg_mlp* m) {
+  const cudaError_t r = m->launch_err;
+  m->launch_err = cudaSuccess;
+  return r == cudaSuccess ? DCG_OK : (r == cudaErrorInvalidValue ? DCG_ERR_ARG : DCG_ERR_CUDA);
 }
 
 dcg_status dcg_mlp_forward(dcg_mlp* m, const uint16_t* x, int32_t B, float* prob, void* stream) {
   if (!m || !x || !prob || B <= 0 || B > m->max_batch || B % 64) return DCG_ERR_ARG;
   mlp_forward(m, x, B, prob, (cudaStream_t)stream);
+  const dcg_status ls = take_launch_err(m);
+  if (ls != DCG_OK) return ls;
   return cudaGetLastError() == cudaSuccess ? DCG_OK : DCG_ERR_CUDA;
 }
 
@@ -428,6 +808,8 @@ dcg_status dcg_mlp_grads(dcg_mlp* m, const uint16_t* x, const float* y, int32_t 
   mlp_forward(m, x, B, nullptr, s);
   mlp_backward(m, x, y, B, loss, s);
   if (grads) cudaMemcpyAsync(grads, m->G, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s);
+  const dcg_status ls = take_launch_err(m);
+  if (ls != DCG_OK) return ls;
   return cudaGetLastError() == cudaSuccess ? DCG_OK : DCG_ERR_CUDA;
 }
 

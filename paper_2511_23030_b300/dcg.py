@@ -126,6 +126,7 @@ _SIGS = {
     "dcg_cull_chunks_noalloc": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(dcg_camera),
                                                _I32, _P, _P, _P, _P]),
     "dcg_inject_fault": (ctypes.c_int, [_P, _I32, _I32]),
+    "dcg_mlp_set_gemm": (ctypes.c_int, [_P, _I32]),
     "dcg_cull_chunks_async": (ctypes.c_int, [_P, ctypes.POINTER(dcg_camera), _I32, _P, _P, _P, _P]),
     "dcg_fault_parse": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
 }
@@ -599,3 +600,13 @@ def dcg_cull_chunks_async(ctx, cams, list_out, n_out, mask_out=None, stream=None
     arr = make_cameras(cams)
     check(ctx, lib().dcg_cull_chunks_async(ctx, arr, len(cams), ptr(mask_out), ptr(list_out), ptr(n_out),
                                            stream_ptr(stream)))
+
+
+MLP_GEMM = {"tcgen05": 0, "mma_sync": 1}
+
+
+def dcg_mlp_set_gemm(m, kind: str):
+    """Select the MLP's GEMM kernels: "tcgen05" (TMA + tcgen05.mma, the default on sm_100+) or "mma_sync"."""
+    st = lib().dcg_mlp_set_gemm(m, MLP_GEMM[kind])
+    if st != DCG_OK:
+        raise DcgError(st, "dcg_mlp_set_gemm failed")
