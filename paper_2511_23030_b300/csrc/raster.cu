@@ -2461,6 +2461,16 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   }
   a.prof(PH_PRE_FWD, false, st);
   a.prof(PH_BINNING, true, st);
+  // Partitions of the scans and sorts: about one 2048-key scatter chunk each,
+  // from the host's bound on the item count (visible pairs <= V n; instances
+  // taken as <= 4 V n, a bound for speed only: any count is sorted correctly),
+  // at most the 8 per SM the scratch is sized for.  Small views then run a
+  // few hundred partitions instead of 1184 nearly empty ones.
+  auto parts = [&](long long bound) {
+    return (int)std::max(1ll, std::min<long long>((bound + 2047) / 2048, (long long)a.P));
+  };
+  const int Pp = parts(pairs);
+  const int Pi = parts(std::min<long long>(a.cap_inst, 4 * pairs));
   // compaction into depth keys
   DepthKey dk;
   dk.ib = a.idx_bits;
@@ -2469,16 +2479,16 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   dk.cs = 31 + dk.ib + dk.vb;
   const int cbits = 64 - dk.cs;
   dk.cmax = cbits >= 4 ? (1u << (cbits < 20 ? cbits : 20)) - 1u : 0u;
-  part_scan_emit(nullptr, (u64)pairs, VisCount{a.touched}, VisEmit{a.depth, a.touched, a.list_a, a.n, dk}, a.part, a.P,
+  part_scan_emit(nullptr, (u64)pairs, VisCount{a.touched}, VisEmit{a.depth, a.touched, a.list_a, a.n, dk}, a.part, Pp,
                  &a.counters->n_vis, st);
   // Only the 31 depth bits are sorted: the view bits above them ride along,
   // since the stable tile sort below separates the views anyway.
   const int lbits = 31;
-  u64* ls = radix_sort(a.list_a, a.list_b, &a.counters->n_vis, a.idx_bits, a.idx_bits + lbits, a.hist, a.P, st);
+  u64* ls = radix_sort(a.list_a, a.list_b, &a.counters->n_vis, a.idx_bits, a.idx_bits + lbits, a.hist, Pp, st);
   // instance offsets by an ordered scan (the free list buffer holds them),
   // then the emission itself, one thread per visible pair with no barriers
   u64* offs = ls == a.list_a ? a.list_b : a.list_a;
-  part_scan_emit(&a.counters->n_vis, 0, InstCount{ls, a.touched, a.n, dk}, InstOffset{offs}, a.part, a.P,
+  part_scan_emit(&a.counters->n_vis, 0, InstCount{ls, a.touched, a.n, dk}, InstOffset{offs}, a.part, Pp,
                  &a.counters->n_inst, st);
   k_emit_at<<<a.num_sms * 8, 256, 0, st>>>(
       &a.counters->n_vis, offs,
@@ -2487,7 +2497,7 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   k_clamp_inst<<<1, 1, 0, st>>>(a.counters, (u64)a.cap_inst, a.errword);
   int tb = 1;
   while ((1ll << tb) < (long long)a.n_tiles) ++tb;
-  u64* is = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, kTileShift, kTileShift + tb, a.hist, a.P, st);
+  u64* is = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, kTileShift, kTileShift + tb, a.hist, Pi, st);
   cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)max(a.n_tiles, 1), st);
   k_ranges<<<a.num_sms * 8, 256, 0, st>>>(is, &a.counters->n_inst_c, a.ranges, (unsigned)a.n_tiles, a.errword);
   count_launch(7 + 3 * ((lbits + 7) / 8) + 3 * ((tb + 7) / 8) + 2);
