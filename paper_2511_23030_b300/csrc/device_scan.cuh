@@ -134,7 +134,7 @@ __global__ void k_part_emit(const u64* n_ptr, u64 n_host, CountF f, EmitF e, con
 
 // ----------------------------------------------------------------------------
 // LSD radix sort passes over u64 keys on digits [shift, shift+nbits),
-// nbits <= 8 (kernels in sort_scan.cu).  hist layout: [256][P] digit-major
+// nbits <= 8 (kernels in radix.cuh).  hist layout: [256][P] digit-major
 // (per-block counts, then per-digit exclusive prefixes over blocks),
 // followed by the 256 digit totals.
 

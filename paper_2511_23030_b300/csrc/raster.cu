@@ -30,7 +30,7 @@
 #include <algorithm>
 #include <cstdio>
 
-#include "device_scan.cuh"
+#include "radix.cuh"
 #include "kernels.cuh"
 
 namespace dcg {
@@ -455,10 +455,6 @@ __global__ void __launch_bounds__(256, 4) k_preprocess_fwd(RasterArgs a) {
 // ============================================================================
 // 2-6. binning
 // ============================================================================
-struct VisCount {
-  const uint32_t* touched;
-  __device__ u64 operator()(u64 k) const { return touched[k] ? 1ull : 0ull; }
-};
 // Depth keys: [count | view | depth bits | index].  The bits above the view
 // carry min(tiles touched, cmax) when the key has room (cmax > 0), so that
 // the instance-offset scan reads the key alone; cmax itself means "look the
@@ -475,17 +471,23 @@ struct DepthKey {
   }
   __device__ int view(u64 key) const { return (int)((key >> (31 + ib)) & ((1ull << vb) - 1ull)); }
 };
-struct VisEmit {
-  const float* depth;
+// Key source of the depth sort's first pass: pair k = v n + i (every pair
+// of the views, in order) yields the depth key of a visible pair (one that
+// touches a tile); the pass keeps the visible pairs in pair order, so the
+// compaction and the first digit's scatter are one pass.
+struct PairKeySrc {
+  const float* depth;  // written for every pair by the preprocess
   const uint32_t* touched;
-  u64* list;
-  long long n;
+  unsigned n;          // pair indices fit in 28 bits
   DepthKey dk;
-  __device__ void operator()(u64 k, u64 off, u64) const {
-    const u64 v = k / (u64)n, i = k - v * (u64)n;
-    u64 key = (v << (31 + dk.ib)) | ((u64)__float_as_uint(depth[k]) << dk.ib) | i;
-    if (dk.cmax) key |= (u64)min(touched[k], dk.cmax) << dk.cs;
-    list[off] = key;
+  __device__ __forceinline__ bool operator()(u64 k, u64* key) const {
+    const uint32_t t = touched[k];
+    const float z = depth[k];
+    const unsigned kk = (unsigned)k, v = kk / n, i = kk - v * n;
+    u64 x = ((u64)v << (31 + dk.ib)) | ((u64)__float_as_uint(z) << dk.ib) | (u64)i;
+    if (dk.cmax) x |= (u64)min(t, dk.cmax) << dk.cs;
+    *key = x;
+    return t != 0u;
   }
 };
 struct InstCount {
@@ -1257,7 +1259,7 @@ __device__ __forceinline__ int ring_steps(int pL, int pR, bool more, int R) {
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(256) k_blend_fwd_h(RasterArgs a, const u64* __restrict__ inst,
+__global__ void __launch_bounds__(256, TW * TH == 256 ? 4 : 0) k_blend_fwd_h(RasterArgs a, const u64* __restrict__ inst,
                                                      float* __restrict__ rgb, float* __restrict__ dout) {
   using L = TileLayout<TW, TH>;
   constexpr int PPT = L::PPT;
@@ -2479,12 +2481,14 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   dk.cs = 31 + dk.ib + dk.vb;
   const int cbits = 64 - dk.cs;
   dk.cmax = cbits >= 4 ? (1u << (cbits < 20 ? cbits : 20)) - 1u : 0u;
-  part_scan_emit(nullptr, (u64)pairs, VisCount{a.touched}, VisEmit{a.depth, a.touched, a.list_a, a.n, dk}, a.part, Pp,
-                 &a.counters->n_vis, st);
   // Only the 31 depth bits are sorted: the view bits above them ride along,
-  // since the stable tile sort below separates the views anyway.
+  // since the stable tile sort below separates the views anyway.  The first
+  // pass reads the pairs themselves and keeps the visible ones (the
+  // compaction), counting them into n_vis; the other passes sort the list.
   const int lbits = 31;
-  u64* ls = radix_sort(a.list_a, a.list_b, &a.counters->n_vis, a.idx_bits, a.idx_bits + lbits, a.hist, Pp, st);
+  radix_pass(PairKeySrc{a.depth, a.touched, (unsigned)a.n, dk}, nullptr, (u64)pairs, a.list_b, a.idx_bits, 8, a.hist,
+             Pp, &a.counters->n_vis, st);
+  u64* ls = radix_sort(a.list_b, a.list_a, &a.counters->n_vis, a.idx_bits + 8, a.idx_bits + lbits, a.hist, Pp, st);
   // instance offsets by an ordered scan (the free list buffer holds them),
   // then the emission itself, one thread per visible pair with no barriers
   u64* offs = ls == a.list_a ? a.list_b : a.list_a;
@@ -2500,7 +2504,7 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   u64* is = radix_sort(a.inst_a, a.inst_b, &a.counters->n_inst_c, kTileShift, kTileShift + tb, a.hist, Pi, st);
   cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)max(a.n_tiles, 1), st);
   k_ranges<<<a.num_sms * 8, 256, 0, st>>>(is, &a.counters->n_inst_c, a.ranges, (unsigned)a.n_tiles, a.errword);
-  count_launch(7 + 3 * ((lbits + 7) / 8) + 3 * ((tb + 7) / 8) + 2);
+  count_launch(4 + 3 * ((lbits + 7) / 8) + 3 * ((tb + 7) / 8) + 2);
   a.prof(PH_BINNING, false, st);
   a.prof(PH_BLEND_FWD, true, st);
   if (a.stage == 32) {
