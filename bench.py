@@ -335,7 +335,7 @@ def run_ours(args, rank, world):
     render_p = sum(plain_phases[k] for k in render_phases) if plain_phases else None
     n_act = n_all
     roof = roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, f"{tile[0]}x{tile[1]}/{stage}",
-                    n_views=len(cams))
+                    n_views=len(cams), n_eval=n_eval)
     out = {
         "metric": METRIC, "value": round(mpix_b, 2), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(ms_b / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -754,10 +754,13 @@ TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profile
 RASTER_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2511_23030_b300", "csrc", "raster.cu")
 
 
-def measured_traffic(phase: str, launch: str, n_inst: int, field: str = "dram_bytes_per_launch"):
+def measured_traffic(phase: str, launch: str, units: int, field: str = "dram_bytes_per_launch",
+                     unit_key: str = "instances"):
     """A per-launch figure of the phase's kernel from the committed ncu capture (DRAM bytes, or warp
-    instructions), scaled from the captured workload to this one by instances; None unless the
-    capture is of this launch shape and of the rasteriser source as it is now."""
+    instructions), scaled from the captured workload to this one by the units the kernel processes
+    (instances for DRAM bytes: the blends read one record per instance; pixel-Gaussian evaluations
+    for warp instructions: the per-pixel loops dominate them); None unless the capture is of this
+    launch shape and of the rasteriser source as it is now."""
     import hashlib
 
     try:
@@ -768,10 +771,12 @@ def measured_traffic(phase: str, launch: str, n_inst: int, field: str = "dram_by
     k = rec.get("kernels", {}).get(phase)
     if not k or field not in k or rec.get("raster_cu_sha256") != sha or rec.get("launch") != launch:
         return None
-    return int(k[field] * n_inst / rec["instances"])
+    if not rec.get(unit_key) or not units:
+        return None
+    return int(k[field] * units / rec[unit_key])
 
 
-def roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, launch="", n_views=8):
+def roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, launch="", n_views=8, n_eval=0):
     """Dominant phase with its algorithmic bytes (or FLOPs) per launch over its live duration."""
     hbm, sm_max, src = peaks()
     rec = 48
@@ -807,8 +812,8 @@ def roofline(phases, n_act, n_vis, n_inst, n_blend, npix, deg, F, clocks, launch
                "hbm_frac": round(algo_bytes[dom] / t / 1e9 / hbm, 4), "peak_source": f"derived (sm_max {sm_max} MHz)",
                "hbm_by_phase": by_phase}
         # what bounds it: the warp-instruction issue rate (148 SMs x 4 schedulers x 1 per clock) against
-        # the instructions ncu counted per launch (scaled by instances)
-        inst = measured_traffic(dom, launch, n_inst, "warp_instructions_per_launch")
+        # the instructions ncu counted per launch (scaled by pixel-Gaussian evaluations)
+        inst = measured_traffic(dom, launch, n_eval, "warp_instructions_per_launch", "evaluations")
         if inst is not None:
             ipeak = 148 * 4 * sm_max * 1e6
             out["issue"] = {"warp_instructions": inst, "achieved_ginst_s": round(inst / t / 1e9, 1),
