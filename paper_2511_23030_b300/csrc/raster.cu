@@ -1655,8 +1655,24 @@ __device__ __forceinline__ void red_add_v2(float* p, float a, float b) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
 
+// Asynchronous global -> shared copies (no registers hold the data in
+// flight); a thread's copies complete in commit-group order.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(256) k_blend_bwd_g(RasterArgs a, const u64* __restrict__ inst,
+__global__ void __launch_bounds__(256, 4) k_blend_bwd_g(RasterArgs a, const u64* __restrict__ inst,
                                                      const float* __restrict__ dL_drgb,
                                                      const float* __restrict__ dL_ddepth) {
   using L = TileLayout<TW, TH>;
@@ -1664,11 +1680,12 @@ __global__ void __launch_bounds__(256) k_blend_bwd_g(RasterArgs a, const u64* __
   constexpr int NP = 4 * WY;  // pixels of a half block
   constexpr int R = kRingG;
   constexpr int CH = kChunkG;
-  __shared__ float2 s_xy[8][R];
+  __shared__ float4 s_r0[8][R];   // the ring: pair records as stored (centre, conic, colour)
   __shared__ float4 s_con[8][R];
   __shared__ float4 s_col[8][R];
   __shared__ int s_rel[8][R];
   __shared__ unsigned s_vi[8][R];
+  __shared__ u64 s_key[8][32];    // the next refill's instance keys
   __shared__ float4 s_g[8][NP];   // dL/d(r, g, b, depth) of each pixel of the half
   __shared__ float4 s_st[8][NP];  // (T behind, Q behind, last contributor (int bits), unused)
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, hl = lane >> 4, gl = lane & 15;
@@ -1711,41 +1728,61 @@ __global__ void __launch_bounds__(256) k_blend_bwd_g(RasterArgs a, const u64* __
     int hi = (int)__reduce_max_sync(0xffffffffu, mylast);  // instances [0, hi) are still to scan
     const uint2 rg = a.ranges[gt];
     if (dcg_oob((u64)rg.x + (u64)hi, (u64)a.cap_inst + 1ull, a.errword)) hi = 0;
-    int hd = 0, pc = 0;  // ring head and count
+    // The ring is refilled while it holds fewer than two chunks, so the
+    // records of the next chunk are in flight (cp.async) while this one is
+    // blended; the keys of the next refill are staged one refill ahead.
+    // Commit groups: one per refill (its records and the next keys); old =
+    // ring entries from the head whose records lie in older groups.
+    int hd = 0, pc = 0, old = 0;  // ring head, count, entries of older groups
+    if (hi > 0 && hi - 1 - lane >= 0) cp_async8(&s_key[w][lane], inst + rg.x + (hi - 1 - lane));
+    cp_async_commit();
     __syncwarp();
     for (;;) {
-      while (hi > 0 && pc < CH) {
+      while (hi > 0 && pc < 2 * CH) {
+        cp_async_wait<0>();  // this refill's keys, and every record asked for so far
+        __syncwarp();
+        old = pc;
         const int rel = hi - 1 - lane;  // lane 0 takes the largest index: the ring keeps reverse order
         bool take = false;
         unsigned vi = 0;
         if (rel >= 0) {
-          const u64 key = inst[rg.x + rel];
+          const u64 key = s_key[w][lane];
           vi = pair_of_inst(key);
           take = (half_bits(key, (int)wb) >> h) & 1u;
           if (take && dcg_oob(vi, (u64)a.cap_pairs, a.errword)) take = false;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, take);
+        const unsigned m = __ballot_sync(0xffffffffu, take);  // also: every lane has read its key
         if (take) {
           int sl = hd + pc + __popc(m & lt);
           sl -= sl >= R ? R : 0;
           sl -= sl >= R ? R : 0;
-          const float4 r0 = a.rec[3ull * vi + 0];
-          s_xy[w][sl] = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
-          s_con[w][sl] = a.rec[3ull * vi + 1];
-          s_col[w][sl] = a.rec[3ull * vi + 2];
+          cp_async16(&s_r0[w][sl], a.rec + 3ull * vi + 0);
+          cp_async16(&s_con[w][sl], a.rec + 3ull * vi + 1);
+          cp_async16(&s_col[w][sl], a.rec + 3ull * vi + 2);
           s_rel[w][sl] = rel;
           s_vi[w][sl] = vi;
         }
         pc += __popc(m);
         hi -= 32;
+        if (hi > 0 && hi - 1 - lane >= 0) cp_async8(&s_key[w][lane], inst + rg.x + (hi - 1 - lane));
+        cp_async_commit();
       }
-      __syncwarp();
       if (pc == 0) break;
       const int cnt = min(pc, CH);
+      // the chunk's records: in older groups, or also in the newest one
+      if (cnt <= old)
+        cp_async_wait<1>();
+      else
+        cp_async_wait<0>();
+      __syncwarp();
       int e = hd + gl;
       e -= e >= R ? R : 0;
       const bool mine = gl < cnt;
-      const float2 xy = mine ? s_xy[w][e] : make_float2(0.f, 0.f);
+      float2 xy = make_float2(0.f, 0.f);
+      if (mine) {
+        const float4 r0 = s_r0[w][e];
+        xy = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
+      }
       const float4 cq = mine ? s_con[w][e] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 cl = mine ? s_col[w][e] : make_float4(0.f, 0.f, 0.f, 0.f);
       const int rl = mine ? s_rel[w][e] : 0x7fffffff;
@@ -1836,8 +1873,11 @@ __global__ void __launch_bounds__(256) k_blend_bwd_g(RasterArgs a, const u64* __
       hd += cnt;
       hd -= hd >= R ? R : 0;
       pc -= cnt;
+      old = old > cnt ? old - cnt : 0;
       __syncwarp();
     }
+    cp_async_wait<0>();  // nothing of this item left in flight
+    __syncwarp();
   }
 }
 
