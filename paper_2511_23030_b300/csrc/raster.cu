@@ -1229,6 +1229,22 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
   }
 }
 
+// Asynchronous global -> shared copies (no registers hold the data in
+// flight); a thread's copies complete in commit-group order.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ============================================================================
 // Half-warp blends.  As the warp-per-block kernels, but the two halves of a
 // warp own the two 4 x WY halves of its 8 x WY block (lane l: half l / 16,
@@ -1268,6 +1284,10 @@ __global__ void __launch_bounds__(256, TW * TH == 256 ? 4 : 0) k_blend_fwd_h(Ras
   __shared__ float4 s_con[8][2][32];
   __shared__ float4 s_col[8][2][32];
   __shared__ unsigned s_rel[8][2][32];
+  // per warp and lane: the next batch's pair record and the key after it,
+  // staged by cp.async while the current batch blends
+  __shared__ float4 s_srec[8][3][32];
+  __shared__ u64 s_skey[8][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4;
   const unsigned lt = lanemask_lt();
   const unsigned n_items = 8u * (unsigned)a.n_tiles;
@@ -1303,39 +1323,47 @@ __global__ void __launch_bounds__(256, TW * TH == 256 ? 4 : 0) k_blend_fwd_h(Ras
     }
     uint2 rg = a.ranges[gt];
     if (dcg_oob(rg.y, (u64)a.cap_inst + 1ull, a.errword)) rg.y = rg.x;
-    // software pipeline over the batches: keys two batches ahead, records
-    // of the instances that reach this warp block one batch ahead
-    u64 key2 = rg.x + 32 + lane < rg.y ? inst[rg.x + 32 + lane] : 0ull;
-    unsigned hbn = 0, vin = 0;
-    float4 r0n = make_float4(0.f, 0.f, 0.f, 0.f), cnn = r0n, cln = r0n;
+    // software pipeline over the batches, staged in shared memory by
+    // cp.async (no registers hold loads in flight): while a batch blends, the
+    // records of the next batch's instances that reach this warp block and
+    // the keys of the batch after it are on their way.  A lane overwrites its
+    // staging slots only after it has used what they held.
+    unsigned hbn = 0;
+    if (rg.x + lane < rg.y) cp_async8(&s_skey[w][lane], inst + rg.x + lane);
+    cp_async_commit();
+    cp_async_wait<0>();
     if (rg.x + lane < rg.y) {
-      const u64 k0 = inst[rg.x + lane];
-      vin = pair_of_inst(k0);
+      const u64 k0 = s_skey[w][lane];
+      const unsigned vi0 = pair_of_inst(k0);
       hbn = half_bits(k0, wb);
-      if (hbn && dcg_oob(vin, (u64)a.cap_pairs, a.errword)) hbn = 0u;
+      if (hbn && dcg_oob(vi0, (u64)a.cap_pairs, a.errword)) hbn = 0u;
       if (hbn) {
-        r0n = a.rec[3ull * vin + 0];
-        cnn = a.rec[3ull * vin + 1];
-        cln = a.rec[3ull * vin + 2];
+        cp_async16(&s_srec[w][0][lane], a.rec + 3ull * vi0 + 0);
+        cp_async16(&s_srec[w][1][lane], a.rec + 3ull * vi0 + 1);
+        cp_async16(&s_srec[w][2][lane], a.rec + 3ull * vi0 + 2);
       }
     }
+    if (rg.x + 32 + lane < rg.y) cp_async8(&s_skey[w][lane], inst + rg.x + 32 + lane);
+    cp_async_commit();
     for (unsigned b0 = rg.x; b0 < rg.y; b0 += 32) {
       const unsigned am = __ballot_sync(0xffffffffu, alive);
       if (am == 0u) break;
       const unsigned idx = b0 + lane;
       unsigned hb = hbn;
-      const float4 r0 = r0n, cn = cnn, cl = cln;
-      {  // the next batch's records, the batch after next's keys
-        const u64 k1 = key2;
-        key2 = idx + 64 < rg.y ? inst[idx + 64] : 0ull;
-        hbn = idx + 32 < rg.y ? half_bits(k1, wb) : 0u;
+      cp_async_wait<0>();  // this batch's records, the next batch's keys
+      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), cn = r0, cl = r0;
+      if (hb) {
+        r0 = s_srec[w][0][lane];
+        cn = s_srec[w][1][lane];
+        cl = s_srec[w][2][lane];
+      }
+      unsigned vin = 0;
+      hbn = 0;
+      if (idx + 32 < rg.y) {
+        const u64 k1 = s_skey[w][lane];
         vin = pair_of_inst(k1);
+        hbn = half_bits(k1, wb);
         if (hbn && dcg_oob(vin, (u64)a.cap_pairs, a.errword)) hbn = 0u;
-        if (hbn) {
-          r0n = a.rec[3ull * vin + 0];
-          cnn = a.rec[3ull * vin + 1];
-          cln = a.rec[3ull * vin + 2];
-        }
       }
       if ((am & 0xffffu) == 0u) hb &= 2u;
       if ((am >> 16) == 0u) hb &= 1u;
@@ -1371,6 +1399,15 @@ __global__ void __launch_bounds__(256, TW * TH == 256 ? 4 : 0) k_blend_fwd_h(Ras
         s_xy[w][1][lane] = make_float2(0.f, 0.f);
         s_con[w][1][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      // the next batch's records and the keys after it (this lane's staged
+      // record and key were used above)
+      if (hbn) {
+        cp_async16(&s_srec[w][0][lane], a.rec + 3ull * vin + 0);
+        cp_async16(&s_srec[w][1][lane], a.rec + 3ull * vin + 1);
+        cp_async16(&s_srec[w][2][lane], a.rec + 3ull * vin + 2);
+      }
+      if (idx + 64 < rg.y) cp_async8(&s_skey[w][lane], inst + idx + 64);
+      cp_async_commit();
       __syncwarp();
       // evaluations counted per batch: a pixel live at its start is evaluated
       // by every real step until it terminates
@@ -1419,6 +1456,7 @@ __global__ void __launch_bounds__(256, TW * TH == 256 ? 4 : 0) k_blend_fwd_h(Ras
         ev += nev[k];
       }
     }
+    cp_async_wait<0>();  // nothing of this item left in flight (a batch loop that stops early)
     {
       const unsigned wev = __reduce_add_sync(0xffffffffu, ev), wnb = __reduce_add_sync(0xffffffffu, nb);
       if (lane == 0 && wev) atomicAdd(&a.counters->n_eval, (unsigned long long)wev);
@@ -1655,21 +1693,6 @@ __device__ __forceinline__ void red_add_v2(float* p, float a, float b) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
 
-// Asynchronous global -> shared copies (no registers hold the data in
-// flight); a thread's copies complete in commit-group order.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(256, 4) k_blend_bwd_g(RasterArgs a, const u64* __restrict__ inst,
