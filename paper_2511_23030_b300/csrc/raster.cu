@@ -194,6 +194,26 @@ __device__ __forceinline__ float sqrt_hw(float x) {
   return y;
 }
 
+// Asynchronous global -> shared copies (no registers hold the data in
+// flight); a thread's copies complete in commit-group order.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ SupportEllipse support_of(float4 cn) {
   SupportEllipse e;
   e.ia = __frcp_rn(-cn.x);
@@ -1229,21 +1249,6 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
   }
 }
 
-// Asynchronous global -> shared copies (no registers hold the data in
-// flight); a thread's copies complete in commit-group order.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 // ============================================================================
 // Half-warp blends.  As the warp-per-block kernels, but the two halves of a
@@ -2105,20 +2110,22 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
   constexpr int D = (DEG + 1) * (DEG + 1);
   constexpr int T = kPreBwdThreads;
   // dynamic shared memory, one column per thread: its SH coefficients
-  // (loaded once, at its first contributing view; element k at shc[k T]) and
-  // the colour gradient of each contributing view (channel ch of view v at
-  // gcv[(3 v + ch) T]), from which the SH gradients are summed after the
-  // view loop
+  // (element k at shc[k T]), the colour gradient of each contributing view
+  // (channel ch of view v at gcv[(3 v + ch) T]), from which the SH gradients
+  // are summed after the view loop, and two slots for the 2D gradients of
+  // the views it reaches (slot s, component c at gsl[(3 s + c) T]).  The
+  // coefficients and each next reached view's gradients arrive by cp.async
+  // while the current view is worked on.
   extern __shared__ float s_dyn[];
   float* const shc = s_dyn + threadIdx.x;
   float* const gcv = s_dyn + 3 * D * T + threadIdx.x;
+  float4* const gsl = reinterpret_cast<float4*>(s_dyn + (3 * D + 3 * a.V) * T) + threadIdx.x;
   const long long S = a.stride;
   // one pass over all threads of the grid; lanes past n still join the warp reductions
   const long long n_round = ((n + 31) / 32) * 32;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_round; i += (long long)gridDim.x * blockDim.x) {
     const bool live = i < n;
     const float* g = a.g;
-    bool have_sh = false;
     unsigned vact = 0;  // views with a colour gradient
     float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.f;
     float mx = 0, my = 0, mz = 0, sc[3] = {1, 1, 1}, qn[4] = {1, 0, 0, 0}, qlen = 1.f, R[9], M[9], opac = 0.5f;
@@ -2150,30 +2157,40 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
 #pragma unroll
     for (int v = 0; v < kMaxViewsApi; ++v)
       if (live && in_cap && v < a.V && a.touched[(long long)v * n + i] != 0u) tmask |= 1u << v;
-    // the 2D gradients of the next reached view are loaded one view ahead
-    float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, n2 = n0;
+    // the SH coefficients of a Gaussian that reaches a view, then the 2D
+    // gradients of its first reached view (commit groups in that order)
+    if (tmask) {
+#pragma unroll
+      for (int k = 0; k < 3 * D; ++k) cp_async4(shc + k * T, g + (11 + k) * S + i);
+    }
+    cp_async_commit();
     if (tmask) {
       const long long vi0 = (long long)(__ffs(tmask) - 1) * n + i;
-      n0 = a.grad2d[3 * vi0 + 0];
-      n1 = a.grad2d[3 * vi0 + 1];
-      n2 = a.grad2d[3 * vi0 + 2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cp_async16(gsl + c * T, a.grad2d + 3 * vi0 + c);
     }
+    cp_async_commit();
+    int slot = 0;
     for (int v = 0; v < a.V; ++v) {
       float pose[6] = {0, 0, 0, 0, 0, 0};
       const long long vi = (long long)v * n + i;
       bool act = (tmask >> v) & 1u;
       float4 g0 = make_float4(0, 0, 0, 0), g1 = g0, g2 = g0;
       if (act) {
-        g0 = n0;
-        g1 = n1;
-        g2 = n2;
+        // the next reached view's gradients into the other slot (read, and
+        // used, at the previous reached view), then this view's
         const unsigned rest = tmask & ~((2u << v) - 1u);
         if (rest) {
           const long long vn = (long long)(__ffs(rest) - 1) * n + i;
-          n0 = a.grad2d[3 * vn + 0];
-          n1 = a.grad2d[3 * vn + 1];
-          n2 = a.grad2d[3 * vn + 2];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) cp_async16(gsl + (3 * (slot ^ 1) + c) * T, a.grad2d + 3 * vn + c);
         }
+        cp_async_commit();
+        cp_async_wait<1>();
+        g0 = gsl[(3 * slot + 0) * T];
+        g1 = gsl[(3 * slot + 1) * T];
+        g2 = gsl[(3 * slot + 2) * T];
+        slot ^= 1;
         act = (g0.x != 0.f) | (g0.y != 0.f) | (g0.z != 0.f) | (g0.w != 0.f) | (g1.x != 0.f) | (g1.y != 0.f) |
               (g1.z != 0.f) | (g1.w != 0.f) | (g2.x != 0.f) | (g2.y != 0.f);
         if (act) {  // consumed: the slot is zero again for the next backward
@@ -2276,11 +2293,6 @@ __global__ void __launch_bounds__(kPreBwdThreads, 4) k_preprocess_bwd(RasterArgs
         float wsum[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
-        if (!have_sh) {
-#pragma unroll
-          for (int k = 0; k < 3 * D; ++k) shc[k * T] = g[(11 + k) * S + i];
-          have_sh = true;
-        }
         vact |= 1u << v;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
@@ -2487,7 +2499,11 @@ static void blend_q_dispatch(bool fwd, RasterArgs& a, const u64* inst, float* rg
 // every thread of the block (3 (deg + 1)^2 floats each).
 static size_t sh_smem(int deg, int threads) { return sizeof(float) * 3 * (deg + 1) * (deg + 1) * threads; }
 // ... and, in the backward, the colour gradient of every view (3 floats each)
-static size_t sh_smem_bwd(int deg, int V) { return sh_smem(deg, kPreBwdThreads) + sizeof(float) * 3 * V * kPreBwdThreads; }
+// SH coefficients, per-view colour gradients, and two staging slots of a
+// view's 2D gradients (3 float4) per thread
+static size_t sh_smem_bwd(int deg, int V) {
+  return sh_smem(deg, kPreBwdThreads) + sizeof(float) * 3 * V * kPreBwdThreads + sizeof(float4) * 6 * kPreBwdThreads;
+}
 
 static void preprocess_smem_init() {
   static bool done = false;
