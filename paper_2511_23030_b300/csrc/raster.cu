@@ -540,13 +540,12 @@ struct InstEmit {
   u64 cap_pairs;     // bounds-check build: pair and tile indices against their buffers
   unsigned n_tiles;
   unsigned* errword;
-  __device__ void operator()(u64 s, u64 off, u64) const {
-    const u64 key = list[s];
+  // The instances of the pair of depth key `key` from offset `off` on, from
+  // its 32-byte binning record (b0, b1: centre (leading parts), conic, tile
+  // rectangle); the caller has checked the pair index.
+  __device__ void emit(u64 key, u64 off, float4 b0, float4 b1) const {
     const u64 vi = dk.pair(key, n);
     const int v = dk.view(key);
-    if (dcg_oob(vi, cap_pairs, errword)) return;
-    // one 32-byte binning record: centre (leading parts), conic, tile rectangle
-    const float4 b0 = bin[2 * vi + 0], b1 = bin[2 * vi + 1];
     const int p0 = __float_as_int(b1.y), p1 = __float_as_int(b1.z);
     const short4 r = make_short4((short)(p0 & 0xffff), (short)(p0 >> 16), (short)(p1 & 0xffff), (short)(p1 >> 16));
     const float4 r0 = make_float4(b0.x, b0.y, 0.f, 0.f), cn = make_float4(b0.z, b0.w, b1.x, 0.f);
@@ -572,17 +571,66 @@ struct InstEmit {
   }
 };
 
+// The emission, one thread per visible pair in depth order (grid-stride),
+// software-pipelined through shared memory by cp.async: while a thread emits
+// pair s, the binning record of its next pair and the key and offset of the
+// pair after that are on their way (double-buffered per thread; a slot is
+// refilled only after the thread has used what it held).
+__global__ void __launch_bounds__(256) k_emit_inst(const u64* n_ptr, const u64* __restrict__ offs, InstEmit e) {
+  __shared__ u64 s_key[2][256], s_off[2][256];
+  __shared__ float4 s_bin[2][2][256];
+  const int t = threadIdx.x;
+  const u64 n = *n_ptr;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  u64 s = blockIdx.x * (u64)blockDim.x + t;
+  if (s >= n) return;
+  // the first pair's key and offset, then its record; the next pair's key and offset
+  cp_async8(&s_key[0][t], e.list + s);
+  cp_async8(&s_off[0][t], offs + s);
+  cp_async_commit();
+  cp_async_wait<0>();
+  bool ok = true;
+  {
+    const u64 vi = e.dk.pair(s_key[0][t], e.n);
+    ok = !dcg_oob(vi, e.cap_pairs, e.errword);
+    if (ok) {
+      cp_async16(&s_bin[0][0][t], e.bin + 2 * vi + 0);
+      cp_async16(&s_bin[0][1][t], e.bin + 2 * vi + 1);
+    }
+  }
+  if (s + stride < n) {
+    cp_async8(&s_key[1][t], e.list + s + stride);
+    cp_async8(&s_off[1][t], offs + s + stride);
+  }
+  cp_async_commit();
+  for (int c = 0; s < n; s += stride, c ^= 1) {
+    cp_async_wait<0>();  // this pair's record, the next pair's key and offset
+    const u64 key = s_key[c][t], off = s_off[c][t];
+    const float4 b0 = s_bin[c][0][t], b1 = s_bin[c][1][t];
+    const bool ok_here = ok;
+    ok = true;
+    if (s + stride < n) {
+      const u64 vi = e.dk.pair(s_key[c ^ 1][t], e.n);
+      ok = !dcg_oob(vi, e.cap_pairs, e.errword);
+      if (ok) {
+        cp_async16(&s_bin[c ^ 1][0][t], e.bin + 2 * vi + 0);
+        cp_async16(&s_bin[c ^ 1][1][t], e.bin + 2 * vi + 1);
+      }
+    }
+    if (ok_here) e.emit(key, off, b0, b1);  // uses this slot's key, offset and record
+    if (s + 2 * stride < n) {
+      cp_async8(&s_key[c][t], e.list + s + 2 * stride);
+      cp_async8(&s_off[c][t], offs + s + 2 * stride);
+    }
+    cp_async_commit();
+  }
+}
+
 struct InstOffset {
   u64* off;
   __device__ void operator()(u64 s, u64 o, u64) const { off[s] = o; }
 };
 
-// Runs an emission functor for items [0, *n_ptr) at precomputed offsets.
-template <class EmitF>
-__global__ void __launch_bounds__(256) k_emit_at(const u64* n_ptr, const u64* off, EmitF e) {
-  const u64 n = *n_ptr;
-  for (u64 s = blockIdx.x * (u64)blockDim.x + threadIdx.x; s < n; s += (u64)gridDim.x * blockDim.x) e(s, off[s], 0);
-}
 
 __global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
   const u64 k = c->n_inst;
@@ -2573,7 +2621,7 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   u64* offs = ls == a.list_a ? a.list_b : a.list_a;
   part_scan_emit(&a.counters->n_vis, 0, InstCount{ls, a.touched, a.n, dk}, InstOffset{offs}, a.part, Pp,
                  &a.counters->n_inst, st);
-  k_emit_at<<<a.num_sms * 8, 256, 0, st>>>(
+  k_emit_inst<<<a.num_sms * 8, 256, 0, st>>>(
       &a.counters->n_vis, offs,
       InstEmit{ls, a.bin, a.cams, a.n, dk, a.tile_w, a.tile_h, a.inst_a, (u64)a.cap_inst, (u64)a.cap_pairs,
                (unsigned)a.n_tiles, a.errword});
