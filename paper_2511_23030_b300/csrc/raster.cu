@@ -1423,7 +1423,7 @@ __global__ void __launch_bounds__(256, TW * TH == 256 ? 4 : 0) k_blend_fwd_h(Ras
       const unsigned mL = __ballot_sync(0xffffffffu, hb & 1u), mR = __ballot_sync(0xffffffffu, hb & 2u);
       if (hb) {
         const float2 xy = make_float2(df_sub_round(r0.x, r0.z, x0f), df_sub_round(r0.y, r0.w, y0f));
-        const unsigned rel = idx - rg.x;
+        const unsigned rel = idx - rg.x + 1;  // the instance's rank in the tile list + 1: its "last" value
         if (hb & 1u) {
           const int sl = __popc(mL & lt);
           s_xy[w][0][sl] = xy;
@@ -1496,7 +1496,7 @@ __global__ void __launch_bounds__(256, TW * TH == 256 ? 4 : 0) k_blend_fwd_h(Ras
             Cb[k] += wgt * cl.z;
             Dz[k] += wgt * cl.w;
             T[k] = Tn;
-            last[k] = s_rel[w][h][j] + 1;
+            last[k] = s_rel[w][h][j];
             ++nb;
           }
         }
@@ -1926,10 +1926,10 @@ __global__ void __launch_bounds__(256, 4) k_blend_bwd_g(RasterArgs a, const u64*
               acc[4] += gy * dy;
             }
           }
-          const float At = __shfl_sync(0xffffffffu, A, CH - 1, CH), Bt = __shfl_sync(0xffffffffu, B, CH - 1, CH);
+          // the half's last lane holds the whole chunk's map: the pixel moves past it
           if (gl == CH - 1) {
-            s_st[w][p].x = st.x * At;
-            s_st[w][p].y = fmaf(st.x, Bt, st.y);
+            s_st[w][p].x = st.x * A;
+            s_st[w][p].y = fmaf(st.x, B, st.y);
           }
         }
       }
