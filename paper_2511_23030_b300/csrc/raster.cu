@@ -619,15 +619,39 @@ __global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
   if (k > cap) atomicOr(errword, ERRW_CAPACITY_BIT);
 }
 
-// Per-tile ranges [start, end) of the sorted instances.
+// Per-tile ranges [start, end) of the sorted instances.  A thread takes 4
+// consecutive instances (two 16-byte loads where all 4 exist) and compares
+// their tiles with each other and with the instances either side.
+__device__ __forceinline__ unsigned tile_of_inst(u64 key) { return (unsigned)(key >> kTileShift) & kTileMask; }
+
 __global__ void k_ranges(const u64* __restrict__ inst, const u64* n_ptr, uint2* __restrict__ ranges, unsigned n_tiles,
                          unsigned* errword) {
   const u64 K = *n_ptr;
-  for (u64 k = blockIdx.x * (u64)blockDim.x + threadIdx.x; k < K; k += (u64)gridDim.x * blockDim.x) {
-    const unsigned t = (unsigned)(inst[k] >> kTileShift) & kTileMask;
-    if (dcg_oob(t, n_tiles, errword)) continue;
-    if (k == 0 || ((unsigned)(inst[k - 1] >> kTileShift) & kTileMask) != t) ranges[t].x = (unsigned)k;
-    if (k + 1 == K || ((unsigned)(inst[k + 1] >> kTileShift) & kTileMask) != t) ranges[t].y = (unsigned)(k + 1);
+  const u64 G = (K + 3) / 4;
+  for (u64 gi = blockIdx.x * (u64)blockDim.x + threadIdx.x; gi < G; gi += (u64)gridDim.x * blockDim.x) {
+    const u64 k0 = 4 * gi;
+    unsigned t[6];  // t[0]: the instance before, t[1..4]: the group, t[5]: the instance after
+    if (k0 + 4 <= K) {
+      const ulonglong2 a = reinterpret_cast<const ulonglong2*>(inst)[2 * gi];
+      const ulonglong2 b = reinterpret_cast<const ulonglong2*>(inst)[2 * gi + 1];
+      t[1] = tile_of_inst(a.x);
+      t[2] = tile_of_inst(a.y);
+      t[3] = tile_of_inst(b.x);
+      t[4] = tile_of_inst(b.y);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) t[1 + j] = k0 + j < K ? tile_of_inst(inst[k0 + j]) : 0xffffffffu;
+    }
+    t[0] = k0 > 0 ? tile_of_inst(inst[k0 - 1]) : 0xffffffffu;
+    t[5] = k0 + 4 < K ? tile_of_inst(inst[k0 + 4]) : 0xffffffffu;
+#pragma unroll
+    for (int j = 1; j <= 4; ++j) {
+      const u64 k = k0 + j - 1;
+      if (k >= K) break;
+      if (dcg_oob(t[j], n_tiles, errword)) continue;
+      if (t[j - 1] != t[j]) ranges[t[j]].x = (unsigned)k;
+      if (t[j + 1] != t[j]) ranges[t[j]].y = (unsigned)(k + 1);
+    }
   }
 }
 
