@@ -496,15 +496,90 @@ struct InstCount {
   const uint32_t* touched;
   long long n;
   DepthKey dk;
-  __device__ u64 operator()(u64 s) const {
-    const u64 key = list[s];
+  __device__ u64 of_key(u64 key) const {
     if (dk.cmax) {
       const unsigned c = (unsigned)(key >> dk.cs);
       if (c < dk.cmax) return c;
     }
     return touched[dk.pair(key, n)];
   }
+  __device__ u64 operator()(u64 s) const { return of_key(list[s]); }
 };
+
+// Instance offsets: the exclusive scan, in depth order, of the tiles each
+// visible pair reaches (an ordered partitioned scan as part_scan_emit, with
+// partitions of a multiple of 4 pairs so that a thread reads 4 consecutive
+// keys and writes 4 offsets with 16-byte accesses).
+__device__ __forceinline__ void partition4_of(u64 n, u64* beg, u64* end) {
+  const u64 P = gridDim.x;
+  const u64 len = (((n + P - 1) / P) + 3) & ~3ull;
+  const u64 b = (u64)blockIdx.x * len, e = b + len;
+  *beg = b < n ? b : n;
+  *end = e < n ? e : n;
+}
+
+// 4 counts of the group of pairs [k0, k0 + 4) (0 past end)
+__device__ __forceinline__ void inst_counts4(const InstCount& f, u64 k0, u64 end, u64 c[4]) {
+  if (k0 + 4 <= end) {
+    const ulonglong2 a = reinterpret_cast<const ulonglong2*>(f.list + k0)[0];
+    const ulonglong2 b = reinterpret_cast<const ulonglong2*>(f.list + k0)[1];
+    c[0] = f.of_key(a.x);
+    c[1] = f.of_key(a.y);
+    c[2] = f.of_key(b.x);
+    c[3] = f.of_key(b.y);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) c[r] = k0 + r < end ? f(k0 + r) : 0ull;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_inst_reduce(const u64* n_ptr, InstCount f, u64* part) {
+  const u64 n = *n_ptr;
+  u64 beg, end;
+  partition4_of(n, &beg, &end);
+  u64 acc = 0;
+  for (u64 k0 = beg + 4ull * threadIdx.x; k0 < end; k0 += 4ull * blockDim.x) {
+    u64 c[4];
+    inst_counts4(f, k0, end, c);
+    acc += c[0] + c[1] + c[2] + c[3];
+  }
+  __shared__ u64 red[32];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane_id() == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    u64 s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_inst_offsets(const u64* n_ptr, InstCount f, const u64* part, u64* offs) {
+  const u64 n = *n_ptr;
+  u64 beg, end;
+  partition4_of(n, &beg, &end);
+  u64 base = part[blockIdx.x];
+  for (u64 c0 = beg; c0 < end; c0 += 4ull * blockDim.x) {
+    const u64 k0 = c0 + 4ull * threadIdx.x;
+    u64 c[4];
+    inst_counts4(f, k0, end, c);
+    u64 tot;
+    const u64 o0 = base + block_excl_scan<u64>(c[0] + c[1] + c[2] + c[3], &tot);
+    const u64 o1 = o0 + c[0], o2 = o1 + c[1], o3 = o2 + c[2];
+    if (k0 + 4 <= end) {
+      reinterpret_cast<ulonglong2*>(offs + k0)[0] = make_ulonglong2(o0, o1);
+      reinterpret_cast<ulonglong2*>(offs + k0)[1] = make_ulonglong2(o2, o3);
+    } else {
+      const u64 o[4] = {o0, o1, o2, o3};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (k0 + r < end) offs[k0 + r] = o[r];
+    }
+    base += tot;
+  }
+}
 // One thread per visible pair (in depth order) writes its instances: the
 // tiles of its rectangle that the support ellipse reaches (row spans, the
 // same as the count in k_preprocess_fwd), each with the mask of the tile's
@@ -606,11 +681,6 @@ __global__ void __launch_bounds__(256) k_emit_inst(const u64* n_ptr, const u64* 
     cp_async_commit();
   }
 }
-
-struct InstOffset {
-  u64* off;
-  __device__ void operator()(u64 s, u64 o, u64) const { off[s] = o; }
-};
 
 
 __global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
@@ -2624,8 +2694,12 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   // instance offsets by an ordered scan (the free list buffer holds them),
   // then the emission itself, one thread per visible pair with no barriers
   u64* offs = ls == a.list_a ? a.list_b : a.list_a;
-  part_scan_emit(&a.counters->n_vis, 0, InstCount{ls, a.touched, a.n, dk}, InstOffset{offs}, a.part, Pp,
-                 &a.counters->n_inst, st);
+  {
+    const InstCount ic{ls, a.touched, a.n, dk};
+    k_inst_reduce<<<Pp, 256, 0, st>>>(&a.counters->n_vis, ic, a.part);
+    k_part_scan<<<1, 1024, 0, st>>>(a.part, Pp, &a.counters->n_inst);
+    k_inst_offsets<<<Pp, 256, 0, st>>>(&a.counters->n_vis, ic, a.part, offs);
+  }
   k_emit_inst<<<a.num_sms * 8, 256, 0, st>>>(
       &a.counters->n_vis, offs,
       InstEmit{ls, a.bin, a.cams, a.n, dk, a.tile_w, a.tile_h, a.inst_a, (u64)a.cap_inst, (u64)a.cap_pairs,
