@@ -258,7 +258,7 @@ __device__ __forceinline__ bool row_span(const SupportEllipse& e, float4 r0, sho
   float xl, xr;
   if (!band_extent(e, -vl, __fsub_rn((float)(th - 1), vl), &xl, &xr)) return false;
   const float ux = df_sub_round(r0.x, r0.z, (float)(r.x * tw));  // centre relative to the rectangle's left edge
-  const float itw = 1.f / (float)tw;                             // tw is a power of two: exact
+  const float itw = __int_as_float((127 - (__ffs(tw) - 1)) << 23);  // 1 / tw (a power of two): exact
   const float a0 = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(ux, xl), (float)(tw - 1)), itw));
   const float a1 = floorf(__fmul_rn(__fadd_rn(ux, xr), itw));
   *j0 = (int)fminf(fmaxf(a0, 0.f), 32767.f);
@@ -409,8 +409,10 @@ __global__ void __launch_bounds__(256, 4) k_preprocess_fwd(RasterArgs a) {
         a.rect[vi] = make_short4(0, 0, -1, -1);
         continue;
       }
-      const int tx0 = (int)px0 / a.tile_w, tx1 = (int)px1 / a.tile_w;
-      const int ty0 = (int)py0 / a.tile_h, ty1 = (int)py1 / a.tile_h;
+      // tile sizes are powers of two and the pixel bounds are >= 0: shifts
+      const int sw = __ffs(a.tile_w) - 1, sh = __ffs(a.tile_h) - 1;
+      const int tx0 = (int)px0 >> sw, tx1 = (int)px1 >> sw;
+      const int ty0 = (int)py0 >> sh, ty1 = (int)py1 >> sh;
       const short4 rc = make_short4((short)tx0, (short)ty0, (short)tx1, (short)ty1);
       a.rect[vi] = rc;
       const float idet = 1.f / det;
@@ -609,7 +611,7 @@ struct InstEmit {
     const SupportEllipse e = support_of(cn);
     const u64 base = (u64)cams[v].tile_base;
     const int ntx = cams[v].ntx;
-    const int wy = tw * th / 64, wpr = tw / 8, nbr = th / wy;
+    const int wy = tw * th / 64, wpr = tw / 8, nbr = 64 >> (__ffs(tw) - 1);  // th / wy = 64 / tw (a power of two)
     u64 o = off;
     for (int ty = r.y; ty <= r.w; ++ty) {
       int j0, j1;
