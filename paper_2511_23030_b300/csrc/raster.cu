@@ -478,15 +478,39 @@ struct DepthKey {
 // of the views, in order) yields the depth key of a visible pair (one that
 // touches a tile); the pass keeps the visible pairs in pair order, so the
 // compaction and the first digit's scatter are one pass.
+// Unsigned 32-bit division by an invariant divisor d >= 1 with one
+// multiply-high, after Granlund and Montgomery, "Division by Invariant
+// Integers using Multiplication" (PLDI 1994), Fig. 4.1: with l = ceil(log2 d)
+// and m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((k - t) >> min(l, 1))) >>
+// max(l - 1, 0), t = the high word of m k; exact for every 32-bit k.
+struct DivU32 {
+  unsigned m;
+  int s1, s2;
+  static DivU32 make(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < (unsigned long long)d) ++l;
+    DivU32 r;
+    r.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1ull);
+    r.s1 = l < 1 ? l : 1;
+    r.s2 = l > 1 ? l - 1 : 0;
+    return r;
+  }
+  __device__ __forceinline__ unsigned div(unsigned k) const {
+    const unsigned t = __umulhi(m, k);
+    return (t + ((k - t) >> s1)) >> s2;
+  }
+};
+
 struct PairKeySrc {
   const float* depth;  // written for every pair by the preprocess
   const uint32_t* touched;
   unsigned n;          // pair indices fit in 28 bits
+  DivU32 dn;           // division by n
   DepthKey dk;
   __device__ __forceinline__ bool operator()(u64 k, u64* key) const {
     const uint32_t t = touched[k];
     const float z = depth[k];
-    const unsigned kk = (unsigned)k, v = kk / n, i = kk - v * n;
+    const unsigned kk = (unsigned)k, v = dn.div(kk), i = kk - v * n;
     u64 x = ((u64)v << (31 + dk.ib)) | ((u64)__float_as_uint(z) << dk.ib) | (u64)i;
     if (dk.cmax) x |= (u64)min(t, dk.cmax) << dk.cs;
     *key = x;
@@ -2690,7 +2714,7 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   // pass reads the pairs themselves and keeps the visible ones (the
   // compaction), counting them into n_vis; the other passes sort the list.
   const int lbits = 31;
-  radix_pass(PairKeySrc{a.depth, a.touched, (unsigned)a.n, dk}, nullptr, (u64)pairs, a.list_b, a.idx_bits, 8, a.hist,
+  radix_pass(PairKeySrc{a.depth, a.touched, (unsigned)a.n, DivU32::make((unsigned)std::max<long long>(a.n, 1)), dk}, nullptr, (u64)pairs, a.list_b, a.idx_bits, 8, a.hist,
              Pp, &a.counters->n_vis, st);
   u64* ls = radix_sort(a.list_b, a.list_a, &a.counters->n_vis, a.idx_bits + 8, a.idx_bits + lbits, a.hist, Pp, st);
   // instance offsets by an ordered scan (the free list buffer holds them),
