@@ -194,7 +194,6 @@ __device__ __forceinline__ float sqrt_hw(float x) {
   return y;
 }
 
-
 __device__ __forceinline__ SupportEllipse support_of(float4 cn) {
   SupportEllipse e;
   e.ia = __frcp_rn(-cn.x);
@@ -474,10 +473,6 @@ struct DepthKey {
   }
   __device__ int view(u64 key) const { return (int)((key >> (31 + ib)) & ((1ull << vb) - 1ull)); }
 };
-// Key source of the depth sort's first pass: pair k = v n + i (every pair
-// of the views, in order) yields the depth key of a visible pair (one that
-// touches a tile); the pass keeps the visible pairs in pair order, so the
-// compaction and the first digit's scatter are one pass.
 // Unsigned 32-bit division by an invariant divisor d >= 1 with one
 // multiply-high, after Granlund and Montgomery, "Division by Invariant
 // Integers using Multiplication" (PLDI 1994), Fig. 4.1: with l = ceil(log2 d)
@@ -501,6 +496,10 @@ struct DivU32 {
   }
 };
 
+// Key source of the depth sort's first pass: pair k = v n + i (every pair
+// of the views, in order) yields the depth key of a visible pair (one that
+// touches a tile); the pass keeps the visible pairs in pair order, so the
+// compaction and the first digit's scatter are one pass.
 struct PairKeySrc {
   const float* depth;  // written for every pair by the preprocess
   const uint32_t* touched;
@@ -606,6 +605,7 @@ __global__ void __launch_bounds__(256) k_inst_offsets(const u64* n_ptr, InstCoun
     base += tot;
   }
 }
+
 // One thread per visible pair (in depth order) writes its instances: the
 // tiles of its rectangle that the support ellipse reaches (row spans, the
 // same as the count in k_preprocess_fwd), each with the mask of the tile's
@@ -707,7 +707,6 @@ __global__ void __launch_bounds__(256) k_emit_inst(const u64* n_ptr, const u64* 
     cp_async_commit();
   }
 }
-
 
 __global__ void k_clamp_inst(DevCounters* c, u64 cap, unsigned* errword) {
   const u64 k = c->n_inst;
@@ -1398,7 +1397,6 @@ __global__ void __launch_bounds__(256) k_blend_bwd_q(RasterArgs a, const u64* __
   }
 }
 
-
 // ============================================================================
 // Half-warp blends.  As the warp-per-block kernels, but the two halves of a
 // warp own the two 4 x WY halves of its 8 x WY block (lane l: half l / 16,
@@ -1846,7 +1844,6 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
 __device__ __forceinline__ void red_add_v2(float* p, float a, float b) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
-
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(256, 4) k_blend_bwd_g(RasterArgs a, const u64* __restrict__ inst,
