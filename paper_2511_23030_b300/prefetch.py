@@ -246,6 +246,17 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
     hit_g = miss_g = 0
     dcg.dcg_profile(ctx, True)
     dcg.dcg_profile_read(ctx)
+    # The phase timers hold a bounded number of intervals between reads (about
+    # 22 a step here), so they are read, and summed, every `read_every` steps.
+    read_every = 200
+    prof = {}
+
+    def read_timers():
+        for k, (ms, cnt) in dcg.dcg_profile_read(ctx).items():
+            a = prof.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += cnt
+
     side = torch.cuda.Stream()
     cvp = ConstantVelocity(ctx) if mode == "cv" else None
     resident_trace = []  # Gaussians on the device after each step's gather
@@ -258,6 +269,8 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
             hits = misses = wasted = hit_g = miss_g = 0
             resident_trace = []
             e0.record()
+        elif t > warm and (t - warm) % read_every == 0:
+            read_timers()
         lst = dcg.dcg_cull_chunks(ctx, [cam])
         res = dcg.dcg_chunk_info(ctx)["resident"].astype(bool)
         for c in lst:
@@ -305,7 +318,7 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
                     wasted += 1
     e1.record()
     torch.cuda.synchronize()
-    prof = dcg.dcg_profile_read(ctx)
+    read_timers()
     dcg.dcg_profile(ctx, False)
     wasted += len(pending)
     tr = np.asarray(resident_trace, np.int64)
@@ -313,4 +326,6 @@ def run_corridor(ctx, cams, mode, chunk_size, radius, pm: PrefetchMLP | None = N
             "hits": hits, "misses": misses, "wasted_prefetches": wasted,
             "hidden_load_frac": hit_g / max(hit_g + miss_g, 1), "tier": dcg.dcg_tier_stats(ctx),
             "resident_max": int(tr.max()) if tr.size else 0,
-            "resident_trace": [int(v) for v in tr[:: max(1, len(tr) // 40)]]}
+            "resident_trace": [int(v) for v in tr[:: max(1, len(tr) // 40)]],
+            # device time of each phase per counted step (the phase timers' CUDA events)
+            "phases_ms_per_step": {k: round(v[0] / max(len(cams) - warm, 1), 4) for k, v in prof.items() if v[1]}}
