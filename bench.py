@@ -286,19 +286,32 @@ def run_ours(args, rank, world):
             dcg.dcg_profile_read(ctx)
         l0 = dcg.dcg_launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # the phase timers hold 4096 intervals between reads (a plain step of 8
+        # views records about 80): a long profiled run reads and sums them
+        # every 25 steps
+        prof = {} if profile else None
+
+        def read_timers():
+            for key, (v, c) in dcg.dcg_profile_read(ctx).items():
+                a = prof.setdefault(key, [0.0, 0])
+                a[0] += v
+                a[1] += c
+
         e0.record(stream)
-        for _ in range(k):
+        for j in range(k):
             fn()
+            if profile and j % 25 == 24 and j + 1 < k:
+                read_timers()
         e1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         ms = e0.elapsed_time(e1)
         launches = dcg.dcg_launch_count() - l0
-        prof = None
         if profile:
-            prof = dcg.dcg_profile_read(ctx)
+            read_timers()
             dcg.dcg_profile(ctx, False)
+            prof = {key: (v[0], v[1]) for key, v in prof.items()}
         return max_over_ranks(ms, world, "cuda"), launches, prof
 
     K, W = args.steps, args.warmup
@@ -439,12 +452,17 @@ def indoor_leg(K, W, cpu_pixels=24):
         dcg.dcg_profile(ctx, True)
         dcg.dcg_profile_read(ctx)
         vis = inst = blend = 0
+        prof = {}
         for t in range(W, steps):
             step(t)
             nv, ni, _ = dcg.dcg_state_stats(ctx)
             _, nb = dcg.dcg_state_evals(ctx)
             vis, inst, blend = vis + nv, inst + ni, blend + nb
-        prof = dcg.dcg_profile_read(ctx)
+            if (t - W) % 100 == 99 or t + 1 == steps:  # the timers hold 4096 intervals between reads
+                for key, (v, c) in dcg.dcg_profile_read(ctx).items():
+                    a = prof.setdefault(key, [0.0, 0])
+                    a[0] += v
+                    a[1] += c
         dcg.dcg_profile(ctx, False)
         phases = {k: round(v[0] / K, 4) for k, v in prof.items() if k not in ("log_sample", "loop_closure")}
         roof = roofline(phases, n_act, vis // K, inst // K, blend // K, npx, deg, F, None, "", n_views=1)
