@@ -595,8 +595,10 @@ dcg_status dcg_fault_parse(const char* spec, int32_t* kind, int32_t* skip);
  * milliseconds (ms, DCG_PH_COUNT floats) and the number of timed intervals
  * (counts, may be NULL) since the last read.  Enabling creates the events;
  * the timed calls allocate nothing.  The pool holds 8192 events (two per
- * interval) between reads: intervals past it are not recorded, so a long run
- * reads the timers every few hundred steps and sums them. */
+ * interval) between reads: intervals past it are not recorded, and the next
+ * dcg_profile_read still writes ms and counts of the recorded ones but
+ * returns DCG_ERR_CAPACITY, so a long run reads the timers every few hundred
+ * steps and sums them. */
 enum {
   DCG_PH_CULL = 0,
   DCG_PH_GATHER = 1,

@@ -185,6 +185,7 @@ struct dcg_ctx {
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_next = 0;
+  uint64_t ev_dropped = 0;  // marks not recorded since the last read (the pool was used up)
   cudaEvent_t open_ev[PH_COUNT] = {};
   struct Rec {
     int phase;
@@ -201,7 +202,12 @@ static_assert((int)PH_COUNT == (int)DCG_PH_COUNT && (int)PH_SAMPLE == (int)DCG_P
 
 void prof_mark(void* h, int phase, bool begin, cudaStream_t s) {
   dcg_ctx* ctx = (dcg_ctx*)h;
-  if (!ctx->prof_on || ctx->ev_next >= ctx->ev_pool.size()) return;
+  if (!ctx->prof_on) return;
+  if (ctx->ev_next >= ctx->ev_pool.size()) {
+    ctx->ev_dropped++;
+    if (!begin) ctx->open_ev[phase] = nullptr;  // its interval is not recorded
+    return;
+  }
   cudaEvent_t e = ctx->ev_pool[ctx->ev_next++];
   cudaEventRecord(e, s);
   if (begin) {
@@ -2469,6 +2475,13 @@ dcg_status dcg_profile_read(dcg_ctx* ctx, float* ms, int32_t* counts) {
   ctx->recs.clear();
   ctx->ev_next = 0;
   for (auto& e : ctx->open_ev) e = nullptr;
+  if (ctx->ev_dropped) {
+    const uint64_t d = ctx->ev_dropped;
+    ctx->ev_dropped = 0;
+    return fail(ctx, DCG_ERR_CAPACITY,
+                "phase timers full: " + std::to_string(d) + " marks since the last read were not recorded "
+                "(the figures returned are partial; read more often)");
+  }
   return DCG_OK;
 }
 

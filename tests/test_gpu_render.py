@@ -391,3 +391,31 @@ def test_sixteen_views_batched_equal_single_and_oracle(deg, orc):
         assert rel_l2(pose[0], opose) <= GRAD_TOL
     finally:
         dcg.dcg_destroy(ctx)
+
+
+def test_phase_timers_report_a_full_pool(ctx0):
+    # the timers hold 4096 intervals between reads (three a forward call); a read after more
+    # returns the recorded figures and reports DCG_ERR_CAPACITY, and the next read is clean
+    sc = synth.room_small(0)
+    P, cam = sc["params"], sc["cams"][0]
+    g_t = planar(P)
+    g = dcg.gaussians(g_t, 0)
+    rgb, depth = out_buffers([cam])
+    dcg.dcg_profile(ctx0, True)
+    try:
+        dcg.dcg_profile_read(ctx0)
+        for _ in range(1000):
+            dcg.dcg_render_fwd(ctx0, g, P.shape[0], [cam], rgb, depth)
+        prof = dcg.dcg_profile_read(ctx0)  # 3000 intervals: within the pool
+        assert prof["blend_fwd"][1] == 1000
+        for _ in range(1500):
+            dcg.dcg_render_fwd(ctx0, g, P.shape[0], [cam], rgb, depth)
+        with pytest.raises(dcg.DcgError) as err:
+            dcg.dcg_profile_read(ctx0)
+        assert dcg.STATUS[err.value.status] == "DCG_ERR_CAPACITY"
+        dcg.dcg_render_fwd(ctx0, g, P.shape[0], [cam], rgb, depth)
+        prof = dcg.dcg_profile_read(ctx0)
+        assert prof["blend_fwd"][1] == 1
+    finally:
+        dcg.dcg_profile(ctx0, False)
+        dcg.dcg_sync(ctx0)
