@@ -2711,8 +2711,8 @@ void raster_forward(RasterArgs& a, float* rgb, float* dout, u64** list_sorted, u
   // pass reads the pairs themselves and keeps the visible ones (the
   // compaction), counting them into n_vis; the other passes sort the list.
   const int lbits = 31;
-  radix_pass(PairKeySrc{a.depth, a.touched, (unsigned)a.n, DivU32::make((unsigned)std::max<long long>(a.n, 1)), dk}, nullptr, (u64)pairs, a.list_b, a.idx_bits, 8, a.hist,
-             Pp, &a.counters->n_vis, st);
+  const PairKeySrc psrc{a.depth, a.touched, (unsigned)a.n, DivU32::make((unsigned)std::max<long long>(a.n, 1)), dk};
+  radix_pass(psrc, nullptr, (u64)pairs, a.list_b, a.idx_bits, 8, a.hist, Pp, &a.counters->n_vis, st);
   u64* ls = radix_sort(a.list_b, a.list_a, &a.counters->n_vis, a.idx_bits + 8, a.idx_bits + lbits, a.hist, Pp, st);
   // instance offsets by an ordered scan (the free list buffer holds them),
   // then the emission itself, one thread per visible pair with no barriers
